@@ -1,0 +1,210 @@
+/*
+ * femnfft.h - C ABI of the GB300 (sm_103a) FEM-NFFT fast summation.
+ *
+ * The library evaluates, for N targets x_i and M sources y_j with charges q_j,
+ *
+ *     phi(x_i) = sum_{j : y_j != x_i} q_j G(x_i - y_j),   G(d) = -(1/2 pi) log|d|,
+ *     H(x_i)   = -grad phi(x_i),
+ *
+ * the discretised Green convolution of Eq. (2) of Kritsikis, Toussaint and
+ * Fruchart, "Fast computation of magnetostatic fields by Non-uniform Fast
+ * Fourier Transforms" (Eq. (1) with G the 2D Green function), by the NFFT
+ * fast summation the paper describes after Eq. (2): the charges are spread
+ * onto an oversampled regular grid with a smooth localised window, the grid
+ * is Fourier transformed, divided by the window's Fourier coefficients and
+ * multiplied by the coefficients b_l of the log kernel smoothed near the
+ * origin, transformed back and interpolated at the targets, and a near-field
+ * correction is added for pairs inside the smoothing radius eps_I.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers marked [device] are CUDA device pointers on the device that is
+ *    current when the plan is created; [host] pointers are host memory.
+ *  - Point arrays are interleaved (x, y) pairs, row-major: point k at [2k, 2k+1].
+ *  - The caller owns every buffer it passes; the plan owns its workspace
+ *    (grids, sorted copies, coefficient tables) until fs_plan_destroy.
+ *  - Compute calls are enqueued on the plan's stream (fs_opts.stream) and
+ *    return before the work finishes, unless stated otherwise.
+ *  - No call exits or aborts the process.  On failure a call returns a
+ *    non-zero fs_status and fs_last_error() describes it; the plan stays
+ *    valid for fs_plan_destroy.  Errors raised by kernels (points outside
+ *    the admissible radius) are reported by fs_sync_status.
+ *  - Radii eps_I and eps_B are in torus units: the plan scales all points by
+ *    s = (1/4 - eps_B/2) / R_max (R_max = largest |point|, points centred at
+ *    the origin) onto the torus [-1/2, 1/2)^2; results are returned in the
+ *    caller's (physical) units.
+ */
+#ifndef FEMNFFT_H
+#define FEMNFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fs_plan fs_plan;
+
+typedef enum {
+    FS_OK = 0,
+    FS_EINVAL = 1,        /* invalid argument (null pointer, size, parameter range) */
+    FS_EDOMAIN = 2,       /* a point fell outside the admissible region */
+    FS_ENOMEM = 3,        /* device or host allocation failed */
+    FS_ECUDA = 4,         /* a CUDA runtime call failed */
+    FS_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    FS_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} fs_status;
+
+typedef enum { FS_F32 = 32, FS_F64 = 64 } fs_dtype;
+
+/* Option flags (fs_opts.flags). */
+#define FS_FLAG_NO_KAHAN 1u   /* FP32 path: plain (uncompensated) grid accumulation */
+#define FS_FLAG_TIMING 2u     /* record per-stage CUDA events (see fs_stage_times) */
+
+/* Plan options.  A zeroed struct (or NULL) selects every default. */
+typedef struct {
+    int precision;    /* 32 (default) or 64: arithmetic of spread, FFT, multiply,
+                         interpolation and near field.  Coefficients b_l are always
+                         computed in FP64. */
+    int p;            /* smoothness degree of the regularised kernel;
+                         0 -> max(2, round(n_grid * eps_I)) */
+    double eps_B;     /* width of the torus-boundary smoothing zone; 0 -> eps_I */
+    int cell;         /* near-field cell edge in oversampled-grid cells;
+                         0 -> ceil(eps_I * n_os) (cells never narrower than eps_I) */
+    int tile_cells;   /* spreading tile edge in near-field cells; 0 -> about 32 grid cells */
+    unsigned flags;   /* FS_FLAG_* */
+    void *stream;     /* cudaStream_t for every enqueued call; NULL = default stream */
+} fs_opts;
+
+/* Read-only plan facts (fs_plan_info). */
+typedef struct {
+    int64_t n_src, n_tgt;     /* M, N */
+    int n_grid, n_os, m, p;   /* n, sigma*n, window half-width, smoothness degree */
+    int precision;            /* 32 or 64 */
+    double eps_I, eps_B;      /* torus units */
+    double scale;             /* s: torus coordinate = s * physical coordinate */
+    int window_lo, window_n;  /* active oversampled window [lo, lo+window_n)^2 */
+    int cell, cells_per_dim;  /* near-field cells */
+    int tile_cells, spread_items;
+    int64_t near_pairs;       /* candidate-filtered pairs with r < eps_I (counted at plan time) */
+    int64_t near_pairs_fp64;  /* of those, pairs with r < eps_I/8 (difference taken in FP64) */
+    int64_t workspace_bytes;
+    int is_fem;               /* plan built by fs_plan_create_fem */
+    int64_t n_nodes, n_tris, n_bedges;
+} fs_info;
+
+/*
+ * Create a plan for the fast summation from M sources to N targets.
+ *
+ * Method: NFFT fast summation (paper, paragraph after Eq. (2)): frequencies
+ * l in I_n = {-n/2..n/2-1}^2, oversampled grid n_os = sigma_os * n_grid per
+ * dimension, Kaiser-Bessel window of half-width m_window grid cells (support
+ * |x| < m_window), near-field radius eps_I.  Binning (cell sort of sources and
+ * targets), the FP64 coefficients b_l of the regularised kernel and the
+ * deconvolution table are computed here, on the device.
+ *
+ *  src_xy  [device] (M, 2) float64 source positions
+ *  tgt_xy  [device] (N, 2) float64 target positions (may equal src_xy)
+ *  n_grid  even power of two, 8..2048
+ *  sigma_os oversampling; n_os = sigma_os * n_grid must be a power of two, > n_grid, <= 4096
+ *  m_window 2..8, and m_window < n_os / 4
+ *  eps_I   0 < eps_I < 1/4, torus units
+ *  opts    NULL for defaults
+ *  out     receives the plan
+ * Returns FS_EINVAL on a bad argument, FS_ENOMEM, FS_ECUDA.  Synchronises the
+ * plan's stream (it reads the binning counts back to the host).
+ */
+fs_status fs_plan_create(const double *src_xy, int64_t M, const double *tgt_xy, int64_t N,
+                         int n_grid, double sigma_os, int m_window, double eps_I,
+                         const fs_opts *opts, fs_plan **out);
+
+/*
+ * Create a plan for a P1 triangle mesh (paper, Eq. (2) with the quadrature of
+ * Eq. (1)): targets are the Nv mesh nodes; sources are the quadrature points,
+ * in this order: 3 points per triangle at barycentric (2/3,1/6,1/6) and its
+ * permutations (triangle-major), then 2 Gauss-Legendre points
+ * t = 1/2 -+ 1/(2 sqrt 3) per boundary edge (edges used by one triangle only,
+ * sorted by (lower node index, higher node index), the first point nearer the
+ * lower index).
+ *
+ *  nodes [device] (Nv, 2) float64;  tris [device] (Nt, 3) int32 node indices
+ *  Other arguments as fs_plan_create.
+ */
+fs_status fs_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tris, int64_t Nt,
+                             int n_grid, double sigma_os, int m_window, double eps_I,
+                             const fs_opts *opts, fs_plan **out);
+
+/*
+ * Set nrhs charge vectors q [device] (nrhs, M) of dtype FS_F32 or FS_F64
+ * (converted to the plan's precision and permuted into cell order).
+ * The values are copied; q may be reused once the stream reaches this call.
+ */
+fs_status fs_set_charges(fs_plan *plan, const void *q, fs_dtype dtype, int nrhs);
+
+/*
+ * FEM plans only: charges from nodal magnetisation (kernel (a), Eq. (2)):
+ * rho_T = -div M constant per P1 triangle, q = rho_T |T| / 3 per triangle
+ * point; sigma = M(t).n_e along boundary edges (outward unit normal, M linear
+ * along the edge), q = sigma |e| / 2 per edge point.
+ *  mag [device] (nrhs, Nv, 2) float64.
+ */
+fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs);
+
+/* FEM plans only: kernel (a) alone, charges written in source order.
+ *  mag [device] (nrhs, Nv, 2) float64;  q_out [device] (nrhs, M) float64. */
+fs_status fs_fem_charges(fs_plan *plan, const double *mag, double *q_out, int nrhs);
+
+/* FEM plans only: the quadrature points [device] (M, 2) float64, in source order. */
+fs_status fs_fem_sources(fs_plan *plan, double *src_out);
+
+/*
+ * Evaluate phi at the targets for every charge vector set last.
+ *  phi [device] (nrhs, N) of dtype FS_F32 or FS_F64.
+ */
+fs_status fs_eval_potential(fs_plan *plan, void *phi, fs_dtype dtype);
+
+/*
+ * Evaluate H = -grad phi (and phi, unless phi is NULL) in one pass.
+ *  phi [device] (nrhs, N) or NULL;  H [device] (nrhs, N, 2); dtype FS_F32|FS_F64.
+ */
+fs_status fs_eval_field(fs_plan *plan, void *phi, void *H, fs_dtype dtype);
+
+/*
+ * End-to-end solve from host memory: copies q [host] (nrhs, M) to the device,
+ * sets the charges, evaluates phi and H and copies them back to phi [host]
+ * (nrhs, N) (may be NULL) and H [host] (nrhs, N, 2).  Blocking: returns after
+ * the results are in host memory.  Page-locked host buffers make the copies
+ * asynchronous DMA transfers.
+ */
+fs_status fs_solve_host(fs_plan *plan, const void *q, fs_dtype q_dtype, int nrhs,
+                        void *phi, void *H, fs_dtype out_dtype);
+
+/* Wait for the plan's stream and report device-side errors (FS_EDOMAIN, FS_ETIMEOUT). */
+fs_status fs_sync_status(fs_plan *plan);
+
+/* Copy the plan's facts into *info (host). */
+fs_status fs_plan_info(const fs_plan *plan, fs_info *info);
+
+/*
+ * With FS_FLAG_TIMING: milliseconds of each stage of the last evaluation,
+ * measured with CUDA events on the plan's stream.  Stage order: 0 charges,
+ * 1 spread, 2 fft rows fwd, 3 fft cols + multiply, 4 fft rows inv,
+ * 5 interpolate, 6 near field, 7 unpermute.  Synchronises the stream.
+ * count = number of doubles available in ms (8 or more).
+ */
+fs_status fs_stage_times(fs_plan *plan, double *ms, int count);
+
+/* Release the plan and its workspace (synchronises its stream first). */
+fs_status fs_plan_destroy(fs_plan *plan);
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char *fs_last_error(void);
+
+/* Library version string. */
+const char *fs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEMNFFT_H */

@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) FEM-NFFT fast summation of 2D magnetostatic potentials and fields.
+
+Python binding of the C ABI declared in ``include/femnfft.h``.  Every step of
+the computation runs in the library's CUDA kernels (``libfemnfft.so``);
+PyTorch only provides device memory and the stream.  There is no CPU path: if
+the library is missing, importing works but the first call raises
+``NativeLibraryMissing``.
+
+The functions ``fs_plan_create``, ``fs_plan_create_fem``, ``fs_set_charges``,
+``fs_set_magnetization``, ``fs_fem_charges``, ``fs_fem_sources``,
+``fs_eval_potential``, ``fs_eval_field``, ``fs_solve_host``, ``fs_sync_status``,
+``fs_plan_info``, ``fs_stage_times`` and ``fs_plan_destroy`` mirror the C entry
+points one to one, taking torch tensors (or numpy arrays for host buffers).
+``FastSum`` wraps a plan with tensor-returning methods.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+from ._native import (FS_F32, FS_F64, FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FastSumError,  # noqa: F401
+                      FsInfo, FsOpts, NativeLibraryMissing, check, load)
+
+__all__ = [
+    "FastSum", "FastSumError", "NativeLibraryMissing", "FS_F32", "FS_F64", "FS_FLAG_NO_KAHAN",
+    "FS_FLAG_TIMING", "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization",
+    "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host",
+    "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path",
+]
+
+
+def library_path() -> str:
+    from ._native import LIB_PATH
+    return LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t, dtype=None, name="tensor"):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(dt):
+    torch = _torch()
+    if dt == torch.float32:
+        return FS_F32
+    if dt == torch.float64:
+        return FS_F64
+    raise TypeError("dtype must be torch.float32 or torch.float64")
+
+
+def _opts(precision=32, p=0, eps_B=0.0, cell=0, tile_cells=0, flags=0, stream=None):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return FsOpts(int(precision), int(p), float(eps_B), int(cell), int(tile_cells), int(flags),
+                  ctypes.c_void_p(int(stream)))
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+
+def fs_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts):
+    """src (M,2), tgt (N,2) float64 CUDA tensors -> opaque plan handle (ctypes.c_void_p)."""
+    torch = _torch()
+    lib = load()
+    handle = ctypes.c_void_p()
+    o = _opts(**opts)
+    st = lib.fs_plan_create(_dev_ptr(src, torch.float64, "src"), int(src.shape[0]),
+                            _dev_ptr(tgt, torch.float64, "tgt"), int(tgt.shape[0]), int(n_grid),
+                            float(sigma_os), int(m_window), float(eps_I), ctypes.byref(o), ctypes.byref(handle))
+    check(st, "fs_plan_create")
+    return handle
+
+
+def fs_plan_create_fem(nodes, tris, n_grid, sigma_os, m_window, eps_I, **opts):
+    """nodes (Nv,2) float64, tris (Nt,3) int32 CUDA tensors -> plan handle (sources = quadrature points)."""
+    torch = _torch()
+    lib = load()
+    handle = ctypes.c_void_p()
+    o = _opts(**opts)
+    st = lib.fs_plan_create_fem(_dev_ptr(nodes, torch.float64, "nodes"), int(nodes.shape[0]),
+                                _dev_ptr(tris, torch.int32, "tris"), int(tris.shape[0]), int(n_grid),
+                                float(sigma_os), int(m_window), float(eps_I), ctypes.byref(o), ctypes.byref(handle))
+    check(st, "fs_plan_create_fem")
+    return handle
+
+
+def fs_set_charges(plan, q, nrhs=None):
+    if nrhs is None:
+        nrhs = 1 if q.dim() == 1 else int(q.shape[0])
+    check(load().fs_set_charges(plan, _dev_ptr(q, None, "q"), _dtype_code(q.dtype), int(nrhs)), "fs_set_charges")
+
+
+def fs_set_magnetization(plan, mag, nrhs=None):
+    torch = _torch()
+    if nrhs is None:
+        nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+    check(load().fs_set_magnetization(plan, _dev_ptr(mag, torch.float64, "mag"), int(nrhs)),
+          "fs_set_magnetization")
+
+
+def fs_fem_charges(plan, mag, q_out, nrhs=None):
+    torch = _torch()
+    if nrhs is None:
+        nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+    check(load().fs_fem_charges(plan, _dev_ptr(mag, torch.float64, "mag"), _dev_ptr(q_out, torch.float64, "q_out"),
+                                int(nrhs)), "fs_fem_charges")
+
+
+def fs_fem_sources(plan, src_out):
+    torch = _torch()
+    check(load().fs_fem_sources(plan, _dev_ptr(src_out, torch.float64, "src_out")), "fs_fem_sources")
+
+
+def fs_eval_potential(plan, phi):
+    check(load().fs_eval_potential(plan, _dev_ptr(phi, None, "phi"), _dtype_code(phi.dtype)), "fs_eval_potential")
+
+
+def fs_eval_field(plan, phi, H):
+    dt = H.dtype
+    if phi is not None and phi.dtype != dt:
+        raise TypeError("phi and H must share a dtype")
+    check(load().fs_eval_field(plan, _dev_ptr(phi, None, "phi"), _dev_ptr(H, None, "H"), _dtype_code(dt)),
+          "fs_eval_field")
+
+
+def fs_solve_host(plan, q, phi, H):
+    """q, phi, H: C-contiguous numpy arrays (host); page-locked memory makes the copies DMA."""
+    import numpy as np
+
+    def code(a):
+        if a.dtype == np.float32:
+            return FS_F32
+        if a.dtype == np.float64:
+            return FS_F64
+        raise TypeError("host arrays must be float32 or float64")
+
+    for a in (q, phi, H):
+        if a is not None and not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+    nrhs = 1 if q.ndim == 1 else q.shape[0]
+    check(load().fs_solve_host(plan, ctypes.c_void_p(q.ctypes.data), code(q), int(nrhs),
+                               ctypes.c_void_p(phi.ctypes.data) if phi is not None else None,
+                               ctypes.c_void_p(H.ctypes.data), code(H)), "fs_solve_host")
+
+
+def fs_solve_host_ptr(plan, q_ptr, q_code, nrhs, phi_ptr, H_ptr, out_code):
+    """Raw-pointer form of fs_solve_host (for page-locked torch tensors)."""
+    check(load().fs_solve_host(plan, ctypes.c_void_p(q_ptr), int(q_code), int(nrhs),
+                               ctypes.c_void_p(phi_ptr) if phi_ptr else None, ctypes.c_void_p(H_ptr), int(out_code)),
+          "fs_solve_host")
+
+
+def fs_sync_status(plan):
+    check(load().fs_sync_status(plan), "fs_sync_status")
+
+
+def fs_plan_info(plan) -> dict:
+    info = FsInfo()
+    check(load().fs_plan_info(plan, ctypes.byref(info)), "fs_plan_info")
+    return info.as_dict()
+
+
+def fs_stage_times(plan):
+    arr = (ctypes.c_double * 8)()
+    check(load().fs_stage_times(plan, arr, 8), "fs_stage_times")
+    return list(arr)
+
+
+def fs_plan_destroy(plan):
+    if plan:
+        check(load().fs_plan_destroy(plan), "fs_plan_destroy")
+
+
+STAGES = ("charges", "spread", "fft_rows_fwd", "fft_cols_mul", "fft_rows_inv", "interp", "near", "unpermute")
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class FastSum:
+    """A plan for the fast summation phi(x_i) = sum_j q_j G(x_i - y_j), H = -grad phi.
+
+    ``FastSum(src, tgt, n, sigma, m, eps_I, precision=32)`` with float64 CUDA
+    tensors of shape (M, 2) and (N, 2); ``FastSum.fem(nodes, tris, ...)`` for a
+    P1 mesh (targets = nodes, sources = quadrature points).
+    """
+
+    def __init__(self, src=None, tgt=None, n_grid=None, sigma_os=2.0, m_window=6, eps_I=None, _handle=None,
+                 **opts):
+        torch = _torch()
+        if _handle is None:
+            self._h = fs_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
+            self.device = src.device
+        else:
+            self._h = _handle
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.info = fs_plan_info(self._h)
+        self.nrhs = 0
+
+    @classmethod
+    def fem(cls, nodes, tris, n_grid, sigma_os=2.0, m_window=6, eps_I=None, **opts):
+        h = fs_plan_create_fem(nodes, tris, n_grid, sigma_os, m_window, eps_I, **opts)
+        obj = cls(_handle=h)
+        obj.device = nodes.device
+        obj._nodes = nodes            # the plan reads the caller's node array
+        return obj
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_charges(self, q):
+        self.nrhs = 1 if q.dim() == 1 else int(q.shape[0])
+        fs_set_charges(self._h, q.contiguous(), self.nrhs)
+        return self
+
+    def set_magnetization(self, mag):
+        self.nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+        fs_set_magnetization(self._h, mag.contiguous(), self.nrhs)
+        return self
+
+    def fem_charges(self, mag):
+        torch = _torch()
+        nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+        out = torch.empty((nrhs, self.info["n_src"]), dtype=torch.float64, device=self.device)
+        fs_fem_charges(self._h, mag.contiguous(), out, nrhs)
+        return out[0] if mag.dim() == 2 else out
+
+    def sources(self):
+        torch = _torch()
+        out = torch.empty((self.info["n_src"], 2), dtype=torch.float64, device=self.device)
+        fs_fem_sources(self._h, out)
+        return out
+
+    def potential(self, dtype=None):
+        torch = _torch()
+        dtype = dtype or (torch.float64 if self.info["precision"] == 64 else torch.float32)
+        phi = torch.empty((self.nrhs, self.info["n_tgt"]), dtype=dtype, device=self.device)
+        fs_eval_potential(self._h, phi)
+        return phi[0] if self.nrhs == 1 else phi
+
+    def field(self, dtype=None, with_phi=True):
+        torch = _torch()
+        dtype = dtype or (torch.float64 if self.info["precision"] == 64 else torch.float32)
+        n = self.info["n_tgt"]
+        phi = torch.empty((self.nrhs, n), dtype=dtype, device=self.device) if with_phi else None
+        H = torch.empty((self.nrhs, n, 2), dtype=dtype, device=self.device)
+        fs_eval_field(self._h, phi, H)
+        if self.nrhs == 1:
+            return (phi[0] if with_phi else None), H[0]
+        return phi, H
+
+    def sync(self):
+        fs_sync_status(self._h)
+
+    def stage_times(self) -> dict:
+        return dict(zip(STAGES, fs_stage_times(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            fs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,124 @@
+// Device-side building blocks shared by the FEM-NFFT kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fs {
+
+constexpr int kMaxP = 16;        // largest smoothness degree
+constexpr int kMaxM = 8;         // largest window half-width; taps per dimension = 2m <= 16
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+template <typename real> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b)
+{
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Error codes written by kernels into the plan's device status word.
+enum DeviceError : int { kDevOk = 0, kDevDomain = 2, kDevTimeout = 5 };
+
+// Kaiser-Bessel window in grid-cell units x = n_os t, normalised to psi(0) = 1:
+//   psi(x) = [m / sinh(b m)] sinh(b tau) / tau,   tau = sqrt(m^2 - x^2),  |x| < m,
+// and 0 for |x| >= m.  Written without overflow as
+//   psi = S e^{z - b m} (1 - e^{-2z}) / z,   z = b tau,   S = m b / (1 - e^{-2 b m}),
+//   psi' = -x b^2 S e^{z - b m} F(z),   F(z) = ((z - 1) + (z + 1) e^{-2z}) / z^3,
+// with F(z) = 2 e^{-z} sum_{k>=1} 2k z^{2k-2} / (2k+1)! for small z.
+template <typename real> struct Window {
+    real m;
+    real m2;
+    real b;
+    real bm;
+    real S;
+};
+
+template <typename real> __device__ __forceinline__ real fexp(real x);
+template <> __device__ __forceinline__ float fexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double fexp<double>(double x) { return exp(x); }
+template <typename real> __device__ __forceinline__ real fexpm1(real x);
+template <> __device__ __forceinline__ float fexpm1<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double fexpm1<double>(double x) { return expm1(x); }
+template <typename real> __device__ __forceinline__ real fsqrt(real x);
+template <> __device__ __forceinline__ float fsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double fsqrt<double>(double x) { return sqrt(x); }
+template <typename real> __device__ __forceinline__ real flog(real x);
+template <> __device__ __forceinline__ float flog<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double flog<double>(double x) { return log(x); }
+
+template <typename real>
+__device__ __forceinline__ real kb_value(const Window<real> &w, real x)
+{
+    const real t = w.m2 - x * x;
+    if (!(t > real(0)))
+        return real(0);
+    const real z = w.b * fsqrt<real>(t);
+    return w.S * fexp<real>(z - w.bm) * (-fexpm1<real>(real(-2) * z)) / z;
+}
+
+// F(z) = ((z-1) + (z+1) e^{-2z}) / z^3 (the slope factor of psi').
+template <typename real>
+__device__ __forceinline__ real kb_slope(real z)
+{
+    if (z < real(1)) {
+        // 2 e^{-z} (1/3 + z^2/30 + z^4/840 + ...): coefficients 2k/(2k+1)!, k = 1..10
+        const real z2 = z * z;
+        real acc = real(20.0 / 51090942171709440000.0);
+        acc = acc * z2 + real(18.0 / 121645100408832000.0);
+        acc = acc * z2 + real(16.0 / 355687428096000.0);
+        acc = acc * z2 + real(14.0 / 1307674368000.0);
+        acc = acc * z2 + real(12.0 / 6227020800.0);
+        acc = acc * z2 + real(10.0 / 39916800.0);
+        acc = acc * z2 + real(8.0 / 362880.0);
+        acc = acc * z2 + real(6.0 / 5040.0);
+        acc = acc * z2 + real(4.0 / 120.0);
+        acc = acc * z2 + real(2.0 / 6.0);
+        return real(2) * fexp<real>(-z) * acc;
+    }
+    const real e = fexp<real>(real(-2) * z);
+    return ((z - real(1)) + (z + real(1)) * e) / (z * z * z);
+}
+
+// psi and dpsi/dx together.
+template <typename real>
+__device__ __forceinline__ void kb_value_slope(const Window<real> &w, real x, real &v, real &d)
+{
+    const real t = w.m2 - x * x;
+    if (!(t > real(0))) {
+        v = real(0);
+        d = real(0);
+        return;
+    }
+    const real z = w.b * fsqrt<real>(t);
+    const real e = w.S * fexp<real>(z - w.bm);
+    v = e * (-fexpm1<real>(real(-2) * z)) / z;
+    d = -x * w.b * w.b * e * kb_slope<real>(z);
+}
+
+// Point record fields in cell-sorted order.
+//   base: packed (b1 | b2 << 16), b = floor(u), u = n_os (s x + 1/2) - window_lo
+//   frac: u - b in [0, 1), per dimension
+__host__ __device__ __forceinline__ int base1(int packed) { return packed & 0xffff; }
+__host__ __device__ __forceinline__ int base2(int packed) { return (packed >> 16) & 0xffff; }
+
+// Tile-major cell key: cells of one spreading tile are contiguous, cells row-major inside.
+struct CellGrid {
+    int cell;      // cell edge in grid cells
+    int n_c;       // cells per dimension
+    int T;         // cells per tile edge
+    int n_t;       // tiles per dimension
+    __host__ __device__ __forceinline__ int key(int c1, int c2) const
+    {
+        const int t1 = c1 / T, t2 = c2 / T;
+        return (t1 * n_t + t2) * (T * T) + (c1 - t1 * T) * T + (c2 - t2 * T);
+    }
+    __host__ __device__ __forceinline__ int n_keys() const { return n_t * n_t * T * T; }
+};
+
+}  // namespace fs

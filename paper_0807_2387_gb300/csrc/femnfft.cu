@@ -1,0 +1,967 @@
+// C ABI of the FEM-NFFT fast summation: plan, charges, evaluation (host side).
+//
+// Declared in include/femnfft.h.  Every compute step runs in the kernels of
+// this directory; this file validates arguments, sizes the workspace, derives
+// the method's constants (torus scale, T_I and T_B, window transform) and
+// enqueues the kernels on the plan's stream.
+#include <algorithm>
+#include <cstdint>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/femnfft.h"
+#include "internal.h"
+
+using namespace fs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fs_status fail(fs_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+#define FS_CUDA(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(FS_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_));           \
+    } while (0)
+
+#define FS_TRY(expr)                                                                                    \
+    do {                                                                                                \
+        fs_status s_ = (expr);                                                                          \
+        if (s_ != FS_OK)                                                                                \
+            return s_;                                                                                  \
+    } while (0)
+
+constexpr int kStages = 8;
+constexpr int kSpreadChunk = 512;   // sources per spreading work item
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Modified Bessel function I_0 by its power series sum_k (x^2/4)^k / (k!)^2 (all terms positive).
+double bessel_i0(double x)
+{
+    const double y = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= y / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-18 * sum && k > x)
+            break;
+    }
+    return sum;
+}
+
+// Solve the p x p system that makes T_I(r) = sum_k beta_k (r/eps)^(2k) match k(r) = -(1/2pi) log r
+// and its first p-1 derivatives at r = eps (scaled variable u = r/eps; Gaussian elimination with
+// partial pivoting).
+bool near_coefficients(double eps, int p, double *beta)
+{
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    std::vector<double> a(p * p, 0.0), rhs(p, 0.0);
+    for (int j = 0; j < p; ++j) {
+        for (int k = 0; k < p; ++k) {
+            const int e = 2 * k;
+            if (e < j)
+                continue;
+            double f = 1.0;
+            for (int t = 0; t < j; ++t)
+                f *= (double)(e - t);
+            a[j * p + k] = f;
+        }
+        if (j == 0) {
+            rhs[j] = -std::log(eps) * inv2pi;
+        } else {
+            double fact = 1.0;   // (j-1)!
+            for (int t = 2; t < j; ++t)
+                fact *= t;
+            rhs[j] = -((j % 2 == 1) ? 1.0 : -1.0) * fact * inv2pi;   // eps^j k^(j)(eps)
+        }
+    }
+    for (int col = 0; col < p; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < p; ++r)
+            if (std::fabs(a[r * p + col]) > std::fabs(a[piv * p + col]))
+                piv = r;
+        if (a[piv * p + col] == 0.0)
+            return false;
+        if (piv != col) {
+            for (int c = 0; c < p; ++c)
+                std::swap(a[piv * p + c], a[col * p + c]);
+            std::swap(rhs[piv], rhs[col]);
+        }
+        for (int r = col + 1; r < p; ++r) {
+            const double f = a[r * p + col] / a[col * p + col];
+            if (f == 0.0)
+                continue;
+            for (int c = col; c < p; ++c)
+                a[r * p + c] -= f * a[col * p + c];
+            rhs[r] -= f * rhs[col];
+        }
+    }
+    for (int r = p - 1; r >= 0; --r) {
+        double s = rhs[r];
+        for (int c = r + 1; c < p; ++c)
+            s -= a[r * p + c] * beta[c];
+        beta[r] = s / a[r * p + r];
+    }
+    return true;
+}
+
+}  // namespace
+
+struct fs_plan {
+    // parameters
+    int precision = 32;
+    int n = 0, n_os = 0, m = 0, p = 0;
+    double sigma = 0, eps_I = 0, eps_B = 0, s = 1.0;
+    int64_t M = 0, N = 0;
+    int window_lo = 0, n_a = 0, pitch = 0, ld = 0;
+    CellGrid cg{};
+    int n_keys = 0;
+    unsigned flags = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool kahan = true;
+    KernelParams kp{};
+    double beta[kMaxP] = {0};
+    // device memory
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    int *status = nullptr;
+    int *src_perm = nullptr, *tgt_perm = nullptr;
+    int *src_base = nullptr, *tgt_base = nullptr;
+    void *src_frac = nullptr, *tgt_frac = nullptr;
+    double2 *src_pos = nullptr, *tgt_pos = nullptr;
+    float2 *src_pos32 = nullptr, *tgt_pos32 = nullptr;
+    int *src_start = nullptr, *tgt_start = nullptr;
+    SpreadItem *items = nullptr;
+    int n_items = 0;
+    void *mul = nullptr, *tw = nullptr;
+    void *grid = nullptr, *spec = nullptr;
+    void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
+    // charges
+    void *q_sorted = nullptr;
+    double *q_sum = nullptr;
+    int nrhs = 0, nrhs_cap = 0;
+    // FEM
+    bool is_fem = false;
+    int64_t Nv = 0, Nt = 0, Ne = 0;
+    const double2 *nodes = nullptr;   // caller's (valid while the plan is used)
+    int *tris = nullptr, *bedges = nullptr;
+    double2 *fem_src = nullptr;
+    double *q_canon = nullptr;
+    int64_t q_canon_cap = 0;
+    // host staging for fs_solve_host
+    void *d_q_stage = nullptr, *d_phi_stage = nullptr, *d_H_stage = nullptr;
+    size_t q_stage_bytes = 0, phi_stage_bytes = 0, H_stage_bytes = 0;
+    // stats
+    int64_t near_pairs = 0, near_pairs_fp64 = 0;
+    // timing
+    cudaEvent_t ev[kStages + 1] = {};
+    cudaEvent_t ev_q0 = nullptr, ev_q1 = nullptr;
+    bool events = false;
+
+    template <typename T> fs_status alloc(T **out, size_t count)
+    {
+        *out = nullptr;
+        if (count == 0)
+            count = 1;
+        void *p_ = nullptr;
+        const size_t nbytes = count * sizeof(T);
+        cudaError_t e = cudaMalloc(&p_, nbytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FS_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed: " +
+                                       cudaGetErrorString(e));
+        }
+        allocs.push_back(p_);
+        bytes += (int64_t)nbytes;
+        *out = static_cast<T *>(p_);
+        return FS_OK;
+    }
+    fs_status alloc_bytes(void **out, size_t nbytes)
+    {
+        unsigned char *p_ = nullptr;
+        FS_TRY(alloc(&p_, nbytes));
+        *out = p_;
+        return FS_OK;
+    }
+    void release(void *ptr)
+    {
+        if (!ptr)
+            return;
+        auto it = std::find(allocs.begin(), allocs.end(), ptr);
+        if (it != allocs.end()) {
+            cudaFree(ptr);
+            allocs.erase(it);
+        }
+    }
+    size_t rsize() const { return precision == 64 ? 8 : 4; }
+};
+
+namespace {
+
+template <typename real> Window<real> make_window(const fs_plan *pl)
+{
+    const double b = kPi * (2.0 - 1.0 / pl->sigma);
+    const double m = pl->m;
+    Window<real> w;
+    w.m = (real)m;
+    w.m2 = (real)(m * m);
+    w.b = (real)b;
+    w.bm = (real)(b * m);
+    w.S = (real)(m * b / (1.0 - std::exp(-2.0 * b * m)));
+    return w;
+}
+
+template <typename real> NearParams<real> make_near(const fs_plan *pl)
+{
+    NearParams<real> np{};
+    np.p = pl->p;
+    np.eps2 = (real)(pl->eps_I * pl->eps_I);
+    np.inv_eps2 = (real)(1.0 / (pl->eps_I * pl->eps_I));
+    np.close2 = (pl->eps_I / 8.0) * (pl->eps_I / 8.0);
+    np.hcell = (real)((double)pl->cg.cell / pl->n_os);
+    for (int k = 0; k < pl->p; ++k)
+        np.beta[k] = (real)pl->beta[k];
+    for (int k = 1; k < pl->p; ++k)
+        np.dbeta[k - 1] = (real)(2.0 * k * pl->beta[k] / (pl->eps_I * pl->eps_I));
+    return np;
+}
+
+// Bin one point set: keys, counting sort, per-point records.
+template <typename real>
+fs_status bin_points(fs_plan *pl, const double *xy, int64_t n, int **perm, int **base, void **frac, double2 **pos,
+                     float2 **pos32, int **start)
+{
+    FS_TRY(pl->alloc(perm, n));
+    FS_TRY(pl->alloc(base, n));
+    FS_TRY(pl->alloc_bytes(frac, (size_t)std::max<int64_t>(n, 1) * 2 * sizeof(real)));
+    FS_TRY(pl->alloc(pos, n));
+    if (pl->precision == 32)
+        FS_TRY(pl->alloc(pos32, n));
+    else
+        *pos32 = nullptr;
+    FS_TRY(pl->alloc(start, (size_t)pl->n_keys + 1));
+    int *key = nullptr, *count = nullptr, *fill = nullptr, *tmp = nullptr;
+    FS_TRY(pl->alloc(&key, n));
+    FS_TRY(pl->alloc(&count, pl->n_keys));
+    FS_TRY(pl->alloc(&fill, (size_t)pl->n_keys + 1));
+    FS_TRY(pl->alloc(&tmp, (size_t)pl->n_keys / 4096 + 2));
+    cudaStream_t st = pl->stream;
+    FS_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * pl->n_keys, st));
+    FS_CUDA(cudaMemsetAsync(*start, 0, sizeof(int) * ((size_t)pl->n_keys + 1), st));
+    FS_CUDA(launch_point_keys(xy, n, pl->s, pl->n_os, pl->window_lo, pl->n_a, pl->m, pl->cg, key, count, pl->status,
+                              st));
+    FS_CUDA(launch_exclusive_scan(count, *start, pl->n_keys, tmp, st));
+    FS_CUDA(cudaMemcpyAsync(fill, *start, sizeof(int) * ((size_t)pl->n_keys + 1), cudaMemcpyDeviceToDevice, st));
+    FS_CUDA(launch_scatter(key, n, fill, *perm, st));
+    FS_CUDA(launch_gather_points<real>(xy, *perm, n, pl->s, pl->n_os, pl->window_lo, pl->n_a, pl->m, pl->cg.cell, *pos,
+                                       *frac, *base, *pos32, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    pl->release(key);
+    pl->release(count);
+    pl->release(fill);
+    pl->release(tmp);
+    return FS_OK;
+}
+
+template <typename real> fs_status twiddles(fs_plan *pl, int L, void **out)
+{
+    std::vector<real> h(2 * (size_t)L);
+    for (int t = 0; t < L; ++t) {
+        const double ang = 2.0 * kPi * (double)t / (double)L;
+        h[2 * t] = (real)std::cos(ang);
+        h[2 * t + 1] = (real)(-std::sin(ang));
+    }
+    FS_TRY(pl->alloc_bytes(out, h.size() * sizeof(real)));
+    FS_CUDA(cudaMemcpyAsync(*out, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, pl->stream));
+    FS_CUDA(cudaStreamSynchronize(pl->stream));
+    return FS_OK;
+}
+
+// b_l on the device in FP64 and the multiplier table in the working precision.
+template <typename real> fs_status coefficients(fs_plan *pl)
+{
+    const int n = pl->n;
+    cudaStream_t st = pl->stream;
+    double2 *samp = nullptr, *tmp = nullptr;
+    void *tw64 = nullptr;
+    double *c_tab = nullptr;
+    FS_TRY(pl->alloc(&samp, (size_t)n * n));
+    FS_TRY(pl->alloc(&tmp, (size_t)n * n));
+    FS_TRY(twiddles<double>(pl, n, &tw64));
+    FS_CUDA(launch_kernel_samples(samp, n, pl->kp, st));
+    FS_CUDA(launch_fft_lines_c64(samp, n, n, (const double2 *)tw64, st));
+    FS_CUDA(launch_transpose_c64(samp, tmp, n, st));
+    FS_CUDA(launch_fft_lines_c64(tmp, n, n, (const double2 *)tw64, st));
+    // window transform c(l) = n_os phi_1-hat(l) / phi_1(0) = I_0(m sqrt(b^2 - (2 pi l / n_os)^2)) pi m / sinh(b m)
+    const double b = kPi * (2.0 - 1.0 / pl->sigma);
+    const double m = pl->m;
+    std::vector<double> c(n / 2 + 1);
+    for (int l = 0; l <= n / 2; ++l) {
+        const double arg = b * b - std::pow(2.0 * kPi * l / pl->n_os, 2);
+        c[l] = bessel_i0(m * std::sqrt(arg)) * kPi * m / std::sinh(b * m);
+    }
+    FS_TRY(pl->alloc(&c_tab, c.size()));
+    FS_CUDA(cudaMemcpyAsync(c_tab, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    FS_TRY(pl->alloc_bytes(&pl->mul, (size_t)(n / 2 + 1) * (n + 1) * sizeof(real)));
+    FS_CUDA(launch_build_mul<real>(tmp, n, c_tab, (real *)pl->mul, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    pl->release(samp);
+    pl->release(tmp);
+    pl->release(tw64);
+    pl->release(c_tab);
+    return FS_OK;
+}
+
+fs_status validate_params(int n_grid, double sigma_os, int m, double eps_I, const fs_opts &o)
+{
+    if (!is_pow2(n_grid) || n_grid < 8 || n_grid > 2048)
+        return fail(FS_EINVAL, "n_grid must be a power of two in [8, 2048]");
+    if (!(sigma_os > 1.0))
+        return fail(FS_EINVAL, "sigma_os must exceed 1");
+    const double nos = sigma_os * n_grid;
+    const int n_os = (int)std::lround(nos);
+    if (std::fabs(nos - n_os) > 1e-9 || !is_pow2(n_os) || n_os > 4096 || n_os <= n_grid)
+        return fail(FS_EINVAL, "sigma_os * n_grid must be a power of two in (n_grid, 4096]");
+    if (m < 2 || m > kMaxM || 4 * m >= n_os)
+        return fail(FS_EINVAL, "m_window must be in [2, 8] and below n_os / 4");
+    if (!(eps_I > 0.0) || !(eps_I < 0.25))
+        return fail(FS_EINVAL, "eps_I must be in (0, 1/4) (torus units)");
+    if (o.precision != 0 && o.precision != 32 && o.precision != 64)
+        return fail(FS_EINVAL, "precision must be 32 or 64");
+    if (o.p < 0 || o.p > kMaxP)
+        return fail(FS_EINVAL, "p must be in [1, 16] (0 = default)");
+    if (o.eps_B < 0.0 || o.eps_B >= 0.25 || std::isnan(o.eps_B))
+        return fail(FS_EINVAL, "eps_B must be in (0, 1/4) (0 = default)");
+    if (o.cell < 0 || o.tile_cells < 0)
+        return fail(FS_EINVAL, "cell and tile_cells must be >= 0");
+    return FS_OK;
+}
+
+template <typename real>
+fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt, int64_t N, int n_grid,
+                    double sigma_os, int m, double eps_I, const fs_opts &o)
+{
+    pl->n = n_grid;
+    pl->sigma = sigma_os;
+    pl->n_os = (int)std::lround(sigma_os * n_grid);
+    pl->m = m;
+    pl->eps_I = eps_I;
+    pl->p = o.p > 0 ? o.p : std::min(kMaxP, std::max(2, (int)std::lround(n_grid * eps_I)));
+    pl->eps_B = o.eps_B > 0 ? o.eps_B : eps_I;
+    pl->M = M;
+    pl->N = N;
+    pl->flags = o.flags;
+    pl->kahan = !(o.flags & FS_FLAG_NO_KAHAN);
+    pl->stream = (cudaStream_t)o.stream;
+    FS_CUDA(cudaGetDevice(&pl->device));
+    cudaStream_t st = pl->stream;
+    FS_TRY(pl->alloc(&pl->status, 1));
+    FS_CUDA(cudaMemsetAsync(pl->status, 0, sizeof(int), st));
+
+    // torus scale from the largest radius
+    unsigned long long *d_r = nullptr;
+    FS_TRY(pl->alloc(&d_r, 1));
+    FS_CUDA(cudaMemsetAsync(d_r, 0, sizeof(unsigned long long), st));
+    FS_CUDA(launch_rmax(src, M, d_r, st));
+    FS_CUDA(launch_rmax(tgt, N, d_r, st));
+    unsigned long long r_bits = 0;
+    FS_CUDA(cudaMemcpyAsync(&r_bits, d_r, sizeof(r_bits), cudaMemcpyDeviceToHost, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    pl->release(d_r);
+    double r2max;
+    std::memcpy(&r2max, &r_bits, sizeof(double));
+    if (!std::isfinite(r2max))
+        return fail(FS_EINVAL, "non-finite point coordinates");
+    const double rmax = std::sqrt(r2max);
+    pl->s = rmax > 0.0 ? (0.25 - 0.5 * pl->eps_B) / rmax : 1.0;
+
+    // active window: grid lines that can hold a tap, with a one-line margin
+    const int L = pl->n_os;
+    pl->window_lo = (int)std::floor(L * (0.25 + 0.5 * pl->eps_B)) - m - 1;
+    const int hi = (int)std::floor(L * (0.75 - 0.5 * pl->eps_B)) + 1;
+    int n_a = hi - pl->window_lo + m + 1;
+    n_a = (n_a + 3) & ~3;
+    if (n_a > L)
+        return fail(FS_EINVAL, "window half-width too large for this grid (active window exceeds n_os)");
+    pl->n_a = n_a;
+    pl->pitch = n_a;
+    pl->ld = n_a;
+
+    // cells and tiles
+    int cell = o.cell;
+    const int min_cell = (int)std::ceil(eps_I * L - 1e-9);
+    if (cell == 0)
+        cell = std::max(1, min_cell);
+    else if (cell < min_cell)
+        return fail(FS_EINVAL, "cell narrower than eps_I");
+    pl->cg.cell = cell;
+    pl->cg.n_c = (n_a + cell - 1) / cell;
+    int T = o.tile_cells > 0 ? o.tile_cells : std::max(1, (int)std::lround(32.0 / cell));
+    auto smem_for = [&](int t) {
+        const int P = t * cell + 2 * m - 1;
+        return (size_t)P * P * sizeof(real) * ((pl->kahan && sizeof(real) == 4) ? 2 : 1);
+    };
+    while (T > 1 && smem_for(T) > 160 * 1024)
+        --T;
+    if (smem_for(T) > 200 * 1024)
+        return fail(FS_EINVAL, "spreading tile does not fit in shared memory (cell too wide)");
+    pl->cg.T = T;
+    pl->cg.n_t = (pl->cg.n_c + T - 1) / T;
+    pl->n_keys = pl->cg.n_keys();
+    if (pl->n_keys > 4096 * 4096)
+        return fail(FS_EINVAL, "too many cells (eps_I too small for this grid)");
+
+    // regularised kernel data
+    pl->kp.eps_I = eps_I;
+    pl->kp.eps_B = pl->eps_B;
+    pl->kp.p = pl->p;
+    if (!near_coefficients(eps_I, pl->p, pl->beta))
+        return fail(FS_EINVAL, "singular near-field interpolation system");
+    for (int k = 0; k < pl->p; ++k)
+        pl->kp.beta[k] = pl->beta[k];
+    {
+        const double inv2pi = 1.0 / (2.0 * kPi);
+        const double r0 = 0.5 - pl->eps_B;
+        double fact = 1.0;   // j!
+        for (int j = 0; j < pl->p; ++j) {
+            double kj;
+            if (j == 0) {
+                kj = -std::log(r0) * inv2pi;
+            } else {
+                double f1 = 1.0;   // (j-1)!
+                for (int t = 2; t < j; ++t)
+                    f1 *= t;
+                kj = -((j % 2 == 1) ? 1.0 : -1.0) * f1 * std::pow(r0, -(double)j) * inv2pi;
+            }
+            if (j > 0)
+                fact *= j;
+            pl->kp.tb_f0[j] = std::pow(pl->eps_B, (double)j) * kj / fact;
+            // C(p-1+j, j)
+            double cbin = 1.0;
+            for (int t = 1; t <= j; ++t)
+                cbin = cbin * (double)(pl->p - 1 + t) / (double)t;
+            pl->kp.tb_binom[j] = cbin;
+        }
+        pl->kp.k_half = std::log(2.0) * inv2pi;
+    }
+
+    // binning
+    FS_TRY(bin_points<real>(pl, src, M, &pl->src_perm, &pl->src_base, &pl->src_frac, &pl->src_pos, &pl->src_pos32,
+                            &pl->src_start));
+    FS_TRY(bin_points<real>(pl, tgt, N, &pl->tgt_perm, &pl->tgt_base, &pl->tgt_frac, &pl->tgt_pos, &pl->tgt_pos32,
+                            &pl->tgt_start));
+    int dev_status = 0;
+    FS_CUDA(cudaMemcpy(&dev_status, pl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_status != 0)
+        return fail(FS_EDOMAIN, "a point fell outside the admissible radius after scaling");
+
+    // spreading work items: tiles split into slices of at most kSpreadChunk sources
+    {
+        std::vector<int> start(pl->n_keys + 1);
+        FS_CUDA(cudaMemcpy(start.data(), pl->src_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
+        std::vector<SpreadItem> items;
+        const int TT = T * T;
+        const int n_tiles = pl->cg.n_t * pl->cg.n_t;
+        for (int t = 0; t < n_tiles; ++t) {
+            const int a = start[t * TT], b2 = start[(t + 1) * TT];
+            for (int s0 = a; s0 < b2; s0 += kSpreadChunk)
+                items.push_back(SpreadItem{t, s0, std::min(kSpreadChunk, b2 - s0), 0});
+        }
+        pl->n_items = (int)items.size();
+        FS_TRY(pl->alloc(&pl->items, items.size()));
+        if (!items.empty())
+            FS_CUDA(cudaMemcpy(pl->items, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
+    }
+
+    // coefficient table and FFT twiddles
+    FS_TRY(coefficients<real>(pl));
+    FS_TRY(twiddles<real>(pl, L, &pl->tw));
+
+    // grids and per-target intermediates
+    FS_TRY(pl->alloc_bytes(&pl->grid, (size_t)n_a * pl->pitch * sizeof(real)));
+    FS_TRY(pl->alloc_bytes(&pl->spec, (size_t)(pl->n / 2 + 1) * pl->ld * 2 * sizeof(real)));
+    FS_TRY(pl->alloc_bytes(&pl->phi_s, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
+    FS_TRY(pl->alloc_bytes(&pl->grad_s, (size_t)std::max<int64_t>(N, 1) * 2 * sizeof(real)));
+    FS_TRY(pl->alloc_bytes(&pl->coinc, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
+
+    // near-field pair statistics (FP64 distances)
+    {
+        unsigned long long *cnt = nullptr;
+        FS_TRY(pl->alloc(&cnt, 2));
+        FS_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+        FS_CUDA(launch_near_count(pl->tgt_pos, pl->tgt_base, N, pl->src_pos, pl->src_start, pl->cg, eps_I * eps_I,
+                                  (eps_I / 8) * (eps_I / 8), cnt, st));
+        unsigned long long h[2] = {0, 0};
+        FS_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        pl->near_pairs = (int64_t)h[0];
+        pl->near_pairs_fp64 = (int64_t)h[1];
+        pl->release(cnt);
+    }
+
+    if (pl->flags & FS_FLAG_TIMING) {
+        for (int i = 0; i <= kStages; ++i)
+            FS_CUDA(cudaEventCreate(&pl->ev[i]));
+        FS_CUDA(cudaEventCreate(&pl->ev_q0));
+        FS_CUDA(cudaEventCreate(&pl->ev_q1));
+        pl->events = true;
+    }
+    return FS_OK;
+}
+
+fs_status plan_create_common(const double *src, int64_t M, const double *tgt, int64_t N, int n_grid,
+                             double sigma_os, int m, double eps_I, const fs_opts *opts, fs_plan *pl)
+{
+    fs_opts o{};
+    if (opts)
+        o = *opts;
+    FS_TRY(validate_params(n_grid, sigma_os, m, eps_I, o));
+    pl->precision = o.precision == 64 ? 64 : 32;
+    if (pl->precision == 64)
+        return plan_init<double>(pl, src, M, tgt, N, n_grid, sigma_os, m, eps_I, o);
+    return plan_init<float>(pl, src, M, tgt, N, n_grid, sigma_os, m, eps_I, o);
+}
+
+void destroy(fs_plan *pl)
+{
+    if (!pl)
+        return;
+    cudaStreamSynchronize(pl->stream);
+    for (void *p : pl->allocs)
+        cudaFree(p);
+    for (int i = 0; i <= kStages; ++i)
+        if (pl->ev[i])
+            cudaEventDestroy(pl->ev[i]);
+    if (pl->ev_q0)
+        cudaEventDestroy(pl->ev_q0);
+    if (pl->ev_q1)
+        cudaEventDestroy(pl->ev_q1);
+    delete pl;
+}
+
+template <typename real> fs_status set_charges_t(fs_plan *pl, const void *q, fs_dtype dtype, int nrhs)
+{
+    cudaStream_t st = pl->stream;
+    if (nrhs > pl->nrhs_cap) {
+        pl->release(pl->q_sorted);
+        pl->release(pl->q_sum);
+        pl->q_sorted = nullptr;
+        pl->q_sum = nullptr;
+        FS_TRY(pl->alloc_bytes(&pl->q_sorted, (size_t)std::max<int64_t>(pl->M, 1) * nrhs * sizeof(real)));
+        FS_TRY(pl->alloc(&pl->q_sum, nrhs));
+        pl->nrhs_cap = nrhs;
+    }
+    pl->nrhs = nrhs;
+    if (pl->events)
+        FS_CUDA(cudaEventRecord(pl->ev_q0, st));
+    FS_CUDA(cudaMemsetAsync(pl->q_sum, 0, sizeof(double) * nrhs, st));
+    FS_CUDA(launch_gather_charges<real>(q, dtype == FS_F64, pl->src_perm, pl->M, nrhs, (real *)pl->q_sorted,
+                                        pl->q_sum, st));
+    if (pl->events)
+        FS_CUDA(cudaEventRecord(pl->ev_q1, st));
+    return FS_OK;
+}
+
+template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dtype dtype)
+{
+    cudaStream_t st = pl->stream;
+    const Window<real> w = make_window<real>(pl);
+    const NearParams<real> np = make_near<real>(pl);
+    using C = typename Cplx<real>::type;
+    const double shift = std::log(pl->s) / (2.0 * kPi);
+    const size_t osz = dtype == FS_F64 ? 8 : 4;
+    for (int r = 0; r < pl->nrhs; ++r) {
+        const bool rec = pl->events && r == pl->nrhs - 1;
+        const real *q = (const real *)pl->q_sorted + (int64_t)r * pl->M;
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[0], st));
+        FS_CUDA(cudaMemsetAsync(pl->grid, 0, (size_t)pl->n_a * pl->pitch * sizeof(real), st));
+        FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w,
+                                    (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[1], st));
+        FS_CUDA(launch_fft_rows_fwd<real>((const real *)pl->grid, pl->pitch, pl->n_a, pl->n_os, pl->n / 2,
+                                          (C *)pl->spec, pl->ld, (const C *)pl->tw, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[2], st));
+        FS_CUDA(launch_fft_cols<real>((C *)pl->spec, pl->ld, pl->n_a, pl->n_os, pl->n, (const real *)pl->mul,
+                                      (const C *)pl->tw, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[3], st));
+        FS_CUDA(launch_fft_rows_inv<real>((const C *)pl->spec, pl->ld, pl->n_a, pl->n_os, pl->n / 2,
+                                          (real *)pl->grid, pl->pitch, (const C *)pl->tw, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[4], st));
+        FS_CUDA(launch_interp<real>(pl->N, pl->m, pl->tgt_base, pl->tgt_frac, w, (const real *)pl->grid, pl->pitch,
+                                    (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[5], st));
+        FS_CUDA(launch_near<real>(pl->N, pl->tgt_base, pl->tgt_pos, pl->tgt_pos32, pl->src_pos, pl->src_pos32,
+                                  pl->src_start, pl->cg, q, np, (real *)pl->phi_s, (real *)pl->grad_s,
+                                  (real *)pl->coinc, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[6], st));
+        void *po = phi ? (unsigned char *)phi + (size_t)r * pl->N * osz : nullptr;
+        void *ho = H ? (unsigned char *)H + (size_t)r * pl->N * 2 * osz : nullptr;
+        FS_CUDA(launch_unpermute<real>(pl->N, (const real *)pl->phi_s, (const real *)pl->grad_s,
+                                       (const real *)pl->coinc, pl->tgt_perm, shift, pl->q_sum + r, pl->s, po, ho,
+                                       dtype == FS_F64, st));
+        if (rec)
+            FS_CUDA(cudaEventRecord(pl->ev[7], st));
+    }
+    return FS_OK;
+}
+
+fs_status check_plan(const fs_plan *pl)
+{
+    if (!pl)
+        return fail(FS_EINVAL, "null plan");
+    return FS_OK;
+}
+
+fs_status check_dtype(fs_dtype d)
+{
+    if (d != FS_F32 && d != FS_F64)
+        return fail(FS_EINVAL, "dtype must be FS_F32 or FS_F64");
+    return FS_OK;
+}
+
+// Boundary edges (used by one triangle), sorted by (lo, hi), with the owner's third node.
+fs_status boundary_edges(const std::vector<int> &tris, int64_t Nt, int64_t Nv, std::vector<int> &out)
+{
+    struct E {
+        int lo, hi, third;
+    };
+    std::vector<E> e;
+    e.reserve(3 * Nt);
+    for (int64_t t = 0; t < Nt; ++t) {
+        const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        for (int k = 0; k < 3; ++k) {
+            if (v[k] < 0 || v[k] >= Nv)
+                return fail(FS_EINVAL, "triangle node index out of range");
+        }
+        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2])
+            return fail(FS_EINVAL, "degenerate triangle (repeated node)");
+        for (int k = 0; k < 3; ++k) {
+            const int a = v[k], b = v[(k + 1) % 3], c = v[(k + 2) % 3];
+            e.push_back(E{std::min(a, b), std::max(a, b), c});
+        }
+    }
+    std::sort(e.begin(), e.end(), [](const E &x, const E &y) { return x.lo != y.lo ? x.lo < y.lo : x.hi < y.hi; });
+    out.clear();
+    size_t i = 0;
+    while (i < e.size()) {
+        size_t j = i + 1;
+        while (j < e.size() && e[j].lo == e[i].lo && e[j].hi == e[i].hi)
+            ++j;
+        if (j - i == 1) {
+            out.push_back(e[i].lo);
+            out.push_back(e[i].hi);
+            out.push_back(e[i].third);
+        } else if (j - i > 2) {
+            return fail(FS_EINVAL, "non-manifold mesh: an edge is shared by more than two triangles");
+        }
+        i = j;
+    }
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fs_last_error(void) { return g_last_error.c_str(); }
+
+const char *fs_version(void) { return "femnfft-gb300 0.1 (sm_103a)"; }
+
+fs_status fs_plan_create(const double *src_xy, int64_t M, const double *tgt_xy, int64_t N, int n_grid,
+                         double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs_plan **out)
+{
+    g_last_error.clear();
+    if (!out)
+        return fail(FS_EINVAL, "out is null");
+    *out = nullptr;
+    if (M < 0 || N < 0 || M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX)
+        return fail(FS_EINVAL, "M and N must be in [0, 2^31)");
+    if ((M > 0 && !src_xy) || (N > 0 && !tgt_xy))
+        return fail(FS_EINVAL, "null point array");
+    fs_plan *pl = new (std::nothrow) fs_plan();
+    if (!pl)
+        return fail(FS_ENOMEM, "host allocation failed");
+    fs_status st = plan_create_common(src_xy, M, tgt_xy, N, n_grid, sigma_os, m_window, eps_I, opts, pl);
+    if (st != FS_OK) {
+        const std::string msg = g_last_error;
+        destroy(pl);
+        g_last_error = msg;
+        return st;
+    }
+    *out = pl;
+    return FS_OK;
+}
+
+fs_status fs_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tris, int64_t Nt, int n_grid,
+                             double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs_plan **out)
+{
+    g_last_error.clear();
+    if (!out)
+        return fail(FS_EINVAL, "out is null");
+    *out = nullptr;
+    if (Nv <= 0 || Nt <= 0 || !nodes || !tris)
+        return fail(FS_EINVAL, "a mesh needs nodes and triangles");
+    if (Nv > (int64_t)INT32_MAX || 3 * Nt > (int64_t)INT32_MAX)
+        return fail(FS_EINVAL, "mesh too large");
+    if ((reinterpret_cast<uintptr_t>(nodes) & 15u) != 0)
+        return fail(FS_EINVAL, "nodes must be 16-byte aligned (read as (x, y) pairs)");
+    fs_opts o{};
+    if (opts)
+        o = *opts;
+    fs_plan *pl = new (std::nothrow) fs_plan();
+    if (!pl)
+        return fail(FS_ENOMEM, "host allocation failed");
+    auto body = [&]() -> fs_status {
+        FS_TRY(validate_params(n_grid, sigma_os, m_window, eps_I, o));
+        cudaStream_t st = (cudaStream_t)o.stream;
+        std::vector<int> h_tris(3 * Nt), h_edges;
+        FS_CUDA(cudaMemcpyAsync(h_tris.data(), tris, sizeof(int) * 3 * Nt, cudaMemcpyDeviceToHost, st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        FS_TRY(boundary_edges(h_tris, Nt, Nv, h_edges));
+        pl->is_fem = true;
+        pl->Nv = Nv;
+        pl->Nt = Nt;
+        pl->Ne = (int64_t)h_edges.size() / 3;
+        pl->nodes = (const double2 *)nodes;
+        FS_TRY(pl->alloc(&pl->tris, 3 * Nt));
+        FS_TRY(pl->alloc(&pl->bedges, std::max<size_t>(h_edges.size(), 1)));
+        FS_CUDA(cudaMemcpyAsync(pl->tris, h_tris.data(), sizeof(int) * 3 * Nt, cudaMemcpyHostToDevice, st));
+        if (!h_edges.empty())
+            FS_CUDA(cudaMemcpyAsync(pl->bedges, h_edges.data(), sizeof(int) * h_edges.size(), cudaMemcpyHostToDevice,
+                                    st));
+        const int64_t Ms = 3 * Nt + 2 * pl->Ne;
+        FS_TRY(pl->alloc(&pl->fem_src, Ms));
+        FS_CUDA(launch_fem_sources((const double2 *)nodes, pl->tris, Nt, pl->bedges, pl->Ne, pl->fem_src, st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        pl->precision = o.precision == 64 ? 64 : 32;
+        if (pl->precision == 64)
+            return plan_init<double>(pl, (const double *)pl->fem_src, Ms, nodes, Nv, n_grid, sigma_os, m_window,
+                                     eps_I, o);
+        return plan_init<float>(pl, (const double *)pl->fem_src, Ms, nodes, Nv, n_grid, sigma_os, m_window, eps_I,
+                                o);
+    };
+    fs_status st = body();
+    if (st != FS_OK) {
+        const std::string msg = g_last_error;
+        destroy(pl);
+        g_last_error = msg;
+        return st;
+    }
+    *out = pl;
+    return FS_OK;
+}
+
+fs_status fs_set_charges(fs_plan *plan, const void *q, fs_dtype dtype, int nrhs)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    FS_TRY(check_dtype(dtype));
+    if (nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "nrhs must be in [1, 65535]");
+    if (!q && plan->M > 0)
+        return fail(FS_EINVAL, "null charges");
+    if (plan->precision == 64)
+        return set_charges_t<double>(plan, q, dtype, nrhs);
+    return set_charges_t<float>(plan, q, dtype, nrhs);
+}
+
+fs_status fs_fem_charges(fs_plan *plan, const double *mag, double *q_out, int nrhs)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!mag || !q_out || nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "bad magnetisation/charge arguments");
+    if ((reinterpret_cast<uintptr_t>(mag) & 15u) != 0)
+        return fail(FS_EINVAL, "magnetisation must be 16-byte aligned (read as (Mx, My) pairs)");
+    FS_CUDA(launch_fem_charges(plan->nodes, plan->tris, plan->Nt, plan->bedges, plan->Ne, (const double2 *)mag,
+                               plan->Nv, nrhs, q_out, plan->M, plan->stream));
+    return FS_OK;
+}
+
+fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!mag || nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "bad magnetisation arguments");
+    if ((int64_t)nrhs * plan->M > plan->q_canon_cap) {
+        plan->release(plan->q_canon);
+        plan->q_canon = nullptr;
+        FS_TRY(plan->alloc(&plan->q_canon, (size_t)nrhs * plan->M));
+        plan->q_canon_cap = (int64_t)nrhs * plan->M;
+    }
+    FS_TRY(fs_fem_charges(plan, mag, plan->q_canon, nrhs));
+    return fs_set_charges(plan, plan->q_canon, FS_F64, nrhs);
+}
+
+fs_status fs_fem_sources(fs_plan *plan, double *src_out)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!src_out)
+        return fail(FS_EINVAL, "null output");
+    FS_CUDA(cudaMemcpyAsync(src_out, plan->fem_src, sizeof(double2) * plan->M, cudaMemcpyDeviceToDevice,
+                            plan->stream));
+    return FS_OK;
+}
+
+fs_status fs_eval_field(fs_plan *plan, void *phi, void *H, fs_dtype dtype)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    FS_TRY(check_dtype(dtype));
+    if (plan->nrhs < 1)
+        return fail(FS_EINVAL, "charges not set");
+    if (plan->N > 0 && !phi && !H)
+        return fail(FS_EINVAL, "no output requested");
+    if (plan->precision == 64)
+        return eval_t<double>(plan, phi, H, dtype);
+    return eval_t<float>(plan, phi, H, dtype);
+}
+
+fs_status fs_eval_potential(fs_plan *plan, void *phi, fs_dtype dtype)
+{
+    if (!phi && plan && plan->N > 0)
+        return fail(FS_EINVAL, "null phi");
+    return fs_eval_field(plan, phi, nullptr, dtype);
+}
+
+fs_status fs_solve_host(fs_plan *plan, const void *q, fs_dtype q_dtype, int nrhs, void *phi, void *H,
+                        fs_dtype out_dtype)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    FS_TRY(check_dtype(q_dtype));
+    FS_TRY(check_dtype(out_dtype));
+    if (nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "nrhs must be in [1, 65535]");
+    if ((!q && plan->M > 0) || (!H && plan->N > 0))
+        return fail(FS_EINVAL, "null host buffer");
+    cudaStream_t st = plan->stream;
+    const size_t qb = (size_t)nrhs * plan->M * (q_dtype == FS_F64 ? 8 : 4);
+    const size_t ob = (size_t)nrhs * plan->N * (out_dtype == FS_F64 ? 8 : 4);
+    if (qb > plan->q_stage_bytes) {
+        plan->release(plan->d_q_stage);
+        FS_TRY(plan->alloc_bytes(&plan->d_q_stage, qb));
+        plan->q_stage_bytes = qb;
+    }
+    if (ob > plan->phi_stage_bytes) {
+        plan->release(plan->d_phi_stage);
+        FS_TRY(plan->alloc_bytes(&plan->d_phi_stage, ob));
+        plan->phi_stage_bytes = ob;
+    }
+    if (2 * ob > plan->H_stage_bytes) {
+        plan->release(plan->d_H_stage);
+        FS_TRY(plan->alloc_bytes(&plan->d_H_stage, 2 * ob));
+        plan->H_stage_bytes = 2 * ob;
+    }
+    if (qb)
+        FS_CUDA(cudaMemcpyAsync(plan->d_q_stage, q, qb, cudaMemcpyHostToDevice, st));
+    FS_TRY(fs_set_charges(plan, plan->d_q_stage, q_dtype, nrhs));
+    FS_TRY(fs_eval_field(plan, phi ? plan->d_phi_stage : nullptr, plan->d_H_stage, out_dtype));
+    if (phi && ob)
+        FS_CUDA(cudaMemcpyAsync(phi, plan->d_phi_stage, ob, cudaMemcpyDeviceToHost, st));
+    if (ob)
+        FS_CUDA(cudaMemcpyAsync(H, plan->d_H_stage, 2 * ob, cudaMemcpyDeviceToHost, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    return fs_sync_status(plan);
+}
+
+fs_status fs_sync_status(fs_plan *plan)
+{
+    FS_TRY(check_plan(plan));
+    FS_CUDA(cudaStreamSynchronize(plan->stream));
+    int code = 0;
+    FS_CUDA(cudaMemcpy(&code, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code == 0)
+        return FS_OK;
+    FS_CUDA(cudaMemset(plan->status, 0, sizeof(int)));
+    if (code == kDevTimeout)
+        return fail(FS_ETIMEOUT, "a bounded device wait gave up");
+    return fail(FS_EDOMAIN, "a point fell outside the admissible region");
+}
+
+fs_status fs_plan_info(const fs_plan *plan, fs_info *info)
+{
+    FS_TRY(check_plan(plan));
+    if (!info)
+        return fail(FS_EINVAL, "null info");
+    std::memset(info, 0, sizeof(*info));
+    info->n_src = plan->M;
+    info->n_tgt = plan->N;
+    info->n_grid = plan->n;
+    info->n_os = plan->n_os;
+    info->m = plan->m;
+    info->p = plan->p;
+    info->precision = plan->precision;
+    info->eps_I = plan->eps_I;
+    info->eps_B = plan->eps_B;
+    info->scale = plan->s;
+    info->window_lo = plan->window_lo;
+    info->window_n = plan->n_a;
+    info->cell = plan->cg.cell;
+    info->cells_per_dim = plan->cg.n_c;
+    info->tile_cells = plan->cg.T;
+    info->spread_items = plan->n_items;
+    info->near_pairs = plan->near_pairs;
+    info->near_pairs_fp64 = plan->near_pairs_fp64;
+    info->workspace_bytes = plan->bytes;
+    info->is_fem = plan->is_fem;
+    info->n_nodes = plan->Nv;
+    info->n_tris = plan->Nt;
+    info->n_bedges = plan->Ne;
+    return FS_OK;
+}
+
+fs_status fs_stage_times(fs_plan *plan, double *ms, int count)
+{
+    FS_TRY(check_plan(plan));
+    if (!plan->events)
+        return fail(FS_EINVAL, "plan created without FS_FLAG_TIMING");
+    if (!ms || count < kStages)
+        return fail(FS_EINVAL, "need room for 8 stage times");
+    FS_CUDA(cudaStreamSynchronize(plan->stream));
+    float t = 0.f;
+    FS_CUDA(cudaEventElapsedTime(&t, plan->ev_q0, plan->ev_q1));
+    ms[0] = t;
+    for (int i = 1; i < kStages; ++i) {
+        FS_CUDA(cudaEventElapsedTime(&t, plan->ev[i - 1], plan->ev[i]));
+        ms[i] = t;
+    }
+    return FS_OK;
+}
+
+fs_status fs_plan_destroy(fs_plan *plan)
+{
+    if (!plan)
+        return FS_OK;
+    destroy(plan);
+    return FS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Launch wrappers of the FEM-NFFT kernels; each is defined in the .cu file that holds its kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace fs {
+
+// One spreading work unit: sources [start, start+count) of tile `tile` (cell-sorted order).
+struct SpreadItem {
+    int tile;
+    int start;
+    int count;
+    int pad;
+};
+
+// Regularised-kernel description for the b_l samples and the near field (FP64, host-filled).
+struct KernelParams {
+    double eps_I;
+    double eps_B;
+    int p;
+    double beta[kMaxP];    // T_I(r) = sum_k beta_k (r/eps_I)^(2k)
+    double tb_f0[kMaxP];   // eps_B^j k^(j)(1/2 - eps_B) / j!   (two-point Taylor data at the left end)
+    double tb_binom[kMaxP];// C(p-1+i, i)
+    double k_half;         // k(1/2)
+};
+
+// Near-field constants in the arithmetic precision.
+template <typename real> struct NearParams {
+    real eps2;             // eps_I^2
+    real inv_eps2;
+    double close2;         // (eps_I/8)^2: pairs below use an FP64 coordinate difference
+    real hcell;            // cell width in torus units (FP32 positions are relative to cell corners)
+    real beta[kMaxP];      // T_I coefficients in u^2 = (r/eps_I)^2
+    real dbeta[kMaxP];     // coefficients of T_I'(r)/r in u^2: 2k beta_k / eps_I^2 (index k-1)
+    int p;
+};
+
+// ---- binning (kernels_bin.cu)
+cudaError_t launch_rmax(const double *xy, int64_t n, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_point_keys(const double *xy, int64_t n, double s, int n_os, int window_lo, int n_a,
+                              int m, CellGrid cg, int *key, int *count, int *status, cudaStream_t st);
+cudaError_t launch_exclusive_scan(const int *count, int *start, int n, int *block_tmp, cudaStream_t st);
+cudaError_t launch_scatter(const int *key, int64_t n, int *fill, int *perm, cudaStream_t st);
+template <typename real>
+cudaError_t launch_gather_points(const double *xy, const int *perm, int64_t n, double s, int n_os,
+                                 int window_lo, int n_a, int m, int cell, double2 *pos, void *frac, int *base,
+                                 float2 *pos32, cudaStream_t st);
+template <typename real>
+cudaError_t launch_gather_charges(const void *q, int q_is_f64, const int *perm, int64_t M, int nrhs,
+                                  real *q_sorted, double *q_sum, cudaStream_t st);
+cudaError_t launch_near_count(const double2 *tgt_pos, const int *tgt_base, int64_t N,
+                              const double2 *src_pos, const int *src_start, CellGrid cg, double eps2,
+                              double close2, unsigned long long *counts, cudaStream_t st);
+
+// ---- spreading / interpolation (kernels_spread.cu)
+template <typename real>
+cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
+                          const void *frac, const real *q, Window<real> w, real *grid, int pitch,
+                          int n_a, bool kahan, cudaStream_t st);
+template <typename real>
+cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w,
+                          const real *grid, int pitch, real n_os, real *phi_s, real *grad_s,
+                          cudaStream_t st);
+
+// ---- FFT and spectral multiply (kernels_fft.cu)
+template <typename real>
+cudaError_t launch_fft_rows_fwd(const real *grid, int pitch, int n_a, int L, int n_half,
+                                typename Cplx<real>::type *spec, int ld, const typename Cplx<real>::type *tw,
+                                cudaStream_t st);
+template <typename real>
+cudaError_t launch_fft_cols(typename Cplx<real>::type *spec, int ld, int n_a, int L, int n,
+                            const real *mul, const typename Cplx<real>::type *tw, cudaStream_t st);
+template <typename real>
+cudaError_t launch_fft_rows_inv(const typename Cplx<real>::type *spec, int ld, int n_a, int L, int n_half,
+                                real *grid, int pitch, const typename Cplx<real>::type *tw, cudaStream_t st);
+cudaError_t launch_kernel_samples(double2 *samp, int n, KernelParams kp, cudaStream_t st);
+cudaError_t launch_fft_lines_c64(double2 *data, int lines, int L, const double2 *tw, cudaStream_t st);
+cudaError_t launch_transpose_c64(const double2 *in, double2 *out, int n, cudaStream_t st);
+template <typename real>
+cudaError_t launch_build_mul(const double2 *bhat, int n, const double *c_tab, real *mul, cudaStream_t st);
+
+// ---- near field and output (kernels_near.cu)
+template <typename real>
+cudaError_t launch_near(int64_t N, const int *tgt_base, const double2 *tgt_pos, const float2 *tgt_pos32,
+                        const double2 *src_pos, const float2 *src_pos32, const int *src_start, CellGrid cg,
+                        const real *q, NearParams<real> np, real *phi_s, real *grad_s, real *coinc,
+                        cudaStream_t st);
+template <typename real>
+cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, const real *coinc,
+                             const int *perm, double shift, const double *q_sum, double s, void *phi_out,
+                             void *H_out, int out_is_f64, cudaStream_t st);
+
+// ---- FEM charge assembly (kernels_fem.cu)
+cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
+                               int64_t Ne, double2 *src, cudaStream_t st);
+cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
+                               int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, double *q,
+                               int64_t M, cudaStream_t st);
+
+}  // namespace fs

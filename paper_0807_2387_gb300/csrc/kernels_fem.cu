@@ -1,0 +1,104 @@
+// FEM magnetic-charge assembly (step a): the quadrature of Eq. (2).
+//
+// With M linear in each P1 triangle T (nodes a, b, c), rho = -div M is constant
+// on T:  rho_T = -(M_a . grad la_a + M_b . grad la_b + M_c . grad la_c), where
+// grad la_a = (y_b - y_c, x_c - x_b) / (2A) (A the signed area, cyclic in a,b,c).
+// Three interior points at barycentric (2/3, 1/6, 1/6) and permutations carry
+// q = rho_T |T| / 3 each (omega det J = |T|/3).  Each boundary edge e (used by one
+// triangle; endpoints lo < hi; `third` the owner's remaining node) carries two
+// Gauss-Legendre points t = 1/2 -+ 1/(2 sqrt 3) measured from lo, with
+// q = (M(t) . n_e) |e| / 2, n_e the outward unit normal (pointing away from
+// `third`) and M(t) = (1-t) M_lo + t M_hi.
+//
+// Source order: 3 per triangle (triangle-major), then 2 per boundary edge.
+#include "internal.h"
+
+namespace fs {
+
+namespace {
+
+constexpr double kGaussLo = 0.5 - 0.28867513459481288225457439025097873;   // 1/2 - 1/(2 sqrt 3)
+constexpr double kGaussHi = 0.5 + 0.28867513459481288225457439025097873;
+
+__global__ void k_fem_sources(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
+                              const int *__restrict__ bedges, int64_t Ne, double2 *__restrict__ src)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < Nt) {
+        const double2 pa = nodes[tris[3 * i]], pb = nodes[tris[3 * i + 1]], pc = nodes[tris[3 * i + 2]];
+        const double big = 2.0 / 3.0, small = 1.0 / 6.0;
+        src[3 * i] = make_double2(big * pa.x + small * pb.x + small * pc.x, big * pa.y + small * pb.y + small * pc.y);
+        src[3 * i + 1] = make_double2(small * pa.x + big * pb.x + small * pc.x, small * pa.y + big * pb.y + small * pc.y);
+        src[3 * i + 2] = make_double2(small * pa.x + small * pb.x + big * pc.x, small * pa.y + small * pb.y + big * pc.y);
+    } else if (i < Nt + Ne) {
+        const int64_t e = i - Nt;
+        const double2 p0 = nodes[bedges[3 * e]], p1 = nodes[bedges[3 * e + 1]];
+        const int64_t o = 3 * Nt + 2 * e;
+        src[o] = make_double2(p0.x + kGaussLo * (p1.x - p0.x), p0.y + kGaussLo * (p1.y - p0.y));
+        src[o + 1] = make_double2(p0.x + kGaussHi * (p1.x - p0.x), p0.y + kGaussHi * (p1.y - p0.y));
+    }
+}
+
+__global__ void k_fem_charges(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
+                              const int *__restrict__ bedges, int64_t Ne, const double2 *__restrict__ mag, int64_t Nv,
+                              double *__restrict__ q, int64_t M)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    const double2 *mg = mag + (int64_t)r * Nv;
+    double *qr = q + (int64_t)r * M;
+    if (i < Nt) {
+        const int ia = tris[3 * i], ib = tris[3 * i + 1], ic = tris[3 * i + 2];
+        const double2 pa = nodes[ia], pb = nodes[ib], pc = nodes[ic];
+        const double two_a = (pb.x - pa.x) * (pc.y - pa.y) - (pb.y - pa.y) * (pc.x - pa.x);
+        const double2 ma = mg[ia], mb = mg[ib], mc = mg[ic];
+        // sum_k M_k . (rotated opposite edge), divided by 2A
+        const double div = (ma.x * (pb.y - pc.y) + ma.y * (pc.x - pb.x) + mb.x * (pc.y - pa.y) + mb.y * (pa.x - pc.x) +
+                            mc.x * (pa.y - pb.y) + mc.y * (pb.x - pa.x)) / two_a;
+        const double qt = -div * fabs(two_a) / 6.0;
+        qr[3 * i] = qt;
+        qr[3 * i + 1] = qt;
+        qr[3 * i + 2] = qt;
+    } else if (i < Nt + Ne) {
+        const int64_t e = i - Nt;
+        const int i0 = bedges[3 * e], i1 = bedges[3 * e + 1], i3 = bedges[3 * e + 2];
+        const double2 p0 = nodes[i0], p1 = nodes[i1], p3 = nodes[i3];
+        const double tx = p1.x - p0.x, ty = p1.y - p0.y;
+        const double len = sqrt(tx * tx + ty * ty);
+        double nx = ty / len, ny = -tx / len;
+        if (nx * (p3.x - p0.x) + ny * (p3.y - p0.y) > 0.0) {
+            nx = -nx;
+            ny = -ny;
+        }
+        const double2 m0 = mg[i0], m1 = mg[i1];
+        const int64_t o = 3 * Nt + 2 * e;
+        const double tl = kGaussLo, th = kGaussHi;
+        qr[o] = (((1.0 - tl) * m0.x + tl * m1.x) * nx + ((1.0 - tl) * m0.y + tl * m1.y) * ny) * len * 0.5;
+        qr[o + 1] = (((1.0 - th) * m0.x + th * m1.x) * nx + ((1.0 - th) * m0.y + th * m1.y) * ny) * len * 0.5;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges, int64_t Ne,
+                               double2 *src, cudaStream_t st)
+{
+    const int64_t n = Nt + Ne;
+    if (n <= 0)
+        return cudaSuccess;
+    k_fem_sources<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nodes, tris, Nt, bedges, Ne, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges, int64_t Ne,
+                               const double2 *mag, int64_t Nv, int nrhs, double *q, int64_t M, cudaStream_t st)
+{
+    const int64_t n = Nt + Ne;
+    if (n <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)((n + 255) / 256), nrhs);
+    k_fem_charges<<<grid, 256, 0, st>>>(nodes, tris, Nt, bedges, Ne, mag, Nv, q, M);
+    return cudaGetLastError();
+}
+
+}  // namespace fs

@@ -1,0 +1,410 @@
+// Oversampled 2D FFT (steps d), diagonal multiply with deconvolution (step e),
+// and the FP64 Fourier coefficients b_l of the regularised kernel.
+//
+// The paper: "perform ... a FFT on the X grid", "divide these numbers by the
+// Fourier coefficients of the Gaussian", and the smoothing of G near the
+// origin whose coefficients enter the product.  The grid is real and only
+// the frequencies l in I_n = {-n/2..n/2-1}^2 are kept, so the transform is
+//   rows:    two real rows per complex Stockham FFT of length L = n_os,
+//            keeping bins l1 = 0..n/2 (half spectrum, stored column-major);
+//   columns: one CTA per kept l1: forward FFT, multiply by the table
+//            mul[l1][l2] (b_l / (c(l1)^2 c(l2)^2) with the weights that make
+//            the real part of the sum over I_n exact), inverse FFT - no HBM
+//            round trip between the two;
+//   rows:    Hermitian-extended inverse, two real rows per complex FFT.
+// Only the active window of n_a rows/columns that hold points is read or
+// written; the rest of the L x L grid is known to be zero and is never stored.
+//
+// Each 1D transform is a Stockham autosort FFT in shared memory: radix-4
+// passes (radix 2 for the last when log2 L is odd), ping-pong buffers, one
+// __syncthreads per pass, twiddles from a table of exp(-2 pi i t / L).
+#include "internal.h"
+
+namespace fs {
+
+namespace {
+
+template <typename real> using cplx = typename Cplx<real>::type;
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+// In-place (via ping-pong) FFT of one line of length L held in shared memory.
+// Returns the buffer holding the result (a or b).  All threads of the block take part.
+template <typename real, bool INV>
+__device__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<real> *__restrict__ tw)
+{
+    cplx<real> *src = a, *dst = b;
+    for (int Ns = 1; Ns < L;) {
+        const int R = ((L / Ns) % 4 == 0) ? 4 : 2;
+        const int nb = L / R;
+        const int tstep = L / (Ns * R);
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            const int k = j & (Ns - 1);
+            const int idx = (j - k) * R + k;
+            if (R == 4) {
+                cplx<real> v0 = src[j], v1 = src[j + nb], v2 = src[j + 2 * nb], v3 = src[j + 3 * nb];
+                if (k) {
+                    cplx<real> t1 = tw[k * tstep], t2 = tw[2 * k * tstep], t3 = tw[3 * k * tstep];
+                    if (INV) { t1.y = -t1.y; t2.y = -t2.y; t3.y = -t3.y; }
+                    v1 = cmul(v1, t1);
+                    v2 = cmul(v2, t2);
+                    v3 = cmul(v3, t3);
+                }
+                const cplx<real> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3);
+                cplx<real> a3 = csub(v1, v3);
+                // forward multiplies (v1 - v3) by -i, inverse by +i
+                cplx<real> r3;
+                if (INV) { r3.x = -a3.y; r3.y = a3.x; } else { r3.x = a3.y; r3.y = -a3.x; }
+                dst[idx] = cadd(a0, a2);
+                dst[idx + Ns] = cadd(a1, r3);
+                dst[idx + 2 * Ns] = csub(a0, a2);
+                dst[idx + 3 * Ns] = csub(a1, r3);
+            } else {
+                cplx<real> v0 = src[j], v1 = src[j + nb];
+                if (k) {
+                    cplx<real> t1 = tw[k * tstep];
+                    if (INV) t1.y = -t1.y;
+                    v1 = cmul(v1, t1);
+                }
+                dst[idx] = cadd(v0, v1);
+                dst[idx + Ns] = csub(v0, v1);
+            }
+        }
+        __syncthreads();
+        cplx<real> *t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+// Two real rows (r, r+1) of the window -> half spectra, bins 0..n_half, written to spec[l1 * ld + r].
+template <typename real>
+__global__ void k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a, int L, int n_half,
+                               cplx<real> *__restrict__ spec, int ld, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    cplx<real> *b = a + L;
+    const int r = 2 * blockIdx.x;
+    const bool has2 = r + 1 < n_a;
+    for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        cplx<real> z;
+        z.x = c < n_a ? grid[(int64_t)r * pitch + c] : real(0);
+        z.y = (c < n_a && has2) ? grid[(int64_t)(r + 1) * pitch + c] : real(0);
+        a[c] = z;
+    }
+    __syncthreads();
+    const cplx<real> *Z = fft_line<real, false>(a, b, L, tw);
+    for (int k = threadIdx.x; k <= n_half; k += blockDim.x) {
+        const cplx<real> zk = Z[k];
+        const cplx<real> zc = Z[(L - k) & (L - 1)];
+        cplx<real> X, Y;
+        // X = (Z_k + conj Z_{-k}) / 2,  Y = (Z_k - conj Z_{-k}) / (2i)
+        X.x = real(0.5) * (zk.x + zc.x);
+        X.y = real(0.5) * (zk.y - zc.y);
+        Y.x = real(0.5) * (zk.y + zc.y);
+        Y.y = real(-0.5) * (zk.x - zc.x);
+        spec[(int64_t)k * ld + r] = X;
+        if (has2)
+            spec[(int64_t)k * ld + r + 1] = Y;
+    }
+}
+
+// Column l1 = blockIdx.x: forward FFT over rows, multiply, inverse FFT, keep the window rows.
+template <typename real>
+__global__ void k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
+                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    cplx<real> *b = a + L;
+    const int l1 = blockIdx.x;
+    cplx<real> *col = spec + (int64_t)l1 * ld;
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        cplx<real> v;
+        if (r < n_a) {
+            v = col[r];
+        } else {
+            v.x = real(0);
+            v.y = real(0);
+        }
+        a[r] = v;
+    }
+    __syncthreads();
+    cplx<real> *F = fft_line<real, false>(a, b, L, tw);
+    cplx<real> *other = (F == a) ? b : a;
+    const real *mrow = mul + (int64_t)l1 * (n + 1);
+    const int h = n / 2;
+    for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x) {
+        const int l2 = k2 < L / 2 ? k2 : k2 - L;
+        cplx<real> v = F[k2];
+        if (l2 >= -h && l2 <= h) {
+            const real f = mrow[l2 + h];
+            v.x *= f;
+            v.y *= f;
+        } else {
+            v.x = real(0);
+            v.y = real(0);
+        }
+        F[k2] = v;
+    }
+    __syncthreads();
+    const cplx<real> *G = fft_line<real, true>(F, other, L, tw);
+    for (int r = threadIdx.x; r < n_a; r += blockDim.x)
+        col[r] = G[r];
+}
+
+// Hermitian-extended inverse of two rows (r, r+1): real outputs on the window columns.
+template <typename real>
+__global__ void k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n_half,
+                               real *__restrict__ grid, int pitch, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    cplx<real> *b = a + L;
+    const int r = 2 * blockIdx.x;
+    const bool has2 = r + 1 < n_a;
+    for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        cplx<real> X, Y;
+        X.x = X.y = Y.x = Y.y = real(0);
+        if (c <= n_half) {
+            X = spec[(int64_t)c * ld + r];
+            if (has2)
+                Y = spec[(int64_t)c * ld + r + 1];
+            if (c == 0) {
+                X.y = real(0);
+                Y.y = real(0);
+            }
+        } else if (c >= L - n_half) {
+            X = spec[(int64_t)(L - c) * ld + r];
+            X.y = -X.y;
+            if (has2) {
+                Y = spec[(int64_t)(L - c) * ld + r + 1];
+                Y.y = -Y.y;
+            }
+        }
+        cplx<real> z;   // X + i Y
+        z.x = X.x - Y.y;
+        z.y = X.y + Y.x;
+        a[c] = z;
+    }
+    __syncthreads();
+    const cplx<real> *Z = fft_line<real, true>(a, b, L, tw);
+    for (int c = threadIdx.x; c < n_a; c += blockDim.x) {
+        grid[(int64_t)r * pitch + c] = Z[c].x;
+        if (has2)
+            grid[(int64_t)(r + 1) * pitch + c] = Z[c].y;
+    }
+}
+
+// ---- FP64 coefficients b_l
+
+__device__ double kr_sample(double r, const KernelParams &kp)
+{
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    if (r < kp.eps_I) {
+        const double u2 = (r / kp.eps_I) * (r / kp.eps_I);
+        double acc = 0.0;
+        for (int k = kp.p - 1; k >= 0; --k)
+            acc = acc * u2 + kp.beta[k];
+        return acc;
+    }
+    if (r <= 0.5 - kp.eps_B)
+        return -log(r) * inv2pi;
+    if (r <= 0.5) {
+        // two-point Taylor form on v in [0, 1]:
+        //   sum_j f0_j v^j (1-v)^p S_{p-1-j}(v) + k(1/2) v^p S_{p-1}(1-v),  S_k(x) = sum_{i<=k} C(p-1+i,i) x^i
+        const int p = kp.p;
+        const double v = (r - (0.5 - kp.eps_B)) / kp.eps_B;
+        const double w = 1.0 - v;
+        double wp = 1.0, vp = 1.0;
+        for (int i = 0; i < p; ++i) {
+            wp *= w;
+            vp *= v;
+        }
+        double total = 0.0, vj = 1.0;
+        for (int j = 0; j < p; ++j) {
+            double sk = 0.0;
+            for (int i = p - 1 - j; i >= 0; --i)
+                sk = sk * v + kp.tb_binom[i];
+            total += kp.tb_f0[j] * vj * wp * sk;
+            vj *= v;
+        }
+        double sr = 0.0;
+        for (int i = p - 1; i >= 0; --i)
+            sr = sr * w + kp.tb_binom[i];
+        return total + kp.k_half * vp * sr;
+    }
+    return kp.k_half;
+}
+
+__global__ void k_kernel_samples(double2 *__restrict__ samp, int n, KernelParams kp)
+{
+    const int j2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j1 = blockIdx.y;
+    if (j2 >= n)
+        return;
+    const int s1 = j1 < n / 2 ? j1 : j1 - n;
+    const int s2 = j2 < n / 2 ? j2 : j2 - n;
+    const double x1 = (double)s1 / n, x2 = (double)s2 / n;
+    samp[(int64_t)j1 * n + j2] = make_double2(kr_sample(sqrt(x1 * x1 + x2 * x2), kp), 0.0);
+}
+
+__global__ void k_fft_lines_c64(double2 *__restrict__ data, int L, const double2 *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    double2 *a = reinterpret_cast<double2 *>(smem_raw);
+    double2 *b = a + L;
+    double2 *line = data + (int64_t)blockIdx.x * L;
+    for (int c = threadIdx.x; c < L; c += blockDim.x)
+        a[c] = line[c];
+    __syncthreads();
+    const double2 *Z = fft_line<double, false>(a, b, L, tw);
+    for (int c = threadIdx.x; c < L; c += blockDim.x)
+        line[c] = Z[c];
+}
+
+__global__ void k_transpose_c64(const double2 *__restrict__ in, double2 *__restrict__ out, int n)
+{
+    __shared__ double2 tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = by + i, c = bx + threadIdx.x;
+        if (r < n && c < n)
+            tile[i][threadIdx.x] = in[(int64_t)r * n + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = bx + i, c = by + threadIdx.x;
+        if (r < n && c < n)
+            out[(int64_t)r * n + c] = tile[threadIdx.x][i];
+    }
+}
+
+// mul[l1][l2 + n/2] for l1 in [0, n/2], l2 in [-n/2, n/2].  bhat is the transposed
+// unnormalised n x n DFT of the K_R samples: bhat[l2 * n + l1] = n^2 b_(l1,l2).
+// c_tab[l] = c(l), l = 0..n/2 (even in l).  Weights: for l1 < n/2 the symmetric
+// half weight at l2 = +-n/2; for l1 = n/2 the set -I_n in l2 with the factor 1/2
+// that undoes the row inverse's Hermitian doubling.
+template <typename real>
+__global__ void k_build_mul(const double2 *__restrict__ bhat, int n, const double *__restrict__ c_tab,
+                            real *__restrict__ mul)
+{
+    const int h = n / 2;
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;   // l2 + h
+    const int l1 = blockIdx.y;
+    if (i2 > n)
+        return;
+    const int l2 = i2 - h;
+    const int m1 = l1 % n, m2 = ((l2 % n) + n) % n;
+    const double b = bhat[(int64_t)m2 * n + m1].x / ((double)n * (double)n);
+    const double c1 = c_tab[l1], c2 = c_tab[l2 < 0 ? -l2 : l2];
+    double wgt;
+    if (l1 < h)
+        wgt = (l2 == h || l2 == -h) ? 0.5 : 1.0;
+    else
+        wgt = (l2 == -h) ? 0.0 : 0.5;
+    mul[(int64_t)l1 * (n + 1) + i2] = (real)(wgt * b / (c1 * c1 * c2 * c2));
+}
+
+template <typename real> inline int fft_threads(int L)
+{
+    int t = L / 4;
+    if (t > 256) t = 256;
+    if (t < 32) t = 32;
+    return t;
+}
+
+template <typename K> cudaError_t set_smem(K kern, size_t bytes)
+{
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <typename real>
+cudaError_t launch_fft_rows_fwd(const real *grid, int pitch, int n_a, int L, int n_half, cplx<real> *spec, int ld,
+                                const cplx<real> *tw, cudaStream_t st)
+{
+    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    cudaError_t e = set_smem(k_fft_rows_fwd<real>, smem);
+    if (e != cudaSuccess)
+        return e;
+    k_fft_rows_fwd<real><<<(n_a + 1) / 2, fft_threads<real>(L), smem, st>>>(grid, pitch, n_a, L, n_half, spec, ld,
+                                                                            tw);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_fft_cols(cplx<real> *spec, int ld, int n_a, int L, int n, const real *mul, const cplx<real> *tw,
+                            cudaStream_t st)
+{
+    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    cudaError_t e = set_smem(k_fft_cols<real>, smem);
+    if (e != cudaSuccess)
+        return e;
+    k_fft_cols<real><<<n / 2 + 1, fft_threads<real>(L), smem, st>>>(spec, ld, n_a, L, n, mul, tw);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_fft_rows_inv(const cplx<real> *spec, int ld, int n_a, int L, int n_half, real *grid, int pitch,
+                                const cplx<real> *tw, cudaStream_t st)
+{
+    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    cudaError_t e = set_smem(k_fft_rows_inv<real>, smem);
+    if (e != cudaSuccess)
+        return e;
+    k_fft_rows_inv<real><<<(n_a + 1) / 2, fft_threads<real>(L), smem, st>>>(spec, ld, n_a, L, n_half, grid, pitch,
+                                                                            tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kernel_samples(double2 *samp, int n, KernelParams kp, cudaStream_t st)
+{
+    dim3 grid((n + 127) / 128, n);
+    k_kernel_samples<<<grid, 128, 0, st>>>(samp, n, kp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_lines_c64(double2 *data, int lines, int L, const double2 *tw, cudaStream_t st)
+{
+    const size_t smem = 2 * (size_t)L * sizeof(double2);
+    cudaError_t e = set_smem(k_fft_lines_c64, smem);
+    if (e != cudaSuccess)
+        return e;
+    k_fft_lines_c64<<<lines, fft_threads<double>(L), smem, st>>>(data, L, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_c64(const double2 *in, double2 *out, int n, cudaStream_t st)
+{
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    k_transpose_c64<<<grid, block, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_build_mul(const double2 *bhat, int n, const double *c_tab, real *mul, cudaStream_t st)
+{
+    dim3 grid((n + 1 + 127) / 128, n / 2 + 1);
+    k_build_mul<real><<<grid, 128, 0, st>>>(bhat, n, c_tab, mul);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fft_rows_fwd<float>(const float *, int, int, int, int, float2 *, int, const float2 *,
+                                                cudaStream_t);
+template cudaError_t launch_fft_rows_fwd<double>(const double *, int, int, int, int, double2 *, int, const double2 *,
+                                                 cudaStream_t);
+template cudaError_t launch_fft_cols<float>(float2 *, int, int, int, int, const float *, const float2 *, cudaStream_t);
+template cudaError_t launch_fft_cols<double>(double2 *, int, int, int, int, const double *, const double2 *,
+                                             cudaStream_t);
+template cudaError_t launch_fft_rows_inv<float>(const float2 *, int, int, int, int, float *, int, const float2 *,
+                                                cudaStream_t);
+template cudaError_t launch_fft_rows_inv<double>(const double2 *, int, int, int, int, double *, int, const double2 *,
+                                                 cudaStream_t);
+template cudaError_t launch_build_mul<float>(const double2 *, int, const double *, float *, cudaStream_t);
+template cudaError_t launch_build_mul<double>(const double2 *, int, const double *, double *, cudaStream_t);
+
+}  // namespace fs

@@ -1,0 +1,204 @@
+// Window spreading (step c) and interpolation (step f) on the oversampled grid.
+//
+// Spreading is the paper's "let the data diffuse to the X nodes through
+// convolution with a ... smooth localized function":
+//     g_k = sum_j q_j psi(k_1 - u_j1) psi(k_2 - u_j2),
+// over the 2m x 2m grid lines k with |k - u_j| < m.  Interpolation reads the
+// same stencil back: phi(x_i) = sum_k g'_k psi(u_i1 - k_1) psi(u_i2 - k_2), and
+// the gradient uses the analytic window slope psi'.
+//
+// Spreading: one CTA per work item (a tile of cells, or a slice of a crowded
+// tile).  It accumulates into a padded shared-memory tile with shared atomics;
+// in FP32 each addition's rounding error is recovered exactly (TwoSum on the
+// value the atomic returns) into a second, compensation tile, so the tile
+// holds a double-FP32 sum.  The padded tile is then added to the grid with
+// global atomics (tiles overlap by 2m-1 lines).
+#include "internal.h"
+
+namespace fs {
+
+namespace {
+
+template <typename real> using real2_t = typename Cplx<real>::type;
+
+template <typename real, int M2, bool KAHAN>
+__global__ void __launch_bounds__(256) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
+                                                const int *__restrict__ base, const real2_t<real> *__restrict__ frac,
+                                                const real *__restrict__ q, Window<real> w, real *__restrict__ grid,
+                                                int pitch, int n_a)
+{
+    constexpr int m = M2 / 2;
+    extern __shared__ unsigned char smem_raw[];
+    real *acc = reinterpret_cast<real *>(smem_raw);
+    const int TG = cg.T * cg.cell;
+    const int P = TG + M2 - 1;
+    real *comp = acc + P * P;
+    const SpreadItem it = items[blockIdx.x];
+    const int t1 = it.tile / cg.n_t, t2 = it.tile - (it.tile / cg.n_t) * cg.n_t;
+    const int o1 = t1 * TG - (m - 1), o2 = t2 * TG - (m - 1);
+    for (int i = threadIdx.x; i < P * P * (KAHAN ? 2 : 1); i += blockDim.x)
+        acc[i] = real(0);
+    __syncthreads();
+    for (int j = it.start + threadIdx.x; j < it.start + it.count; j += blockDim.x) {
+        const int packed = base[j];
+        const real2_t<real> f = frac[j];
+        const real qj = q[j];
+        real w1[M2], w2[M2];
+#pragma unroll
+        for (int a = 0; a < M2; ++a) {
+            w1[a] = kb_value<real>(w, f.x + real(m - 1 - a));
+            w2[a] = kb_value<real>(w, f.y + real(m - 1 - a)) * qj;
+        }
+        const int row0 = base1(packed) - m + 1 - o1;
+        const int col0 = base2(packed) - m + 1 - o2;
+#pragma unroll
+        for (int a = 0; a < M2; ++a) {
+            real *rowp = acc + (row0 + a) * P + col0;
+#pragma unroll
+            for (int b = 0; b < M2; ++b) {
+                const real v = w1[a] * w2[b];
+                if (KAHAN) {
+                    const real old = atomicAdd(rowp + b, v);
+                    const real s = old + v;
+                    const real bb = s - old;
+                    const real err = (old - (s - bb)) + (v - bb);
+                    atomicAdd(rowp + b + P * P, err);
+                } else {
+                    atomicAdd(rowp + b, v);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, c = i - (i / P) * P;
+        const real v = KAHAN ? acc[i] + comp[i] : acc[i];
+        const int g1 = o1 + r, g2 = o2 + c;
+        if (v != real(0) && g1 >= 0 && g1 < n_a && g2 >= 0 && g2 < n_a)
+            atomicAdd(grid + (int64_t)g1 * pitch + g2, v);
+    }
+}
+
+template <typename real, int M2>
+__global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict__ base,
+                                                const real2_t<real> *__restrict__ frac, Window<real> w,
+                                                const real *__restrict__ grid, int pitch, real n_os,
+                                                real *__restrict__ phi_s, real *__restrict__ grad_s)
+{
+    constexpr int m = M2 / 2;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N)
+        return;
+    const int packed = base[k];
+    const real2_t<real> f = frac[k];
+    real w1[M2], d1[M2], w2[M2], d2[M2];
+#pragma unroll
+    for (int a = 0; a < M2; ++a) {
+        kb_value_slope<real>(w, f.x + real(m - 1 - a), w1[a], d1[a]);
+        kb_value_slope<real>(w, f.y + real(m - 1 - a), w2[a], d2[a]);
+    }
+    const int row0 = base1(packed) - m + 1;
+    const int col0 = base2(packed) - m + 1;
+    real phi = 0, g1 = 0, g2 = 0;
+#pragma unroll
+    for (int a = 0; a < M2; ++a) {
+        const real *rowp = grid + (int64_t)(row0 + a) * pitch + col0;
+        real rs = 0, rd = 0;
+#pragma unroll
+        for (int b = 0; b < M2; ++b) {
+            const real gv = __ldg(rowp + b);
+            rs += w2[b] * gv;
+            rd += d2[b] * gv;
+        }
+        phi += w1[a] * rs;
+        g1 += d1[a] * rs;
+        g2 += w1[a] * rd;
+    }
+    phi_s[k] = phi;
+    grad_s[2 * k] = n_os * g1;
+    grad_s[2 * k + 1] = n_os * g2;
+}
+
+template <typename real, int M2>
+cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const int *base, const void *frac,
+                     const real *q, Window<real> w, real *grid, int pitch, int n_a, bool kahan, cudaStream_t st)
+{
+    const int TG = cg.T * cg.cell;
+    const int P = TG + M2 - 1;
+    const size_t smem = (size_t)P * P * sizeof(real) * (kahan ? 2 : 1);
+    const real2_t<real> *fr = (const real2_t<real> *)frac;
+    if (kahan) {
+        auto kern = k_spread<real, M2, true>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        kern<<<n_items, 256, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
+    } else {
+        auto kern = k_spread<real, M2, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        kern<<<n_items, 256, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename real, int M2>
+cudaError_t interp_m(int64_t N, const int *base, const void *frac, Window<real> w, const real *grid, int pitch,
+                     real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    k_interp<real, M2><<<blocks, 256, 0, st>>>(N, base, (const real2_t<real> *)frac, w, grid, pitch, n_os, phi_s,
+                                                grad_s);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename real>
+cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base, const void *frac,
+                          const real *q, Window<real> w, real *grid, int pitch, int n_a, bool kahan, cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    const bool comp = kahan && sizeof(real) == 4;
+    switch (m) {
+    case 2: return spread_m<real, 4>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 3: return spread_m<real, 6>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 4: return spread_m<real, 8>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 5: return spread_m<real, 10>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 6: return spread_m<real, 12>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 7: return spread_m<real, 14>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 8: return spread_m<real, 16>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename real>
+cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w, const real *grid,
+                          int pitch, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+{
+    if (N <= 0)
+        return cudaSuccess;
+    switch (m) {
+    case 2: return interp_m<real, 4>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 3: return interp_m<real, 6>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 4: return interp_m<real, 8>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 5: return interp_m<real, 10>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 6: return interp_m<real, 12>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 7: return interp_m<real, 14>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 8: return interp_m<real, 16>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_spread<float>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
+                                          const float *, Window<float>, float *, int, int, bool, cudaStream_t);
+template cudaError_t launch_spread<double>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
+                                           const double *, Window<double>, double *, int, int, bool, cudaStream_t);
+template cudaError_t launch_interp<float>(int64_t, int, const int *, const void *, Window<float>, const float *, int,
+                                          float, float *, float *, cudaStream_t);
+template cudaError_t launch_interp<double>(int64_t, int, const int *, const void *, Window<double>, const double *,
+                                           int, double, double *, double *, cudaStream_t);
+
+}  // namespace fs

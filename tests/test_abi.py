@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every entry point include/*.h declares (no GPU needed)."""
+
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fs_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0807_2387_gb300 import build
+    build.build()
+    import paper_0807_2387_gb300 as pkg
+    return pkg.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_eval_potential", "fs_eval_field",
+              "fs_plan_destroy", "fs_last_error"):
+        assert n in names, n
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), f"libfemnfft.so does not export {name}"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_0807_2387_gb300 import _native
+    import paper_0807_2387_gb300 as pkg
+    for name in _declared():
+        assert name in _native.EXPORTED, name
+        if name not in ("fs_last_error", "fs_version"):
+            assert hasattr(pkg, name), f"python binding lacks {name}"
+
+
+def test_version_and_error_string_without_gpu(lib):
+    assert b"sm_103a" in lib.fs_version()
+    assert isinstance(lib.fs_last_error(), bytes)
+
+
+def test_library_is_sm103a_only():
+    from paper_0807_2387_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_0807_2387_gb300 import _native
+    saved = _native._lib
+    try:
+        _native._lib = None
+        with pytest.raises(_native.NativeLibraryMissing):
+            _native.load(str(tmp_path / "absent.so"))
+    finally:
+        _native._lib = saved
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg_dir = os.path.join(ROOT, "paper_0807_2387_gb300")
+    for path in glob.glob(os.path.join(pkg_dir, "**", "*.py"), recursive=True) + \
+            glob.glob(os.path.join(pkg_dir, "csrc", "*")):
+        text = open(path, errors="replace").read()
+        assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), path

@@ -1,0 +1,336 @@
+"""GPU parity: the CUDA fast summation (through the C ABI) against the CPU oracle.
+
+Tolerances:
+* FP64 path vs oracle O3 (same algorithm, FP64): relative L2 <= 1e-12 for phi
+  and for H separately; only the rounding order differs (FFT factorisation,
+  atomic accumulation order, transcendental implementations).
+* FP32 path vs FP64 path: relative L2 <= 1e-5 for phi and H (the metric's bar).
+* FEM charges (kernel a) vs the oracle's assembly: <= 1e-14 relative (FP64,
+  a handful of operations per charge).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_0807_2387_gb300 import build
+    build.build()
+    import paper_0807_2387_gb300 as p
+    p.load()
+    torch.cuda.set_device(0)
+    return p
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def gpu_field(pkg, case, precision, out=torch.float64, q=None, **opts):
+    dev = torch.device("cuda", 0)
+    src = torch.tensor(np.asarray(case["src"]).reshape(-1, 2), device=dev)
+    tgt = torch.tensor(np.asarray(case["tgt"]).reshape(-1, 2), device=dev)
+    qv = torch.tensor(case["q"] if q is None else q, device=dev)
+    fs = pkg.FastSum(src, tgt, case["n"], case["sigma"], case["m"], case["eps_I"], precision=precision, **opts)
+    fs.set_charges(qv)
+    phi, H = fs.field(dtype=out)
+    fs.sync()
+    info = fs.info
+    res = phi.cpu().numpy(), H.cpu().numpy(), info
+    fs.close()
+    return res
+
+
+def oracle_field(case, method="nfft", targets=None, p=None):
+    from oracle import fastsum as F
+    from oracle import kernel as K
+    par = K.make_params(case["n"], case["sigma"], case["m"], case["eps_I"], p)
+    return F.fast_sum(case["src"], case["tgt"], case["q"], par, method, far_only_targets=targets)
+
+
+def test_c0_fp64_matches_oracle(pkg):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.uniform_disc_c0()
+    phi, H, info = gpu_field(pkg, case, 64)
+    phi_o, H_o = oracle_field(case)
+    assert info["p"] == 2 and info["n_os"] == 256
+    assert rel(phi, phi_o) <= 1e-12, rel(phi, phi_o)
+    assert rel(H, H_o) <= 1e-12, rel(H, H_o)
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_c0_fp32_matches_fp64(pkg, flags):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.uniform_disc_c0()
+    phi64, H64, _ = gpu_field(pkg, case, 64)
+    phi32, H32, _ = gpu_field(pkg, case, 32, flags=flags)
+    assert rel(phi32, phi64) <= 1e-5, rel(phi32, phi64)
+    assert rel(H32, H64) <= 1e-5, rel(H32, H64)
+
+
+SMALL = [
+    # seed, n_src, n_tgt, n, m, eps_I
+    (101, 1, 1, 16, 2, 2 / 16),
+    (102, 2, 3, 16, 3, 2 / 16),
+    (103, 37, 53, 32, 4, 2 / 32),
+    (104, 1000, 999, 64, 5, 4 / 64),
+    (105, 3001, 2777, 128, 6, 6 / 128),
+    (106, 2500, 2500, 256, 7, 8 / 256),
+    (107, 2000, 1500, 64, 8, 4 / 64),
+    (108, 4000, 4000, 32, 3, 3 / 32),      # crowded cells: several spreading slices per tile
+]
+
+
+@pytest.mark.parametrize("seed,ns,nt,n,m,eps", SMALL)
+def test_small_cases_fp64(pkg, seed, ns, nt, n, m, eps):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(seed, ns, nt, n=n, m=m, eps_I=eps)
+    phi, H, _ = gpu_field(pkg, case, 64)
+    phi_o, H_o = oracle_field(case)
+    assert rel(phi, phi_o) <= 1e-12, rel(phi, phi_o)
+    assert rel(H, H_o) <= 1e-12, rel(H, H_o)
+
+
+@pytest.mark.parametrize("seed,ns,nt,n,m,eps", SMALL[2:6])
+def test_small_cases_fp32(pkg, seed, ns, nt, n, m, eps):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(seed, ns, nt, n=n, m=m, eps_I=eps)
+    phi, H, _ = gpu_field(pkg, case, 32)
+    phi_o, H_o = oracle_field(case)
+    assert rel(phi, phi_o) <= 2e-5, rel(phi, phi_o)
+    assert rel(H, H_o) <= 2e-5, rel(H, H_o)
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 2e-5)])
+def test_coincident_sources_and_targets(pkg, precision, tol):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(111, 3000, 3000, n=128, m=6, eps_I=6 / 128, coincident=True)
+    phi, H, _ = gpu_field(pkg, case, precision)
+    phi_o, H_o = oracle_field(case)
+    assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))
+
+
+def test_duplicate_points_and_single_cell(pkg):
+    """Many sources piled on a few positions and a target on each: coincident and r < eps_I/8 pairs."""
+    rng = np.random.default_rng(5)
+    base = rng.uniform(-0.05, 0.05, (20, 2))
+    src = np.repeat(base, 30, axis=0) + rng.normal(0, 1e-9, (600, 2)) * (rng.random((600, 1)) < 0.5)
+    case = dict(src=src, tgt=np.concatenate([base, src[:50]]), q=rng.standard_normal(600), n=64, sigma=2.0, m=5,
+                eps_I=4 / 64)
+    for precision, tol in ((64, 1e-12), (32, 2e-5)):
+        phi, H, _ = gpu_field(pkg, case, precision)
+        phi_o, H_o = oracle_field(case)
+        assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (precision, rel(phi, phi_o), rel(H, H_o))
+
+
+def test_empty_sources_and_targets(pkg):
+    dev = torch.device("cuda", 0)
+    tgt = torch.tensor(np.random.default_rng(1).uniform(-0.2, 0.2, (10, 2)), device=dev)
+    src = torch.zeros((0, 2), dtype=torch.float64, device=dev)
+    for precision in (32, 64):
+        fs = pkg.FastSum(src, tgt, 32, 2.0, 4, 2 / 32, precision=precision)
+        fs.set_charges(torch.zeros(0, dtype=torch.float64, device=dev))
+        phi, H = fs.field(dtype=torch.float64)
+        fs.sync()
+        assert torch.count_nonzero(phi).item() == 0 and torch.count_nonzero(H).item() == 0
+        fs.close()
+    fs = pkg.FastSum(tgt, src, 32, 2.0, 4, 2 / 32, precision=64)
+    fs.set_charges(torch.ones(10, dtype=torch.float64, device=dev))
+    phi, H = fs.field(dtype=torch.float64)
+    fs.sync()
+    assert phi.numel() == 0 and H.numel() == 0
+    fs.close()
+
+
+def test_multiple_charge_vectors_and_f32_output(pkg):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(121, 2000, 1800, n=64, m=5, eps_I=4 / 64)
+    rng = np.random.default_rng(3)
+    qs = rng.standard_normal((3, 2000))
+    dev = torch.device("cuda", 0)
+    src = torch.tensor(case["src"], device=dev)
+    tgt = torch.tensor(case["tgt"], device=dev)
+    fs = pkg.FastSum(src, tgt, case["n"], case["sigma"], case["m"], case["eps_I"], precision=64)
+    fs.set_charges(torch.tensor(qs, device=dev))
+    phi, H = fs.field(dtype=torch.float64)
+    phi32, H32 = fs.field(dtype=torch.float32)
+    fs.sync()
+    for r in range(3):
+        c = dict(case, q=qs[r])
+        phi_o, H_o = oracle_field(c)
+        assert rel(phi[r].cpu().numpy(), phi_o) <= 1e-12
+        assert rel(H[r].cpu().numpy(), H_o) <= 1e-12
+        assert rel(phi32[r].cpu().numpy(), phi_o) <= 1e-7
+        assert rel(H32[r].cpu().numpy(), H_o) <= 1e-7
+    fs.close()
+
+
+def test_potential_only_and_float32_charges(pkg):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(131, 1500, 1400, n=64, m=5, eps_I=4 / 64)
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum(torch.tensor(case["src"], device=dev), torch.tensor(case["tgt"], device=dev), case["n"],
+                     case["sigma"], case["m"], case["eps_I"], precision=64)
+    q32 = case["q"].astype(np.float32)
+    fs.set_charges(torch.tensor(q32, device=dev))
+    phi = fs.potential(dtype=torch.float64)
+    fs.sync()
+    phi_o, _ = oracle_field(dict(case, q=q32.astype(np.float64)))
+    assert rel(phi.cpu().numpy(), phi_o) <= 1e-12
+    fs.close()
+
+
+def test_fem_charges_and_sources_match_oracle(pkg):
+    from oracle import fem
+    from paper_0807_2387_gb300 import workloads as W
+    rng = np.random.default_rng(2)
+    nodes, tris = W.ring_mesh(rng, 24)
+    mag = np.stack([W.uniform_magnetisation(nodes), W.vortex_magnetisation(nodes),
+                    rng.standard_normal(nodes.shape)])
+    dev = torch.device("cuda", 0)
+    tn = torch.tensor(nodes, device=dev)
+    tt = torch.tensor(tris, device=dev)
+    fs = pkg.FastSum.fem(tn, tt, 64, 2.0, 5, 4 / 64, precision=64)
+    src = fs.sources().cpu().numpy()
+    src_o = fem.quadrature_points(nodes, tris)
+    assert src.shape == src_o.shape
+    assert np.max(np.abs(src - src_o)) <= 1e-15
+    q = fs.fem_charges(torch.tensor(mag, device=dev)).cpu().numpy()
+    for r in range(3):
+        q_o = fem.assemble_charges(nodes, tris, mag[r])
+        assert np.max(np.abs(q[r] - q_o)) <= 1e-14 * np.max(np.abs(q_o)) + 1e-300
+    assert fs.info["n_bedges"] == 6 * 24 and fs.info["is_fem"] == 1
+    fs.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 2e-5)])
+def test_fem_field_matches_oracle(pkg, precision, tol):
+    from oracle import fastsum as F
+    from oracle import fem
+    from oracle import kernel as K
+    from paper_0807_2387_gb300 import workloads as W
+    rng = np.random.default_rng(2)
+    nodes, tris = W.ring_mesh(rng, 40)
+    mag = W.vortex_magnetisation(nodes) + 0.3 * W.uniform_magnetisation(nodes)
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum.fem(torch.tensor(nodes, device=dev), torch.tensor(tris, device=dev), 128, 2.0, 6, 6 / 128,
+                         precision=precision)
+    fs.set_magnetization(torch.tensor(mag, device=dev))
+    phi, H = fs.field(dtype=torch.float64)
+    fs.sync()
+    src = fem.quadrature_points(nodes, tris)
+    q = fem.assemble_charges(nodes, tris, mag)
+    par = K.make_params(128, 2.0, 6, 6 / 128)
+    phi_o, H_o = F.fast_sum(src, nodes, q, par, "nfft")
+    assert rel(phi.cpu().numpy(), phi_o) <= tol, rel(phi.cpu().numpy(), phi_o)
+    assert rel(H.cpu().numpy(), H_o) <= tol, rel(H.cpu().numpy(), H_o)
+    fs.close()
+
+
+def test_c1_uniform_disk_closed_form(pkg):
+    """Paper's first test case on the 50k-node mesh: phi = x/2 and H = (-1/2, 0) at interior nodes."""
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.mesh_disc_c1()
+    nodes, tris = case["nodes"], case["tris"]
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum.fem(torch.tensor(nodes, device=dev), torch.tensor(tris, device=dev), case["n"], case["sigma"],
+                         case["m"], case["eps_I"], precision=64)
+    fs.set_magnetization(torch.tensor(np.stack([case["M_uniform"], case["M_vortex"]]), device=dev))
+    phi, H = fs.field(dtype=torch.float64)
+    fs.sync()
+    phi, H = phi.cpu().numpy(), H.cpu().numpy()
+    r = np.hypot(nodes[:, 0], nodes[:, 1])
+    inner = r < 1 - 5.0 / 129
+    assert np.max(np.abs(phi[0, inner] - nodes[inner, 0] / 2)) < 1e-6
+    assert np.max(np.abs(H[0, inner] - np.array([-0.5, 0.0]))) < 1e-4
+    err_uniform = np.sqrt(np.mean((phi[0] - nodes[:, 0] / 2) ** 2)) / 2.0   # paper's metric, L = 2
+    err_vortex = np.sqrt(np.mean(phi[1] ** 2)) / 2.0
+    assert err_uniform < 50e-6 and err_vortex < 5e-6, (err_uniform, err_vortex)
+    assert fs.info["n_src"] == 3 * len(tris) + 2 * fs.info["n_bedges"]
+    fs.close()
+
+
+@pytest.fixture(scope="module")
+def c2():
+    from paper_0807_2387_gb300 import workloads as W
+    return W.mixture_c2()
+
+
+def test_c2_fp32_within_1e5_of_fp64(pkg, c2):
+    """The headline configuration: 2^20 sources and targets, FP32 path vs FP64 path."""
+    phi64, H64, info = gpu_field(pkg, c2, 64)
+    phi32, H32, _ = gpu_field(pkg, c2, 32)
+    e_phi, e_H = rel(phi32, phi64), rel(H32, H64)
+    print(f"C2 fp32 vs fp64: phi {e_phi:.2e} H {e_H:.2e}; near pairs {info['near_pairs']}")
+    assert e_phi <= 1e-5 and e_H <= 1e-5
+
+
+def test_c2_fp64_sampled_against_oracle(pkg, c2):
+    phi64, H64, _ = gpu_field(pkg, c2, 64)
+    idx = np.random.default_rng(9).choice(len(c2["tgt"]), 2048, replace=False)
+    phi_o, H_o = oracle_field(c2, targets=idx)
+    assert rel(phi64[idx], phi_o) <= 1e-12, rel(phi64[idx], phi_o)
+    assert rel(H64[idx], H_o) <= 1e-12, rel(H64[idx], H_o)
+    # approximation error against the plain direct sum on a subsample
+    from oracle import direct as D
+    sub = idx[:512]
+    phi_d, H_d = D.direct_sum(c2["tgt"][sub], c2["src"], c2["q"])
+    assert rel(phi64[sub], phi_d) < 1e-7 and rel(H64[sub], H_d) < 1e-5
+
+
+def test_invalid_arguments_return_errors(pkg):
+    dev = torch.device("cuda", 0)
+    pts = torch.tensor(np.random.default_rng(0).uniform(-0.2, 0.2, (10, 2)), device=dev)
+    bad = [
+        dict(n_grid=48, sigma_os=2.0, m_window=4, eps_I=0.05),     # not a power of two
+        dict(n_grid=64, sigma_os=1.0, m_window=4, eps_I=0.05),     # no oversampling
+        dict(n_grid=64, sigma_os=2.0, m_window=9, eps_I=0.05),     # window too wide
+        dict(n_grid=64, sigma_os=2.0, m_window=4, eps_I=0.3),      # eps_I too large
+        dict(n_grid=64, sigma_os=2.0, m_window=4, eps_I=-1.0),
+    ]
+    for kw in bad:
+        with pytest.raises(pkg.FastSumError) as ei:
+            pkg.FastSum(pts, pts, **kw)
+        assert ei.value.status == 1
+    with pytest.raises(pkg.FastSumError):
+        pkg.FastSum(pts, pts, 64, 2.0, 4, 0.05, precision=16)
+    fs = pkg.FastSum(pts, pts, 64, 2.0, 4, 0.05)
+    with pytest.raises(pkg.FastSumError):
+        pkg.fs_eval_field(fs.handle, None, torch.empty((10, 2), device=dev))   # charges not set
+    fs.close()
+
+
+def test_solve_host_matches_device_path(pkg):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(141, 2500, 2400, n=64, m=5, eps_I=4 / 64)
+    phi_d, H_d, _ = gpu_field(pkg, case, 32)
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum(torch.tensor(case["src"], device=dev), torch.tensor(case["tgt"], device=dev), case["n"],
+                     case["sigma"], case["m"], case["eps_I"], precision=32)
+    phi = np.zeros(2400)
+    H = np.zeros((2400, 2))
+    pkg.fs_solve_host(fs.handle, np.ascontiguousarray(case["q"]), phi, H)
+    assert rel(phi, phi_d) <= 1e-6 and rel(H, H_d) <= 1e-6
+    fs.close()
+
+
+def test_stage_times(pkg):
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(151, 5000, 5000, n=128, m=6, eps_I=6 / 128)
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum(torch.tensor(case["src"], device=dev), torch.tensor(case["tgt"], device=dev), case["n"],
+                     case["sigma"], case["m"], case["eps_I"], precision=32, flags=pkg.FS_FLAG_TIMING)
+    fs.set_charges(torch.tensor(case["q"], device=dev))
+    fs.field()
+    t = fs.stage_times()
+    assert len(t) == 8 and all(v >= 0 for v in t.values()) and sum(t.values()) > 0
+    fs.close()
