@@ -1,0 +1,350 @@
+"""Benchmark: FP32 FEM-NFFT fast summation of 2^20 points on one GB300 (per rank).
+
+One step = fs_set_charges + fs_eval_field (phi and H) for the 2^20-source /
+2^20-target Gaussian-mixture workload (n = 1024, oversampled 2048^2, m = 6,
+eps_I = 1/128, p = 8), inputs resident in HBM.  The plan (binning, FP64
+coefficients b_l) is built once, outside the timed region.  L2 is flushed
+(256 MiB write) between timed steps, outside the CUDA-event brackets.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the FP64 direct sum of Eq. (2)) on host cores on a bounded sample of the
+same workload instead.
+
+Multi-GPU (torchrun): every rank solves its own replica of the workload
+(weak scaling, no collective on the data path); the timed region is bracketed
+by a barrier and the time is the maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N=2^20 fast-summation points/s at rel L2 err <=1e-5 vs FP64 path; % HBM peak"
+WORKLOAD = ("mixture_c2: 2^20 sources + 2^20 targets, 8-Gaussian mixture (sd 0.02-0.08) in the r<=0.25 disc, "
+            "charges N(0,1); n=1024 (oversampled 2048^2), m=6, eps_I=1/128, p=8")
+STAGES = ("charges", "spread", "fft_rows_fwd", "fft_cols_mul", "fft_rows_inv", "interp", "near", "unpermute")
+KERNELS_PER_STEP = 8   # gather_charges, spread, 3 FFT kernels, interp, near, unpermute
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(work, targets: int, seed: int = 17):
+    """Oracle O1 (plain FP64 direct sum) on `targets` random targets against all sources."""
+    from oracle import direct as D
+    idx = np.random.default_rng(seed).choice(len(work["tgt"]), targets, replace=False)
+    t0 = time.perf_counter()
+    D.direct_sum(work["tgt"][idx], work["src"], work["q"])
+    dt = time.perf_counter() - t0
+    return {"value": targets / dt, "unit": "points/s", "cores": D.threads(), "kind": "oracle",
+            "sample": f"O1 FP64 direct sum (Eq. 2) at {targets} random targets of the workload against all "
+                      f"{len(work['src'])} sources; {dt:.2f} s"}, dt
+
+
+def algorithmic_bytes(info, n_points):
+    """Minimum HBM bytes per stage per step for the FP32 path (see the design notes)."""
+    n_a = info["window_n"]
+    n = info["n_grid"]
+    L = info["n_os"]
+    M = info["n_src"]
+    N = info["n_tgt"]
+    grid = 4 * n_a * n_a                      # FP32 active window
+    half = 8 * (n // 2 + 1) * n_a             # complex half spectrum over the window rows
+    return {
+        "charges": 8 * M + 4 * M + 4 * M,     # q f64 read, perm read, q f32 write
+        "spread": (4 + 8 + 4) * M + grid,     # base, frac, q read; grid written once
+        "fft_rows_fwd": grid + half,
+        "fft_cols_mul": 2 * half + 4 * (n // 2 + 1) * (n + 1),
+        "fft_rows_inv": half + grid,
+        "interp": grid + (4 + 8) * N + 12 * N,  # grid read once, records, phi/grad write
+        "near": (8 + 4 + 8) * N + (8 + 4) * M + 12 * N + 4 * N,  # positions/q read once, accumulators
+        "unpermute": 16 * N + 4 * N + 12 * N,
+    }
+
+
+def near_flops_per_pair(p):
+    # FP32 near-pair work: difference + r^2 (7), w (1), P(w) Horner (2(p-1)), (w-1)^(p-1) (p-1 + 1),
+    # log and reciprocal (2 MUFU, counted 1 each), value and coefficient (4), three accumulations (6)
+    return 7 + 1 + 2 * (p - 1) + p + 2 + 4 + 6
+
+
+def run_ours(args):
+    import torch
+    import paper_0807_2387_gb300 as pkg
+    from paper_0807_2387_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    work = W.mixture_c2(seed=W.SEEDS["c2"] + rank)
+    src = torch.tensor(work["src"], device=dev)
+    tgt = torch.tensor(work["tgt"], device=dev)
+    q64 = torch.tensor(work["q"], device=dev)
+    stream = torch.cuda.current_stream(dev)
+    fs = pkg.FastSum(src, tgt, work["n"], work["sigma"], work["m"], work["eps_I"], precision=32,
+                     flags=pkg.FS_FLAG_TIMING, stream=stream)
+    info = fs.info
+    n_pts = info["n_tgt"]
+    phi = torch.empty(n_pts, dtype=torch.float32, device=dev)
+    H = torch.empty((n_pts, 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        pkg.fs_set_charges(fs.handle, q64, 1)
+        pkg.fs_eval_field(fs.handle, phi, H)
+
+    for _ in range(args.warmup):
+        step()
+    fs.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = {s: 0.0 for s in STAGES}
+    wall0 = time.perf_counter()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            st = pkg.fs_stage_times(fs.handle)       # synchronises; outside the event bracket
+            for s, v in zip(STAGES, st):
+                stage_ms[s] += v
+        torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    fs.sync()
+    ms_step = total_ms / args.steps
+    value = n_pts * args.steps * world / (total_ms / 1e3)
+    stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+
+    # accuracy of this FP32 run against the FP64 GPU path (untimed)
+    acc = None
+    if not args.quick:
+        fs64 = pkg.FastSum(src, tgt, work["n"], work["sigma"], work["m"], work["eps_I"], precision=64)
+        fs64.set_charges(q64)
+        phi64, H64 = fs64.field(dtype=torch.float64)
+        fs64.sync()
+        e_phi = float(torch.linalg.norm(phi.double() - phi64) / torch.linalg.norm(phi64))
+        e_H = float(torch.linalg.norm(H.double() - H64) / torch.linalg.norm(H64))
+        t64 = []
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fs64.set_charges(q64)
+            fs64.field(dtype=torch.float64)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t64.append(a.elapsed_time(b))
+        fs64.close()
+        acc = {"phi_rel_l2": e_phi, "H_rel_l2": e_H, "fp64_path_points_per_s": n_pts / (min(t64) / 1e3)}
+
+    # end to end through the C ABI from page-locked host memory
+    e2e = None
+    if not args.quick:
+        qh = torch.tensor(work["q"], dtype=torch.float32).pin_memory()
+        ph = torch.empty(n_pts, dtype=torch.float32).pin_memory()
+        Hh = torch.empty((n_pts, 2), dtype=torch.float32).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            pkg.fs_solve_host_ptr(fs.handle, qh.data_ptr(), pkg.FS_F32, 1, ph.data_ptr(), Hh.data_ptr(), pkg.FS_F32)
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            pkg.fs_solve_host_ptr(fs.handle, qh.data_ptr(), pkg.FS_F32, 1, ph.data_ptr(), Hh.data_ptr(), pkg.FS_F32)
+            times.append(time.perf_counter() - t0)
+        e2e = {"value": n_pts * world / statistics.mean(times), "unit": "points/s",
+               "h2d_bytes_per_step": qh.numel() * 4, "d2h_bytes_per_step": (ph.numel() + Hh.numel()) * 4}
+
+    hbm, peak_src = peaks()
+    abytes = algorithmic_bytes(info, n_pts)
+    stages = {}
+    for s in STAGES:
+        t = stage_ms[s]
+        gbs = abytes[s] / (t / 1e3) / 1e9 if t > 0 else None
+        stages[s] = {"ms": round(t, 5), "algorithmic_bytes": abytes[s],
+                     "GB_per_s": round(gbs, 1) if gbs else None,
+                     "frac_hbm": round(gbs / hbm, 4) if gbs else None}
+    dominant = max(STAGES, key=lambda s: stage_ms[s])
+    if dominant == "near":
+        fpp = near_flops_per_pair(info["p"])
+        achieved = info["near_pairs"] * fpp / (stage_ms["near"] / 1e3) / 1e12
+        sm_max = 2070.0
+        peak_alu = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        roof = {"kernel": "k_near<float>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": args.traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "work": f"{info['near_pairs']} pairs x {fpp} flop"}
+    else:
+        t = stage_ms[dominant]
+        achieved = abytes[dominant] / (t / 1e3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": args.traffic, "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.quick and not args.no_cpu:
+        cpu, _ = cpu_baseline(work, args.cpu_targets)
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp32 (Kahan-compensated spreading)",
+                       "global_batch": n_pts * world, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "plan_excluded": True},
+            "roofline": roof, "stages": stages, "accuracy": acc, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "near_pairs": info["near_pairs"], "near_pairs_fp64": info["near_pairs_fp64"],
+            "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src},
+        }
+        print(json.dumps(out))
+    fs.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_0807_2387_gb300 import workloads as W
+    work = W.mixture_c2()
+    targets = args.ref_targets
+    for _ in range(args.warmup):
+        cpu_baseline(work, targets, seed=1)
+    times = []
+    for i in range(args.steps):
+        _, dt = cpu_baseline(work, targets, seed=100 + i)
+        times.append(dt)
+    total = sum(times)
+    value = targets * args.steps / total
+    from oracle import direct as D
+    cpu = {"value": value, "unit": "points/s", "cores": D.threads(), "kind": "oracle",
+           "sample": f"each step: O1 FP64 direct sum (Eq. 2) at {targets} random targets against all "
+                     f"{len(work['src'])} sources of the workload"}
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_targets_per_step": targets}, "cpu_baseline": cpu,
+           "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU baseline (profiling runs)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-targets", type=int, default=32768)
+    ap.add_argument("--ref-targets", type=int, default=64)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.quick:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

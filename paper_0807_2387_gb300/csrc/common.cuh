@@ -30,7 +30,8 @@ enum DeviceError : int { kDevOk = 0, kDevDomain = 2, kDevTimeout = 5 };
 // and 0 for |x| >= m.  Written without overflow as
 //   psi = S e^{z - b m} (1 - e^{-2z}) / z,   z = b tau,   S = m b / (1 - e^{-2 b m}),
 //   psi' = -x b^2 S e^{z - b m} F(z),   F(z) = ((z - 1) + (z + 1) e^{-2z}) / z^3,
-// with F(z) = 2 e^{-z} sum_{k>=1} 2k z^{2k-2} / (2k+1)! for small z.
+// with F(z) = 2 e^{-z} sum_{k>=1} 2k z^{2k-2} / (2k+1)! for small z, and
+// z - b m = b (tau - m) = -b x^2 / (tau + m).
 template <typename real> struct Window {
     real m;
     real m2;
@@ -52,14 +53,21 @@ template <typename real> __device__ __forceinline__ real flog(real x);
 template <> __device__ __forceinline__ float flog<float>(float x) { return logf(x); }
 template <> __device__ __forceinline__ double flog<double>(double x) { return log(x); }
 
+// psi at x = j + frac (j an integer tap offset, frac in [0, 1)).  tau^2 is formed as
+// (m - x)(m + x) from exact integer parts, and the exponent z - b m as -b x^2 / (tau + m),
+// so no cancellation occurs (e^{z - b m} computed from z ~ b m would lose ~log2(b m) bits).
 template <typename real>
-__device__ __forceinline__ real kb_value(const Window<real> &w, real x)
+__device__ __forceinline__ real kb_value(const Window<real> &w, real frac, int j)
 {
-    const real t = w.m2 - x * x;
-    if (!(t > real(0)))
+    const real t1 = (w.m - real(j)) - frac;   // m - x
+    const real t2 = (w.m + real(j)) + frac;   // m + x
+    if (!(t1 > real(0)) || !(t2 > real(0)))
         return real(0);
-    const real z = w.b * fsqrt<real>(t);
-    return w.S * fexp<real>(z - w.bm) * (-fexpm1<real>(real(-2) * z)) / z;
+    const real tau = fsqrt<real>(t1 * t2);
+    const real x = real(j) + frac;
+    const real z = w.b * tau;
+    const real e = w.S * fexp<real>(-w.b * x * x / (tau + w.m));
+    return e * (-fexpm1<real>(real(-2) * z)) / z;
 }
 
 // F(z) = ((z-1) + (z+1) e^{-2z}) / z^3 (the slope factor of psi').
@@ -85,18 +93,21 @@ __device__ __forceinline__ real kb_slope(real z)
     return ((z - real(1)) + (z + real(1)) * e) / (z * z * z);
 }
 
-// psi and dpsi/dx together.
+// psi and dpsi/dx together, at x = j + frac (see kb_value).
 template <typename real>
-__device__ __forceinline__ void kb_value_slope(const Window<real> &w, real x, real &v, real &d)
+__device__ __forceinline__ void kb_value_slope(const Window<real> &w, real frac, int j, real &v, real &d)
 {
-    const real t = w.m2 - x * x;
-    if (!(t > real(0))) {
+    const real t1 = (w.m - real(j)) - frac;
+    const real t2 = (w.m + real(j)) + frac;
+    if (!(t1 > real(0)) || !(t2 > real(0))) {
         v = real(0);
         d = real(0);
         return;
     }
-    const real z = w.b * fsqrt<real>(t);
-    const real e = w.S * fexp<real>(z - w.bm);
+    const real tau = fsqrt<real>(t1 * t2);
+    const real x = real(j) + frac;
+    const real z = w.b * tau;
+    const real e = w.S * fexp<real>(-w.b * x * x / (tau + w.m));
     v = e * (-fexpm1<real>(real(-2) * z)) / z;
     d = -x * w.b * w.b * e * kb_slope<real>(z);
 }
@@ -108,6 +119,11 @@ __host__ __device__ __forceinline__ int base1(int packed) { return packed & 0xff
 __host__ __device__ __forceinline__ int base2(int packed) { return (packed >> 16) & 0xffff; }
 
 // Tile-major cell key: cells of one spreading tile are contiguous, cells row-major inside.
+// Points are sorted by key * kSub + sub, where sub is the Morton index of the point's
+// 4 x 4 sub-cell, so consecutive points inside a cell are spatially compact; the
+// sorted range of cell `key` is [start[key * kSub], start[(key + 1) * kSub]).
+constexpr int kSub = 16;
+
 struct CellGrid {
     int cell;      // cell edge in grid cells
     int n_c;       // cells per dimension
@@ -119,6 +135,12 @@ struct CellGrid {
         return (t1 * n_t + t2) * (T * T) + (c1 - t1 * T) * T + (c2 - t2 * T);
     }
     __host__ __device__ __forceinline__ int n_keys() const { return n_t * n_t * T * T; }
+    // Morton index of the 4 x 4 sub-cell holding grid line pair (b1, b2) of cell (c1, c2).
+    __host__ __device__ __forceinline__ int sub(int b1, int b2, int c1, int c2) const
+    {
+        const int s1 = ((b1 - c1 * cell) * 4) / cell, s2 = ((b2 - c2 * cell) * 4) / cell;
+        return ((s2 & 1) | ((s1 & 1) << 1) | ((s2 & 2) << 1) | ((s1 & 2) << 2));
+    }
 };
 
 }  // namespace fs

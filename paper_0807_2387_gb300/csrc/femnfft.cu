@@ -142,9 +142,12 @@ struct fs_plan {
     void *src_frac = nullptr, *tgt_frac = nullptr;
     double2 *src_pos = nullptr, *tgt_pos = nullptr;
     float2 *src_pos32 = nullptr, *tgt_pos32 = nullptr;
+    float2 *src_lo32 = nullptr, *tgt_lo32 = nullptr;
     int *src_start = nullptr, *tgt_start = nullptr;
     SpreadItem *items = nullptr;
     int n_items = 0;
+    int2 *near_items = nullptr;       // FP32 near field: (first target, count <= 32) per warp
+    int64_t n_near_items = 0;
     void *mul = nullptr, *tw = nullptr;
     void *grid = nullptr, *spec = nullptr;
     void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
@@ -229,28 +232,38 @@ template <typename real> NearParams<real> make_near(const fs_plan *pl)
     np.p = pl->p;
     np.eps2 = (real)(pl->eps_I * pl->eps_I);
     np.inv_eps2 = (real)(1.0 / (pl->eps_I * pl->eps_I));
-    np.close2 = (pl->eps_I / 8.0) * (pl->eps_I / 8.0);
+    np.close2 = (real)((pl->eps_I / 8.0) * (pl->eps_I / 8.0));
     np.hcell = (real)((double)pl->cg.cell / pl->n_os);
     for (int k = 0; k < pl->p; ++k)
         np.beta[k] = (real)pl->beta[k];
     for (int k = 1; k < pl->p; ++k)
         np.dbeta[k - 1] = (real)(2.0 * k * pl->beta[k] / (pl->eps_I * pl->eps_I));
+    // T_I - k(eps_I) vanishes at r = eps_I; and since k - T_I has a zero of order p there, the
+    // gradient numerator R(w) = -(1/2pi) - sum_k 2k beta_k w^k (degree p-1) is c (w-1)^(p-1).
+    const double k_eps = -std::log(pl->eps_I) / (2.0 * kPi);
+    for (int k = 0; k < pl->p; ++k)
+        np.pbeta[k] = (real)(k == 0 ? pl->beta[0] - k_eps : pl->beta[k]);
+    // R(w) = c (w-1)^(p-1) with R(0) = -(1/2pi) gives c = (-1)^p / (2pi), independent of beta
+    np.rcoef = (real)(((pl->p % 2 == 0) ? 1.0 : -1.0) / (2.0 * kPi * pl->eps_I * pl->eps_I));
     return np;
 }
 
 // Bin one point set: keys, counting sort, per-point records.
 template <typename real>
 fs_status bin_points(fs_plan *pl, const double *xy, int64_t n, int **perm, int **base, void **frac, double2 **pos,
-                     float2 **pos32, int **start)
+                     float2 **pos32, float2 **lo32, int **start)
 {
     FS_TRY(pl->alloc(perm, n));
     FS_TRY(pl->alloc(base, n));
     FS_TRY(pl->alloc_bytes(frac, (size_t)std::max<int64_t>(n, 1) * 2 * sizeof(real)));
     FS_TRY(pl->alloc(pos, n));
-    if (pl->precision == 32)
+    if (pl->precision == 32) {
         FS_TRY(pl->alloc(pos32, n));
-    else
+        FS_TRY(pl->alloc(lo32, n));
+    } else {
         *pos32 = nullptr;
+        *lo32 = nullptr;
+    }
     FS_TRY(pl->alloc(start, (size_t)pl->n_keys + 1));
     int *key = nullptr, *count = nullptr, *fill = nullptr, *tmp = nullptr;
     FS_TRY(pl->alloc(&key, n));
@@ -266,7 +279,7 @@ fs_status bin_points(fs_plan *pl, const double *xy, int64_t n, int **perm, int *
     FS_CUDA(cudaMemcpyAsync(fill, *start, sizeof(int) * ((size_t)pl->n_keys + 1), cudaMemcpyDeviceToDevice, st));
     FS_CUDA(launch_scatter(key, n, fill, *perm, st));
     FS_CUDA(launch_gather_points<real>(xy, *perm, n, pl->s, pl->n_os, pl->window_lo, pl->n_a, pl->m, pl->cg.cell, *pos,
-                                       *frac, *base, *pos32, st));
+                                       *frac, *base, *pos32, *lo32, st));
     FS_CUDA(cudaStreamSynchronize(st));
     pl->release(key);
     pl->release(count);
@@ -411,7 +424,7 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     int T = o.tile_cells > 0 ? o.tile_cells : std::max(1, (int)std::lround(32.0 / cell));
     auto smem_for = [&](int t) {
         const int P = t * cell + 2 * m - 1;
-        return (size_t)P * P * sizeof(real) * ((pl->kahan && sizeof(real) == 4) ? 2 : 1);
+        return (size_t)kSpreadWarps * P * P * sizeof(real) * ((pl->kahan && sizeof(real) == 4) ? 2 : 1);
     };
     while (T > 1 && smem_for(T) > 160 * 1024)
         --T;
@@ -419,9 +432,9 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         return fail(FS_EINVAL, "spreading tile does not fit in shared memory (cell too wide)");
     pl->cg.T = T;
     pl->cg.n_t = (pl->cg.n_c + T - 1) / T;
-    pl->n_keys = pl->cg.n_keys();
-    if (pl->n_keys > 4096 * 4096)
+    if ((int64_t)pl->cg.n_keys() * kSub > 4096 * 4096)
         return fail(FS_EINVAL, "too many cells (eps_I too small for this grid)");
+    pl->n_keys = pl->cg.n_keys() * kSub;   // cell keys refined by the 4 x 4 sub-cell index
 
     // regularised kernel data
     pl->kp.eps_I = eps_I;
@@ -459,9 +472,9 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
 
     // binning
     FS_TRY(bin_points<real>(pl, src, M, &pl->src_perm, &pl->src_base, &pl->src_frac, &pl->src_pos, &pl->src_pos32,
-                            &pl->src_start));
+                            &pl->src_lo32, &pl->src_start));
     FS_TRY(bin_points<real>(pl, tgt, N, &pl->tgt_perm, &pl->tgt_base, &pl->tgt_frac, &pl->tgt_pos, &pl->tgt_pos32,
-                            &pl->tgt_start));
+                            &pl->tgt_lo32, &pl->tgt_start));
     int dev_status = 0;
     FS_CUDA(cudaMemcpy(&dev_status, pl->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (dev_status != 0)
@@ -472,7 +485,7 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         std::vector<int> start(pl->n_keys + 1);
         FS_CUDA(cudaMemcpy(start.data(), pl->src_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
         std::vector<SpreadItem> items;
-        const int TT = T * T;
+        const int TT = T * T * kSub;
         const int n_tiles = pl->cg.n_t * pl->cg.n_t;
         for (int t = 0; t < n_tiles; ++t) {
             const int a = start[t * TT], b2 = start[(t + 1) * TT];
@@ -483,6 +496,22 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         FS_TRY(pl->alloc(&pl->items, items.size()));
         if (!items.empty())
             FS_CUDA(cudaMemcpy(pl->items, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
+    }
+
+    // near-field warp items: at most 32 consecutive targets of one cell
+    if (pl->precision == 32) {
+        std::vector<int> start(pl->n_keys + 1);
+        FS_CUDA(cudaMemcpy(start.data(), pl->tgt_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
+        std::vector<int2> items;
+        for (int key = 0; key < pl->n_keys / kSub; ++key) {
+            const int a = start[key * kSub], b2 = start[(key + 1) * kSub];
+            for (int t0 = a; t0 < b2; t0 += 32)
+                items.push_back(make_int2(t0, std::min(32, b2 - t0)));
+        }
+        pl->n_near_items = (int64_t)items.size();
+        FS_TRY(pl->alloc(&pl->near_items, items.size()));
+        if (!items.empty())
+            FS_CUDA(cudaMemcpy(pl->near_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
     }
 
     // coefficient table and FFT twiddles
@@ -608,9 +637,14 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
                                     (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[5], st));
-        FS_CUDA(launch_near<real>(pl->N, pl->tgt_base, pl->tgt_pos, pl->tgt_pos32, pl->src_pos, pl->src_pos32,
-                                  pl->src_start, pl->cg, q, np, (real *)pl->phi_s, (real *)pl->grad_s,
-                                  (real *)pl->coinc, st));
+        if constexpr (sizeof(real) == 4)
+            FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
+                                  pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q, np,
+                                  (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc, st));
+        else
+            FS_CUDA(launch_near64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
+                                  (const double *)q, np, (double *)pl->phi_s, (double *)pl->grad_s,
+                                  (double *)pl->coinc, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[6], st));
         void *po = phi ? (unsigned char *)phi + (size_t)r * pl->N * osz : nullptr;

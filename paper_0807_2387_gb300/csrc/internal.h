@@ -8,6 +8,9 @@
 
 namespace fs {
 
+// Warps per spreading CTA; each holds a private padded tile in shared memory.
+constexpr int kSpreadWarps = 4;
+
 // One spreading work unit: sources [start, start+count) of tile `tile` (cell-sorted order).
 struct SpreadItem {
     int tile;
@@ -31,10 +34,12 @@ struct KernelParams {
 template <typename real> struct NearParams {
     real eps2;             // eps_I^2
     real inv_eps2;
-    double close2;         // (eps_I/8)^2: pairs below use an FP64 coordinate difference
+    real close2;           // (eps_I/8)^2: closer pairs refine their coordinate difference
     real hcell;            // cell width in torus units (FP32 positions are relative to cell corners)
-    real beta[kMaxP];      // T_I coefficients in u^2 = (r/eps_I)^2
-    real dbeta[kMaxP];     // coefficients of T_I'(r)/r in u^2: 2k beta_k / eps_I^2 (index k-1)
+    real beta[kMaxP];      // T_I coefficients in w = (r/eps_I)^2
+    real dbeta[kMaxP];     // coefficients of T_I'(r)/r in w: 2k beta_k / eps_I^2 (index k-1)
+    real pbeta[kMaxP];     // P(w) = T_I - k(eps_I): beta with beta_0 - k(eps_I), so P(1) = 0
+    real rcoef;            // (-1)^p / (2 pi eps_I^2): (k' - T_I')(r)/r = rcoef (w - 1)^(p-1) / w
     int p;
 };
 
@@ -47,7 +52,7 @@ cudaError_t launch_scatter(const int *key, int64_t n, int *fill, int *perm, cuda
 template <typename real>
 cudaError_t launch_gather_points(const double *xy, const int *perm, int64_t n, double s, int n_os,
                                  int window_lo, int n_a, int m, int cell, double2 *pos, void *frac, int *base,
-                                 float2 *pos32, cudaStream_t st);
+                                 float2 *pos32, float2 *pos32_lo, cudaStream_t st);
 template <typename real>
 cudaError_t launch_gather_charges(const void *q, int q_is_f64, const int *perm, int64_t M, int nrhs,
                                   real *q_sorted, double *q_sum, cudaStream_t st);
@@ -83,11 +88,14 @@ template <typename real>
 cudaError_t launch_build_mul(const double2 *bhat, int n, const double *c_tab, real *mul, cudaStream_t st);
 
 // ---- near field and output (kernels_near.cu)
-template <typename real>
-cudaError_t launch_near(int64_t N, const int *tgt_base, const double2 *tgt_pos, const float2 *tgt_pos32,
-                        const double2 *src_pos, const float2 *src_pos32, const int *src_start, CellGrid cg,
-                        const real *q, NearParams<real> np, real *phi_s, real *grad_s, real *coinc,
-                        cudaStream_t st);
+cudaError_t launch_near64(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
+                          const int *src_start, CellGrid cg, const double *q, NearParams<double> np, double *phi_s,
+                          double *grad_s, double *coinc, cudaStream_t st);
+// items: (first target, count <= 32) per warp, never spanning two cells
+cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                          const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
+                          CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,
+                          cudaStream_t st);
 template <typename real>
 cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, const real *coinc,
                              const int *perm, double shift, const double *q_sum, double s, void *phi_out,

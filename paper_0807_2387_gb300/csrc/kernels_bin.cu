@@ -67,7 +67,8 @@ __global__ void k_point_keys(const double *__restrict__ xy, int64_t n, double s,
     ok = clamp_base(b2, m, n_a) && ok;
     if (!ok)
         atomicExch(status, (int)kDevDomain);
-    const int k = cg.key(b1 / cg.cell, b2 / cg.cell);
+    const int c1 = b1 / cg.cell, c2 = b2 / cg.cell;
+    const int k = cg.key(c1, c2) * kSub + cg.sub(b1, b2, c1, c2);
     key[i] = k;
     atomicAdd(&count[k], 1);
 }
@@ -146,7 +147,7 @@ template <typename real>
 __global__ void k_gather_points(const double *__restrict__ xy, const int *__restrict__ perm, int64_t n, double s,
                                 int n_os, int window_lo, int n_a, int m, int cell, double2 *__restrict__ pos,
                                 typename Cplx<real>::type *__restrict__ frac, int *__restrict__ base,
-                                float2 *__restrict__ pos32)
+                                float2 *__restrict__ pos32, float2 *__restrict__ pos32_lo)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n)
@@ -168,9 +169,13 @@ __global__ void k_gather_points(const double *__restrict__ xy, const int *__rest
     base[k] = (b1 & 0xffff) | (b2 << 16);
     if (pos32) {
         // torus coordinate of the cell's lower corner: (c * cell + window_lo) / n_os - 1/2
+        // offset from the cell corner as an unevaluated sum hi + lo of two floats
         const double c1 = (double)((b1 / cell) * cell + window_lo) / n_os - 0.5;
         const double c2 = (double)((b2 / cell) * cell + window_lo) / n_os - 0.5;
-        pos32[k] = make_float2((float)(xt - c1), (float)(yt - c2));
+        const double o1 = xt - c1, o2 = yt - c2;
+        const float h1 = (float)o1, h2 = (float)o2;
+        pos32[k] = make_float2(h1, h2);
+        pos32_lo[k] = make_float2((float)(o1 - (double)h1), (float)(o2 - (double)h2));
     }
 }
 
@@ -220,8 +225,8 @@ __global__ void k_near_count(const double2 *__restrict__ tgt_pos, const int *__r
                 if (e2 < 0 || e2 >= cg.n_c)
                     continue;
                 const int key = cg.key(e1, e2);
-                const int end = src_start[key + 1];
-                for (int j = src_start[key]; j < end; ++j) {
+                const int end = src_start[(key + 1) * kSub];
+                for (int j = src_start[key * kSub]; j < end; ++j) {
                     const double dx = x.x - src_pos[j].x, dy = x.y - src_pos[j].y;
                     const double r2 = dx * dx + dy * dy;
                     if (r2 < eps2) {
@@ -298,12 +303,13 @@ cudaError_t launch_scatter(const int *key, int64_t n, int *fill, int *perm, cuda
 template <typename real>
 cudaError_t launch_gather_points(const double *xy, const int *perm, int64_t n, double s, int n_os, int window_lo,
                                  int n_a, int m, int cell, double2 *pos, void *frac, int *base, float2 *pos32,
-                                 cudaStream_t st)
+                                 float2 *pos32_lo, cudaStream_t st)
 {
     if (n <= 0)
         return cudaSuccess;
     k_gather_points<real><<<blocks_for(n, 256), 256, 0, st>>>(
-        xy, perm, n, s, n_os, window_lo, n_a, m, cell, pos, (typename Cplx<real>::type *)frac, base, pos32);
+        xy, perm, n, s, n_os, window_lo, n_a, m, cell, pos, (typename Cplx<real>::type *)frac, base, pos32,
+        pos32_lo);
     return cudaGetLastError();
 }
 
@@ -332,9 +338,9 @@ cudaError_t launch_near_count(const double2 *tgt_pos, const int *tgt_base, int64
 }
 
 template cudaError_t launch_gather_points<float>(const double *, const int *, int64_t, double, int, int, int, int, int,
-                                                 double2 *, void *, int *, float2 *, cudaStream_t);
+                                                 double2 *, void *, int *, float2 *, float2 *, cudaStream_t);
 template cudaError_t launch_gather_points<double>(const double *, const int *, int64_t, double, int, int, int, int,
-                                                  int, double2 *, void *, int *, float2 *, cudaStream_t);
+                                                  int, double2 *, void *, int *, float2 *, float2 *, cudaStream_t);
 template cudaError_t launch_gather_charges<float>(const void *, int, const int *, int64_t, int, float *, double *,
                                                   cudaStream_t);
 template cudaError_t launch_gather_charges<double>(const void *, int, const int *, int64_t, int, double *, double *,

@@ -6,12 +6,28 @@
 //     phi_i  += q_j (G(r) - T_I(r))                       0 < r < eps_I
 //     grad_i += q_j (-(1/2 pi) / r^2 - T_I'(r)/r) d        d = x~_i - y~_j
 //     phi_i  -= q_j T_I(0), coinc_i += q_j                  r = 0 (G(0) := 0)
-// Pairs are found among the 3 x 3 cells around the target's cell (cells are
-// at least eps_I wide).  The FP32 path reads positions relative to their cell
-// corner, so a difference is (offset - offset) + (exact cell step); pairs closer
-// than eps_I/8 take their coordinate difference and squared distance from the
-// FP64 positions, so r keeps full FP32 relative accuracy when points nearly
-// coincide.
+// Cells are at least eps_I wide, so a target's partners lie in the 3 x 3 cells
+// around its own.
+//
+// FP64 path: one thread per target, direct FP64 formulas (the comparison path).
+//
+// FP32 path: one warp per work item of at most 32 consecutive targets of one
+// cell.  Targets are sorted by cell and, inside a cell, by 4 x 4 sub-cell in
+// Morton order, so a warp's targets are spatially compact (and a warp never
+// spans two cells, whose bounding box could cross the whole domain).  The
+// warp forms the bounding box of its targets, walks the 4 x 4 sub-cells within
+// eps_I of it and skips (warp-uniformly) every source outside the box grown by
+// eps_I; each remaining source is read once per warp
+// (a broadcast load) and evaluated by all 32 lanes with branch-free masked
+// arithmetic, so no lane diverges on the pair test.  With w = r^2 / eps_I^2:
+//     G - T_I         = -(ln 2 / 4 pi) log2 w - P(w),   P = T_I - k(eps_I), P(1) = 0
+//     (G' - T_I')/r   = c (w - 1)^(p-1) / w,            c = (-1)^p / (2 pi eps_I^2)
+// (the numerator has a (p-1)-fold root at w = 1 because G - T_I has a p-fold
+// contact there), both free of cancellation near r = eps_I.  Positions are
+// FP32 offsets from the cell corner stored as hi + lo: differences use the hi
+// parts plus the exact cell step; pairs closer than eps_I/8 refine the
+// difference with an exact TwoSum of the hi parts and the lo parts, which
+// keeps full FP32 relative accuracy in r for nearly coincident points.
 //
 // The output kernel adds the far and near fields and rescales:
 //     phi = phi~ + (log s / 2 pi) (sum_j q_j - coinc_i),   H = -s grad~ phi,
@@ -22,33 +38,22 @@ namespace fs {
 
 namespace {
 
-template <typename real>
-__global__ void __launch_bounds__(256) k_near(int64_t N, const int *__restrict__ tgt_base,
-                                              const double2 *__restrict__ tgt_pos, const float2 *__restrict__ tgt_pos32,
-                                              const double2 *__restrict__ src_pos, const float2 *__restrict__ src_pos32,
-                                              const int *__restrict__ src_start, CellGrid cg, const real *__restrict__ q,
-                                              NearParams<real> np, real *__restrict__ phi_s, real *__restrict__ grad_s,
-                                              real *__restrict__ coinc)
+__global__ void __launch_bounds__(256) k_near64(int64_t N, const int *__restrict__ tgt_base,
+                                                const double2 *__restrict__ tgt_pos,
+                                                const double2 *__restrict__ src_pos, const int *__restrict__ src_start,
+                                                CellGrid cg, const double *__restrict__ q, NearParams<double> np,
+                                                double *__restrict__ phi_s, double *__restrict__ grad_s,
+                                                double *__restrict__ coinc)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N)
         return;
-    const bool fp32 = sizeof(real) == 4;
     const double2 X = tgt_pos[k];
-    real xt, yt;
-    if (fp32) {
-        const float2 x32 = tgt_pos32[k];
-        xt = (real)x32.x;
-        yt = (real)x32.y;
-    } else {
-        xt = (real)X.x;
-        yt = (real)X.y;
-    }
     const int packed = tgt_base[k];
     const int c1 = base1(packed) / cg.cell, c2 = base2(packed) / cg.cell;
-    const real inv4pi = real(1.0 / (4.0 * kPi));
-    const real inv2pi = real(1.0 / (2.0 * kPi));
-    real phi = 0, gx = 0, gy = 0, qc = 0;
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    double phi = 0, gx = 0, gy = 0, qc = 0;
     for (int d1 = -1; d1 <= 1; ++d1) {
         const int e1 = c1 + d1;
         if (e1 < 0 || e1 >= cg.n_c)
@@ -58,51 +63,31 @@ __global__ void __launch_bounds__(256) k_near(int64_t N, const int *__restrict__
             if (e2 < 0 || e2 >= cg.n_c)
                 continue;
             const int key = cg.key(e1, e2);
-            const int end = src_start[key + 1];
-            // cell-corner offset between the target's and this source cell (exact: dyadic width)
-            const real ox = (real)(c1 - e1) * np.hcell, oy = (real)(c2 - e2) * np.hcell;
-            for (int j = src_start[key]; j < end; ++j) {
-                real dx, dy, r2;
-                if (fp32) {
-                    const float2 y32 = src_pos32[j];
-                    dx = (xt - (real)y32.x) + ox;
-                    dy = (yt - (real)y32.y) + oy;
-                } else {
-                    const double2 Y = src_pos[j];
-                    dx = (real)(X.x - Y.x);
-                    dy = (real)(X.y - Y.y);
-                }
-                r2 = dx * dx + dy * dy;
+            const int end = src_start[(key + 1) * kSub];
+            for (int j = src_start[key * kSub]; j < end; ++j) {
+                const double2 Y = src_pos[j];
+                const double dx = X.x - Y.x, dy = X.y - Y.y;
+                const double r2 = dx * dx + dy * dy;
                 if (!(r2 < np.eps2))
                     continue;
-                const real qj = q[j];
-                if (fp32 && (double)r2 < np.close2) {
-                    const double2 Y = src_pos[j];
-                    const double ddx = X.x - Y.x, ddy = X.y - Y.y;
-                    const double rr2 = ddx * ddx + ddy * ddy;
-                    dx = (real)ddx;
-                    dy = (real)ddy;
-                    r2 = (real)rr2;
-                    if (rr2 == 0.0)
-                        r2 = real(0);
-                }
-                if (r2 == real(0)) {
+                const double qj = q[j];
+                if (r2 == 0.0) {
                     phi -= qj * np.beta[0];
                     qc += qj;
                     continue;
                 }
-                const real u2 = r2 * np.inv_eps2;
-                real t = np.beta[np.p - 1];
+                const double u2 = r2 * np.inv_eps2;
+                double t = np.beta[np.p - 1];
                 for (int i = np.p - 2; i >= 0; --i)
                     t = t * u2 + np.beta[i];
-                real tp = real(0);
+                double tp = 0.0;
                 if (np.p > 1) {
                     tp = np.dbeta[np.p - 2];
                     for (int i = np.p - 3; i >= 0; --i)
                         tp = tp * u2 + np.dbeta[i];
                 }
-                const real val = -inv4pi * flog<real>(r2) - t;
-                const real coef = -inv2pi / r2 - tp;
+                const double val = -inv4pi * log(r2) - t;
+                const double coef = -inv2pi / r2 - tp;
                 phi += qj * val;
                 gx += qj * coef * dx;
                 gy += qj * coef * dy;
@@ -113,6 +98,153 @@ __global__ void __launch_bounds__(256) k_near(int64_t N, const int *__restrict__
     grad_s[2 * k] += gx;
     grad_s[2 * k + 1] += gy;
     coinc[k] = qc;
+}
+
+template <int E> __device__ __forceinline__ float ipow(float x)
+{
+    if constexpr (E == 0) {
+        return 1.0f;
+    } else if constexpr (E == 1) {
+        return x;
+    } else {
+        const float h = ipow<E / 2>(x);
+        if constexpr (E % 2 == 0)
+            return h * h;
+        else
+            return h * h * x;
+    }
+}
+
+__device__ __forceinline__ float warp_min(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// dx from hi parts (a = x_hi - y_hi by TwoSum), the exact cell step and the lo parts.
+__device__ __forceinline__ float refine_diff(float xh, float yh, float off, float xl, float yl)
+{
+    const float a = xh - yh;
+    const float bb = a - xh;
+    const float e = (xh - (a - bb)) + (-yh - bb);
+    return (a + off) + (e + (xl - yl));
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_near32(int64_t n_items, const int2 *__restrict__ items,
+                                                const int *__restrict__ tgt_base,
+                                                const float2 *__restrict__ tgt_hi, const float2 *__restrict__ tgt_lo,
+                                                const float2 *__restrict__ src_hi, const float2 *__restrict__ src_lo,
+                                                const int *__restrict__ src_start, CellGrid cg,
+                                                const float *__restrict__ q, NearParams<float> np,
+                                                float *__restrict__ phi_s, float *__restrict__ grad_s,
+                                                float *__restrict__ coinc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_items)
+        return;                                   // whole warp past the end (warp-uniform)
+    const int2 item = items[warp];                // (first target, count <= 32), one cell
+    const bool valid = lane < item.y;
+    const int64_t k = item.x + lane;
+    const int64_t kk = valid ? k : item.x;
+    const int packed = tgt_base[kk];
+    const int c1 = base1(packed) / cg.cell, c2 = base2(packed) / cg.cell;
+    const float2 xh = tgt_hi[kk], xl = tgt_lo[kk];
+    const float h = np.hcell, eps = sqrtf(np.eps2);
+    // warp bounding box in "cell units * h + offset" coordinates
+    const float ax = (float)c1 * h + xh.x, ay = (float)c2 * h + xh.y;
+    const float slack = 1e-6f * h;
+    const float bx0 = warp_min(ax) - eps - slack, bx1 = warp_max(ax) + eps + slack;
+    const float by0 = warp_min(ay) - eps - slack, by1 = warp_max(ay) + eps + slack;
+    const int cx0 = max(0, (int)floorf(bx0 / h)), cx1 = min(cg.n_c - 1, (int)floorf(bx1 / h));
+    const int cy0 = max(0, (int)floorf(by0 / h)), cy1 = min(cg.n_c - 1, (int)floorf(by1 / h));
+    const float c_ln = -0.69314718055994531f / (4.0f * 3.14159265358979324f);   // -(ln 2) / (4 pi)
+    const float inv_g = (float)cg.cell / h;   // grid lines per unit length (n_os)
+    float phi = 0.f, gx = 0.f, gy = 0.f, qc = 0.f;
+    for (int ex = cx0; ex <= cx1; ++ex) {
+        const float offx = (float)(c1 - ex) * h;
+        const float sx0 = (float)ex * h;
+        // sub-cell rows of this cell that meet [bx0, bx1] (one grid line of margin for rounding)
+        const int ox0 = max(0, (int)floorf((bx0 - sx0) * inv_g) - 1);
+        const int ox1 = min(cg.cell - 1, (int)floorf((bx1 - sx0) * inv_g) + 1);
+        const int s1a = (ox0 * 4) / cg.cell, s1b = (ox1 * 4) / cg.cell;
+        for (int ey = cy0; ey <= cy1; ++ey) {
+            const float offy = (float)(c2 - ey) * h;
+            const float sy0 = (float)ey * h;
+            const int oy0 = max(0, (int)floorf((by0 - sy0) * inv_g) - 1);
+            const int oy1 = min(cg.cell - 1, (int)floorf((by1 - sy0) * inv_g) + 1);
+            const int s2a = (oy0 * 4) / cg.cell, s2b = (oy1 * 4) / cg.cell;
+            const int kbase = cg.key(ex, ey) * kSub;
+            float cphi = 0.f, cgx = 0.f, cgy = 0.f;
+            for (int s1 = s1a; s1 <= s1b; ++s1)
+            for (int s2 = s2a; s2 <= s2b; ++s2) {
+            const int sub = (s2 & 1) | ((s1 & 1) << 1) | ((s2 & 2) << 1) | ((s1 & 2) << 2);
+            const int end = src_start[kbase + sub + 1];
+            for (int j = src_start[kbase + sub]; j < end; ++j) {
+                const float2 yh = __ldg(src_hi + j);
+                const float sax = sx0 + yh.x, say = sy0 + yh.y;
+                if (sax < bx0 || sax > bx1 || say < by0 || say > by1)
+                    continue;                     // warp-uniform: no target of this warp is within eps_I
+                float dx = (xh.x - yh.x) + offx;
+                float dy = (xh.y - yh.y) + offy;
+                float r2 = dx * dx + dy * dy;
+                float qj = __ldg(q + j);
+                if (r2 < np.close2) {
+                    const float2 yl = __ldg(src_lo + j);
+                    dx = refine_diff(xh.x, yh.x, offx, xl.x, yl.x);
+                    dy = refine_diff(xh.y, yh.y, offy, xl.y, yl.y);
+                    r2 = dx * dx + dy * dy;
+                    if (dx == 0.f && dy == 0.f && valid) {
+                        cphi -= qj * np.beta[0];
+                        qc += qj;
+                        qj = 0.f;
+                    }
+                }
+                qj = (r2 < np.eps2 && valid) ? qj : 0.f;
+                const float w = fmaxf(r2 * np.inv_eps2, 1e-30f);
+                float pw = np.pbeta[P - 1];
+#pragma unroll
+                for (int i = P - 2; i >= 0; --i)
+                    pw = fmaf(pw, w, np.pbeta[i]);
+                const float val = fmaf(c_ln, __log2f(w), -pw);
+                const float coef = np.rcoef * ipow<P - 1>(w - 1.f) * __frcp_rn(w);
+                cphi = fmaf(qj, val, cphi);
+                const float t = qj * coef;
+                cgx = fmaf(t, dx, cgx);
+                cgy = fmaf(t, dy, cgy);
+            }
+            }
+            phi += cphi;
+            gx += cgx;
+            gy += cgy;
+        }
+    }
+    if (valid) {
+        phi_s[k] += phi;
+        grad_s[2 * k] += gx;
+        grad_s[2 * k + 1] += gy;
+        coinc[k] = qc;
+    }
+}
+
+template <int P>
+cudaError_t near32_p(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                     const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start, CellGrid cg,
+                     const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((n_items + 3) / 4);
+    k_near32<P><<<blocks, 128, 0, st>>>(n_items, items, tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start, cg, q,
+                                        np, phi_s, grad_s, coinc);
+    return cudaGetLastError();
 }
 
 template <typename real>
@@ -147,16 +279,49 @@ __global__ void k_unpermute(int64_t N, const real *__restrict__ phi_s, const rea
 
 }  // namespace
 
-template <typename real>
-cudaError_t launch_near(int64_t N, const int *tgt_base, const double2 *tgt_pos, const float2 *tgt_pos32,
-                        const double2 *src_pos, const float2 *src_pos32, const int *src_start, CellGrid cg,
-                        const real *q, NearParams<real> np, real *phi_s, real *grad_s, real *coinc, cudaStream_t st)
+cudaError_t launch_near64(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
+                          const int *src_start, CellGrid cg, const double *q, NearParams<double> np, double *phi_s,
+                          double *grad_s, double *coinc, cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
-    k_near<real><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, tgt_base, tgt_pos, tgt_pos32, src_pos, src_pos32,
-                                                              src_start, cg, q, np, phi_s, grad_s, coinc);
+    k_near64<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, tgt_base, tgt_pos, src_pos, src_start, cg, q, np, phi_s,
+                                                           grad_s, coinc);
     return cudaGetLastError();
+}
+
+cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                          const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
+                          CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,
+                          cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    switch (np.p) {
+#define FS_NEAR_CASE(P)                                                                                          \
+    case P:                                                                                                      \
+        return near32_p<P>(n_items, items, tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start, cg, q, np, phi_s, \
+                           grad_s, coinc, st);
+        FS_NEAR_CASE(1)
+        FS_NEAR_CASE(2)
+        FS_NEAR_CASE(3)
+        FS_NEAR_CASE(4)
+        FS_NEAR_CASE(5)
+        FS_NEAR_CASE(6)
+        FS_NEAR_CASE(7)
+        FS_NEAR_CASE(8)
+        FS_NEAR_CASE(9)
+        FS_NEAR_CASE(10)
+        FS_NEAR_CASE(11)
+        FS_NEAR_CASE(12)
+        FS_NEAR_CASE(13)
+        FS_NEAR_CASE(14)
+        FS_NEAR_CASE(15)
+        FS_NEAR_CASE(16)
+#undef FS_NEAR_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <typename real>
@@ -171,12 +336,6 @@ cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, c
     return cudaGetLastError();
 }
 
-template cudaError_t launch_near<float>(int64_t, const int *, const double2 *, const float2 *, const double2 *,
-                                        const float2 *, const int *, CellGrid, const float *, NearParams<float>,
-                                        float *, float *, float *, cudaStream_t);
-template cudaError_t launch_near<double>(int64_t, const int *, const double2 *, const float2 *, const double2 *,
-                                         const float2 *, const int *, CellGrid, const double *, NearParams<double>,
-                                         double *, double *, double *, cudaStream_t);
 template cudaError_t launch_unpermute<float>(int64_t, const float *, const float *, const float *, const int *,
                                              double, const double *, double, void *, void *, int, cudaStream_t);
 template cudaError_t launch_unpermute<double>(int64_t, const double *, const double *, const double *, const int *,

@@ -7,12 +7,17 @@
 // same stencil back: phi(x_i) = sum_k g'_k psi(u_i1 - k_1) psi(u_i2 - k_2), and
 // the gradient uses the analytic window slope psi'.
 //
-// Spreading: one CTA per work item (a tile of cells, or a slice of a crowded
-// tile).  It accumulates into a padded shared-memory tile with shared atomics;
-// in FP32 each addition's rounding error is recovered exactly (TwoSum on the
-// value the atomic returns) into a second, compensation tile, so the tile
-// holds a double-FP32 sum.  The padded tile is then added to the grid with
-// global atomics (tiles overlap by 2m-1 lines).
+// Spreading: one CTA (kSpreadWarps warps) per work item (a tile of cells, or a
+// slice of a crowded tile).  A warp takes one source at a time: lanes 0..2m-1
+// evaluate the 2m window weights of the first coordinate, lanes 2m..4m-1 those
+// of the second (times q), and every lane owns a fixed subset of the (2m)^2
+// taps, fetching its two factors by shuffle.  Each warp accumulates into its
+// own padded copy of the tile in shared memory, so within a warp every tap
+// address is distinct and the read-modify-write needs no atomics; in FP32 each
+// addition's rounding error is recovered exactly (TwoSum) into a second,
+// compensation tile, so the tile holds a double-FP32 sum.  At the end the warp
+// tiles are summed and added to the grid with global atomics (tiles overlap by
+// 2m-1 lines).
 #include "internal.h"
 
 namespace fs {
@@ -22,63 +27,94 @@ namespace {
 template <typename real> using real2_t = typename Cplx<real>::type;
 
 template <typename real, int M2, bool KAHAN>
-__global__ void __launch_bounds__(256) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
-                                                const int *__restrict__ base, const real2_t<real> *__restrict__ frac,
-                                                const real *__restrict__ q, Window<real> w, real *__restrict__ grid,
-                                                int pitch, int n_a)
+__global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
+                                                              const int *__restrict__ base,
+                                                              const real2_t<real> *__restrict__ frac,
+                                                              const real *__restrict__ q, Window<real> w,
+                                                              real *__restrict__ grid, int pitch, int n_a)
 {
     constexpr int m = M2 / 2;
+    constexpr int TAPS = M2 * M2;
+    constexpr int PER = (TAPS + 31) / 32;
+    constexpr int PLANES = KAHAN ? 2 : 1;
     extern __shared__ unsigned char smem_raw[];
-    real *acc = reinterpret_cast<real *>(smem_raw);
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    real *comp = acc + P * P;
+    const int PP = P * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
+    real *comp = acc + PP;
     const SpreadItem it = items[blockIdx.x];
     const int t1 = it.tile / cg.n_t, t2 = it.tile - (it.tile / cg.n_t) * cg.n_t;
     const int o1 = t1 * TG - (m - 1), o2 = t2 * TG - (m - 1);
-    for (int i = threadIdx.x; i < P * P * (KAHAN ? 2 : 1); i += blockDim.x)
+    for (int i = lane; i < PP * PLANES; i += 32)
         acc[i] = real(0);
-    __syncthreads();
-    for (int j = it.start + threadIdx.x; j < it.start + it.count; j += blockDim.x) {
+    __syncwarp();
+    // this lane's taps: t = lane + 32 i -> (a, b) = (t / 2m, t % 2m)
+    int toff[PER];
+    int ta[PER], tb[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int t = lane + 32 * i;
+        ta[i] = t < TAPS ? t / M2 : 0;
+        tb[i] = t < TAPS ? t - (t / M2) * M2 : 0;
+        toff[i] = ta[i] * P + tb[i];
+    }
+    const bool first = lane < M2;
+    const int jw = first ? lane : lane - M2;
+    for (int j = it.start + warp; j < it.start + it.count; j += kSpreadWarps) {
         const int packed = base[j];
         const real2_t<real> f = frac[j];
-        const real qj = q[j];
-        real w1[M2], w2[M2];
-#pragma unroll
-        for (int a = 0; a < M2; ++a) {
-            w1[a] = kb_value<real>(w, f.x + real(m - 1 - a));
-            w2[a] = kb_value<real>(w, f.y + real(m - 1 - a)) * qj;
+        real wv = real(0);
+        if (lane < 2 * M2) {
+            wv = kb_value<real>(w, first ? f.x : f.y, m - 1 - jw);
+            if (!first)
+                wv *= q[j];
         }
-        const int row0 = base1(packed) - m + 1 - o1;
-        const int col0 = base2(packed) - m + 1 - o2;
+        real *corner = acc + (base1(packed) - m + 1 - o1) * P + (base2(packed) - m + 1 - o2);
 #pragma unroll
-        for (int a = 0; a < M2; ++a) {
-            real *rowp = acc + (row0 + a) * P + col0;
-#pragma unroll
-            for (int b = 0; b < M2; ++b) {
-                const real v = w1[a] * w2[b];
+        for (int i = 0; i < PER; ++i) {
+            const real w1 = __shfl_sync(0xffffffffu, wv, ta[i]);
+            const real w2 = __shfl_sync(0xffffffffu, wv, M2 + tb[i]);
+            if (lane + 32 * i < TAPS) {
+                real *cell = corner + toff[i];
+                const real v = w1 * w2;
+                const real old = *cell;
+                const real s = old + v;
+                *cell = s;
                 if (KAHAN) {
-                    const real old = atomicAdd(rowp + b, v);
-                    const real s = old + v;
                     const real bb = s - old;
-                    const real err = (old - (s - bb)) + (v - bb);
-                    atomicAdd(rowp + b + P * P, err);
-                } else {
-                    atomicAdd(rowp + b, v);
+                    cell[PP] += (old - (s - bb)) + (v - bb);
                 }
             }
         }
+        __syncwarp();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+    const real *base_tile = reinterpret_cast<const real *>(smem_raw);
+    for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+        real v = real(0);
+#pragma unroll
+        for (int ww = 0; ww < kSpreadWarps; ++ww) {
+            const real *tile = base_tile + (size_t)ww * PP * PLANES;
+            v += tile[i];
+            if (KAHAN)
+                v += tile[i + PP];
+        }
         const int r = i / P, c = i - (i / P) * P;
-        const real v = KAHAN ? acc[i] + comp[i] : acc[i];
         const int g1 = o1 + r, g2 = o2 + c;
         if (v != real(0) && g1 >= 0 && g1 < n_a && g2 >= 0 && g2 < n_a)
             atomicAdd(grid + (int64_t)g1 * pitch + g2, v);
     }
 }
 
+// In FP32 with m >= 5 the derivative sums are formed against a reference tap:
+// the window's periodisation sum_k psi(x - k) is flat (to ~1e-9 relative for
+// m = 5, ~1e-11 for m = 6), so sum_k psi'(x - k) vanishes to that level and
+// sum_a d_a s_a = sum_a d_a (s_a - s_c) avoids the cancellation between terms of
+// size n_os |s| that would otherwise dominate the FP32 gradient error.  For
+// m <= 4 the periodisation is flat only to ~1e-7, no better than FP32 rounding,
+// so those widths (and the FP64 path) sum directly.
 template <typename real, int M2>
 __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict__ base,
                                                 const real2_t<real> *__restrict__ frac, Window<real> w,
@@ -86,6 +122,7 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
                                                 real *__restrict__ phi_s, real *__restrict__ grad_s)
 {
     constexpr int m = M2 / 2;
+    constexpr bool kRef = sizeof(real) == 4 && m >= 5;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N)
         return;
@@ -94,26 +131,34 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
     real w1[M2], d1[M2], w2[M2], d2[M2];
 #pragma unroll
     for (int a = 0; a < M2; ++a) {
-        kb_value_slope<real>(w, f.x + real(m - 1 - a), w1[a], d1[a]);
-        kb_value_slope<real>(w, f.y + real(m - 1 - a), w2[a], d2[a]);
+        kb_value_slope<real>(w, f.x, m - 1 - a, w1[a], d1[a]);
+        kb_value_slope<real>(w, f.y, m - 1 - a, w2[a], d2[a]);
     }
     const int row0 = base1(packed) - m + 1;
     const int col0 = base2(packed) - m + 1;
-    real phi = 0, g1 = 0, g2 = 0;
+    real rsv[M2];
+    real phi = 0, g2 = 0;
 #pragma unroll
     for (int a = 0; a < M2; ++a) {
         const real *rowp = grid + (int64_t)(row0 + a) * pitch + col0;
+        real gv[M2];
+#pragma unroll
+        for (int b = 0; b < M2; ++b)
+            gv[b] = __ldg(rowp + b);
         real rs = 0, rd = 0;
 #pragma unroll
         for (int b = 0; b < M2; ++b) {
-            const real gv = __ldg(rowp + b);
-            rs += w2[b] * gv;
-            rd += d2[b] * gv;
+            rs += w2[b] * gv[b];
+            rd += d2[b] * (kRef ? gv[b] - gv[m - 1] : gv[b]);
         }
+        rsv[a] = rs;
         phi += w1[a] * rs;
-        g1 += d1[a] * rs;
         g2 += w1[a] * rd;
     }
+    real g1 = 0;
+#pragma unroll
+    for (int a = 0; a < M2; ++a)
+        g1 += d1[a] * (kRef ? rsv[a] - rsv[m - 1] : rsv[a]);
     phi_s[k] = phi;
     grad_s[2 * k] = n_os * g1;
     grad_s[2 * k + 1] = n_os * g2;
@@ -125,20 +170,20 @@ cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const in
 {
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const size_t smem = (size_t)P * P * sizeof(real) * (kahan ? 2 : 1);
+    const size_t smem = (size_t)kSpreadWarps * P * P * sizeof(real) * (kahan ? 2 : 1);
     const real2_t<real> *fr = (const real2_t<real> *)frac;
     if (kahan) {
         auto kern = k_spread<real, M2, true>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        kern<<<n_items, 256, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
+        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
     } else {
         auto kern = k_spread<real, M2, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        kern<<<n_items, 256, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
+        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
     }
     return cudaGetLastError();
 }
