@@ -150,6 +150,32 @@ fs_status fs_set_charges(fs_plan *plan, const void *q, fs_dtype dtype, int nrhs)
  */
 fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs);
 
+/*
+ * FEM plans only: the same as fs_set_magnetization, but the call allocates no
+ * memory at all.  The paper has no counterpart; this exists for callers that
+ * must not call cudaMalloc: code that runs while a CUDA stream capture is
+ * active (allocation is not permitted there), code that works inside a fixed
+ * memory budget or an external arena, and time-stepping loops that must not
+ * stall on the allocator every step.
+ *
+ * The intermediate charges (nrhs x M doubles, which fs_set_magnetization keeps in
+ * memory it allocates on first use) live instead in one static device array of
+ * 2^19 doubles (4 MiB) inside the library.  Every GPU that loads the library
+ * holds that array until the process exits.
+ *  - nrhs * M above 524288 is rejected with FS_EINVAL.
+ *  - The plan's charge storage must already hold nrhs vectors, reserved by an
+ *    earlier fs_set_charges or fs_set_magnetization call with at least nrhs
+ *    vectors; otherwise FS_EINVAL (this call will not allocate it).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array and each call overwrites every element it
+ *    reads, so nothing needs clearing; but calls that overlap on the GPU (on
+ *    other streams, or for other plans on the same device) race on it, so the
+ *    caller must serialise them.
+ *  mag [device] (nrhs, Nv, 2) float64, 16-byte aligned.
+ */
+fs_status fs_set_magnetization_static(fs_plan *plan, const double *mag, int nrhs);
+
 /* FEM plans only: kernel (a) alone, charges written in source order.
  *  mag [device] (nrhs, Nv, 2) float64;  q_out [device] (nrhs, M) float64. */
 fs_status fs_fem_charges(fs_plan *plan, const double *mag, double *q_out, int nrhs);

@@ -113,6 +113,17 @@ def fs_set_magnetization(plan, mag, nrhs=None):
           "fs_set_magnetization")
 
 
+def fs_set_magnetization_static(plan, mag, nrhs=None):
+    """Allocation-free fs_set_magnetization for callers that must not call cudaMalloc (stream
+    capture, fixed memory budgets, per-step loops); see its declaration for the 4 MiB limit and
+    the rule that calls must not overlap on the GPU."""
+    torch = _torch()
+    if nrhs is None:
+        nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+    check(load().fs_set_magnetization_static(plan, _dev_ptr(mag, torch.float64, "mag"), int(nrhs)),
+          "fs_set_magnetization_static")
+
+
 def fs_fem_charges(plan, mag, q_out, nrhs=None):
     torch = _torch()
     if nrhs is None:

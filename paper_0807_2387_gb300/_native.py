@@ -15,7 +15,7 @@ FS_F32, FS_F64 = 32, 64
 FS_FLAG_NO_KAHAN, FS_FLAG_TIMING = 1, 2
 
 EXPORTED = (
-    "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization",
+    "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization", "fs_set_magnetization_static",
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "fs_last_error",
     "fs_version",
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         "fs_plan_create_fem": [P, I64, P, I64, I32, D, I32, D, ctypes.POINTER(FsOpts), PP],
         "fs_set_charges": [P, P, I32, I32],
         "fs_set_magnetization": [P, P, I32],
+        "fs_set_magnetization_static": [P, P, I32],
         "fs_fem_charges": [P, P, P, I32],
         "fs_fem_sources": [P, P],
         "fs_eval_potential": [P, P, I32],

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -999,3 +1000,85 @@ fs_status fs_plan_destroy(fs_plan *plan)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of fs_set_magnetization.
+//
+// The intermediate FEM charges live in this file-scope device array instead of memory the
+// plan allocates.  Host code cannot use the array's name as a device address (on the host it
+// is only a stand-in symbol), so the address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, and passed to the kernels.
+
+namespace {
+
+constexpr int64_t kStaticFemCharges = int64_t(1) << 19;   // doubles (4 MiB)
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_fem_charge_scratch[kStaticFemCharges];
+
+std::mutex g_scratch_mutex;
+double *g_scratch_addr[kMaxDevices] = {};
+
+fs_status static_scratch_address(double **out)
+{
+    int dev = 0;
+    FS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(FS_EUNSUPPORTED, "device index beyond the static scratch table");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_fem_charge_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(FS_ECUDA, std::string("cudaGetSymbolAddress of the static charge scratch failed: ") +
+                                      cudaGetErrorString(e));
+        g_scratch_addr[dev] = static_cast<double *>(ptr);
+    }
+    *out = g_scratch_addr[dev];
+    return FS_OK;
+}
+
+template <typename real> fs_status gather_static_charges(fs_plan *pl, const double *q, int nrhs)
+{
+    cudaStream_t st = pl->stream;
+    pl->nrhs = nrhs;
+    if (pl->events)
+        FS_CUDA(cudaEventRecord(pl->ev_q0, st));
+    FS_CUDA(cudaMemsetAsync(pl->q_sum, 0, sizeof(double) * nrhs, st));
+    FS_CUDA(launch_gather_charges<real>(q, 1, pl->src_perm, pl->M, nrhs, (real *)pl->q_sorted, pl->q_sum, st));
+    if (pl->events)
+        FS_CUDA(cudaEventRecord(pl->ev_q1, st));
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" fs_status fs_set_magnetization_static(fs_plan *plan, const double *mag, int nrhs)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!mag || nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "bad magnetisation arguments");
+    if ((reinterpret_cast<uintptr_t>(mag) & 15u) != 0)
+        return fail(FS_EINVAL, "magnetisation must be 16-byte aligned (read as (Mx, My) pairs)");
+    if ((int64_t)nrhs * plan->M > kStaticFemCharges)
+        return fail(FS_EINVAL, "nrhs * n_src = " + std::to_string((int64_t)nrhs * plan->M) +
+                                   " exceeds the static scratch limit of 524288 charges");
+    if (nrhs > plan->nrhs_cap)
+        return fail(FS_EINVAL, "charge storage for " + std::to_string(nrhs) +
+                                   " vectors is not reserved: call fs_set_charges or fs_set_magnetization "
+                                   "once with at least that many vectors first");
+    int dev = 0;
+    FS_CUDA(cudaGetDevice(&dev));
+    if (dev != plan->device)
+        return fail(FS_EINVAL, "the plan's device is not the current device");
+    double *scratch = nullptr;
+    FS_TRY(static_scratch_address(&scratch));
+    FS_CUDA(launch_fem_charges(plan->nodes, plan->tris, plan->Nt, plan->bedges, plan->Ne, (const double2 *)mag,
+                               plan->Nv, nrhs, scratch, plan->M, plan->stream));
+    if (plan->precision == 64)
+        return gather_static_charges<double>(plan, scratch, nrhs);
+    return gather_static_charges<float>(plan, scratch, nrhs);
+}
