@@ -143,6 +143,21 @@ def algorithmic_bytes(info, n_points):
     }
 
 
+# DRAM bytes per launch of the near-field kernel from an ncu capture, keyed by the SHA-256 of
+# the kernel source it was taken on (a changed kernel reports null until it is re-captured).
+NEAR_TRAFFIC = {
+    # profiles/k_near32_mixture_2p19.md: 28.13 MB at 2^19 points, scaled by the point count
+    "ca94ec2142a597bb983867d936f3b5d2cd8baabefba22c0dc5fb0c1c2c07d9c0": 2 * 28.13e6,
+}
+
+
+def near_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_0807_2387_gb300", "csrc", "kernels_near.cu")
+    sha = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    return NEAR_TRAFFIC.get(sha), sha
+
+
 def near_flops_per_pair(p):
     # FP32 near-pair work: difference + r^2 (7), w (1), P(w) Horner (2(p-1)), (w-1)^(p-1) (p-1 + 1),
     # log and reciprocal (2 MUFU, counted 1 each), value and coefficient (4), three accumulations (6)
@@ -161,7 +176,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    work = W.mixture_c2(seed=W.SEEDS["c2"] + rank)
+    work = W.mixture_c2(seed=W.SEEDS["c2"] + rank, count=args.points)
     src = torch.tensor(work["src"], device=dev)
     tgt = torch.tensor(work["tgt"], device=dev)
     q64 = torch.tensor(work["q"], device=dev)
@@ -262,8 +277,12 @@ def run_ours(args):
         achieved = info["near_pairs"] * fpp / (stage_ms["near"] / 1e3) / 1e12
         sm_max = 2070.0
         peak_alu = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-        roof = {"kernel": "k_near<float>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": args.traffic,
+        traffic, sha = near_traffic()
+        if args.traffic is not None:
+            traffic = args.traffic
+        roof = {"kernel": "k_near32<8>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
+                "kernel_source_sha256": sha[:16],
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "work": f"{info['near_pairs']} pairs x {fpp} flop"}
     else:
@@ -335,6 +354,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=32768)
     ap.add_argument("--ref-targets", type=int, default=64)
+    ap.add_argument("--points", type=int, default=1 << 20,
+                    help="points per set (sources = targets count); the benchmark is 2^20, smaller for ncu captures")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

@@ -112,6 +112,25 @@ __device__ __forceinline__ void kb_value_slope(const Window<real> &w, real frac,
     d = -x * w.b * w.b * e * kb_slope<real>(z);
 }
 
+// FP32 window: per tap a (x = frac + m - 1 - a), a polynomial of degree kPolyD in
+// t = frac - 1/2 interpolating psi at Chebyshev points (fitted in FP64 on the host;
+// |error| <= 3e-11 of psi(0) for m = 6), and its exact derivative for psi'.  Only
+// FMA-pipe work, where the closed form needs five MUFU operations per tap.
+constexpr int kPolyD = 12;
+struct WindowPoly {
+    float c[2 * kMaxM][kPolyD + 1];   // value coefficients, c[a][i] multiplies t^i
+    float d[2 * kMaxM][kPolyD];       // slope coefficients (d/dx), d[a][i] multiplies t^i
+};
+
+template <int DEG> __device__ __forceinline__ float poly_eval(const float *c, float t)
+{
+    float acc = c[DEG];
+#pragma unroll
+    for (int i = DEG - 1; i >= 0; --i)
+        acc = fmaf(acc, t, c[i]);
+    return acc;
+}
+
 // Point record fields in cell-sorted order.
 //   base: packed (b1 | b2 << 16), b = floor(u), u = n_os (s x + 1/2) - window_lo
 //   frac: u - b in [0, 1), per dimension
@@ -120,9 +139,20 @@ __host__ __device__ __forceinline__ int base2(int packed) { return (packed >> 16
 
 // Tile-major cell key: cells of one spreading tile are contiguous, cells row-major inside.
 // Points are sorted by key * kSub + sub, where sub is the Morton index of the point's
-// 4 x 4 sub-cell, so consecutive points inside a cell are spatially compact; the
-// sorted range of cell `key` is [start[key * kSub], start[(key + 1) * kSub]).
-constexpr int kSub = 16;
+// 8 x 8 sub-cell, so consecutive points inside a cell are spatially compact; the sorted
+// range of cell `key` is [start[key * kSub], start[(key + 1) * kSub]) and that of one
+// sub-cell is [start[key * kSub + sub], start[key * kSub + sub + 1]).
+constexpr int kSubEdge = 8;
+constexpr int kSub = kSubEdge * kSubEdge;
+
+__host__ __device__ __forceinline__ int morton_sub(int s1, int s2)
+{
+    int r = 0;
+#pragma unroll
+    for (int bit = 0; bit < 3; ++bit)
+        r |= (((s2 >> bit) & 1) << (2 * bit)) | (((s1 >> bit) & 1) << (2 * bit + 1));
+    return r;
+}
 
 struct CellGrid {
     int cell;      // cell edge in grid cells
@@ -135,11 +165,13 @@ struct CellGrid {
         return (t1 * n_t + t2) * (T * T) + (c1 - t1 * T) * T + (c2 - t2 * T);
     }
     __host__ __device__ __forceinline__ int n_keys() const { return n_t * n_t * T * T; }
-    // Morton index of the 4 x 4 sub-cell holding grid line pair (b1, b2) of cell (c1, c2).
+    // sub-cell row of grid line offset o (0 <= o < cell) inside a cell, and the first offset of row s
+    __host__ __device__ __forceinline__ int sub_row(int o) const { return (o * kSubEdge) / cell; }
+    __host__ __device__ __forceinline__ int sub_first(int s) const { return (s * cell + kSubEdge - 1) / kSubEdge; }
+    // Morton index of the sub-cell holding grid line pair (b1, b2) of cell (c1, c2)
     __host__ __device__ __forceinline__ int sub(int b1, int b2, int c1, int c2) const
     {
-        const int s1 = ((b1 - c1 * cell) * 4) / cell, s2 = ((b2 - c2 * cell) * 4) / cell;
-        return ((s2 & 1) | ((s1 & 1) << 1) | ((s2 & 2) << 1) | ((s1 & 2) << 2));
+        return morton_sub(sub_row(b1 - c1 * cell), sub_row(b2 - c2 * cell));
     }
 };
 

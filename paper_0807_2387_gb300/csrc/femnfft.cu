@@ -134,6 +134,7 @@ struct fs_plan {
     bool kahan = true;
     KernelParams kp{};
     double beta[kMaxP] = {0};
+    WindowPoly wpoly{};               // FP32 window polynomials (per tap)
     // device memory
     std::vector<void *> allocs;
     int64_t bytes = 0;
@@ -225,6 +226,59 @@ template <typename real> Window<real> make_window(const fs_plan *pl)
     w.bm = (real)(b * m);
     w.S = (real)(m * b / (1.0 - std::exp(-2.0 * b * m)));
     return w;
+}
+
+// Per-tap polynomial form of the normalised window for the FP32 kernels: for tap a the
+// function frac -> psi(frac + m - 1 - a) on [0, 1) is interpolated at kPolyD + 1 Chebyshev
+// points in FP64 and rewritten in monomials of t = frac - 1/2; the slope polynomial is its
+// exact derivative.
+void build_window_poly(const fs_plan *pl, WindowPoly *wp)
+{
+    const double b = kPi * (2.0 - 1.0 / pl->sigma);
+    const int m = pl->m;
+    const int D = kPolyD, K = kPolyD + 1;
+    auto psi = [&](double x) {
+        const double t = (double)m * m - x * x;
+        if (!(t > 0.0))
+            return 0.0;
+        const double tau = std::sqrt(t);
+        return (double)m * std::sinh(b * tau) / (tau * std::sinh(b * m));
+    };
+    // monomial coefficients of T_n(u), u in [-1, 1]
+    std::vector<std::vector<double>> T(K, std::vector<double>(K, 0.0));
+    T[0][0] = 1.0;
+    if (K > 1)
+        T[1][1] = 1.0;
+    for (int n = 2; n < K; ++n)
+        for (int i = 0; i < K; ++i)
+            T[n][i] = (i > 0 ? 2.0 * T[n - 1][i - 1] : 0.0) - T[n - 2][i];
+    std::memset(wp, 0, sizeof(*wp));
+    for (int a = 0; a < 2 * m; ++a) {
+        const int j = m - 1 - a;
+        std::vector<double> f(K), cheb(K, 0.0), mono(K, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const double u = std::cos(kPi * (k + 0.5) / K);
+            f[k] = psi(0.5 + 0.5 * u + j);
+        }
+        for (int n = 0; n < K; ++n) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k)
+                acc += f[k] * std::cos(kPi * n * (k + 0.5) / K);
+            cheb[n] = acc * (n == 0 ? 1.0 : 2.0) / K;
+        }
+        for (int n = 0; n < K; ++n)
+            for (int i = 0; i < K; ++i)
+                mono[i] += cheb[n] * T[n][i];
+        // u = 2t: coefficient of t^i is 2^i times that of u^i
+        double scale = 1.0;
+        for (int i = 0; i < K; ++i) {
+            wp->c[a][i] = (float)(mono[i] * scale);
+            if (i > 0)
+                wp->d[a][i - 1] = (float)(mono[i] * scale * i);
+            scale *= 2.0;
+        }
+    }
+    (void)D;
 }
 
 template <typename real> NearParams<real> make_near(const fs_plan *pl)
@@ -422,10 +476,11 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         return fail(FS_EINVAL, "cell narrower than eps_I");
     pl->cg.cell = cell;
     pl->cg.n_c = (n_a + cell - 1) / cell;
-    int T = o.tile_cells > 0 ? o.tile_cells : std::max(1, (int)std::lround(32.0 / cell));
+    int T = o.tile_cells > 0 ? o.tile_cells : std::max(1, (int)std::lround(16.0 / cell));
     auto smem_for = [&](int t) {
         const int P = t * cell + 2 * m - 1;
-        return (size_t)kSpreadWarps * P * P * sizeof(real) * ((pl->kahan && sizeof(real) == 4) ? 2 : 1);
+        return (size_t)kSpreadWarps * P * P * sizeof(real) * ((pl->kahan && sizeof(real) == 4) ? 2 : 1) +
+               sizeof(float) * 2 * m * (kPolyD + 1);
     };
     while (T > 1 && smem_for(T) > 160 * 1024)
         --T;
@@ -435,7 +490,7 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     pl->cg.n_t = (pl->cg.n_c + T - 1) / T;
     if ((int64_t)pl->cg.n_keys() * kSub > 4096 * 4096)
         return fail(FS_EINVAL, "too many cells (eps_I too small for this grid)");
-    pl->n_keys = pl->cg.n_keys() * kSub;   // cell keys refined by the 4 x 4 sub-cell index
+    pl->n_keys = pl->cg.n_keys() * kSub;   // cell keys refined by the 8 x 8 sub-cell index
 
     // regularised kernel data
     pl->kp.eps_I = eps_I;
@@ -471,6 +526,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         pl->kp.k_half = std::log(2.0) * inv2pi;
     }
 
+    build_window_poly(pl, &pl->wpoly);
+
     // binning
     FS_TRY(bin_points<real>(pl, src, M, &pl->src_perm, &pl->src_base, &pl->src_frac, &pl->src_pos, &pl->src_pos32,
                             &pl->src_lo32, &pl->src_start));
@@ -499,15 +556,75 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
             FS_CUDA(cudaMemcpy(pl->items, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
     }
 
-    // near-field warp items: at most 32 consecutive targets of one cell
+    // near-field warp items: at most 64 consecutive targets of one cell (two per lane).  A
+    // sub-cell holding 32 or more targets gets items of its own (so its warps' bounding boxes
+    // stay an eighth of a cell wide); sparser sub-cells of the same cell are merged up to 64.
     if (pl->precision == 32) {
+        constexpr int kCap = 64, kOwn = 32;
         std::vector<int> start(pl->n_keys + 1);
         FS_CUDA(cudaMemcpy(start.data(), pl->tgt_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
         std::vector<int2> items;
         for (int key = 0; key < pl->n_keys / kSub; ++key) {
-            const int a = start[key * kSub], b2 = start[(key + 1) * kSub];
-            for (int t0 = a; t0 < b2; t0 += 32)
-                items.push_back(make_int2(t0, std::min(32, b2 - t0)));
+            int open_start = -1, open_count = 0;
+            for (int sub = 0; sub < kSub; ++sub) {
+                const int a = start[key * kSub + sub], c = start[key * kSub + sub + 1] - a;
+                if (c == 0)
+                    continue;
+                if (c >= kOwn) {
+                    if (open_count > 0)
+                        items.push_back(make_int2(open_start, open_count));
+                    open_count = 0;
+                    const int pieces = (c + kCap - 1) / kCap;
+                    for (int i = 0; i < pieces; ++i) {
+                        const int lo = a + (int)((int64_t)c * i / pieces), hi = a + (int)((int64_t)c * (i + 1) / pieces);
+                        items.push_back(make_int2(lo, hi - lo));
+                    }
+                    continue;
+                }
+                if (open_count > 0 && open_count + c > kCap) {
+                    items.push_back(make_int2(open_start, open_count));
+                    open_count = 0;
+                }
+                if (open_count == 0)
+                    open_start = a;
+                open_count += c;   // contiguous: sub-cells of a cell follow each other in the sorted order
+            }
+            if (open_count > 0)
+                items.push_back(make_int2(open_start, open_count));
+        }
+        // largest items first (estimated work: targets x sources in the 3 x 3 cells around the
+        // item's cell), so the heavy warps start early and the tail of the launch stays short
+        {
+            std::vector<int> src_h(pl->n_keys + 1);
+            FS_CUDA(cudaMemcpy(src_h.data(), pl->src_start, sizeof(int) * src_h.size(), cudaMemcpyDeviceToHost));
+            std::vector<int> tkey(pl->n_keys / kSub);
+            std::vector<int64_t> nb(pl->n_keys / kSub, 0);
+            const int nc = pl->cg.n_c;
+            for (int c1 = 0; c1 < nc; ++c1)
+                for (int c2 = 0; c2 < nc; ++c2) {
+                    int64_t acc = 0;
+                    for (int d1 = -1; d1 <= 1; ++d1)
+                        for (int d2 = -1; d2 <= 1; ++d2) {
+                            const int e1 = c1 + d1, e2 = c2 + d2;
+                            if (e1 < 0 || e2 < 0 || e1 >= nc || e2 >= nc)
+                                continue;
+                            const int kk = pl->cg.key(e1, e2);
+                            acc += src_h[(kk + 1) * kSub] - src_h[kk * kSub];
+                        }
+                    nb[pl->cg.key(c1, c2)] = acc;
+                }
+            // the cell of an item: the key whose target range contains its first target
+            std::vector<std::pair<int64_t, int2>> wi;
+            wi.reserve(items.size());
+            size_t key = 0;
+            for (const int2 &it : items) {
+                while (key + 1 < nb.size() && start[(key + 1) * kSub] <= it.x)
+                    ++key;
+                wi.push_back({(int64_t)it.y * nb[key], it});
+            }
+            std::stable_sort(wi.begin(), wi.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+            for (size_t i = 0; i < items.size(); ++i)
+                items[i] = wi[i].second;
         }
         pl->n_near_items = (int64_t)items.size();
         FS_TRY(pl->alloc(&pl->near_items, items.size()));
@@ -618,7 +735,7 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[0], st));
         FS_CUDA(cudaMemsetAsync(pl->grid, 0, (size_t)pl->n_a * pl->pitch * sizeof(real), st));
-        FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w,
+        FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w, pl->wpoly,
                                     (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[1], st));
@@ -634,7 +751,7 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
                                           (real *)pl->grid, pl->pitch, (const C *)pl->tw, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[4], st));
-        FS_CUDA(launch_interp<real>(pl->N, pl->m, pl->tgt_base, pl->tgt_frac, w, (const real *)pl->grid, pl->pitch,
+        FS_CUDA(launch_interp<real>(pl->N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly, (const real *)pl->grid, pl->pitch,
                                     (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[5], st));

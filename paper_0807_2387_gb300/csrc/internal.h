@@ -63,11 +63,11 @@ cudaError_t launch_near_count(const double2 *tgt_pos, const int *tgt_base, int64
 // ---- spreading / interpolation (kernels_spread.cu)
 template <typename real>
 cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
-                          const void *frac, const real *q, Window<real> w, real *grid, int pitch,
-                          int n_a, bool kahan, cudaStream_t st);
+                          const void *frac, const real *q, Window<real> w, const WindowPoly &wp, real *grid,
+                          int pitch, int n_a, bool kahan, cudaStream_t st);
 template <typename real>
 cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w,
-                          const real *grid, int pitch, real n_os, real *phi_s, real *grad_s,
+                          const WindowPoly &wp, const real *grid, int pitch, real n_os, real *phi_s, real *grad_s,
                           cudaStream_t st);
 
 // ---- FFT and spectral multiply (kernels_fft.cu)
@@ -91,7 +91,7 @@ cudaError_t launch_build_mul(const double2 *bhat, int n, const double *c_tab, re
 cudaError_t launch_near64(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
                           const int *src_start, CellGrid cg, const double *q, NearParams<double> np, double *phi_s,
                           double *grad_s, double *coinc, cudaStream_t st);
-// items: (first target, count <= 32) per warp, never spanning two cells
+// items: (first target, count <= 64) per warp, never spanning two cells
 cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
                           const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                           CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,

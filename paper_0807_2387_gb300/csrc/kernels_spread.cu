@@ -30,26 +30,32 @@ template <typename real, int M2, bool KAHAN>
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
                                                               const int *__restrict__ base,
                                                               const real2_t<real> *__restrict__ frac,
-                                                              const real *__restrict__ q, Window<real> w,
+                                                              const real *__restrict__ q, Window<real> w, WindowPoly wp,
                                                               real *__restrict__ grid, int pitch, int n_a)
 {
     constexpr int m = M2 / 2;
     constexpr int TAPS = M2 * M2;
     constexpr int PER = (TAPS + 31) / 32;
     constexpr int PLANES = KAHAN ? 2 : 1;
+    constexpr bool kPoly = sizeof(real) == 4;
     extern __shared__ unsigned char smem_raw[];
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
     const int PP = P * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
-    real *comp = acc + PP;
+    // FP32 window polynomials, one row per tap, after the warp tiles (taps differ across lanes)
+    float *poly = reinterpret_cast<float *>(reinterpret_cast<real *>(smem_raw) + (size_t)kSpreadWarps * PP * PLANES);
+    if (kPoly) {
+        for (int i = threadIdx.x; i < M2 * (kPolyD + 1); i += blockDim.x)
+            poly[i] = wp.c[i / (kPolyD + 1)][i % (kPolyD + 1)];
+    }
     const SpreadItem it = items[blockIdx.x];
     const int t1 = it.tile / cg.n_t, t2 = it.tile - (it.tile / cg.n_t) * cg.n_t;
     const int o1 = t1 * TG - (m - 1), o2 = t2 * TG - (m - 1);
     for (int i = lane; i < PP * PLANES; i += 32)
         acc[i] = real(0);
-    __syncwarp();
+    __syncthreads();
     // this lane's taps: t = lane + 32 i -> (a, b) = (t / 2m, t % 2m)
     int toff[PER];
     int ta[PER], tb[PER];
@@ -62,14 +68,36 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *
     }
     const bool first = lane < M2;
     const int jw = first ? lane : lane - M2;
-    for (int j = it.start + warp; j < it.start + it.count; j += kSpreadWarps) {
-        const int packed = base[j];
-        const real2_t<real> f = frac[j];
+    const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
+    const int end = it.start + it.count;
+    int j = it.start + warp;
+    // software pipeline: the next source's record is in flight while this one is spread
+    int nb = 0;
+    real2_t<real> nf{};
+    real nq = real(0);
+    if (j < end) {
+        nb = base[j];
+        nf = frac[j];
+        nq = q[j];
+    }
+    for (; j < end; j += kSpreadWarps) {
+        const int packed = nb;
+        const real2_t<real> f = nf;
+        const real qj = nq;
+        if (j + kSpreadWarps < end) {
+            nb = base[j + kSpreadWarps];
+            nf = frac[j + kSpreadWarps];
+            nq = q[j + kSpreadWarps];
+        }
         real wv = real(0);
         if (lane < 2 * M2) {
-            wv = kb_value<real>(w, first ? f.x : f.y, m - 1 - jw);
+            const real fr = first ? f.x : f.y;
+            if constexpr (kPoly)
+                wv = poly_eval<kPolyD>(prow, (float)fr - 0.5f);
+            else
+                wv = kb_value<real>(w, fr, m - 1 - jw);
             if (!first)
-                wv *= q[j];
+                wv *= qj;
         }
         real *corner = acc + (base1(packed) - m + 1 - o1) * P + (base2(packed) - m + 1 - o2);
 #pragma unroll
@@ -117,7 +145,7 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *
 // so those widths (and the FP64 path) sum directly.
 template <typename real, int M2>
 __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict__ base,
-                                                const real2_t<real> *__restrict__ frac, Window<real> w,
+                                                const real2_t<real> *__restrict__ frac, Window<real> w, WindowPoly wp,
                                                 const real *__restrict__ grid, int pitch, real n_os,
                                                 real *__restrict__ phi_s, real *__restrict__ grad_s)
 {
@@ -129,10 +157,22 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
     const int packed = base[k];
     const real2_t<real> f = frac[k];
     real w1[M2], d1[M2], w2[M2], d2[M2];
+    if constexpr (sizeof(real) == 4) {
+        // FP32: per-tap window polynomials (coefficients are warp-uniform kernel parameters)
+        const float t1 = (float)f.x - 0.5f, t2 = (float)f.y - 0.5f;
 #pragma unroll
-    for (int a = 0; a < M2; ++a) {
-        kb_value_slope<real>(w, f.x, m - 1 - a, w1[a], d1[a]);
-        kb_value_slope<real>(w, f.y, m - 1 - a, w2[a], d2[a]);
+        for (int a = 0; a < M2; ++a) {
+            w1[a] = poly_eval<kPolyD>(wp.c[a], t1);
+            d1[a] = poly_eval<kPolyD - 1>(wp.d[a], t1);
+            w2[a] = poly_eval<kPolyD>(wp.c[a], t2);
+            d2[a] = poly_eval<kPolyD - 1>(wp.d[a], t2);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < M2; ++a) {
+            kb_value_slope<real>(w, f.x, m - 1 - a, w1[a], d1[a]);
+            kb_value_slope<real>(w, f.y, m - 1 - a, w2[a], d2[a]);
+        }
     }
     const int row0 = base1(packed) - m + 1;
     const int col0 = base2(packed) - m + 1;
@@ -166,34 +206,36 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
 
 template <typename real, int M2>
 cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const int *base, const void *frac,
-                     const real *q, Window<real> w, real *grid, int pitch, int n_a, bool kahan, cudaStream_t st)
+                     const real *q, Window<real> w, const WindowPoly &wp, real *grid, int pitch, int n_a, bool kahan,
+                     cudaStream_t st)
 {
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const size_t smem = (size_t)kSpreadWarps * P * P * sizeof(real) * (kahan ? 2 : 1);
+    const size_t smem = (size_t)kSpreadWarps * P * P * sizeof(real) * (kahan ? 2 : 1) +
+                        sizeof(float) * M2 * (kPolyD + 1);
     const real2_t<real> *fr = (const real2_t<real> *)frac;
     if (kahan) {
         auto kern = k_spread<real, M2, true>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
+        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, wp, grid, pitch, n_a);
     } else {
         auto kern = k_spread<real, M2, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, grid, pitch, n_a);
+        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, wp, grid, pitch, n_a);
     }
     return cudaGetLastError();
 }
 
 template <typename real, int M2>
-cudaError_t interp_m(int64_t N, const int *base, const void *frac, Window<real> w, const real *grid, int pitch,
-                     real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+cudaError_t interp_m(int64_t N, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
+                     const real *grid, int pitch, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((N + 255) / 256);
-    k_interp<real, M2><<<blocks, 256, 0, st>>>(N, base, (const real2_t<real> *)frac, w, grid, pitch, n_os, phi_s,
+    k_interp<real, M2><<<blocks, 256, 0, st>>>(N, base, (const real2_t<real> *)frac, w, wp, grid, pitch, n_os, phi_s,
                                                 grad_s);
     return cudaGetLastError();
 }
@@ -202,48 +244,52 @@ cudaError_t interp_m(int64_t N, const int *base, const void *frac, Window<real> 
 
 template <typename real>
 cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base, const void *frac,
-                          const real *q, Window<real> w, real *grid, int pitch, int n_a, bool kahan, cudaStream_t st)
+                          const real *q, Window<real> w, const WindowPoly &wp, real *grid, int pitch, int n_a,
+                          bool kahan, cudaStream_t st)
 {
     if (n_items <= 0)
         return cudaSuccess;
     const bool comp = kahan && sizeof(real) == 4;
     switch (m) {
-    case 2: return spread_m<real, 4>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
-    case 3: return spread_m<real, 6>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
-    case 4: return spread_m<real, 8>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
-    case 5: return spread_m<real, 10>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
-    case 6: return spread_m<real, 12>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
-    case 7: return spread_m<real, 14>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
-    case 8: return spread_m<real, 16>(items, n_items, cg, base, frac, q, w, grid, pitch, n_a, comp, st);
+    case 2: return spread_m<real, 4>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
+    case 3: return spread_m<real, 6>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
+    case 4: return spread_m<real, 8>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
+    case 5: return spread_m<real, 10>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
+    case 6: return spread_m<real, 12>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
+    case 7: return spread_m<real, 14>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
+    case 8: return spread_m<real, 16>(items, n_items, cg, base, frac, q, w, wp, grid, pitch, n_a, comp, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename real>
-cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w, const real *grid,
-                          int pitch, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
+                          const real *grid, int pitch, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
     switch (m) {
-    case 2: return interp_m<real, 4>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
-    case 3: return interp_m<real, 6>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
-    case 4: return interp_m<real, 8>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
-    case 5: return interp_m<real, 10>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
-    case 6: return interp_m<real, 12>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
-    case 7: return interp_m<real, 14>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
-    case 8: return interp_m<real, 16>(N, base, frac, w, grid, pitch, n_os, phi_s, grad_s, st);
+    case 2: return interp_m<real, 4>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 3: return interp_m<real, 6>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 4: return interp_m<real, 8>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 5: return interp_m<real, 10>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 6: return interp_m<real, 12>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 7: return interp_m<real, 14>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 8: return interp_m<real, 16>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template cudaError_t launch_spread<float>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
-                                          const float *, Window<float>, float *, int, int, bool, cudaStream_t);
+                                          const float *, Window<float>, const WindowPoly &, float *, int, int, bool,
+                                          cudaStream_t);
 template cudaError_t launch_spread<double>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
-                                           const double *, Window<double>, double *, int, int, bool, cudaStream_t);
-template cudaError_t launch_interp<float>(int64_t, int, const int *, const void *, Window<float>, const float *, int,
-                                          float, float *, float *, cudaStream_t);
-template cudaError_t launch_interp<double>(int64_t, int, const int *, const void *, Window<double>, const double *,
-                                           int, double, double *, double *, cudaStream_t);
+                                           const double *, Window<double>, const WindowPoly &, double *, int, int,
+                                           bool, cudaStream_t);
+template cudaError_t launch_interp<float>(int64_t, int, const int *, const void *, Window<float>, const WindowPoly &,
+                                          const float *, int, float, float *, float *, cudaStream_t);
+template cudaError_t launch_interp<double>(int64_t, int, const int *, const void *, Window<double>,
+                                           const WindowPoly &, const double *, int, double, double *, double *,
+                                           cudaStream_t);
 
 }  // namespace fs
