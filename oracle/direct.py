@@ -46,6 +46,8 @@ def _lib():
             lib.o1_direct.argtypes = [dp, ctypes.c_long, dp, ctypes.c_long, dp, dp, dp, dp]
             lib.o1_direct.restype = None
             lib.o1_threads.restype = ctypes.c_int
+            lib.o1_adjoint.argtypes = [dp, ctypes.c_long, dp, ctypes.c_long, dp, dp, dp, dp, dp, dp]
+            lib.o1_adjoint.restype = None
             _handle = lib
     return _handle
 
@@ -77,3 +79,18 @@ def direct_sum(tgt, src, q, field: bool = True, hessian: bool = False):
     if hessian:
         out.append(hes)
     return tuple(out) if len(out) > 1 else phi
+
+
+def direct_adjoint(tgt, src, q, gphi, gH):
+    """Gradients of L(phi, H) through the direct sum: (dL/dq (M,), dL/dy (M,2), dL/dx (N,2))."""
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    gphi = np.ascontiguousarray(gphi, dtype=np.float64)
+    gH = np.ascontiguousarray(gH, dtype=np.float64)
+    dq = np.zeros(len(src))
+    dy = np.zeros((len(src), 2))
+    dx = np.zeros((len(tgt), 2))
+    _lib().o1_adjoint(_ptr(tgt), len(tgt), _ptr(src), len(src), _ptr(q), _ptr(gphi), _ptr(gH),
+                      _ptr(dq), _ptr(dy), _ptr(dx))
+    return dq, dy, dx

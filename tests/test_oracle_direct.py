@@ -125,3 +125,29 @@ def test_field_and_hessian_central_differences():
     assert np.allclose(hes[:, 0], -dH[0][:, 0], rtol=1e-6, atol=1e-8)
     assert np.allclose(hes[:, 1], -dH[0][:, 1], rtol=1e-6, atol=1e-8)
     assert np.allclose(hes[:, 2], -dH[1][:, 1], rtol=1e-6, atol=1e-8)
+
+
+def test_adjoint_against_finite_differences():
+    """o1_adjoint is the gradient of L = <gphi, phi> + <gH, H> of the direct sum (central differences)."""
+    rng = np.random.default_rng(6)
+    x = rng.uniform(-1, 1, (30, 2))
+    y = rng.uniform(-1, 1, (25, 2))
+    q = rng.standard_normal(25)
+    gphi = rng.standard_normal(30)
+    gH = rng.standard_normal((30, 2))
+
+    def loss(xx, yy, qq):
+        phi, H = D.direct_sum(xx, yy, qq)
+        return float(gphi @ phi + np.sum(gH * H))
+
+    dq, dy, dx = D.direct_adjoint(x, y, q, gphi, gH)
+    # linear in q: exact
+    e = np.zeros(25)
+    e[3] = 1.0
+    assert abs(loss(x, y, q + e) - loss(x, y, q) - dq[3]) < 1e-10 * max(1.0, abs(dq[3]))
+    h = 1e-6
+    for _ in range(6):
+        vx, vy = rng.standard_normal(x.shape), rng.standard_normal(y.shape)
+        fd = (loss(x + h * vx, y + h * vy, q) - loss(x - h * vx, y - h * vy, q)) / (2 * h)
+        an = float(np.sum(dx * vx) + np.sum(dy * vy))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
