@@ -205,6 +205,27 @@ fs_status fs_eval_field(fs_plan *plan, void *phi, void *H, fs_dtype dtype);
 fs_status fs_solve_host(fs_plan *plan, const void *q, fs_dtype q_dtype, int nrhs,
                         void *phi, void *H, fs_dtype out_dtype);
 
+/*
+ * Adjoint: gradients of a loss L(phi, H) through the fast summation, for every charge
+ * vector set last (the paper has no adjoint; it is the transpose of the steps above).
+ * With gphi = dL/dphi and gH = dL/dH and
+ *     A(y) = sum_i gphi_i G(x_i - y) - sum_i gH_i . grad G(x_i - y),
+ *   dq   = dL/dq_j   = A(y_j)                          (the transposed fast summation:
+ *                                                       spread gphi, gH at the targets with the
+ *                                                       window and its slope, same spectral
+ *                                                       multiply, interpolate at the sources)
+ *   dsrc = dL/dy_j   = q_j grad A(y_j)
+ *   dtgt = dL/dx_i   = -gphi_i H(x_i) - Hess phi(x_i) gH_i   (the forward grid is recomputed and
+ *                                                       interpolated with the window's curvature)
+ * The torus scale s is held fixed (gradients through R_max are not taken).
+ *  g_phi [device] (nrhs, N) or NULL (zero);  g_H [device] (nrhs, N, 2) or NULL (zero);
+ *  in_dtype FS_F32|FS_F64 for both; dq (nrhs, M), dsrc (nrhs, M, 2), dtgt (nrhs, N, 2) [device]
+ *  of out_dtype, each may be NULL (not computed).  The first call allocates the adjoint
+ *  workspace.
+ */
+fs_status fs_adjoint(fs_plan *plan, const void *g_phi, const void *g_H, fs_dtype in_dtype, void *dq,
+                     void *dsrc, void *dtgt, fs_dtype out_dtype);
+
 /* Wait for the plan's stream and report device-side errors (FS_EDOMAIN, FS_ETIMEOUT). */
 fs_status fs_sync_status(fs_plan *plan);
 

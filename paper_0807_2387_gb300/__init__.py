@@ -24,8 +24,8 @@ from ._native import (FS_F32, FS_F64, FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FastSumE
 __all__ = [
     "FastSum", "FastSumError", "NativeLibraryMissing", "FS_F32", "FS_F64", "FS_FLAG_NO_KAHAN",
     "FS_FLAG_TIMING", "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization",
-    "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host",
-    "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path",
+    "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
+    "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path", "FastSumFn",
 ]
 
 
@@ -147,6 +147,20 @@ def fs_eval_field(plan, phi, H):
         raise TypeError("phi and H must share a dtype")
     check(load().fs_eval_field(plan, _dev_ptr(phi, None, "phi"), _dev_ptr(H, None, "H"), _dtype_code(dt)),
           "fs_eval_field")
+
+
+def fs_adjoint(plan, g_phi, g_H, dq=None, dsrc=None, dtgt=None):
+    """Gradients of L(phi, H) for the charges set last: g_phi (nrhs,N) or None, g_H (nrhs,N,2) or None;
+    outputs dq (nrhs,M), dsrc (nrhs,M,2), dtgt (nrhs,N,2) (any may be None; all of one dtype)."""
+    ins = [t for t in (g_phi, g_H) if t is not None]
+    outs = [t for t in (dq, dsrc, dtgt) if t is not None]
+    if not ins or not outs:
+        raise ValueError("need at least one loss gradient and one output")
+    if any(t.dtype != ins[0].dtype for t in ins) or any(t.dtype != outs[0].dtype for t in outs):
+        raise TypeError("inputs share one dtype, outputs share one dtype")
+    check(load().fs_adjoint(plan, _dev_ptr(g_phi, None, "g_phi"), _dev_ptr(g_H, None, "g_H"),
+                            _dtype_code(ins[0].dtype), _dev_ptr(dq, None, "dq"), _dev_ptr(dsrc, None, "dsrc"),
+                            _dev_ptr(dtgt, None, "dtgt"), _dtype_code(outs[0].dtype)), "fs_adjoint")
 
 
 def fs_solve_host(plan, q, phi, H):
@@ -275,6 +289,21 @@ class FastSum:
             return (phi[0] if with_phi else None), H[0]
         return phi, H
 
+    def adjoint(self, g_phi=None, g_H=None, want_q=True, want_src=False, want_tgt=False, dtype=None):
+        """(dL/dq, dL/dsrc, dL/dtgt) for L(phi, H) with g_phi = dL/dphi, g_H = dL/dH (None where not wanted)."""
+        torch = _torch()
+        ref = g_phi if g_phi is not None else g_H
+        dtype = dtype or ref.dtype
+        nr = self.nrhs
+        shape = (lambda *d: (nr,) + d) if nr > 1 else (lambda *d: d)
+        M, N = self.info["n_src"], self.info["n_tgt"]
+        dq = torch.empty(shape(M), dtype=dtype, device=self.device) if want_q else None
+        dsrc = torch.empty(shape(M, 2), dtype=dtype, device=self.device) if want_src else None
+        dtgt = torch.empty(shape(N, 2), dtype=dtype, device=self.device) if want_tgt else None
+        fs_adjoint(self._h, None if g_phi is None else g_phi.contiguous(),
+                   None if g_H is None else g_H.contiguous(), dq, dsrc, dtgt)
+        return dq, dsrc, dtgt
+
     def sync(self):
         fs_sync_status(self._h)
 
@@ -291,3 +320,53 @@ class FastSum:
             self.close()
         except Exception:
             pass
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class _FastSumFn(torch.autograd.Function):
+        """(phi, H) = FastSumFn.apply(q, src, tgt, plan) with a backward through fs_adjoint.
+
+        ``plan`` must have been built on the same positions ``src``/``tgt``; their
+        gradients are returned (the plan is not rebuilt when positions change).  For
+        sources = targets pass the same tensor twice and autograd adds both parts.
+        """
+
+        @staticmethod
+        def forward(ctx, q, src, tgt, plan):
+            plan.set_charges(q.detach().contiguous())
+            phi, H = plan.field(dtype=q.dtype)
+            ctx.plan = plan
+            ctx.save_for_backward(q)
+            return phi, H
+
+        @staticmethod
+        def backward(ctx, g_phi, g_H):
+            (q,) = ctx.saved_tensors
+            plan = ctx.plan
+            plan.set_charges(q.detach().contiguous())
+            want_q, want_src, want_tgt = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            if not (want_q or want_src or want_tgt):
+                return None, None, None, None
+            if g_phi is None:
+                g_phi = torch.zeros(plan.info["n_tgt"], dtype=q.dtype, device=q.device)
+            if g_H is None:
+                g_H = torch.zeros((plan.info["n_tgt"], 2), dtype=q.dtype, device=q.device)
+            dq, dsrc, dtgt = plan.adjoint(g_phi.to(q.dtype), g_H.to(q.dtype), want_q=True,
+                                          want_src=want_src, want_tgt=want_tgt, dtype=q.dtype)
+            return (dq if want_q else None), dsrc, dtgt, None
+
+    return _FastSumFn
+
+
+class _LazyFn:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _make_autograd()
+        return _LazyFn._fn.apply(*args)
+
+
+FastSumFn = _LazyFn()

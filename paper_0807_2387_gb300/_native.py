@@ -16,7 +16,7 @@ FS_FLAG_NO_KAHAN, FS_FLAG_TIMING = 1, 2
 
 EXPORTED = (
     "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization", "fs_set_magnetization_static",
-    "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host",
+    "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "fs_last_error",
     "fs_version",
 )
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
         "fs_eval_potential": [P, P, I32],
         "fs_eval_field": [P, P, P, I32],
         "fs_solve_host": [P, P, I32, I32, P, P, I32],
+        "fs_adjoint": [P, P, P, I32, P, P, P, I32],
         "fs_sync_status": [P],
         "fs_plan_info": [P, ctypes.POINTER(FsInfo)],
         "fs_stage_times": [P, ctypes.POINTER(ctypes.c_double), I32],

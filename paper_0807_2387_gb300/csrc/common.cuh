@@ -120,7 +120,54 @@ constexpr int kPolyD = 12;
 struct WindowPoly {
     float c[2 * kMaxM][kPolyD + 1];   // value coefficients, c[a][i] multiplies t^i
     float d[2 * kMaxM][kPolyD];       // slope coefficients (d/dx), d[a][i] multiplies t^i
+    float e[2 * kMaxM][kPolyD - 1];   // curvature coefficients (d^2/dx^2), e[a][i] multiplies t^i
 };
+
+// psi, psi' and psi'' at x = j + frac (closed form, used by the FP64 path):
+//   psi'' = -b^2 S e^{z - bm} [F(z) - b^2 x^2 E(z)],   E(z) = ((z^2-3z+3) - e^{-2z}(z^2+3z+3)) / z^5
+// (E = 2 e^{-z} (f'(z)/z) with f(z) = (z cosh z - sinh z)/z^3; series 2 e^{-z}(1/15 + z^2/210 + ...) near 0).
+template <typename real>
+__device__ __forceinline__ real kb_curv_factor(real z)
+{
+    if (z < real(1)) {
+        // (2k-2)(2k)/(2k+1)! for k = 2..11
+        const real z2 = z * z;
+        real acc = real(20.0 * 22.0 / 25852016738884976640000.0);
+        acc = acc * z2 + real(18.0 * 20.0 / 51090942171709440000.0);
+        acc = acc * z2 + real(16.0 * 18.0 / 121645100408832000.0);
+        acc = acc * z2 + real(14.0 * 16.0 / 355687428096000.0);
+        acc = acc * z2 + real(12.0 * 14.0 / 1307674368000.0);
+        acc = acc * z2 + real(10.0 * 12.0 / 6227020800.0);
+        acc = acc * z2 + real(8.0 * 10.0 / 39916800.0);
+        acc = acc * z2 + real(6.0 * 8.0 / 362880.0);
+        acc = acc * z2 + real(4.0 * 6.0 / 5040.0);
+        acc = acc * z2 + real(2.0 * 4.0 / 120.0);
+        return real(2) * fexp<real>(-z) * acc;
+    }
+    const real e = fexp<real>(real(-2) * z);
+    const real z2 = z * z;
+    return ((z2 - real(3) * z + real(3)) - e * (z2 + real(3) * z + real(3))) / (z2 * z2 * z);
+}
+
+template <typename real>
+__device__ __forceinline__ void kb_value_slope_curv(const Window<real> &w, real frac, int j, real &v, real &d,
+                                                    real &dd)
+{
+    const real t1 = (w.m - real(j)) - frac;
+    const real t2 = (w.m + real(j)) + frac;
+    if (!(t1 > real(0)) || !(t2 > real(0))) {
+        v = d = dd = real(0);
+        return;
+    }
+    const real tau = fsqrt<real>(t1 * t2);
+    const real x = real(j) + frac;
+    const real z = w.b * tau;
+    const real e = w.S * fexp<real>(-w.b * x * x / (tau + w.m));
+    const real F = kb_slope<real>(z);
+    v = e * (-fexpm1<real>(real(-2) * z)) / z;
+    d = -x * w.b * w.b * e * F;
+    dd = -w.b * w.b * e * (F - w.b * w.b * x * x * kb_curv_factor<real>(z));
+}
 
 template <int DEG> __device__ __forceinline__ float poly_eval(const float *c, float t)
 {

@@ -148,6 +148,12 @@ struct fs_plan {
     int *src_start = nullptr, *tgt_start = nullptr;
     SpreadItem *items = nullptr;
     int n_items = 0;
+    SpreadItem *tgt_items = nullptr;  // adjoint: spreading at the targets
+    int n_tgt_items = 0;
+    // adjoint workspace (allocated by the first fs_adjoint call)
+    void *adj_c = nullptr, *adj_dn = nullptr, *adj_df = nullptr;
+    void *adj_a = nullptr, *adj_ga = nullptr, *adj_cg = nullptr, *adj_hess = nullptr;
+    double *adj_gsum = nullptr;
     int2 *near_items = nullptr;       // FP32 near field: (first target, count <= 32) per warp
     int64_t n_near_items = 0;
     void *mul = nullptr, *tw = nullptr;
@@ -275,6 +281,8 @@ void build_window_poly(const fs_plan *pl, WindowPoly *wp)
             wp->c[a][i] = (float)(mono[i] * scale);
             if (i > 0)
                 wp->d[a][i - 1] = (float)(mono[i] * scale * i);
+            if (i > 1)
+                wp->e[a][i - 2] = (float)(mono[i] * scale * i * (i - 1));
             scale *= 2.0;
         }
     }
@@ -538,10 +546,12 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     if (dev_status != 0)
         return fail(FS_EDOMAIN, "a point fell outside the admissible radius after scaling");
 
-    // spreading work items: tiles split into slices of at most kSpreadChunk sources
-    {
+    // spreading work items: tiles split into slices of at most kSpreadChunk points (sources
+    // for the forward spread, targets for the adjoint one)
+    for (int side = 0; side < 2; ++side) {
         std::vector<int> start(pl->n_keys + 1);
-        FS_CUDA(cudaMemcpy(start.data(), pl->src_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
+        FS_CUDA(cudaMemcpy(start.data(), side == 0 ? pl->src_start : pl->tgt_start, sizeof(int) * start.size(),
+                           cudaMemcpyDeviceToHost));
         std::vector<SpreadItem> items;
         const int TT = T * T * kSub;
         const int n_tiles = pl->cg.n_t * pl->cg.n_t;
@@ -550,10 +560,11 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
             for (int s0 = a; s0 < b2; s0 += kSpreadChunk)
                 items.push_back(SpreadItem{t, s0, std::min(kSpreadChunk, b2 - s0), 0});
         }
-        pl->n_items = (int)items.size();
-        FS_TRY(pl->alloc(&pl->items, items.size()));
+        SpreadItem **dst = side == 0 ? &pl->items : &pl->tgt_items;
+        (side == 0 ? pl->n_items : pl->n_tgt_items) = (int)items.size();
+        FS_TRY(pl->alloc(dst, items.size()));
         if (!items.empty())
-            FS_CUDA(cudaMemcpy(pl->items, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
+            FS_CUDA(cudaMemcpy(*dst, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
     }
 
     // near-field warp items: at most 64 consecutive targets of one cell (two per lane).  A
@@ -830,6 +841,86 @@ fs_status boundary_edges(const std::vector<int> &tris, int64_t Nt, int64_t Nv, s
     return FS_OK;
 }
 
+// Far-field pipeline on the plan's grid: spread (given launcher) -> FFT rows -> columns x mul -> inverse rows.
+template <typename real> fs_status spectral_pipeline(fs_plan *pl)
+{
+    using C = typename Cplx<real>::type;
+    cudaStream_t st = pl->stream;
+    FS_CUDA(launch_fft_rows_fwd<real>((const real *)pl->grid, pl->pitch, pl->n_a, pl->n_os, pl->n / 2, (C *)pl->spec,
+                                      pl->ld, (const C *)pl->tw, st));
+    FS_CUDA(launch_fft_cols<real>((C *)pl->spec, pl->ld, pl->n_a, pl->n_os, pl->n, (const real *)pl->mul,
+                                  (const C *)pl->tw, st));
+    FS_CUDA(launch_fft_rows_inv<real>((const C *)pl->spec, pl->ld, pl->n_a, pl->n_os, pl->n / 2, (real *)pl->grid,
+                                      pl->pitch, (const C *)pl->tw, st));
+    return FS_OK;
+}
+
+template <typename real>
+fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in_dtype, void *dq, void *dsrc,
+                    void *dtgt, fs_dtype out_dtype)
+{
+    cudaStream_t st = pl->stream;
+    const int64_t M = pl->M, N = pl->N;
+    if (!pl->adj_c) {
+        FS_TRY(pl->alloc_bytes(&pl->adj_c, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
+        FS_TRY(pl->alloc_bytes(&pl->adj_dn, (size_t)std::max<int64_t>(N, 1) * 2 * sizeof(real)));
+        FS_TRY(pl->alloc_bytes(&pl->adj_df, (size_t)std::max<int64_t>(N, 1) * 2 * sizeof(real)));
+        FS_TRY(pl->alloc_bytes(&pl->adj_a, (size_t)std::max<int64_t>(M, 1) * sizeof(real)));
+        FS_TRY(pl->alloc_bytes(&pl->adj_ga, (size_t)std::max<int64_t>(M, 1) * 2 * sizeof(real)));
+        FS_TRY(pl->alloc_bytes(&pl->adj_cg, (size_t)std::max<int64_t>(M, 1) * sizeof(real)));
+        FS_TRY(pl->alloc_bytes(&pl->adj_hess, (size_t)std::max<int64_t>(N, 1) * 3 * sizeof(real)));
+        FS_TRY(pl->alloc(&pl->adj_gsum, 1));
+    }
+    const Window<real> w = make_window<real>(pl);
+    const NearParams<real> np = make_near<real>(pl);
+    const double shift = std::log(pl->s) / (2.0 * kPi);
+    const size_t isz = in_dtype == FS_F64 ? 8 : 4, osz = out_dtype == FS_F64 ? 8 : 4;
+    const size_t grid_bytes = (size_t)pl->n_a * pl->pitch * sizeof(real);
+    for (int r = 0; r < pl->nrhs; ++r) {
+        const real *q = (const real *)pl->q_sorted + (int64_t)r * M;
+        const void *gp = g_phi ? (const unsigned char *)g_phi + (size_t)r * N * isz : nullptr;
+        const void *gh = g_H ? (const unsigned char *)g_H + (size_t)r * N * 2 * isz : nullptr;
+        if (dtgt) {
+            // forward field and its Hessian at the targets (the grid is recomputed, not stored)
+            FS_CUDA(cudaMemsetAsync(pl->grid, 0, grid_bytes, st));
+            FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w,
+                                        pl->wpoly, (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
+            FS_TRY(spectral_pipeline<real>(pl));
+            FS_CUDA(launch_interp_hess<real>(N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly, (const real *)pl->grid,
+                                             pl->pitch, (real)pl->n_os, (real *)pl->grad_s, (real *)pl->adj_hess, st));
+            FS_CUDA(launch_near_hess<real>(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, q, np,
+                                           (real *)pl->grad_s, (real *)pl->adj_hess, st));
+        }
+        FS_CUDA(cudaMemsetAsync(pl->adj_gsum, 0, sizeof(double), st));
+        FS_CUDA(launch_gather_adj<real>(N, pl->tgt_perm, gp, gh, in_dtype == FS_F64, pl->s, (double)pl->n_os,
+                                        (real *)pl->adj_c, pl->adj_dn, pl->adj_df, pl->adj_gsum, st));
+        if (dq || dsrc) {
+            FS_CUDA(cudaMemsetAsync(pl->grid, 0, grid_bytes, st));
+            FS_CUDA(launch_spread_dip<real>(pl->tgt_items, pl->n_tgt_items, pl->cg, pl->m, pl->tgt_base, pl->tgt_frac,
+                                            (const real *)pl->adj_c, pl->adj_df, w, pl->wpoly, (real *)pl->grid,
+                                            pl->pitch, pl->n_a, pl->kahan, st));
+            FS_TRY(spectral_pipeline<real>(pl));
+            FS_CUDA(launch_interp<real>(M, pl->m, pl->src_base, pl->src_frac, w, pl->wpoly, (const real *)pl->grid,
+                                        pl->pitch, (real)pl->n_os, (real *)pl->adj_a, (real *)pl->adj_ga, st));
+            FS_CUDA(launch_near_adj<real>(M, pl->src_base, pl->src_pos, pl->tgt_pos, pl->tgt_start, pl->cg,
+                                          (const real *)pl->adj_c, pl->adj_dn, np, (real *)pl->adj_a,
+                                          (real *)pl->adj_ga, (real *)pl->adj_cg, st));
+            void *o_dq = dq ? (unsigned char *)dq + (size_t)r * M * osz : nullptr;
+            void *o_dy = dsrc ? (unsigned char *)dsrc + (size_t)r * M * 2 * osz : nullptr;
+            FS_CUDA(launch_adj_finish_src<real>(M, pl->src_perm, (const real *)pl->adj_a, (const real *)pl->adj_ga,
+                                                (const real *)pl->adj_cg, q, shift, pl->adj_gsum, pl->s, o_dq, o_dy,
+                                                out_dtype == FS_F64, st));
+        }
+        if (dtgt) {
+            void *o_dx = (unsigned char *)dtgt + (size_t)r * N * 2 * osz;
+            FS_CUDA(launch_adj_finish_tgt<real>(N, pl->tgt_perm, (const real *)pl->grad_s,
+                                                (const real *)pl->adj_hess, (const real *)pl->adj_c, pl->adj_dn, pl->s,
+                                                o_dx, out_dtype == FS_F64, st));
+        }
+    }
+    return FS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1042,6 +1133,22 @@ fs_status fs_solve_host(fs_plan *plan, const void *q, fs_dtype q_dtype, int nrhs
         FS_CUDA(cudaMemcpyAsync(H, plan->d_H_stage, 2 * ob, cudaMemcpyDeviceToHost, st));
     FS_CUDA(cudaStreamSynchronize(st));
     return fs_sync_status(plan);
+}
+
+fs_status fs_adjoint(fs_plan *plan, const void *g_phi, const void *g_H, fs_dtype in_dtype, void *dq, void *dsrc,
+                     void *dtgt, fs_dtype out_dtype)
+{
+    g_last_error.clear();
+    FS_TRY(check_plan(plan));
+    FS_TRY(check_dtype(in_dtype));
+    FS_TRY(check_dtype(out_dtype));
+    if (plan->nrhs < 1)
+        return fail(FS_EINVAL, "charges not set");
+    if (!dq && !dsrc && !dtgt)
+        return fail(FS_EINVAL, "no gradient requested");
+    if (plan->precision == 64)
+        return adjoint_t<double>(plan, g_phi, g_H, in_dtype, dq, dsrc, dtgt, out_dtype);
+    return adjoint_t<float>(plan, g_phi, g_H, in_dtype, dq, dsrc, dtgt, out_dtype);
 }
 
 fs_status fs_sync_status(fs_plan *plan)

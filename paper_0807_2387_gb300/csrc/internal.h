@@ -70,6 +70,15 @@ cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, W
                           const WindowPoly &wp, const real *grid, int pitch, real n_os, real *phi_s, real *grad_s,
                           cudaStream_t st);
 
+template <typename real>
+cudaError_t launch_spread_dip(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
+                              const void *frac, const real *cq, const void *dq, Window<real> w, const WindowPoly &wp,
+                              real *grid, int pitch, int n_a, bool kahan, cudaStream_t st);
+template <typename real>
+cudaError_t launch_interp_hess(int64_t N, int m, const int *base, const void *frac, Window<real> w,
+                               const WindowPoly &wp, const real *grid, int pitch, real n_os, real *grad_s,
+                               real *hess_s, cudaStream_t st);
+
 // ---- FFT and spectral multiply (kernels_fft.cu)
 template <typename real>
 cudaError_t launch_fft_rows_fwd(const real *grid, int pitch, int n_a, int L, int n_half,
@@ -100,6 +109,26 @@ template <typename real>
 cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, const real *coinc,
                              const int *perm, double shift, const double *q_sum, double s, void *phi_out,
                              void *H_out, int out_is_f64, cudaStream_t st);
+
+// ---- adjoint (kernels_adjoint.cu)
+template <typename real>
+cudaError_t launch_gather_adj(int64_t N, const int *perm, const void *gphi, const void *gH, int in_f64, double s,
+                              double n_os, real *c, void *dn, void *df, double *gsum, cudaStream_t st);
+template <typename real>
+cudaError_t launch_near_adj(int64_t M, const int *src_base, const double2 *src_pos, const double2 *tgt_pos,
+                            const int *tgt_start, CellGrid cg, const real *c, const void *dn, NearParams<real> np,
+                            real *a_s, real *ga_s, real *cg_s, cudaStream_t st);
+template <typename real>
+cudaError_t launch_near_hess(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
+                             const int *src_start, CellGrid cg, const real *q, NearParams<real> np, real *grad_s,
+                             real *hess_s, cudaStream_t st);
+template <typename real>
+cudaError_t launch_adj_finish_src(int64_t M, const int *perm, const real *a_s, const real *ga_s, const real *cg_s,
+                                  const real *q, double shift, const double *gsum, double s, void *dq, void *dy,
+                                  int out_f64, cudaStream_t st);
+template <typename real>
+cudaError_t launch_adj_finish_tgt(int64_t N, const int *perm, const real *grad_s, const real *hess_s, const real *c,
+                                  const void *dn, double s, void *dx, int out_f64, cudaStream_t st);
 
 // ---- FEM charge assembly (kernels_fem.cu)
 cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,

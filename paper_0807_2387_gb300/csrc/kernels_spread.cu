@@ -204,6 +204,185 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
     grad_s[2 * k + 1] = n_os * g2;
 }
 
+// Adjoint spreading at the targets: each point carries a monopole c and a dipole d (2-vector)
+// and adds c psi(x1) psi(x2) + d1 psi'(x1) psi(x2) + d2 psi(x1) psi'(x2) at the taps x = u - k,
+// the transpose of interpolating phi and grad phi with the same taps.  Same warp-per-point
+// organisation as k_spread (lanes evaluate one value/slope pair each, lanes own taps).
+template <typename real, int M2, bool KAHAN>
+__global__ void __launch_bounds__(kSpreadWarps * 32) k_spread_dip(const SpreadItem *__restrict__ items, CellGrid cg,
+                                                                  const int *__restrict__ base,
+                                                                  const real2_t<real> *__restrict__ frac,
+                                                                  const real *__restrict__ cq,
+                                                                  const real2_t<real> *__restrict__ dq, Window<real> w,
+                                                                  WindowPoly wp, real *__restrict__ grid, int pitch,
+                                                                  int n_a)
+{
+    constexpr int m = M2 / 2;
+    constexpr int TAPS = M2 * M2;
+    constexpr int PER = (TAPS + 31) / 32;
+    constexpr int PLANES = KAHAN ? 2 : 1;
+    constexpr bool kPoly = sizeof(real) == 4;
+    extern __shared__ unsigned char smem_raw[];
+    const int TG = cg.T * cg.cell;
+    const int P = TG + M2 - 1;
+    const int PP = P * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
+    float *poly = reinterpret_cast<float *>(reinterpret_cast<real *>(smem_raw) + (size_t)kSpreadWarps * PP * PLANES);
+    if (kPoly) {
+        for (int i = threadIdx.x; i < M2 * (kPolyD + 1); i += blockDim.x)
+            poly[i] = wp.c[i / (kPolyD + 1)][i % (kPolyD + 1)];
+        for (int i = threadIdx.x; i < M2 * kPolyD; i += blockDim.x)
+            poly[M2 * (kPolyD + 1) + i] = wp.d[i / kPolyD][i % kPolyD];
+    }
+    const SpreadItem it = items[blockIdx.x];
+    const int t1 = it.tile / cg.n_t, t2 = it.tile - (it.tile / cg.n_t) * cg.n_t;
+    const int o1 = t1 * TG - (m - 1), o2 = t2 * TG - (m - 1);
+    for (int i = lane; i < PP * PLANES; i += 32)
+        acc[i] = real(0);
+    __syncthreads();
+    int toff[PER], ta[PER], tb[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int t = lane + 32 * i;
+        ta[i] = t < TAPS ? t / M2 : 0;
+        tb[i] = t < TAPS ? t - (t / M2) * M2 : 0;
+        toff[i] = ta[i] * P + tb[i];
+    }
+    const bool first = lane < M2;
+    const int jw = first ? lane : lane - M2;
+    const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
+    const float *drow = poly + M2 * (kPolyD + 1) + (lane < 2 * M2 ? jw : 0) * kPolyD;
+    for (int j = it.start + warp; j < it.start + it.count; j += kSpreadWarps) {
+        const int packed = base[j];
+        const real2_t<real> f = frac[j];
+        const real c = cq[j];
+        const real2_t<real> d = dq[j];
+        real wv = real(0), wd = real(0);
+        if (lane < 2 * M2) {
+            const real fr = first ? f.x : f.y;
+            if constexpr (kPoly) {
+                wv = poly_eval<kPolyD>(prow, (float)fr - 0.5f);
+                wd = poly_eval<kPolyD - 1>(drow, (float)fr - 0.5f);
+            } else {
+                kb_value_slope<real>(w, fr, m - 1 - jw, wv, wd);
+            }
+        }
+        real *corner = acc + (base1(packed) - m + 1 - o1) * P + (base2(packed) - m + 1 - o2);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const real w1 = __shfl_sync(0xffffffffu, wv, ta[i]);
+            const real d1 = __shfl_sync(0xffffffffu, wd, ta[i]);
+            const real w2 = __shfl_sync(0xffffffffu, wv, M2 + tb[i]);
+            const real d2 = __shfl_sync(0xffffffffu, wd, M2 + tb[i]);
+            if (lane + 32 * i < TAPS) {
+                real *cell = corner + toff[i];
+                const real v = w2 * (c * w1 + d.x * d1) + d.y * w1 * d2;
+                const real old = *cell;
+                const real s = old + v;
+                *cell = s;
+                if (KAHAN) {
+                    const real bb = s - old;
+                    cell[PP] += (old - (s - bb)) + (v - bb);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    const real *base_tile = reinterpret_cast<const real *>(smem_raw);
+    for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+        real v = real(0);
+#pragma unroll
+        for (int ww = 0; ww < kSpreadWarps; ++ww) {
+            const real *tile = base_tile + (size_t)ww * PP * PLANES;
+            v += tile[i];
+            if (KAHAN)
+                v += tile[i + PP];
+        }
+        const int r = i / P, cc = i - (i / P) * P;
+        const int g1 = o1 + r, g2 = o2 + cc;
+        if (v != real(0) && g1 >= 0 && g1 < n_a && g2 >= 0 && g2 < n_a)
+            atomicAdd(grid + (int64_t)g1 * pitch + g2, v);
+    }
+}
+
+// Gradient and Hessian of the interpolated field (torus units):
+//   grad = n_os sum_k g_k grad Psi(u - k),  Hess = n_os^2 sum_k g_k grad grad Psi(u - k).
+// FP32 with m >= 5 forms the derivative sums against a reference tap (see k_interp).
+template <typename real, int M2>
+__global__ void __launch_bounds__(256) k_interp_hess(int64_t N, const int *__restrict__ base,
+                                                     const real2_t<real> *__restrict__ frac, Window<real> w,
+                                                     WindowPoly wp, const real *__restrict__ grid, int pitch,
+                                                     real n_os, real *__restrict__ grad_s, real *__restrict__ hess_s)
+{
+    constexpr int m = M2 / 2;
+    constexpr bool kRef = sizeof(real) == 4 && m >= 5;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N)
+        return;
+    const int packed = base[k];
+    const real2_t<real> f = frac[k];
+    real w1[M2], d1[M2], e1[M2], w2[M2], d2[M2], e2[M2];
+    if constexpr (sizeof(real) == 4) {
+        const float t1 = (float)f.x - 0.5f, t2 = (float)f.y - 0.5f;
+#pragma unroll
+        for (int a = 0; a < M2; ++a) {
+            w1[a] = poly_eval<kPolyD>(wp.c[a], t1);
+            d1[a] = poly_eval<kPolyD - 1>(wp.d[a], t1);
+            e1[a] = poly_eval<kPolyD - 2>(wp.e[a], t1);
+            w2[a] = poly_eval<kPolyD>(wp.c[a], t2);
+            d2[a] = poly_eval<kPolyD - 1>(wp.d[a], t2);
+            e2[a] = poly_eval<kPolyD - 2>(wp.e[a], t2);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < M2; ++a) {
+            kb_value_slope_curv<real>(w, f.x, m - 1 - a, w1[a], d1[a], e1[a]);
+            kb_value_slope_curv<real>(w, f.y, m - 1 - a, w2[a], d2[a], e2[a]);
+        }
+    }
+    const int row0 = base1(packed) - m + 1;
+    const int col0 = base2(packed) - m + 1;
+    real rs[M2], rd[M2];
+    real gy = 0, hyy = 0, hxy = 0;
+#pragma unroll
+    for (int a = 0; a < M2; ++a) {
+        const real *rowp = grid + (int64_t)(row0 + a) * pitch + col0;
+        real gv[M2];
+#pragma unroll
+        for (int b = 0; b < M2; ++b)
+            gv[b] = __ldg(rowp + b);
+        real s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int b = 0; b < M2; ++b) {
+            const real g = kRef ? gv[b] - gv[m - 1] : gv[b];
+            s0 += w2[b] * gv[b];
+            s1 += d2[b] * g;
+            s2 += e2[b] * g;
+        }
+        rs[a] = s0;
+        rd[a] = s1;
+        gy += w1[a] * s1;
+        hyy += w1[a] * s2;
+    }
+    real gx = 0, hxx = 0;
+#pragma unroll
+    for (int a = 0; a < M2; ++a) {
+        const real r0 = kRef ? rs[a] - rs[m - 1] : rs[a];
+        const real r1 = kRef ? rd[a] - rd[m - 1] : rd[a];
+        gx += d1[a] * r0;
+        hxx += e1[a] * r0;
+        hxy += d1[a] * r1;
+    }
+    grad_s[2 * k] = n_os * gx;
+    grad_s[2 * k + 1] = n_os * gy;
+    const real n2 = n_os * n_os;
+    hess_s[3 * k] = n2 * hxx;
+    hess_s[3 * k + 1] = n2 * hxy;
+    hess_s[3 * k + 2] = n2 * hyy;
+}
+
 template <typename real, int M2>
 cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const int *base, const void *frac,
                      const real *q, Window<real> w, const WindowPoly &wp, real *grid, int pitch, int n_a, bool kahan,
@@ -240,7 +419,104 @@ cudaError_t interp_m(int64_t N, const int *base, const void *frac, Window<real> 
     return cudaGetLastError();
 }
 
+template <typename real, int M2>
+cudaError_t spread_dip_m(const SpreadItem *items, int n_items, CellGrid cg, const int *base, const void *frac,
+                         const real *cq, const void *dq, Window<real> w, const WindowPoly &wp, real *grid, int pitch,
+                         int n_a, bool kahan, cudaStream_t st)
+{
+    const int TG = cg.T * cg.cell;
+    const int P = TG + M2 - 1;
+    const size_t smem = (size_t)kSpreadWarps * P * P * sizeof(real) * (kahan ? 2 : 1) +
+                        sizeof(float) * M2 * (2 * kPolyD + 1);
+    const real2_t<real> *fr = (const real2_t<real> *)frac;
+    const real2_t<real> *dd = (const real2_t<real> *)dq;
+    if (kahan) {
+        auto kern = k_spread_dip<real, M2, true>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, cq, dd, w, wp, grid, pitch, n_a);
+    } else {
+        auto kern = k_spread_dip<real, M2, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, cq, dd, w, wp, grid, pitch, n_a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename real, int M2>
+cudaError_t interp_hess_m(int64_t N, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
+                          const real *grid, int pitch, real n_os, real *grad_s, real *hess_s, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    k_interp_hess<real, M2><<<blocks, 256, 0, st>>>(N, base, (const real2_t<real> *)frac, w, wp, grid, pitch, n_os,
+                                                     grad_s, hess_s);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+template <typename real>
+cudaError_t launch_spread_dip(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
+                              const void *frac, const real *cq, const void *dq, Window<real> w, const WindowPoly &wp,
+                              real *grid, int pitch, int n_a, bool kahan, cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    const bool comp = kahan && sizeof(real) == 4;
+    switch (m) {
+#define FS_DIP_CASE(MM)                                                                                          \
+    case MM:                                                                                                     \
+        return spread_dip_m<real, 2 * MM>(items, n_items, cg, base, frac, cq, dq, w, wp, grid, pitch, n_a, comp, st);
+        FS_DIP_CASE(2)
+        FS_DIP_CASE(3)
+        FS_DIP_CASE(4)
+        FS_DIP_CASE(5)
+        FS_DIP_CASE(6)
+        FS_DIP_CASE(7)
+        FS_DIP_CASE(8)
+#undef FS_DIP_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename real>
+cudaError_t launch_interp_hess(int64_t N, int m, const int *base, const void *frac, Window<real> w,
+                               const WindowPoly &wp, const real *grid, int pitch, real n_os, real *grad_s,
+                               real *hess_s, cudaStream_t st)
+{
+    if (N <= 0)
+        return cudaSuccess;
+    switch (m) {
+#define FS_HESS_CASE(MM)                                                                                         \
+    case MM:                                                                                                     \
+        return interp_hess_m<real, 2 * MM>(N, base, frac, w, wp, grid, pitch, n_os, grad_s, hess_s, st);
+        FS_HESS_CASE(2)
+        FS_HESS_CASE(3)
+        FS_HESS_CASE(4)
+        FS_HESS_CASE(5)
+        FS_HESS_CASE(6)
+        FS_HESS_CASE(7)
+        FS_HESS_CASE(8)
+#undef FS_HESS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_spread_dip<float>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
+                                              const float *, const void *, Window<float>, const WindowPoly &, float *,
+                                              int, int, bool, cudaStream_t);
+template cudaError_t launch_spread_dip<double>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
+                                               const double *, const void *, Window<double>, const WindowPoly &,
+                                               double *, int, int, bool, cudaStream_t);
+template cudaError_t launch_interp_hess<float>(int64_t, int, const int *, const void *, Window<float>,
+                                               const WindowPoly &, const float *, int, float, float *, float *,
+                                               cudaStream_t);
+template cudaError_t launch_interp_hess<double>(int64_t, int, const int *, const void *, Window<double>,
+                                                const WindowPoly &, const double *, int, double, double *, double *,
+                                                cudaStream_t);
 
 template <typename real>
 cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base, const void *frac,

@@ -1,0 +1,167 @@
+"""GPU adjoint (fs_adjoint) and the autograd.Function, checked against:
+
+* the transposition identity <gphi, phi(q)> + <gH, H(q)> = <dL/dq, q> (the far field
+  is an exact transpose of the forward pipeline, so this holds to rounding);
+* central finite differences of the GPU forward in the point positions (FP64,
+  Richardson-extrapolated from h = 2e-6 and 1e-6 so close pairs' third derivatives
+  do not swamp the check; points at the largest radius held fixed so the torus
+  scale does not change);
+* the oracle's direct-sum gradient, within a small multiple of the forward's own
+  approximation error against the direct sum;
+* FP32 against FP64.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_0807_2387_gb300 import build
+    build.build()
+    import paper_0807_2387_gb300 as p
+    p.load()
+    torch.cuda.set_device(0)
+    return p
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(seed, ns, nt, coincident=False, n=64, m=6, eps_I=4 / 64):
+    from paper_0807_2387_gb300 import workloads as W
+    return W.small_case(seed, ns, nt, n=n, m=m, eps_I=eps_I, coincident=coincident)
+
+
+def _forward(pkg, src, tgt, q, case, precision):
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum(torch.tensor(src, device=dev), torch.tensor(tgt, device=dev), case["n"], case["sigma"],
+                     case["m"], case["eps_I"], precision=precision)
+    fs.set_charges(torch.tensor(q, device=dev))
+    phi, H = fs.field(dtype=torch.float64)
+    fs.sync()
+    return fs, phi.cpu().numpy(), H.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 1e-6)])
+def test_transposition_identity(pkg, precision, tol):
+    c = _case(201, 1500, 1300)
+    rng = np.random.default_rng(1)
+    gphi, gH = rng.standard_normal(1300), rng.standard_normal((1300, 2))
+    fs, phi, H = _forward(pkg, c["src"], c["tgt"], c["q"], c, precision)
+    dev = torch.device("cuda", 0)
+    dq, _, _ = fs.adjoint(torch.tensor(gphi, device=dev), torch.tensor(gH, device=dev), dtype=torch.float64)
+    fs.sync()
+    lhs = gphi @ phi + np.sum(gH * H)
+    rhs = dq.cpu().numpy() @ c["q"]
+    scale = np.abs(gphi) @ np.abs(phi) + np.sum(np.abs(gH * H))
+    assert abs(lhs - rhs) <= tol * scale, (lhs, rhs)
+    fs.close()
+
+
+def test_position_gradients_match_finite_differences(pkg):
+    c = _case(202, 900, 800)
+    rng = np.random.default_rng(2)
+    gphi, gH = rng.standard_normal(800), rng.standard_normal((800, 2))
+    src, tgt, q = c["src"], c["tgt"], c["q"]
+    fs, phi, H = _forward(pkg, src, tgt, q, c, 64)
+    dev = torch.device("cuda", 0)
+    dq, dy, dx = fs.adjoint(torch.tensor(gphi, device=dev), torch.tensor(gH, device=dev), want_src=True,
+                            want_tgt=True, dtype=torch.float64)
+    fs.sync()
+    dq, dy, dx = dq.cpu().numpy(), dy.cpu().numpy(), dx.cpu().numpy()
+    fs.close()
+    rmax = max(np.hypot(*src.T).max(), np.hypot(*tgt.T).max())
+    keep_s = (np.hypot(*src.T) < 0.95 * rmax)[:, None]
+    keep_t = (np.hypot(*tgt.T) < 0.95 * rmax)[:, None]
+
+    def loss(q_, s_, t_):
+        _, p_, h_ = _forward(pkg, s_, t_, q_, c, 64)
+        return gphi @ p_ + np.sum(gH * h_)
+
+    def slope(vq, vy, vx):
+        d = [(loss(q + h * vq, src + h * vy, tgt + h * vx) - loss(q - h * vq, src - h * vy, tgt - h * vx)) / (2 * h)
+             for h in (2e-6, 1e-6)]
+        return (4 * d[1] - d[0]) / 3
+
+    zq, zs, zt = 0 * q, 0 * src, 0 * tgt
+    errs = []
+    for k in range(8):
+        vq = rng.standard_normal(q.shape)
+        vy = rng.standard_normal(src.shape) * keep_s
+        vx = rng.standard_normal(tgt.shape) * keep_t
+        # sources only, targets only, then charges and both positions together
+        for wq, wy, wx in ((zq, vy, zt), (zq, zs, vx), (vq, vy, vx)):
+            terms = np.concatenate([dq * wq, (dy * wy).ravel(), (dx * wx).ravel()])
+            errs.append(abs(slope(wq, wy, wx) - terms.sum()) / np.abs(terms).sum())
+    # the fourth-order Richardson residual of the closest pairs stays near 1e-8
+    assert max(errs) <= 1e-7, errs
+
+
+@pytest.mark.parametrize("n,m,eps_I,bound", [(64, 6, 4 / 64, 1e-3), (128, 8, 8 / 128, 5e-5)])
+def test_adjoint_against_direct_gradient(pkg, n, m, eps_I, bound):
+    """The adjoint approximates the direct sum's gradient as well as the forward approximates phi, H."""
+    from oracle import direct as D
+    c = _case(203, 1200, 1100, n=n, m=m, eps_I=eps_I)
+    rng = np.random.default_rng(3)
+    gphi, gH = rng.standard_normal(1100), rng.standard_normal((1100, 2))
+    fs, phi, H = _forward(pkg, c["src"], c["tgt"], c["q"], c, 64)
+    dev = torch.device("cuda", 0)
+    dq, dy, dx = fs.adjoint(torch.tensor(gphi, device=dev), torch.tensor(gH, device=dev), want_src=True,
+                            want_tgt=True, dtype=torch.float64)
+    fs.sync()
+    fs.close()
+    phi_d, H_d = D.direct_sum(c["tgt"], c["src"], c["q"])
+    fwd_err = max(rel(phi, phi_d), rel(H, H_d))
+    dq_o, dy_o, dx_o = D.direct_adjoint(c["tgt"], c["src"], c["q"], gphi, gH)
+    for got, want in ((dq, dq_o), (dy, dy_o), (dx, dx_o)):
+        err = rel(got.cpu().numpy(), want)
+        assert err < 2 * fwd_err and err < bound, (err, fwd_err)
+
+
+def test_fp32_adjoint_close_to_fp64(pkg):
+    c = _case(204, 2000, 2000, coincident=True)
+    rng = np.random.default_rng(4)
+    gphi, gH = rng.standard_normal(2000), rng.standard_normal((2000, 2))
+    dev = torch.device("cuda", 0)
+    out = {}
+    for precision in (32, 64):
+        fs, _, _ = _forward(pkg, c["src"], c["tgt"], c["q"], c, precision)
+        dq, dy, dx = fs.adjoint(torch.tensor(gphi, device=dev), torch.tensor(gH, device=dev), want_src=True,
+                                want_tgt=True, dtype=torch.float64)
+        fs.sync()
+        out[precision] = [t.cpu().numpy() for t in (dq, dy, dx)]
+        fs.close()
+    for a, b in zip(out[32], out[64]):
+        assert rel(a, b) < 1e-4, rel(a, b)
+
+
+def test_autograd_function_energy_and_field_loss(pkg):
+    """L = 1/2 sum q phi + sum w |H|^2 with sources = targets (the differentiation workload, reduced)."""
+    from oracle import direct as D
+    from paper_0807_2387_gb300 import workloads as W
+    rng = np.random.default_rng(5)
+    pts = W.uniform_disc(rng, 1500, 0.25)
+    qn = rng.standard_normal(1500)
+    wn = rng.random(1500)
+    dev = torch.device("cuda", 0)
+    P = torch.tensor(pts, device=dev, requires_grad=True)
+    q = torch.tensor(qn, device=dev, requires_grad=True)
+    w = torch.tensor(wn, device=dev)
+    fs = pkg.FastSum(P.detach(), P.detach(), 128, 2.0, 8, 8 / 128, precision=64)
+    phi, H = pkg.FastSumFn.apply(q, P, P, fs)
+    L = 0.5 * (q * phi).sum() + (w[:, None] * H * H).sum()
+    L.backward()
+    gq, gP = q.grad.cpu().numpy(), P.grad.cpu().numpy()
+    # direct-sum reference: dL/dq = phi/2 + A^T(q/2, 2 w H); positions through the oracle adjoint
+    phi_d, H_d = D.direct_sum(pts, pts, qn)
+    dq_o, dy_o, dx_o = D.direct_adjoint(pts, pts, qn, 0.5 * qn, 2 * wn[:, None] * H_d)
+    assert rel(gq, 0.5 * phi_d + dq_o) < 5e-5
+    assert rel(gP, dy_o + dx_o) < 5e-5
+    fs.close()
