@@ -154,8 +154,10 @@ struct fs_plan {
     void *adj_c = nullptr, *adj_dn = nullptr, *adj_df = nullptr;
     void *adj_a = nullptr, *adj_ga = nullptr, *adj_cg = nullptr, *adj_hess = nullptr;
     double *adj_gsum = nullptr;
-    int2 *near_items = nullptr;       // FP32 near field: (first target, count <= 32) per warp
+    int2 *near_items = nullptr;       // FP32 near field: (first target, count <= 64) per warp
     int64_t n_near_items = 0;
+    int2 *src_near_items = nullptr;   // FP32 adjoint near field: (first source, count <= 64) per warp
+    int64_t n_src_near_items = 0;
     void *mul = nullptr, *tw = nullptr;
     void *grid = nullptr, *spec = nullptr;
     void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
@@ -348,6 +350,81 @@ fs_status bin_points(fs_plan *pl, const double *xy, int64_t n, int **perm, int *
     pl->release(count);
     pl->release(fill);
     pl->release(tmp);
+    return FS_OK;
+}
+
+// FP32 near-field warp items over the "own" points (targets for the forward, sources for
+// the adjoint): at most 64 consecutive points of one cell (two per lane).  A sub-cell holding
+// 32 or more points gets items of its own (so its warps' bounding boxes stay an eighth of a
+// cell wide); sparser sub-cells of the same cell are merged up to 64.  Items are ordered by
+// estimated work (points x "other" points in the 3 x 3 cells around the item's cell),
+// largest first, so the heavy warps start early and the tail of the launch stays short.
+fs_status build_near_items(fs_plan *pl, const int *own_start_d, const int *oth_start_d, int2 **out, int64_t *n_out)
+{
+    constexpr int kCap = 64, kOwn = 32;
+    std::vector<int> start(pl->n_keys + 1), oth(pl->n_keys + 1);
+    FS_CUDA(cudaMemcpy(start.data(), own_start_d, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
+    FS_CUDA(cudaMemcpy(oth.data(), oth_start_d, sizeof(int) * oth.size(), cudaMemcpyDeviceToHost));
+    const int n_cells = pl->n_keys / kSub;
+    std::vector<int2> items;
+    std::vector<int> item_cell;
+    for (int key = 0; key < n_cells; ++key) {
+        int open_start = -1, open_count = 0;
+        auto flush = [&]() {
+            if (open_count > 0) {
+                items.push_back(make_int2(open_start, open_count));
+                item_cell.push_back(key);
+            }
+            open_count = 0;
+        };
+        for (int sub = 0; sub < kSub; ++sub) {
+            const int a = start[key * kSub + sub], c = start[key * kSub + sub + 1] - a;
+            if (c == 0)
+                continue;
+            if (c >= kOwn) {
+                flush();
+                const int pieces = (c + kCap - 1) / kCap;
+                for (int i = 0; i < pieces; ++i) {
+                    const int lo = a + (int)((int64_t)c * i / pieces), hi = a + (int)((int64_t)c * (i + 1) / pieces);
+                    items.push_back(make_int2(lo, hi - lo));
+                    item_cell.push_back(key);
+                }
+                continue;
+            }
+            if (open_count > 0 && open_count + c > kCap)
+                flush();
+            if (open_count == 0)
+                open_start = a;
+            open_count += c;   // contiguous: sub-cells of a cell follow each other in the sorted order
+        }
+        flush();
+    }
+    std::vector<int64_t> nb(n_cells, 0);
+    const int nc = pl->cg.n_c;
+    for (int c1 = 0; c1 < nc; ++c1)
+        for (int c2 = 0; c2 < nc; ++c2) {
+            int64_t acc = 0;
+            for (int d1 = -1; d1 <= 1; ++d1)
+                for (int d2 = -1; d2 <= 1; ++d2) {
+                    const int e1 = c1 + d1, e2 = c2 + d2;
+                    if (e1 < 0 || e2 < 0 || e1 >= nc || e2 >= nc)
+                        continue;
+                    const int kk = pl->cg.key(e1, e2);
+                    acc += oth[(kk + 1) * kSub] - oth[kk * kSub];
+                }
+            nb[pl->cg.key(c1, c2)] = acc;
+        }
+    std::vector<std::pair<int64_t, int2>> wi;
+    wi.reserve(items.size());
+    for (size_t i = 0; i < items.size(); ++i)
+        wi.push_back({(int64_t)items[i].y * nb[item_cell[i]], items[i]});
+    std::stable_sort(wi.begin(), wi.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    for (size_t i = 0; i < items.size(); ++i)
+        items[i] = wi[i].second;
+    *n_out = (int64_t)items.size();
+    FS_TRY(pl->alloc(out, items.size()));
+    if (!items.empty())
+        FS_CUDA(cudaMemcpy(*out, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
     return FS_OK;
 }
 
@@ -567,81 +644,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
             FS_CUDA(cudaMemcpy(*dst, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
     }
 
-    // near-field warp items: at most 64 consecutive targets of one cell (two per lane).  A
-    // sub-cell holding 32 or more targets gets items of its own (so its warps' bounding boxes
-    // stay an eighth of a cell wide); sparser sub-cells of the same cell are merged up to 64.
-    if (pl->precision == 32) {
-        constexpr int kCap = 64, kOwn = 32;
-        std::vector<int> start(pl->n_keys + 1);
-        FS_CUDA(cudaMemcpy(start.data(), pl->tgt_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost));
-        std::vector<int2> items;
-        for (int key = 0; key < pl->n_keys / kSub; ++key) {
-            int open_start = -1, open_count = 0;
-            for (int sub = 0; sub < kSub; ++sub) {
-                const int a = start[key * kSub + sub], c = start[key * kSub + sub + 1] - a;
-                if (c == 0)
-                    continue;
-                if (c >= kOwn) {
-                    if (open_count > 0)
-                        items.push_back(make_int2(open_start, open_count));
-                    open_count = 0;
-                    const int pieces = (c + kCap - 1) / kCap;
-                    for (int i = 0; i < pieces; ++i) {
-                        const int lo = a + (int)((int64_t)c * i / pieces), hi = a + (int)((int64_t)c * (i + 1) / pieces);
-                        items.push_back(make_int2(lo, hi - lo));
-                    }
-                    continue;
-                }
-                if (open_count > 0 && open_count + c > kCap) {
-                    items.push_back(make_int2(open_start, open_count));
-                    open_count = 0;
-                }
-                if (open_count == 0)
-                    open_start = a;
-                open_count += c;   // contiguous: sub-cells of a cell follow each other in the sorted order
-            }
-            if (open_count > 0)
-                items.push_back(make_int2(open_start, open_count));
-        }
-        // largest items first (estimated work: targets x sources in the 3 x 3 cells around the
-        // item's cell), so the heavy warps start early and the tail of the launch stays short
-        {
-            std::vector<int> src_h(pl->n_keys + 1);
-            FS_CUDA(cudaMemcpy(src_h.data(), pl->src_start, sizeof(int) * src_h.size(), cudaMemcpyDeviceToHost));
-            std::vector<int> tkey(pl->n_keys / kSub);
-            std::vector<int64_t> nb(pl->n_keys / kSub, 0);
-            const int nc = pl->cg.n_c;
-            for (int c1 = 0; c1 < nc; ++c1)
-                for (int c2 = 0; c2 < nc; ++c2) {
-                    int64_t acc = 0;
-                    for (int d1 = -1; d1 <= 1; ++d1)
-                        for (int d2 = -1; d2 <= 1; ++d2) {
-                            const int e1 = c1 + d1, e2 = c2 + d2;
-                            if (e1 < 0 || e2 < 0 || e1 >= nc || e2 >= nc)
-                                continue;
-                            const int kk = pl->cg.key(e1, e2);
-                            acc += src_h[(kk + 1) * kSub] - src_h[kk * kSub];
-                        }
-                    nb[pl->cg.key(c1, c2)] = acc;
-                }
-            // the cell of an item: the key whose target range contains its first target
-            std::vector<std::pair<int64_t, int2>> wi;
-            wi.reserve(items.size());
-            size_t key = 0;
-            for (const int2 &it : items) {
-                while (key + 1 < nb.size() && start[(key + 1) * kSub] <= it.x)
-                    ++key;
-                wi.push_back({(int64_t)it.y * nb[key], it});
-            }
-            std::stable_sort(wi.begin(), wi.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
-            for (size_t i = 0; i < items.size(); ++i)
-                items[i] = wi[i].second;
-        }
-        pl->n_near_items = (int64_t)items.size();
-        FS_TRY(pl->alloc(&pl->near_items, items.size()));
-        if (!items.empty())
-            FS_CUDA(cudaMemcpy(pl->near_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    }
+    if (pl->precision == 32)
+        FS_TRY(build_near_items(pl, pl->tgt_start, pl->src_start, &pl->near_items, &pl->n_near_items));
 
     // coefficient table and FFT twiddles
     FS_TRY(coefficients<real>(pl));
@@ -870,6 +874,8 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
         FS_TRY(pl->alloc_bytes(&pl->adj_cg, (size_t)std::max<int64_t>(M, 1) * sizeof(real)));
         FS_TRY(pl->alloc_bytes(&pl->adj_hess, (size_t)std::max<int64_t>(N, 1) * 3 * sizeof(real)));
         FS_TRY(pl->alloc(&pl->adj_gsum, 1));
+        if (pl->precision == 32)
+            FS_TRY(build_near_items(pl, pl->src_start, pl->tgt_start, &pl->src_near_items, &pl->n_src_near_items));
     }
     const Window<real> w = make_window<real>(pl);
     const NearParams<real> np = make_near<real>(pl);
@@ -888,8 +894,13 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
             FS_TRY(spectral_pipeline<real>(pl));
             FS_CUDA(launch_interp_hess<real>(N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly, (const real *)pl->grid,
                                              pl->pitch, (real)pl->n_os, (real *)pl->grad_s, (real *)pl->adj_hess, st));
-            FS_CUDA(launch_near_hess<real>(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, q, np,
-                                           (real *)pl->grad_s, (real *)pl->adj_hess, st));
+            if constexpr (sizeof(real) == 4)
+                FS_CUDA(launch_near_hess32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32,
+                                           pl->tgt_lo32, pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, q, np,
+                                           (float *)pl->grad_s, (float *)pl->adj_hess, st));
+            else
+                FS_CUDA(launch_near_hess64(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, q, np,
+                                           (double *)pl->grad_s, (double *)pl->adj_hess, st));
         }
         FS_CUDA(cudaMemsetAsync(pl->adj_gsum, 0, sizeof(double), st));
         FS_CUDA(launch_gather_adj<real>(N, pl->tgt_perm, gp, gh, in_dtype == FS_F64, pl->s, (double)pl->n_os,
@@ -902,9 +913,15 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
             FS_TRY(spectral_pipeline<real>(pl));
             FS_CUDA(launch_interp<real>(M, pl->m, pl->src_base, pl->src_frac, w, pl->wpoly, (const real *)pl->grid,
                                         pl->pitch, (real)pl->n_os, (real *)pl->adj_a, (real *)pl->adj_ga, st));
-            FS_CUDA(launch_near_adj<real>(M, pl->src_base, pl->src_pos, pl->tgt_pos, pl->tgt_start, pl->cg,
-                                          (const real *)pl->adj_c, pl->adj_dn, np, (real *)pl->adj_a,
-                                          (real *)pl->adj_ga, (real *)pl->adj_cg, st));
+            if constexpr (sizeof(real) == 4)
+                FS_CUDA(launch_near_adj32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
+                                          pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
+                                          (const float *)pl->adj_c, pl->adj_dn, np, (float *)pl->adj_a,
+                                          (float *)pl->adj_ga, (float *)pl->adj_cg, st));
+            else
+                FS_CUDA(launch_near_adj64(M, pl->src_base, pl->src_pos, pl->tgt_pos, pl->tgt_start, pl->cg,
+                                          (const double *)pl->adj_c, pl->adj_dn, np, (double *)pl->adj_a,
+                                          (double *)pl->adj_ga, (double *)pl->adj_cg, st));
             void *o_dq = dq ? (unsigned char *)dq + (size_t)r * M * osz : nullptr;
             void *o_dy = dsrc ? (unsigned char *)dsrc + (size_t)r * M * 2 * osz : nullptr;
             FS_CUDA(launch_adj_finish_src<real>(M, pl->src_perm, (const real *)pl->adj_a, (const real *)pl->adj_ga,

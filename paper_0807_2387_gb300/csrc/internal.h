@@ -114,14 +114,22 @@ cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, c
 template <typename real>
 cudaError_t launch_gather_adj(int64_t N, const int *perm, const void *gphi, const void *gH, int in_f64, double s,
                               double n_os, real *c, void *dn, void *df, double *gsum, cudaStream_t st);
-template <typename real>
-cudaError_t launch_near_adj(int64_t M, const int *src_base, const double2 *src_pos, const double2 *tgt_pos,
-                            const int *tgt_start, CellGrid cg, const real *c, const void *dn, NearParams<real> np,
-                            real *a_s, real *ga_s, real *cg_s, cudaStream_t st);
-template <typename real>
-cudaError_t launch_near_hess(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
-                             const int *src_start, CellGrid cg, const real *q, NearParams<real> np, real *grad_s,
-                             real *hess_s, cudaStream_t st);
+// FP64: one thread per point over the 3 x 3 cells
+cudaError_t launch_near_adj64(int64_t M, const int *src_base, const double2 *src_pos, const double2 *tgt_pos,
+                              const int *tgt_start, CellGrid cg, const double *c, const void *dn,
+                              NearParams<double> np, double *a_s, double *ga_s, double *cg_s, cudaStream_t st);
+cudaError_t launch_near_hess64(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
+                               const int *src_start, CellGrid cg, const double *q, NearParams<double> np,
+                               double *grad_s, double *hess_s, cudaStream_t st);
+// FP32: warp items over the sources (adjoint potential) or the targets (Hessian)
+cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,
+                              const float2 *src_lo, const float2 *tgt_hi, const float2 *tgt_lo, const int *tgt_start,
+                              CellGrid cg, const float *c, const void *dn, NearParams<float> np, float *a_s,
+                              float *ga_s, float *cg_s, cudaStream_t st);
+cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                               const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
+                               CellGrid cg, const float *q, NearParams<float> np, float *grad_s, float *hess_s,
+                               cudaStream_t st);
 template <typename real>
 cudaError_t launch_adj_finish_src(int64_t M, const int *perm, const real *a_s, const real *ga_s, const real *cg_s,
                                   const real *q, double shift, const double *gsum, double s, void *dq, void *dy,

@@ -11,7 +11,18 @@
 // parts (the kernel difference f = G - T_I inside eps_I, its gradient c(w) d and
 // Hessian c(w) I + (2 c'(w) / eps_I^2) d d^T, w = r^2 / eps_I^2), the gathers and
 // the final assembly in physical units.
+//
+// Coincident pairs: the direct sum skips them (G(0) := 0, so also grad G(0) := 0 and
+// Hess G(0) := 0), while the far field holds the smooth T_I there, with T_I(0) =
+// beta_0, grad T_I(0) = 0 and Hess T_I(0) = (2 beta_1 / eps_I^2) I.  The near field
+// removes those: -q beta_0 in phi, -q (2 beta_1 / eps_I^2) I in the Hessian and, in
+// the source gradient of the adjoint potential, +(2 beta_1 / eps_I^2) dn.
+//
+// FP64: one thread per point (the comparison path).  FP32: warp items over the
+// 8 x 8 sub-cells (near_warp.cuh), the Hessian over the forward's target items and
+// the adjoint potential over items of sources against the targets.
 #include "internal.h"
+#include "near_warp.cuh"
 
 namespace fs {
 
@@ -19,43 +30,29 @@ namespace {
 
 template <typename real> using real2_t = typename Cplx<real>::type;
 
-// f(w) = G - T_I, c(w) = (G' - T_I')(r) / r and c'(w) = dc/dw at w = r^2 / eps_I^2.
-template <typename real>
-__device__ __forceinline__ void near_fcd(const NearParams<real> &np, real r2, real &f, real &c, real &cp)
+// f = G - T_I, c(w) = (G' - T_I')(r) / r and c'(w) = dc/dw at w = r^2 / eps_I^2 (FP64 sum forms).
+__device__ __forceinline__ void near_fcd64(const NearParams<double> &np, double r2, double &f, double &c, double &cp)
 {
-    const real w = r2 * np.inv_eps2;
+    const double w = r2 * np.inv_eps2;
     const int p = np.p;
-    if (sizeof(real) == 4) {
-        // P(w) = T_I - k(eps_I) with P(1) = 0; c = rc (w-1)^(p-1) / w; c' = rc (w-1)^(p-2) ((p-2) w + 1) / w^2
-        real t = np.pbeta[p - 1];
-        for (int i = p - 2; i >= 0; --i)
-            t = t * w + np.pbeta[i];
-        f = real(-1.0 / (4.0 * kPi)) * flog<real>(w) - t;
-        const real om = w - real(1);
-        real pw2 = real(1);   // (w-1)^(p-2)
-        for (int i = 0; i < p - 2; ++i)
-            pw2 *= om;
-        if (p >= 2) {
-            c = np.rcoef * pw2 * om / w;
-            cp = np.rcoef * pw2 * (real(p - 2) * w + real(1)) / (w * w);
-        } else {
-            c = np.rcoef / w;
-            cp = -np.rcoef / (w * w);
-        }
-    } else {
-        real t = np.beta[p - 1];
-        for (int i = p - 2; i >= 0; --i)
-            t = t * w + np.beta[i];
-        f = real(-1.0 / (4.0 * kPi)) * flog<real>(r2) - t;
-        real tp = real(0), tpp = real(0);
-        for (int k = p - 1; k >= 1; --k)
-            tp = tp * w + real(2 * k) * np.beta[k];
-        for (int k = p - 1; k >= 2; --k)
-            tpp = tpp * w + real(2 * k * (k - 1)) * np.beta[k];
-        const real inv2pi = real(1.0 / (2.0 * kPi));
-        c = (-inv2pi / w - tp) * np.inv_eps2;
-        cp = (inv2pi / (w * w) - tpp) * np.inv_eps2;
-    }
+    double t = np.beta[p - 1];
+    for (int i = p - 2; i >= 0; --i)
+        t = t * w + np.beta[i];
+    f = -1.0 / (4.0 * kPi) * log(r2) - t;
+    double tp = 0.0, tpp = 0.0;
+    for (int k = p - 1; k >= 1; --k)
+        tp = tp * w + (double)(2 * k) * np.beta[k];
+    for (int k = p - 1; k >= 2; --k)
+        tpp = tpp * w + (double)(2 * k * (k - 1)) * np.beta[k];
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    c = (-inv2pi / w - tp) * np.inv_eps2;
+    cp = (inv2pi / (w * w) - tpp) * np.inv_eps2;
+}
+
+// Hess T_I(0) = hess0 I.
+template <typename real> __host__ __device__ __forceinline__ real self_hessian(const NearParams<real> &np)
+{
+    return np.p > 1 ? real(2) * np.beta[1] * np.inv_eps2 : real(0);
 }
 
 // Loss gradients into sorted target order: c = gphi, dn = -s gH (near field, torus units),
@@ -101,15 +98,14 @@ __global__ void k_gather_adj(int64_t N, const int *__restrict__ perm, const void
 }
 
 // Near part of the adjoint potential at the sources (sorted source order): value, gradient
-// with respect to the source position, and the coincident gphi.
-template <typename real>
-__global__ void __launch_bounds__(256) k_near_adj(int64_t M, const int *__restrict__ src_base,
-                                                  const double2 *__restrict__ src_pos,
-                                                  const double2 *__restrict__ tgt_pos, const int *__restrict__ tgt_start,
-                                                  CellGrid cg, const real *__restrict__ c,
-                                                  const real2_t<real> *__restrict__ dn, NearParams<real> np,
-                                                  real *__restrict__ a_s, real *__restrict__ ga_s,
-                                                  real *__restrict__ cg_s)
+// with respect to the source position, and the coincident gphi.  FP64.
+__global__ void __launch_bounds__(256) k_near_adj64(int64_t M, const int *__restrict__ src_base,
+                                                    const double2 *__restrict__ src_pos,
+                                                    const double2 *__restrict__ tgt_pos,
+                                                    const int *__restrict__ tgt_start, CellGrid cg,
+                                                    const double *__restrict__ c, const double2 *__restrict__ dn,
+                                                    NearParams<double> np, double *__restrict__ a_s,
+                                                    double *__restrict__ ga_s, double *__restrict__ cg_s)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= M)
@@ -117,8 +113,9 @@ __global__ void __launch_bounds__(256) k_near_adj(int64_t M, const int *__restri
     const double2 Y = src_pos[j];
     const int packed = src_base[j];
     const int c1 = base1(packed) / cg.cell, c2 = base2(packed) / cg.cell;
-    const real two_over_eps2 = real(2) * np.inv_eps2;
-    real A = 0, gx = 0, gy = 0, gco = 0;
+    const double two_over_eps2 = 2.0 * np.inv_eps2;
+    const double hess0 = self_hessian(np);
+    double A = 0, gx = 0, gy = 0, gco = 0;
     for (int d1 = -1; d1 <= 1; ++d1) {
         const int e1 = c1 + d1;
         if (e1 < 0 || e1 >= cg.n_c)
@@ -131,22 +128,24 @@ __global__ void __launch_bounds__(256) k_near_adj(int64_t M, const int *__restri
             const int end = tgt_start[(key + 1) * kSub];
             for (int i = tgt_start[key * kSub]; i < end; ++i) {
                 const double2 X = tgt_pos[i];
-                const real Dx = (real)(X.x - Y.x), Dy = (real)(X.y - Y.y);
-                const double rr2 = (X.x - Y.x) * (X.x - Y.x) + (X.y - Y.y) * (X.y - Y.y);
-                if (!(rr2 < (double)np.eps2))
+                const double Dx = X.x - Y.x, Dy = X.y - Y.y;
+                const double rr2 = Dx * Dx + Dy * Dy;
+                if (!(rr2 < np.eps2))
                     continue;
-                const real gp = c[i];
+                const double gp = c[i];
+                const double2 dd = dn[i];
                 if (rr2 == 0.0) {
                     A -= gp * np.beta[0];
                     gco += gp;
+                    gx += hess0 * dd.x;
+                    gy += hess0 * dd.y;
                     continue;
                 }
-                real f, cc, cp;
-                near_fcd<real>(np, (real)rr2, f, cc, cp);
-                const real2_t<real> dd = dn[i];
-                const real dD = dd.x * Dx + dd.y * Dy;
+                double f, cc, cp;
+                near_fcd64(np, rr2, f, cc, cp);
+                const double dD = dd.x * Dx + dd.y * Dy;
                 A += gp * f + dD * cc;
-                const real k2 = two_over_eps2 * cp * dD;
+                const double k2 = two_over_eps2 * cp * dD;
                 gx -= gp * cc * Dx + cc * dd.x + k2 * Dx;
                 gy -= gp * cc * Dy + cc * dd.y + k2 * Dy;
             }
@@ -158,13 +157,13 @@ __global__ void __launch_bounds__(256) k_near_adj(int64_t M, const int *__restri
     cg_s[j] = gco;
 }
 
-// Near part of grad phi and Hess phi at the targets (sorted target order), torus units.
-template <typename real>
-__global__ void __launch_bounds__(256) k_near_hess(int64_t N, const int *__restrict__ tgt_base,
-                                                   const double2 *__restrict__ tgt_pos,
-                                                   const double2 *__restrict__ src_pos, const int *__restrict__ src_start,
-                                                   CellGrid cg, const real *__restrict__ q, NearParams<real> np,
-                                                   real *__restrict__ grad_s, real *__restrict__ hess_s)
+// Near part of grad phi and Hess phi at the targets (sorted target order), torus units.  FP64.
+__global__ void __launch_bounds__(256) k_near_hess64(int64_t N, const int *__restrict__ tgt_base,
+                                                     const double2 *__restrict__ tgt_pos,
+                                                     const double2 *__restrict__ src_pos,
+                                                     const int *__restrict__ src_start, CellGrid cg,
+                                                     const double *__restrict__ q, NearParams<double> np,
+                                                     double *__restrict__ grad_s, double *__restrict__ hess_s)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N)
@@ -172,8 +171,9 @@ __global__ void __launch_bounds__(256) k_near_hess(int64_t N, const int *__restr
     const double2 X = tgt_pos[k];
     const int packed = tgt_base[k];
     const int c1 = base1(packed) / cg.cell, c2 = base2(packed) / cg.cell;
-    const real two_over_eps2 = real(2) * np.inv_eps2;
-    real gx = 0, gy = 0, hxx = 0, hxy = 0, hyy = 0;
+    const double two_over_eps2 = 2.0 * np.inv_eps2;
+    const double hess0 = self_hessian(np);
+    double gx = 0, gy = 0, hxx = 0, hxy = 0, hyy = 0;
     for (int d1 = -1; d1 <= 1; ++d1) {
         const int e1 = c1 + d1;
         if (e1 < 0 || e1 >= cg.n_c)
@@ -186,16 +186,21 @@ __global__ void __launch_bounds__(256) k_near_hess(int64_t N, const int *__restr
             const int end = src_start[(key + 1) * kSub];
             for (int j = src_start[key * kSub]; j < end; ++j) {
                 const double2 Y = src_pos[j];
-                const double rr2 = (X.x - Y.x) * (X.x - Y.x) + (X.y - Y.y) * (X.y - Y.y);
-                if (!(rr2 < (double)np.eps2) || rr2 == 0.0)
+                const double Dx = X.x - Y.x, Dy = X.y - Y.y;
+                const double rr2 = Dx * Dx + Dy * Dy;
+                if (!(rr2 < np.eps2))
                     continue;
-                const real Dx = (real)(X.x - Y.x), Dy = (real)(X.y - Y.y);
-                real f, cc, cp;
-                near_fcd<real>(np, (real)rr2, f, cc, cp);
-                const real qj = q[j];
+                const double qj = q[j];
+                if (rr2 == 0.0) {
+                    hxx -= qj * hess0;
+                    hyy -= qj * hess0;
+                    continue;
+                }
+                double f, cc, cp;
+                near_fcd64(np, rr2, f, cc, cp);
                 gx += qj * cc * Dx;
                 gy += qj * cc * Dy;
-                const real k2 = qj * two_over_eps2 * cp;
+                const double k2 = qj * two_over_eps2 * cp;
                 hxx += qj * cc + k2 * Dx * Dx;
                 hxy += k2 * Dx * Dy;
                 hyy += qj * cc + k2 * Dy * Dy;
@@ -208,6 +213,112 @@ __global__ void __launch_bounds__(256) k_near_hess(int64_t N, const int *__restr
     hess_s[3 * k + 1] += hxy;
     hess_s[3 * k + 2] += hyy;
 }
+
+// Hessian at the targets (FP32 warp items, own = targets, other = sources, d = x - y):
+// grad += q c d, Hess += q (c I + (2 c' / eps_I^2) d d^T).
+template <int P> struct NearHess32 {
+    static constexpr int kMinBlocks = 5;
+    const float *__restrict__ q;
+    float *__restrict__ grad_s;
+    float *__restrict__ hess_s;
+    float two_over_eps2, hess0;
+    float qj;
+    float gx[2], gy[2], hxx[2], hxy[2], hyy[2];
+
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+            gx[t] = gy[t] = hxx[t] = hxy[t] = hyy[t] = 0.f;
+    }
+    __device__ __forceinline__ void load(int j) { qj = __ldg(q + j); }
+    __device__ __forceinline__ void coincident(const NearParams<float> &, int t)
+    {
+        hxx[t] -= qj * hess0;
+        hyy[t] -= qj * hess0;
+    }
+    __device__ __forceinline__ void pair(const NearParams<float> &np, int t, float r2, float dx, float dy)
+    {
+        const bool in = r2 < np.eps2;
+        float c, cp;
+        near_c_cp<P>(np, in ? r2 * np.inv_eps2 : 0.5f, c, cp);
+        const float qm = in ? qj : 0.f;
+        const float qc = qm * c, k = qm * two_over_eps2 * cp;
+        gx[t] = fmaf(qc, dx, gx[t]);
+        gy[t] = fmaf(qc, dy, gy[t]);
+        const float kx = k * dx;
+        hxx[t] += fmaf(kx, dx, qc);
+        hxy[t] = fmaf(kx, dy, hxy[t]);
+        hyy[t] += fmaf(k * dy, dy, qc);
+    }
+    __device__ __forceinline__ void row_begin() {}
+    __device__ __forceinline__ void row_end() {}
+    __device__ __forceinline__ void store(int t, int64_t k)
+    {
+        grad_s[2 * k] += gx[t];
+        grad_s[2 * k + 1] += gy[t];
+        hess_s[3 * k] += hxx[t];
+        hess_s[3 * k + 1] += hxy[t];
+        hess_s[3 * k + 2] += hyy[t];
+    }
+};
+
+// Adjoint potential at the sources (FP32 warp items, own = sources, other = targets,
+// d = y - x = -D):  A += gphi f - (dn . d) c,  grad_y A += c (gphi d - dn) - (2 c' / eps_I^2)(dn . d) d.
+template <int P> struct NearAdj32 {
+    static constexpr int kMinBlocks = 5;
+    const float *__restrict__ cw;
+    const float2 *__restrict__ dnw;
+    float *__restrict__ a_s;
+    float *__restrict__ ga_s;
+    float *__restrict__ cg_s;
+    float two_over_eps2, hess0;
+    float gp;
+    float2 dn;
+    float A[2], gax[2], gay[2], gco[2];
+
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+            A[t] = gax[t] = gay[t] = gco[t] = 0.f;
+    }
+    __device__ __forceinline__ void load(int i)
+    {
+        gp = __ldg(cw + i);
+        dn = __ldg(dnw + i);
+    }
+    __device__ __forceinline__ void coincident(const NearParams<float> &np, int t)
+    {
+        A[t] -= gp * np.beta[0];
+        gco[t] += gp;
+        gax[t] = fmaf(hess0, dn.x, gax[t]);
+        gay[t] = fmaf(hess0, dn.y, gay[t]);
+    }
+    __device__ __forceinline__ void pair(const NearParams<float> &np, int t, float r2, float dx, float dy)
+    {
+        const bool in = r2 < np.eps2;
+        const float w = in ? r2 * np.inv_eps2 : 0.5f;
+        float c, cp;
+        near_c_cp<P>(np, w, c, cp);
+        const float f = near_f<P>(np, w);
+        const float g = in ? gp : 0.f, n1 = in ? dn.x : 0.f, n2 = in ? dn.y : 0.f;
+        const float dD = fmaf(n1, dx, n2 * dy);
+        A[t] = fmaf(g, f, fmaf(-dD, c, A[t]));
+        const float k = two_over_eps2 * cp * dD;
+        gax[t] += fmaf(c, fmaf(g, dx, -n1), -k * dx);
+        gay[t] += fmaf(c, fmaf(g, dy, -n2), -k * dy);
+    }
+    __device__ __forceinline__ void row_begin() {}
+    __device__ __forceinline__ void row_end() {}
+    __device__ __forceinline__ void store(int t, int64_t k)
+    {
+        a_s[k] += A[t];
+        ga_s[2 * k] += gax[t];
+        ga_s[2 * k + 1] += gay[t];
+        cg_s[k] = gco[t];
+    }
+};
 
 // dL/dq_j = A(y_j) + (log s / 2pi)(sum gphi - coincident gphi);  dL/dy_j = q_j s grad~ A(y_j).
 template <typename real>
@@ -285,28 +396,62 @@ cudaError_t launch_gather_adj(int64_t N, const int *perm, const void *gphi, cons
     return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_near_adj(int64_t M, const int *src_base, const double2 *src_pos, const double2 *tgt_pos,
-                            const int *tgt_start, CellGrid cg, const real *c, const void *dn, NearParams<real> np,
-                            real *a_s, real *ga_s, real *cg_s, cudaStream_t st)
+cudaError_t launch_near_adj64(int64_t M, const int *src_base, const double2 *src_pos, const double2 *tgt_pos,
+                              const int *tgt_start, CellGrid cg, const double *c, const void *dn,
+                              NearParams<double> np, double *a_s, double *ga_s, double *cg_s, cudaStream_t st)
 {
     if (M <= 0)
         return cudaSuccess;
-    k_near_adj<real><<<nblocks(M, 256), 256, 0, st>>>(M, src_base, src_pos, tgt_pos, tgt_start, cg, c,
-                                                      (const real2_t<real> *)dn, np, a_s, ga_s, cg_s);
+    k_near_adj64<<<nblocks(M, 256), 256, 0, st>>>(M, src_base, src_pos, tgt_pos, tgt_start, cg, c,
+                                                  (const double2 *)dn, np, a_s, ga_s, cg_s);
     return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_near_hess(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
-                             const int *src_start, CellGrid cg, const real *q, NearParams<real> np, real *grad_s,
-                             real *hess_s, cudaStream_t st)
+cudaError_t launch_near_hess64(int64_t N, const int *tgt_base, const double2 *tgt_pos, const double2 *src_pos,
+                               const int *src_start, CellGrid cg, const double *q, NearParams<double> np,
+                               double *grad_s, double *hess_s, cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
-    k_near_hess<real><<<nblocks(N, 256), 256, 0, st>>>(N, tgt_base, tgt_pos, src_pos, src_start, cg, q, np, grad_s,
-                                                       hess_s);
+    k_near_hess64<<<nblocks(N, 256), 256, 0, st>>>(N, tgt_base, tgt_pos, src_pos, src_start, cg, q, np, grad_s,
+                                                   hess_s);
     return cudaGetLastError();
+}
+
+cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,
+                              const float2 *src_lo, const float2 *tgt_hi, const float2 *tgt_lo, const int *tgt_start,
+                              CellGrid cg, const float *c, const void *dn, NearParams<float> np, float *a_s,
+                              float *ga_s, float *cg_s, cudaStream_t st)
+{
+    const NearSides sd{src_base, src_hi, src_lo, tgt_hi, tgt_lo, tgt_start};
+    return with_degree(np.p, [&](auto pc) {
+        NearAdj32<decltype(pc)::value> op{};
+        op.cw = c;
+        op.dnw = (const float2 *)dn;
+        op.a_s = a_s;
+        op.ga_s = ga_s;
+        op.cg_s = cg_s;
+        op.two_over_eps2 = 2.f * np.inv_eps2;
+        op.hess0 = self_hessian(np);
+        return launch_near_warp(n_items, items, sd, cg, np, op, st);
+    });
+}
+
+cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                               const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
+                               CellGrid cg, const float *q, NearParams<float> np, float *grad_s, float *hess_s,
+                               cudaStream_t st)
+{
+    const NearSides sd{tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start};
+    return with_degree(np.p, [&](auto pc) {
+        NearHess32<decltype(pc)::value> op{};
+        op.q = q;
+        op.grad_s = grad_s;
+        op.hess_s = hess_s;
+        op.two_over_eps2 = 2.f * np.inv_eps2;
+        op.hess0 = self_hessian(np);
+        return launch_near_warp(n_items, items, sd, cg, np, op, st);
+    });
 }
 
 template <typename real>
@@ -335,12 +480,6 @@ cudaError_t launch_adj_finish_tgt(int64_t N, const int *perm, const real *grad_s
 #define FS_INST(real)                                                                                           \
     template cudaError_t launch_gather_adj<real>(int64_t, const int *, const void *, const void *, int, double,  \
                                                  double, real *, void *, void *, double *, cudaStream_t);        \
-    template cudaError_t launch_near_adj<real>(int64_t, const int *, const double2 *, const double2 *,          \
-                                               const int *, CellGrid, const real *, const void *,               \
-                                               NearParams<real>, real *, real *, real *, cudaStream_t);         \
-    template cudaError_t launch_near_hess<real>(int64_t, const int *, const double2 *, const double2 *,         \
-                                                const int *, CellGrid, const real *, NearParams<real>, real *,  \
-                                                real *, cudaStream_t);                                          \
     template cudaError_t launch_adj_finish_src<real>(int64_t, const int *, const real *, const real *,          \
                                                      const real *, const real *, double, const double *,        \
                                                      double, void *, void *, int, cudaStream_t);                \

@@ -1,0 +1,292 @@
+// Warp-cooperative FP32 near-field traversal, shared by the forward correction
+// (phi and grad phi at the targets), the Hessian of phi at the targets and the
+// adjoint potential at the sources.
+//
+// A work item is at most 64 consecutive "own" points of one cell (two per lane),
+// sorted by cell and, inside a cell, by 8 x 8 sub-cell in Morton order.  The warp
+// forms the bounding box of its points and visits only the "other" side's
+// sub-cells whose distance to that box is below eps_I (a warp-uniform test per
+// sub-cell).  Each other point there is read once per warp (a broadcast load) and
+// evaluated by all 32 lanes with branch-free masked arithmetic.  Positions are
+// FP32 offsets from the cell corner stored as hi + lo; pairs closer than eps_I / 8
+// refine their difference with an exact TwoSum of the hi parts plus the lo parts,
+// so r keeps full FP32 relative accuracy for nearly coincident points, and exactly
+// coincident pairs are detected (G(0) := 0).
+//
+// With w = r^2 / eps_I^2 and f = G - T_I (T_I the inner polynomial of the
+// regularised kernel, p-fold contact with G at r = eps_I):
+//     f(w)      = -(ln 2 / 4 pi) log2 w - P(w),      P = T_I - k(eps_I), P(1) = 0
+//     c(w)      = f'(r) / r = rc (w - 1)^(p-1) / w,  rc = (-1)^p / (2 pi eps_I^2)
+//     c'(w)     = dc/dw = rc (w - 1)^(p-2) ((p - 2) w + 1) / w^2
+// (the (p-1)-fold root at w = 1 keeps c free of cancellation near r = eps_I), so
+// grad f = c d and Hess f = c I + (2 c' / eps_I^2) d d^T for d = own - other.
+#pragma once
+
+#include <type_traits>
+
+#include "internal.h"
+
+namespace fs {
+
+template <int E> __device__ __forceinline__ float ipow(float x)
+{
+    if constexpr (E == 0) {
+        return 1.0f;
+    } else if constexpr (E == 1) {
+        return x;
+    } else {
+        const float h = ipow<E / 2>(x);
+        if constexpr (E % 2 == 0)
+            return h * h;
+        else
+            return h * h * x;
+    }
+}
+
+__device__ __forceinline__ float warp_min(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// dx from hi parts (a = x_hi - y_hi by TwoSum), the exact cell step and the lo parts.
+__device__ __forceinline__ float refine_diff(float xh, float yh, float off, float xl, float yl)
+{
+    const float a = xh - yh;
+    const float bb = a - xh;
+    const float e = (xh - (a - bb)) + (-yh - bb);
+    return (a + off) + (e + (xl - yl));
+}
+
+// Single MUFU operations (approximate, flush-to-zero): log2 with ~2^-22 absolute error on
+// (0, 16), and the reciprocal with ~1 ulp error; both arguments here are normal numbers.
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// f(w) = G - T_I of one pair.
+template <int P> __device__ __forceinline__ float near_f(const NearParams<float> &np, float w)
+{
+    float pw = np.pbeta[P - 1];
+#pragma unroll
+    for (int i = P - 2; i >= 0; --i)
+        pw = fmaf(pw, w, np.pbeta[i]);
+    const float c_ln = -0.69314718055994531f / (4.0f * 3.14159265358979324f);   // -(ln 2) / (4 pi)
+    return fmaf(c_ln, lg2_approx(w), -pw);
+}
+
+// c(w) and c'(w) of one pair (the 1 / eps_I^2 of c is in rc).
+template <int P> __device__ __forceinline__ void near_c_cp(const NearParams<float> &np, float w, float &c, float &cp)
+{
+    const float rw = rcp_approx(w);
+    if constexpr (P == 1) {
+        c = np.rcoef * rw;
+        cp = -c * rw;
+    } else {
+        const float om = w - 1.f;
+        const float base = np.rcoef * ipow<P - 2>(om) * rw;
+        c = base * om;
+        cp = base * fmaf((float)(P - 2), w, 1.f) * rw;
+    }
+}
+
+// The two point sets of a traversal: the item's own points (one per lane slot) and the
+// other side's points, visited by sub-cell.
+struct NearSides {
+    const int *own_base;
+    const float2 *own_hi, *own_lo;
+    const float2 *oth_hi, *oth_lo;
+    const int *oth_start;
+};
+
+// One warp work item.  Op provides: init(), load(j) (the other point's weights),
+// coincident(np, t), pair(np, t, r2, dx, dy) (masked by r2 < eps_I^2), row_begin(),
+// row_end() (partial sums per sub-cell row), store(t, k).  No lane-divergent branch:
+// the close-pair refinement is taken warp-uniformly when any lane needs it.
+template <class Op>
+__device__ __forceinline__ void near_traverse(int2 item, int lane, const NearSides &sd, const CellGrid &cg,
+                                              const NearParams<float> &np, Op &op)
+{
+    const float h = np.hcell, eps = sqrtf(np.eps2);
+    const float ginv = h / (float)cg.cell;        // one grid line (1 / n_os)
+    bool valid[2];
+    int64_t kt[2];
+    int cc1[2], cc2[2];
+    float2 xh[2], xl[2];
+    float tx0 = 3e38f, tx1 = -3e38f, ty0 = 3e38f, ty1 = -3e38f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        valid[t] = lane + 32 * t < item.y;
+        kt[t] = item.x + lane + 32 * t;
+        const int64_t kk = valid[t] ? kt[t] : item.x;
+        const int packed = sd.own_base[kk];
+        cc1[t] = base1(packed) / cg.cell;
+        cc2[t] = base2(packed) / cg.cell;
+        xh[t] = sd.own_hi[kk];
+        xl[t] = sd.own_lo[kk];
+        if (valid[t]) {
+            const float ax = (float)cc1[t] * h + xh[t].x, ay = (float)cc2[t] * h + xh[t].y;
+            tx0 = fminf(tx0, ax);
+            tx1 = fmaxf(tx1, ax);
+            ty0 = fminf(ty0, ay);
+            ty1 = fmaxf(ty1, ay);
+        }
+    }
+    // bounding box of the warp's points, in "cell * h + offset" coordinates
+    tx0 = warp_min(tx0);
+    tx1 = warp_max(tx1);
+    ty0 = warp_min(ty0);
+    ty1 = warp_max(ty1);
+    // all points of an item share one cell
+    const int c1 = cc1[0], c2 = cc2[0];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (!valid[t])
+            xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
+    const float reach = eps + ginv;               // eps_I plus one grid line for rounding of positions
+    const float reach2 = reach * reach;
+    const int cx0 = max(0, (int)floorf((tx0 - reach) / h)), cx1 = min(cg.n_c - 1, (int)floorf((tx1 + reach) / h));
+    const int cy0 = max(0, (int)floorf((ty0 - reach) / h)), cy1 = min(cg.n_c - 1, (int)floorf((ty1 + reach) / h));
+    op.init();
+    for (int ex = cx0; ex <= cx1; ++ex) {
+        const float offx = (float)(c1 - ex) * h;
+        const float sx0 = (float)ex * h;
+        float2 xs[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+            xs[t].x = xh[t].x + offx;
+        for (int s1 = 0; s1 < kSubEdge; ++s1) {
+            // gap between this sub-cell row and the points' box (warp-uniform)
+            const float lo = sx0 + (float)cg.sub_first(s1) * ginv, hi = sx0 + (float)cg.sub_first(s1 + 1) * ginv;
+            const float gapx = fmaxf(0.f, fmaxf(lo - tx1, tx0 - hi));
+            if (gapx > reach || !(hi > lo))
+                continue;
+            op.row_begin();
+            for (int ey = cy0; ey <= cy1; ++ey) {
+                const float offy = (float)(c2 - ey) * h;
+                const float sy0 = (float)ey * h;
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+                    xs[t].y = xh[t].y + offy;
+                const int kbase = cg.key(ex, ey) * kSub;
+                for (int s2 = 0; s2 < kSubEdge; ++s2) {
+                    const float ylo = sy0 + (float)cg.sub_first(s2) * ginv;
+                    const float yhi = sy0 + (float)cg.sub_first(s2 + 1) * ginv;
+                    const float gapy = fmaxf(0.f, fmaxf(ylo - ty1, ty0 - yhi));
+                    if (gapx * gapx + gapy * gapy > reach2)
+                        continue;                 // no point of this warp is within eps_I of the sub-cell
+                    const int sub = morton_sub(s1, s2);
+                    const int end = sd.oth_start[kbase + sub + 1];
+                    for (int j = sd.oth_start[kbase + sub]; j < end; ++j) {
+                        const float2 yh = __ldg(sd.oth_hi + j);
+                        op.load(j);
+                        // xs = xh + (cell step): one subtraction per coordinate
+                        float dx[2], dy[2], r2[2];
+                        bool close = false;
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            dx[t] = xs[t].x - yh.x;
+                            dy[t] = xs[t].y - yh.y;
+                            r2[t] = dx[t] * dx[t] + dy[t] * dy[t];
+                            close |= r2[t] < np.close2;
+                        }
+                        if (__any_sync(0xffffffffu, close)) {
+                            const float2 yl = __ldg(sd.oth_lo + j);
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                if (r2[t] < np.close2) {
+                                    dx[t] = refine_diff(xh[t].x, yh.x, offx, xl[t].x, yl.x);
+                                    dy[t] = refine_diff(xh[t].y, yh.y, offy, xl[t].y, yl.y);
+                                    r2[t] = dx[t] * dx[t] + dy[t] * dy[t];
+                                    if (dx[t] == 0.f && dy[t] == 0.f) {
+                                        op.coincident(np, t);
+                                        r2[t] = np.eps2;   // masked out below
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+                            op.pair(np, t, r2[t], dx[t], dy[t]);
+                    }
+                }
+            }
+            op.row_end();
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (valid[t])
+            op.store(t, kt[t]);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(128, Op::kMinBlocks) k_near_warp(int64_t n_items, const int2 *__restrict__ items,
+                                                                   NearSides sd, CellGrid cg, NearParams<float> np,
+                                                                   Op op)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_items)
+        return;                                   // whole warp past the end (warp-uniform)
+    near_traverse(items[warp], lane, sd, cg, np, op);
+}
+
+template <class Op> cudaError_t launch_near_warp(int64_t n_items, const int2 *items, const NearSides &sd, CellGrid cg,
+                                                 const NearParams<float> &np, const Op &op, cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_items + 3) / 4);
+    k_near_warp<Op><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, op);
+    return cudaGetLastError();
+}
+
+// Calls f(std::integral_constant<int, P>) for the expansion degree p in 1..16.
+template <class F> cudaError_t with_degree(int p, F &&f)
+{
+    switch (p) {
+#define FS_P_CASE(P)                                                                                             \
+    case P:                                                                                                      \
+        return f(std::integral_constant<int, P>{});
+        FS_P_CASE(1)
+        FS_P_CASE(2)
+        FS_P_CASE(3)
+        FS_P_CASE(4)
+        FS_P_CASE(5)
+        FS_P_CASE(6)
+        FS_P_CASE(7)
+        FS_P_CASE(8)
+        FS_P_CASE(9)
+        FS_P_CASE(10)
+        FS_P_CASE(11)
+        FS_P_CASE(12)
+        FS_P_CASE(13)
+        FS_P_CASE(14)
+        FS_P_CASE(15)
+        FS_P_CASE(16)
+#undef FS_P_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fs

@@ -125,6 +125,32 @@ def test_adjoint_against_direct_gradient(pkg, n, m, eps_I, bound):
         assert err < 2 * fwd_err and err < bound, (err, fwd_err)
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_coincident_points_split_gradients(pkg, precision):
+    """Sources = targets exactly: dL/dy and dL/dx each follow the direct sum's G(0) := 0.
+
+    The far field holds the smooth T_I for a point's own pair, whose Hessian at 0 is not
+    zero; the near field must remove it from both the source and the target side (their
+    sum cancels it anyway, so only the split shows it).
+    """
+    from oracle import direct as D
+    c = _case(205, 1400, 1400, coincident=True, n=128, m=8, eps_I=8 / 128)
+    rng = np.random.default_rng(6)
+    gphi, gH = rng.standard_normal(1400), rng.standard_normal((1400, 2))
+    fs, phi, H = _forward(pkg, c["src"], c["tgt"], c["q"], c, precision)
+    dev = torch.device("cuda", 0)
+    dq, dy, dx = fs.adjoint(torch.tensor(gphi, device=dev), torch.tensor(gH, device=dev), want_src=True,
+                            want_tgt=True, dtype=torch.float64)
+    fs.sync()
+    fs.close()
+    phi_d, H_d = D.direct_sum(c["tgt"], c["src"], c["q"])
+    fwd_err = max(rel(phi, phi_d), rel(H, H_d))
+    dq_o, dy_o, dx_o = D.direct_adjoint(c["tgt"], c["src"], c["q"], gphi, gH)
+    for got, want in ((dq, dq_o), (dy, dy_o), (dx, dx_o)):
+        err = rel(got.cpu().numpy(), want)
+        assert err < 2 * fwd_err and err < 5e-5, (err, fwd_err)
+
+
 def test_fp32_adjoint_close_to_fp64(pkg):
     c = _case(204, 2000, 2000, coincident=True)
     rng = np.random.default_rng(4)
