@@ -144,7 +144,8 @@ def algorithmic_bytes(info, n_points):
 
 
 # DRAM bytes per launch of the near-field kernel from an ncu capture, keyed by the SHA-256 of
-# the kernel source it was taken on (a changed kernel reports null until it is re-captured).
+# the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
+# reports null until it is re-captured).
 NEAR_TRAFFIC = {
     # profiles/k_near32_mixture_2p19.md: 28.13 MB at 2^19 points, scaled by the point count
     "ca94ec2142a597bb983867d936f3b5d2cd8baabefba22c0dc5fb0c1c2c07d9c0": 2 * 28.13e6,
@@ -153,8 +154,10 @@ NEAR_TRAFFIC = {
 
 def near_traffic():
     import hashlib
-    path = os.path.join(ROOT, "paper_0807_2387_gb300", "csrc", "kernels_near.cu")
-    sha = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("kernels_near.cu", "near_warp.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_0807_2387_gb300", "csrc", name), "rb").read())
+    sha = h.hexdigest()
     return NEAR_TRAFFIC.get(sha), sha
 
 

@@ -60,6 +60,8 @@ typedef enum { FS_F32 = 32, FS_F64 = 64 } fs_dtype;
 /* Option flags (fs_opts.flags). */
 #define FS_FLAG_NO_KAHAN 1u   /* FP32 path: plain (uncompensated) grid accumulation */
 #define FS_FLAG_TIMING 2u     /* record per-stage CUDA events (see fs_stage_times) */
+#define FS_FLAG_AUTOTUNE 4u   /* fs_batch_create: choose cell and tile_cells per instance class
+                                 by timing candidate plans */
 
 /* Plan options.  A zeroed struct (or NULL) selects every default. */
 typedef struct {
@@ -71,7 +73,7 @@ typedef struct {
     double eps_B;     /* width of the torus-boundary smoothing zone; 0 -> eps_I */
     int cell;         /* near-field cell edge in oversampled-grid cells;
                          0 -> ceil(eps_I * n_os) (cells never narrower than eps_I) */
-    int tile_cells;   /* spreading tile edge in near-field cells; 0 -> about 32 grid cells */
+    int tile_cells;   /* spreading tile edge in near-field cells; 0 -> about 16 grid cells */
     unsigned flags;   /* FS_FLAG_* */
     void *stream;     /* cudaStream_t for every enqueued call; NULL = default stream */
 } fs_opts;
@@ -87,7 +89,8 @@ typedef struct {
     int cell, cells_per_dim;  /* near-field cells */
     int tile_cells, spread_items;
     int64_t near_pairs;       /* candidate-filtered pairs with r < eps_I (counted at plan time) */
-    int64_t near_pairs_fp64;  /* of those, pairs with r < eps_I/8 (difference taken in FP64) */
+    int64_t near_pairs_fp64;  /* of those, pairs with r < eps_I/8 (FP32 path: difference refined
+                                 from the hi and lo parts of the positions) */
     int64_t workspace_bytes;
     int is_fem;               /* plan built by fs_plan_create_fem */
     int64_t n_nodes, n_tris, n_bedges;
@@ -243,6 +246,96 @@ fs_status fs_stage_times(fs_plan *plan, double *ms, int count);
 
 /* Release the plan and its workspace (synchronises its stream first). */
 fs_status fs_plan_destroy(fs_plan *plan);
+
+/*
+ * Batched solves.  The paper has no counterpart: it solves one problem at a time.
+ * A batch holds `count` independent instances (own points, grid size n_grid and
+ * radius eps_I; shared sigma_os, m_window, precision and smoothness degree p) and
+ * nrhs charge vectors per instance, and evaluates all of them with one launch per
+ * stage (charges, spreading, FFT + multiply, interpolation, near field, output)
+ * over all (instance, right-hand side, work unit) items, replayed as one CUDA
+ * graph.  The FFT stage is one persistent launch whose blocks wait on each other
+ * through counters; those waits are bounded and a wait that gives up sets an
+ * error word reported by fs_batch_sync_status as FS_ETIMEOUT.
+ */
+typedef struct fs_batch fs_batch;
+
+typedef struct {
+    const double *src_xy;   /* [device] (M, 2) float64 */
+    int64_t M;
+    const double *tgt_xy;   /* [device] (N, 2) float64, may equal src_xy */
+    int64_t N;
+    int n_grid;             /* as fs_plan_create */
+    double eps_I;           /* as fs_plan_create */
+} fs_instance;
+
+typedef struct {
+    int count, nrhs, precision;
+    int64_t total_src, total_tgt;
+    int spread_items;       /* spreading work items over all instances (x nrhs per launch) */
+    int fft_units;          /* row pairs + columns + inverse row pairs, all instances and rhs */
+    int fft_blocks;         /* persistent blocks of the FFT launch */
+    int64_t near_items;     /* FP32 near-field warp items over all instances */
+    int64_t workspace_bytes;
+} fs_batch_facts;
+
+/*
+ * Create a batch.  Every instance is planned as by fs_plan_create (its plan is
+ * reachable through fs_batch_plan); opts applies to all (opts.cell and
+ * opts.tile_cells, if set, to every instance).  With FS_FLAG_AUTOTUNE (and cell,
+ * tile_cells left 0) each class of instances - same n_grid, m, sigma, p,
+ * precision and rounded log2 of N and of M - gets the near-field cell (1, 1.5 or
+ * 2 times the narrowest) and spreading tile (about 16, 32 or 64 grid lines) that
+ * evaluated fastest on the class's first instance; choices are cached for the
+ * process.
+ *  inst   [host] count descriptors; the point arrays are read during the call only
+ *  nrhs   1..4 charge vectors per instance
+ * Returns FS_EINVAL (bad argument; instances with different p), FS_ENOMEM, FS_ECUDA.
+ * With opts.stream NULL the batch creates its own blocking stream (the legacy
+ * default stream cannot be captured into a graph).  Synchronising.
+ */
+fs_status fs_batch_create(const fs_instance *inst, int count, double sigma_os, int m_window, int nrhs,
+                          const fs_opts *opts, fs_batch **out);
+
+/*
+ * Evaluate phi and H of every instance and charge vector.
+ *  q   [host] array of count [device] pointers, instance i: (nrhs, M_i) of q_dtype
+ *  phi [host] array of count [device] pointers (nrhs, N_i), or NULL (no potential);
+ *      individual entries may be NULL
+ *  H   [host] array of count [device] pointers (nrhs, N_i, 2), or NULL; entries may be NULL
+ * The pointer arrays are read during the call; the first evaluation with a given
+ * (q_dtype, out_dtype) captures and instantiates the graph, later ones replay it.
+ * Enqueued on the batch's stream; device-side failures are reported by
+ * fs_batch_sync_status.
+ */
+fs_status fs_batch_eval(fs_batch *batch, const void *const *q, fs_dtype q_dtype, void *const *phi,
+                        void *const *H, fs_dtype out_dtype);
+
+/* Wait for the batch's stream; FS_ETIMEOUT if a bounded device wait gave up since the last call. */
+fs_status fs_batch_sync_status(fs_batch *batch);
+
+/* Batch facts (host). */
+fs_status fs_batch_info(const fs_batch *batch, fs_batch_facts *info);
+
+/*
+ * The plan of instance i (owned by the batch; valid until fs_batch_destroy).  It
+ * accepts every fs_* plan call (fs_plan_info shows the chosen cell and tile;
+ * fs_set_charges + fs_eval_field solve the instance on its own) on the batch's
+ * stream; do not destroy it.
+ */
+fs_status fs_batch_plan(fs_batch *batch, int i, fs_plan **out);
+
+/* Release the batch, its plans and graphs (synchronises its stream first). */
+fs_status fs_batch_destroy(fs_batch *batch);
+
+/*
+ * Runs one bounded device wait (the wait of the batched FFT) on a counter that
+ * nothing increments, giving up after `spins` polls of about 0.1 us.  Returns
+ * FS_ETIMEOUT when the wait gave up and recorded it - the expected outcome - and
+ * leaves the CUDA context usable.  The paper has no counterpart; it exists to
+ * check the timeout path without a fault.
+ */
+fs_status fs_wait_selftest(int spins);
 
 /* Message for the last failing call on this host thread ("" if none). */
 const char *fs_last_error(void);

@@ -9,23 +9,28 @@ the library is missing, importing works but the first call raises
 The functions ``fs_plan_create``, ``fs_plan_create_fem``, ``fs_set_charges``,
 ``fs_set_magnetization``, ``fs_fem_charges``, ``fs_fem_sources``,
 ``fs_eval_potential``, ``fs_eval_field``, ``fs_solve_host``, ``fs_sync_status``,
-``fs_plan_info``, ``fs_stage_times`` and ``fs_plan_destroy`` mirror the C entry
-points one to one, taking torch tensors (or numpy arrays for host buffers).
-``FastSum`` wraps a plan with tensor-returning methods.
+``fs_plan_info``, ``fs_stage_times``, ``fs_plan_destroy``, ``fs_adjoint`` and the
+batch calls ``fs_batch_create``, ``fs_batch_eval``, ``fs_batch_sync_status``,
+``fs_batch_info``, ``fs_batch_plan``, ``fs_batch_destroy`` and
+``fs_wait_selftest`` mirror the C entry points one to one, taking torch tensors
+(or numpy arrays for host buffers).  ``FastSum`` wraps a plan and
+``FastSumBatch`` a batch with tensor-returning methods.
 """
 
 from __future__ import annotations
 
 import ctypes
 
-from ._native import (FS_F32, FS_F64, FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FastSumError,  # noqa: F401
-                      FsInfo, FsOpts, NativeLibraryMissing, check, load)
+from ._native import (FS_F32, FS_F64, FS_FLAG_AUTOTUNE, FS_FLAG_NO_KAHAN, FS_FLAG_TIMING,  # noqa: F401
+                      FastSumError, FsBatchFacts, FsInfo, FsInstance, FsOpts, NativeLibraryMissing, check, load)
 
 __all__ = [
     "FastSum", "FastSumError", "NativeLibraryMissing", "FS_F32", "FS_F64", "FS_FLAG_NO_KAHAN",
     "FS_FLAG_TIMING", "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization",
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path", "FastSumFn",
+    "FS_FLAG_AUTOTUNE", "FastSumBatch", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status",
+    "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest",
 ]
 
 
@@ -211,6 +216,63 @@ def fs_plan_destroy(plan):
         check(load().fs_plan_destroy(plan), "fs_plan_destroy")
 
 
+def fs_batch_create(instances, sigma_os, m_window, nrhs, **opts):
+    """instances: sequence of (src (M,2), tgt (N,2) float64 CUDA tensors, n_grid, eps_I) -> batch handle."""
+    torch = _torch()
+    arr = (FsInstance * len(instances))()
+    for i, (src, tgt, n_grid, eps_I) in enumerate(instances):
+        arr[i] = FsInstance(_dev_ptr(src, torch.float64, "src"), int(src.shape[0]), _dev_ptr(tgt, torch.float64, "tgt"),
+                            int(tgt.shape[0]), int(n_grid), float(eps_I))
+    handle = ctypes.c_void_p()
+    o = _opts(**opts)
+    check(load().fs_batch_create(arr, len(instances), float(sigma_os), int(m_window), int(nrhs), ctypes.byref(o),
+                                 ctypes.byref(handle)), "fs_batch_create")
+    return handle
+
+
+def _ptr_array(tensors, name):
+    if tensors is None:
+        return None
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else _dev_ptr(t, name=name).value
+    return arr
+
+
+def fs_batch_eval(batch, q, phi, H):
+    """q: list of (nrhs, M_i) CUDA tensors; phi: list of (nrhs, N_i) or None; H: list of (nrhs, N_i, 2) or None."""
+    q_code = _dtype_code(q[0].dtype)
+    ref = H[0] if H is not None else phi[0]
+    check(load().fs_batch_eval(batch, _ptr_array(q, "q"), q_code, _ptr_array(phi, "phi"), _ptr_array(H, "H"),
+                               _dtype_code(ref.dtype)), "fs_batch_eval")
+
+
+def fs_batch_sync_status(batch):
+    check(load().fs_batch_sync_status(batch), "fs_batch_sync_status")
+
+
+def fs_batch_info(batch) -> dict:
+    info = FsBatchFacts()
+    check(load().fs_batch_info(batch, ctypes.byref(info)), "fs_batch_info")
+    return info.as_dict()
+
+
+def fs_batch_plan(batch, i):
+    h = ctypes.c_void_p()
+    check(load().fs_batch_plan(batch, int(i), ctypes.byref(h)), "fs_batch_plan")
+    return h
+
+
+def fs_batch_destroy(batch):
+    if batch:
+        check(load().fs_batch_destroy(batch), "fs_batch_destroy")
+
+
+def fs_wait_selftest(spins):
+    """Status of one bounded device wait on a counter nothing increments (FS_ETIMEOUT expected)."""
+    return int(load().fs_wait_selftest(int(spins)))
+
+
 STAGES = ("charges", "spread", "fft_rows_fwd", "fft_cols_mul", "fft_rows_inv", "interp", "near", "unpermute")
 
 
@@ -225,8 +287,9 @@ class FastSum:
     """
 
     def __init__(self, src=None, tgt=None, n_grid=None, sigma_os=2.0, m_window=6, eps_I=None, _handle=None,
-                 **opts):
+                 _owned=True, **opts):
         torch = _torch()
+        self._owned = _owned
         if _handle is None:
             self._h = fs_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
             self.device = src.device
@@ -312,7 +375,61 @@ class FastSum:
 
     def close(self):
         if getattr(self, "_h", None):
-            fs_plan_destroy(self._h)
+            if getattr(self, "_owned", True):
+                fs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FastSumBatch:
+    """Many fast summations evaluated together (one launch per stage, one CUDA graph).
+
+    ``FastSumBatch([(src, tgt, n_grid, eps_I), ...], sigma_os, m_window, nrhs,
+    precision=32, flags=FS_FLAG_AUTOTUNE)``; ``eval(q_list)`` returns the lists
+    of potentials (nrhs, N_i) and fields (nrhs, N_i, 2); ``plan(i)`` is a
+    non-owning ``FastSum`` of instance i (for solving it on its own).
+    """
+
+    def __init__(self, instances, sigma_os=2.0, m_window=5, nrhs=1, **opts):
+        torch = _torch()
+        self._h = fs_batch_create(instances, sigma_os, m_window, nrhs, **opts)
+        self.device = instances[0][0].device
+        self.nrhs = int(nrhs)
+        self.sizes = [(int(src.shape[0]), int(tgt.shape[0])) for src, tgt, _, _ in instances]
+        self.info = fs_batch_info(self._h)
+        self._dtype = torch.float64 if self.info["precision"] == 64 else torch.float32
+
+    def outputs(self, dtype=None, with_phi=True):
+        """Preallocated (phi list, H list) for eval_into."""
+        torch = _torch()
+        dtype = dtype or self._dtype
+        phi = [torch.empty((self.nrhs, n), dtype=dtype, device=self.device) for _, n in self.sizes] \
+            if with_phi else None
+        H = [torch.empty((self.nrhs, n, 2), dtype=dtype, device=self.device) for _, n in self.sizes]
+        return phi, H
+
+    def eval_into(self, q, phi, H):
+        fs_batch_eval(self._h, [t.contiguous() for t in q], phi, H)
+
+    def eval(self, q, dtype=None, with_phi=True):
+        phi, H = self.outputs(dtype, with_phi)
+        self.eval_into(q, phi, H)
+        return phi, H
+
+    def plan(self, i):
+        return FastSum(_handle=fs_batch_plan(self._h, i), _owned=False)
+
+    def sync(self):
+        fs_batch_sync_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            fs_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -12,13 +12,14 @@ FS_OK, FS_EINVAL, FS_EDOMAIN, FS_ENOMEM, FS_ECUDA, FS_ETIMEOUT, FS_EUNSUPPORTED 
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_EDOMAIN", 3: "FS_ENOMEM", 4: "FS_ECUDA",
                 5: "FS_ETIMEOUT", 6: "FS_EUNSUPPORTED"}
 FS_F32, FS_F64 = 32, 64
-FS_FLAG_NO_KAHAN, FS_FLAG_TIMING = 1, 2
+FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FS_FLAG_AUTOTUNE = 1, 2, 4
 
 EXPORTED = (
     "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization", "fs_set_magnetization_static",
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "fs_last_error",
-    "fs_version",
+    "fs_version", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status", "fs_batch_info", "fs_batch_plan",
+    "fs_batch_destroy", "fs_wait_selftest",
 )
 
 
@@ -39,6 +40,21 @@ class FsInfo(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("near_pairs_fp64", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("is_fem", ctypes.c_int),
                 ("n_nodes", ctypes.c_int64), ("n_tris", ctypes.c_int64), ("n_bedges", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class FsInstance(ctypes.Structure):
+    _fields_ = [("src_xy", ctypes.c_void_p), ("M", ctypes.c_int64), ("tgt_xy", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("n_grid", ctypes.c_int), ("eps_I", ctypes.c_double)]
+
+
+class FsBatchFacts(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("nrhs", ctypes.c_int), ("precision", ctypes.c_int),
+                ("total_src", ctypes.c_int64), ("total_tgt", ctypes.c_int64),
+                ("spread_items", ctypes.c_int), ("fft_units", ctypes.c_int), ("fft_blocks", ctypes.c_int),
+                ("near_items", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -80,6 +96,13 @@ def load(path: str = LIB_PATH):
         "fs_plan_info": [P, ctypes.POINTER(FsInfo)],
         "fs_stage_times": [P, ctypes.POINTER(ctypes.c_double), I32],
         "fs_plan_destroy": [P],
+        "fs_batch_create": [ctypes.POINTER(FsInstance), I32, D, I32, I32, ctypes.POINTER(FsOpts), PP],
+        "fs_batch_eval": [P, PP, I32, PP, PP, I32],
+        "fs_batch_sync_status": [P],
+        "fs_batch_info": [P, ctypes.POINTER(FsBatchFacts)],
+        "fs_batch_plan": [P, I32, PP],
+        "fs_batch_destroy": [P],
+        "fs_wait_selftest": [I32],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

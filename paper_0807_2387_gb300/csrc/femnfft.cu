@@ -15,12 +15,15 @@
 
 #include "../../include/femnfft.h"
 #include "internal.h"
+#include "plan.h"
 
 using namespace fs;
 
-namespace {
+namespace fs {
 
+namespace {
 thread_local std::string g_last_error;
+}
 
 fs_status fail(fs_status st, const std::string &msg)
 {
@@ -28,22 +31,9 @@ fs_status fail(fs_status st, const std::string &msg)
     return st;
 }
 
-#define FS_CUDA(call)                                                                                   \
-    do {                                                                                                \
-        cudaError_t e_ = (call);                                                                        \
-        if (e_ != cudaSuccess)                                                                          \
-            return fail(FS_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_));           \
-    } while (0)
+}  // namespace fs
 
-#define FS_TRY(expr)                                                                                    \
-    do {                                                                                                \
-        fs_status s_ = (expr);                                                                          \
-        if (s_ != FS_OK)                                                                                \
-            return s_;                                                                                  \
-    } while (0)
-
-constexpr int kStages = 8;
-constexpr int kSpreadChunk = 512;   // sources per spreading work item
+namespace {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -119,122 +109,8 @@ bool near_coefficients(double eps, int p, double *beta)
 
 }  // namespace
 
-struct fs_plan {
-    // parameters
-    int precision = 32;
-    int n = 0, n_os = 0, m = 0, p = 0;
-    double sigma = 0, eps_I = 0, eps_B = 0, s = 1.0;
-    int64_t M = 0, N = 0;
-    int window_lo = 0, n_a = 0, pitch = 0, ld = 0;
-    CellGrid cg{};
-    int n_keys = 0;
-    unsigned flags = 0;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    bool kahan = true;
-    KernelParams kp{};
-    double beta[kMaxP] = {0};
-    WindowPoly wpoly{};               // FP32 window polynomials (per tap)
-    // device memory
-    std::vector<void *> allocs;
-    int64_t bytes = 0;
-    int *status = nullptr;
-    int *src_perm = nullptr, *tgt_perm = nullptr;
-    int *src_base = nullptr, *tgt_base = nullptr;
-    void *src_frac = nullptr, *tgt_frac = nullptr;
-    double2 *src_pos = nullptr, *tgt_pos = nullptr;
-    float2 *src_pos32 = nullptr, *tgt_pos32 = nullptr;
-    float2 *src_lo32 = nullptr, *tgt_lo32 = nullptr;
-    int *src_start = nullptr, *tgt_start = nullptr;
-    SpreadItem *items = nullptr;
-    int n_items = 0;
-    SpreadItem *tgt_items = nullptr;  // adjoint: spreading at the targets
-    int n_tgt_items = 0;
-    // adjoint workspace (allocated by the first fs_adjoint call)
-    void *adj_c = nullptr, *adj_dn = nullptr, *adj_df = nullptr;
-    void *adj_a = nullptr, *adj_ga = nullptr, *adj_cg = nullptr, *adj_hess = nullptr;
-    double *adj_gsum = nullptr;
-    int2 *near_items = nullptr;       // FP32 near field: (first target, count <= 64) per warp
-    int64_t n_near_items = 0;
-    int2 *src_near_items = nullptr;   // FP32 adjoint near field: (first source, count <= 64) per warp
-    int64_t n_src_near_items = 0;
-    void *mul = nullptr, *tw = nullptr;
-    void *grid = nullptr, *spec = nullptr;
-    void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
-    // charges
-    void *q_sorted = nullptr;
-    double *q_sum = nullptr;
-    int nrhs = 0, nrhs_cap = 0;
-    // FEM
-    bool is_fem = false;
-    int64_t Nv = 0, Nt = 0, Ne = 0;
-    const double2 *nodes = nullptr;   // caller's (valid while the plan is used)
-    int *tris = nullptr, *bedges = nullptr;
-    double2 *fem_src = nullptr;
-    double *q_canon = nullptr;
-    int64_t q_canon_cap = 0;
-    // host staging for fs_solve_host
-    void *d_q_stage = nullptr, *d_phi_stage = nullptr, *d_H_stage = nullptr;
-    size_t q_stage_bytes = 0, phi_stage_bytes = 0, H_stage_bytes = 0;
-    // stats
-    int64_t near_pairs = 0, near_pairs_fp64 = 0;
-    // timing
-    cudaEvent_t ev[kStages + 1] = {};
-    cudaEvent_t ev_q0 = nullptr, ev_q1 = nullptr;
-    bool events = false;
-
-    template <typename T> fs_status alloc(T **out, size_t count)
-    {
-        *out = nullptr;
-        if (count == 0)
-            count = 1;
-        void *p_ = nullptr;
-        const size_t nbytes = count * sizeof(T);
-        cudaError_t e = cudaMalloc(&p_, nbytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(FS_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed: " +
-                                       cudaGetErrorString(e));
-        }
-        allocs.push_back(p_);
-        bytes += (int64_t)nbytes;
-        *out = static_cast<T *>(p_);
-        return FS_OK;
-    }
-    fs_status alloc_bytes(void **out, size_t nbytes)
-    {
-        unsigned char *p_ = nullptr;
-        FS_TRY(alloc(&p_, nbytes));
-        *out = p_;
-        return FS_OK;
-    }
-    void release(void *ptr)
-    {
-        if (!ptr)
-            return;
-        auto it = std::find(allocs.begin(), allocs.end(), ptr);
-        if (it != allocs.end()) {
-            cudaFree(ptr);
-            allocs.erase(it);
-        }
-    }
-    size_t rsize() const { return precision == 64 ? 8 : 4; }
-};
 
 namespace {
-
-template <typename real> Window<real> make_window(const fs_plan *pl)
-{
-    const double b = kPi * (2.0 - 1.0 / pl->sigma);
-    const double m = pl->m;
-    Window<real> w;
-    w.m = (real)m;
-    w.m2 = (real)(m * m);
-    w.b = (real)b;
-    w.bm = (real)(b * m);
-    w.S = (real)(m * b / (1.0 - std::exp(-2.0 * b * m)));
-    return w;
-}
 
 // Per-tap polynomial form of the normalised window for the FP32 kernels: for tap a the
 // function frac -> psi(frac + m - 1 - a) on [0, 1) is interpolated at kPolyD + 1 Chebyshev
@@ -291,28 +167,6 @@ void build_window_poly(const fs_plan *pl, WindowPoly *wp)
     (void)D;
 }
 
-template <typename real> NearParams<real> make_near(const fs_plan *pl)
-{
-    NearParams<real> np{};
-    np.p = pl->p;
-    np.eps2 = (real)(pl->eps_I * pl->eps_I);
-    np.inv_eps2 = (real)(1.0 / (pl->eps_I * pl->eps_I));
-    np.close2 = (real)((pl->eps_I / 8.0) * (pl->eps_I / 8.0));
-    np.hcell = (real)((double)pl->cg.cell / pl->n_os);
-    for (int k = 0; k < pl->p; ++k)
-        np.beta[k] = (real)pl->beta[k];
-    for (int k = 1; k < pl->p; ++k)
-        np.dbeta[k - 1] = (real)(2.0 * k * pl->beta[k] / (pl->eps_I * pl->eps_I));
-    // T_I - k(eps_I) vanishes at r = eps_I; and since k - T_I has a zero of order p there, the
-    // gradient numerator R(w) = -(1/2pi) - sum_k 2k beta_k w^k (degree p-1) is c (w-1)^(p-1).
-    const double k_eps = -std::log(pl->eps_I) / (2.0 * kPi);
-    for (int k = 0; k < pl->p; ++k)
-        np.pbeta[k] = (real)(k == 0 ? pl->beta[0] - k_eps : pl->beta[k]);
-    // R(w) = c (w-1)^(p-1) with R(0) = -(1/2pi) gives c = (-1)^p / (2pi), independent of beta
-    np.rcoef = (real)(((pl->p % 2 == 0) ? 1.0 : -1.0) / (2.0 * kPi * pl->eps_I * pl->eps_I));
-    return np;
-}
-
 // Bin one point set: keys, counting sort, per-point records.
 template <typename real>
 fs_status bin_points(fs_plan *pl, const double *xy, int64_t n, int **perm, int **base, void **frac, double2 **pos,
@@ -359,7 +213,8 @@ fs_status bin_points(fs_plan *pl, const double *xy, int64_t n, int **perm, int *
 // cell wide); sparser sub-cells of the same cell are merged up to 64.  Items are ordered by
 // estimated work (points x "other" points in the 3 x 3 cells around the item's cell),
 // largest first, so the heavy warps start early and the tail of the launch stays short.
-fs_status build_near_items(fs_plan *pl, const int *own_start_d, const int *oth_start_d, int2 **out, int64_t *n_out)
+fs_status build_near_items(fs_plan *pl, const int *own_start_d, const int *oth_start_d, int2 **out, int64_t *n_out,
+                           std::vector<int2> *items_out = nullptr, std::vector<int64_t> *work_out = nullptr)
 {
     constexpr int kCap = 64, kOwn = 32;
     std::vector<int> start(pl->n_keys + 1), oth(pl->n_keys + 1);
@@ -421,6 +276,13 @@ fs_status build_near_items(fs_plan *pl, const int *own_start_d, const int *oth_s
     std::stable_sort(wi.begin(), wi.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
     for (size_t i = 0; i < items.size(); ++i)
         items[i] = wi[i].second;
+    if (items_out)
+        *items_out = items;
+    if (work_out) {
+        work_out->resize(items.size());
+        for (size_t i = 0; i < items.size(); ++i)
+            (*work_out)[i] = wi[i].first;
+    }
     *n_out = (int64_t)items.size();
     FS_TRY(pl->alloc(out, items.size()));
     if (!items.empty())
@@ -637,6 +499,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
             for (int s0 = a; s0 < b2; s0 += kSpreadChunk)
                 items.push_back(SpreadItem{t, s0, std::min(kSpreadChunk, b2 - s0), 0});
         }
+        if (side == 0)
+            pl->items_h = items;
         SpreadItem **dst = side == 0 ? &pl->items : &pl->tgt_items;
         (side == 0 ? pl->n_items : pl->n_tgt_items) = (int)items.size();
         FS_TRY(pl->alloc(dst, items.size()));
@@ -645,7 +509,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     }
 
     if (pl->precision == 32)
-        FS_TRY(build_near_items(pl, pl->tgt_start, pl->src_start, &pl->near_items, &pl->n_near_items));
+        FS_TRY(build_near_items(pl, pl->tgt_start, pl->src_start, &pl->near_items, &pl->n_near_items,
+                                &pl->near_items_h, &pl->near_work_h));
 
     // coefficient table and FFT twiddles
     FS_TRY(coefficients<real>(pl));
@@ -683,6 +548,10 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     return FS_OK;
 }
 
+}  // namespace
+
+namespace fs {
+
 fs_status plan_create_common(const double *src, int64_t M, const double *tgt, int64_t N, int n_grid,
                              double sigma_os, int m, double eps_I, const fs_opts *opts, fs_plan *pl)
 {
@@ -696,7 +565,7 @@ fs_status plan_create_common(const double *src, int64_t M, const double *tgt, in
     return plan_init<float>(pl, src, M, tgt, N, n_grid, sigma_os, m, eps_I, o);
 }
 
-void destroy(fs_plan *pl)
+void plan_destroy(fs_plan *pl)
 {
     if (!pl)
         return;
@@ -712,6 +581,10 @@ void destroy(fs_plan *pl)
         cudaEventDestroy(pl->ev_q1);
     delete pl;
 }
+
+}  // namespace fs
+
+namespace {
 
 template <typename real> fs_status set_charges_t(fs_plan *pl, const void *q, fs_dtype dtype, int nrhs)
 {
@@ -963,7 +836,7 @@ fs_status fs_plan_create(const double *src_xy, int64_t M, const double *tgt_xy, 
     fs_status st = plan_create_common(src_xy, M, tgt_xy, N, n_grid, sigma_os, m_window, eps_I, opts, pl);
     if (st != FS_OK) {
         const std::string msg = g_last_error;
-        destroy(pl);
+        plan_destroy(pl);
         g_last_error = msg;
         return st;
     }
@@ -1022,7 +895,7 @@ fs_status fs_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tri
     fs_status st = body();
     if (st != FS_OK) {
         const std::string msg = g_last_error;
-        destroy(pl);
+        plan_destroy(pl);
         g_last_error = msg;
         return st;
     }
@@ -1236,7 +1109,7 @@ fs_status fs_plan_destroy(fs_plan *plan)
 {
     if (!plan)
         return FS_OK;
-    destroy(plan);
+    plan_destroy(plan);
     return FS_OK;
 }
 

@@ -43,6 +43,83 @@ template <typename real> struct NearParams {
     int p;
 };
 
+// ---- batched solves: one launch per stage over all instances and right-hand sides
+
+// One instance of a batch as its kernels see it (device memory, filled when the batch is
+// created).  Point data, tables and twiddles belong to the instance's plan; the buffers per
+// right-hand side belong to the batch (right-hand side r at offset r * stride).
+template <typename real> struct BatchInst {
+    int n, L, n_a, pitch, ld;
+    CellGrid cg;
+    int64_t M, N;
+    const int *src_base, *tgt_base;
+    const void *src_frac, *tgt_frac;
+    const double2 *src_pos, *tgt_pos;               // FP64 positions (FP64 near field)
+    const float2 *src_hi, *src_lo, *tgt_hi, *tgt_lo; // FP32 cell-relative positions
+    const int *src_start, *src_perm, *tgt_perm;
+    const real *mul;
+    const typename Cplx<real>::type *tw;
+    real *q;                                         // sorted charges, stride M
+    real *grid;                                      // active window, stride grid_stride
+    typename Cplx<real>::type *spec;                 // half spectrum, stride spec_stride
+    real *phi_s, *grad_s, *coinc;                    // strides N, 2N, N
+    double *q_sum;                                   // one per right-hand side
+    int64_t grid_stride, spec_stride;
+    double s, shift;
+    NearParams<real> np;
+};
+
+// Caller buffers of one instance for one batched evaluation (device pointers).
+struct BatchIO {
+    const void *q;   // (nrhs, M)
+    void *phi;       // (nrhs, N) or null
+    void *H;         // (nrhs, N, 2) or null
+};
+
+// Block -> instance map of a per-point batched launch: block b belongs to instance inst[b]
+// and is block b - first[inst[b]] of that instance.
+struct BlockMap {
+    const int *inst;
+    const int *first;
+};
+
+// Work unit of the batched persistent FFT.  kind 0: forward row pair, 1: column (forward
+// FFT, multiply, inverse FFT), 2: inverse row pair; index = row pair or column l1.
+struct FftUnit {
+    int inst, rhs, kind, index;
+};
+
+// Device-side wait budget of the persistent FFT (spins of ~0.1 us each before the wait
+// gives up and records a timeout).
+constexpr int kWaitSpins = 1 << 23;
+
+template <typename real>
+cudaError_t launch_batch_gather_charges(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks,
+                                        int nrhs, int q_is_f64, cudaStream_t st);
+template <typename real>
+cudaError_t launch_batch_spread(const SpreadItem *items, int n_items, int nrhs, const BatchInst<real> *inst, int m,
+                                int max_tile, Window<real> w, const WindowPoly &wp, bool kahan, cudaStream_t st);
+template <typename real>
+cudaError_t prepare_batch_spread(int m, int max_tile, bool kahan);
+template <typename real>
+cudaError_t launch_batch_interp(const BatchInst<real> *inst, BlockMap bm, int blocks, int nrhs, int m,
+                                Window<real> w, const WindowPoly &wp, cudaStream_t st);
+// counters: 2 * n_inst * nrhs ints (rows done, columns done) plus the queue head, zeroed
+// before each launch; err: set to 1 when a wait ran out of spins
+template <typename real>
+cudaError_t launch_batch_fft(const BatchInst<real> *inst, const FftUnit *units, int n_units, int n_inst, int nrhs,
+                             int L_max, int grid_blocks, int *counters, int *err, int spins, cudaStream_t st);
+template <typename real> cudaError_t batch_fft_blocks(int L_max, int *blocks);
+// one bounded wait on a counter that nothing increments (the timeout path, for tests)
+cudaError_t launch_wait_selftest(int *counter, int *err, int spins, cudaStream_t st);
+// items: (first target, count <= 64, instance, 0) per warp
+cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchInst<float> *inst, int p, int nrhs,
+                                cudaStream_t st);
+cudaError_t launch_batch_near64(const BatchInst<double> *inst, BlockMap bm, int blocks, int nrhs, cudaStream_t st);
+template <typename real>
+cudaError_t launch_batch_unpermute(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks, int nrhs,
+                                   int out_is_f64, cudaStream_t st);
+
 // ---- binning (kernels_bin.cu)
 cudaError_t launch_rmax(const double *xy, int64_t n, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_point_keys(const double *xy, int64_t n, double s, int n_os, int window_lo, int n_a,

@@ -179,6 +179,24 @@ __global__ void k_gather_points(const double *__restrict__ xy, const int *__rest
     }
 }
 
+// Sum v over the block (all threads take part) and add the total to *dst.
+__device__ __forceinline__ void block_sum_add(double acc, double *dst)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1)
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0)
+            atomicAdd(dst, acc);
+    }
+}
+
 template <typename real>
 __global__ void k_gather_charges(const void *__restrict__ q, int q_is_f64, const int *__restrict__ perm,
                                  int64_t M, real *__restrict__ q_sorted, double *__restrict__ q_sum)
@@ -191,19 +209,27 @@ __global__ void k_gather_charges(const void *__restrict__ q, int q_is_f64, const
         q_sorted[(int64_t)r * M + k] = (real)v;
         acc += v;
     }
-    for (int o = 16; o > 0; o >>= 1)
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ double part[32];
-    if ((threadIdx.x & 31) == 0)
-        part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1)
-            acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0)
-            atomicAdd(&q_sum[r], acc);
+    block_sum_add(acc, &q_sum[r]);
+}
+
+// Batched gather: block -> (instance, block of its sources), blockIdx.y = right-hand side.
+template <typename real>
+__global__ void k_batch_gather_charges(const BatchInst<real> *__restrict__ inst, const BatchIO *__restrict__ io,
+                                       BlockMap bm, int q_is_f64)
+{
+    const int i = bm.inst[blockIdx.x];
+    const BatchInst<real> &b = inst[i];
+    const int r = blockIdx.y;
+    const int64_t M = b.M;
+    const int64_t k = (int64_t)(blockIdx.x - bm.first[i]) * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (k < M) {
+        const int64_t src = (int64_t)r * M + b.src_perm[k];
+        const void *q = io[i].q;
+        v = q_is_f64 ? ((const double *)q)[src] : (double)((const float *)q)[src];
+        b.q[(int64_t)r * M + k] = (real)v;
     }
+    block_sum_add(v, &b.q_sum[r]);
 }
 
 __global__ void k_near_count(const double2 *__restrict__ tgt_pos, const int *__restrict__ tgt_base, int64_t N,
@@ -336,6 +362,21 @@ cudaError_t launch_near_count(const double2 *tgt_pos, const int *tgt_base, int64
                                                       counts);
     return cudaGetLastError();
 }
+
+template <typename real>
+cudaError_t launch_batch_gather_charges(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks,
+                                        int nrhs, int q_is_f64, cudaStream_t st)
+{
+    if (blocks <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    k_batch_gather_charges<real><<<dim3((unsigned)blocks, (unsigned)nrhs), 256, 0, st>>>(inst, io, bm, q_is_f64);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_batch_gather_charges<float>(const BatchInst<float> *, const BatchIO *, BlockMap, int, int,
+                                                        int, cudaStream_t);
+template cudaError_t launch_batch_gather_charges<double>(const BatchInst<double> *, const BatchIO *, BlockMap, int,
+                                                         int, int, cudaStream_t);
 
 template cudaError_t launch_gather_points<float>(const double *, const int *, int64_t, double, int, int, int, int, int,
                                                  double2 *, void *, int *, float2 *, float2 *, cudaStream_t);

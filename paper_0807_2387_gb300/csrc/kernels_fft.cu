@@ -78,15 +78,24 @@ __device__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<
     return src;
 }
 
-// Two real rows (r, r+1) of the window -> half spectra, bins 0..n_half, written to spec[l1 * ld + r].
-template <typename real>
-__global__ void k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a, int L, int n_half,
-                               cplx<real> *__restrict__ spec, int ld, const cplx<real> *__restrict__ tw)
+// Loads of data that other blocks of the same launch wrote (the batched transform) go
+// through L2 (ld.global.cg); elsewhere plain loads.
+template <bool CG, typename T> __device__ __forceinline__ T load(const T *p)
 {
-    extern __shared__ unsigned char smem_raw[];
-    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cplx<real> *b = a + L;
-    const int r = 2 * blockIdx.x;
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// Two real rows (2 rp, 2 rp + 1) of the window -> half spectra, bins 0..n_half, written to
+// spec[l1 * ld + r].  a, b: 2 L complex values of shared memory.
+template <typename real>
+__device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ grid, int pitch, int n_a, int L,
+                                              int n_half, cplx<real> *__restrict__ spec, int ld,
+                                              const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
+{
+    const int r = 2 * rp;
     const bool has2 = r + 1 < n_a;
     for (int c = threadIdx.x; c < L; c += blockDim.x) {
         cplx<real> z;
@@ -111,20 +120,17 @@ __global__ void k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a
     }
 }
 
-// Column l1 = blockIdx.x: forward FFT over rows, multiply, inverse FFT, keep the window rows.
-template <typename real>
-__global__ void k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
-                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw)
+// Column l1: forward FFT over rows, multiply, inverse FFT, keep the window rows.
+template <typename real, bool CG>
+__device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
+                                          const real *__restrict__ mul, const cplx<real> *__restrict__ tw,
+                                          cplx<real> *a, cplx<real> *b)
 {
-    extern __shared__ unsigned char smem_raw[];
-    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cplx<real> *b = a + L;
-    const int l1 = blockIdx.x;
     cplx<real> *col = spec + (int64_t)l1 * ld;
     for (int r = threadIdx.x; r < L; r += blockDim.x) {
         cplx<real> v;
         if (r < n_a) {
-            v = col[r];
+            v = load<CG>(col + r);
         } else {
             v.x = real(0);
             v.y = real(0);
@@ -155,32 +161,30 @@ __global__ void k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L
         col[r] = G[r];
 }
 
-// Hermitian-extended inverse of two rows (r, r+1): real outputs on the window columns.
-template <typename real>
-__global__ void k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n_half,
-                               real *__restrict__ grid, int pitch, const cplx<real> *__restrict__ tw)
+// Hermitian-extended inverse of two rows (2 rp, 2 rp + 1): real outputs on the window columns.
+template <typename real, bool CG>
+__device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restrict__ spec, int ld, int n_a, int L,
+                                              int n_half, real *__restrict__ grid, int pitch,
+                                              const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
 {
-    extern __shared__ unsigned char smem_raw[];
-    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cplx<real> *b = a + L;
-    const int r = 2 * blockIdx.x;
+    const int r = 2 * rp;
     const bool has2 = r + 1 < n_a;
     for (int c = threadIdx.x; c < L; c += blockDim.x) {
         cplx<real> X, Y;
         X.x = X.y = Y.x = Y.y = real(0);
         if (c <= n_half) {
-            X = spec[(int64_t)c * ld + r];
+            X = load<CG>(spec + (int64_t)c * ld + r);
             if (has2)
-                Y = spec[(int64_t)c * ld + r + 1];
+                Y = load<CG>(spec + (int64_t)c * ld + r + 1);
             if (c == 0) {
                 X.y = real(0);
                 Y.y = real(0);
             }
         } else if (c >= L - n_half) {
-            X = spec[(int64_t)(L - c) * ld + r];
+            X = load<CG>(spec + (int64_t)(L - c) * ld + r);
             X.y = -X.y;
             if (has2) {
-                Y = spec[(int64_t)(L - c) * ld + r + 1];
+                Y = load<CG>(spec + (int64_t)(L - c) * ld + r + 1);
                 Y.y = -Y.y;
             }
         }
@@ -196,6 +200,119 @@ __global__ void k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int 
         if (has2)
             grid[(int64_t)(r + 1) * pitch + c] = Z[c].y;
     }
+}
+
+template <typename real>
+__global__ void k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a, int L, int n_half,
+                               cplx<real> *__restrict__ spec, int ld, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    rows_fwd_unit<real>(blockIdx.x, grid, pitch, n_a, L, n_half, spec, ld, tw, a, a + L);
+}
+
+template <typename real>
+__global__ void k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
+                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    cols_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n, mul, tw, a, a + L);
+}
+
+template <typename real>
+__global__ void k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n_half,
+                               real *__restrict__ grid, int pitch, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    rows_inv_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n_half, grid, pitch, tw, a, a + L);
+}
+
+// Thread 0 waits until *ctr >= target; the wait ends early (failed) when the error word is
+// set, and gives up after `spins` polls of ~0.1 us, setting the error word.  Returns the
+// outcome to every thread of the block.
+__device__ bool block_wait_geq(const int *ctr, int target, int *err, int spins)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const volatile int *vc = ctr;
+        const volatile int *ve = err;
+        int ok = 1;
+        for (int it = 0; *vc < target; ++it) {
+            if (*ve != 0) {
+                ok = 0;
+                break;
+            }
+            if (it >= spins) {
+                atomicCAS(err, 0, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Batched transform of all instances and right-hand sides in one persistent launch.  Blocks
+// take units from a queue in which every row pair precedes every column and every column
+// precedes every inverse row pair; a column waits until all forward row pairs of its
+// (instance, right-hand side) are done, an inverse row pair until all its columns are.  The
+// units a block waits for were taken earlier by blocks that are running and never wait on
+// later units, so the waits end; each is bounded all the same (error word on timeout).
+template <typename real>
+__global__ void __launch_bounds__(256) k_batch_fft(const BatchInst<real> *__restrict__ inst,
+                                                   const FftUnit *__restrict__ units, int n_units, int n_inst,
+                                                   int nrhs, int L_max, int *counters, int *err, int spins)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    cplx<real> *b = a + L_max;
+    __shared__ int s_unit;
+    int *head = counters + 2 * n_inst * nrhs;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_unit = atomicAdd(head, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= n_units)
+            return;
+        const FftUnit fu = units[u];
+        const BatchInst<real> &bi = inst[fu.inst];
+        const int slot = fu.inst * nrhs + fu.rhs;
+        int *rows_done = counters + slot;
+        int *cols_done = counters + n_inst * nrhs + slot;
+        const int L = bi.L, n_a = bi.n_a, n = bi.n;
+        cplx<real> *spec = bi.spec + (int64_t)fu.rhs * bi.spec_stride;
+        real *grid = bi.grid + (int64_t)fu.rhs * bi.grid_stride;
+        bool ok = true;
+        if (fu.kind == 1)
+            ok = block_wait_geq(rows_done, (n_a + 1) / 2, err, spins);
+        else if (fu.kind == 2)
+            ok = block_wait_geq(cols_done, n / 2 + 1, err, spins);
+        if (ok) {
+            if (fu.kind == 0)
+                rows_fwd_unit<real>(fu.index, grid, bi.pitch, n_a, L, n / 2, spec, bi.ld, bi.tw, a, b);
+            else if (fu.kind == 1)
+                cols_unit<real, true>(fu.index, spec, bi.ld, n_a, L, n, bi.mul, bi.tw, a, b);
+            else
+                rows_inv_unit<real, true>(fu.index, spec, bi.ld, n_a, L, n / 2, grid, bi.pitch, bi.tw, a, b);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && fu.kind < 2) {
+            __threadfence();
+            atomicAdd(fu.kind == 0 ? rows_done : cols_done, 1);
+        }
+    }
+}
+
+__global__ void k_wait_selftest(const int *counter, int *err, int spins)
+{
+    block_wait_geq(counter, 1, err, spins);
 }
 
 // ---- FP64 coefficients b_l
@@ -361,6 +478,41 @@ cudaError_t launch_fft_rows_inv(const cplx<real> *spec, int ld, int n_a, int L, 
     return cudaGetLastError();
 }
 
+template <typename real> cudaError_t batch_fft_blocks(int L_max, int *blocks)
+{
+    const size_t smem = 2 * (size_t)L_max * sizeof(cplx<real>);
+    cudaError_t e = set_smem(k_batch_fft<real>, smem);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fft<real>, 256, smem)) != cudaSuccess)
+        return e;
+    *blocks = sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t launch_batch_fft(const BatchInst<real> *inst, const FftUnit *units, int n_units, int n_inst, int nrhs,
+                             int L_max, int grid_blocks, int *counters, int *err, int spins, cudaStream_t st)
+{
+    if (n_units <= 0)
+        return cudaSuccess;
+    const size_t smem = 2 * (size_t)L_max * sizeof(cplx<real>);
+    k_batch_fft<real><<<(unsigned)grid_blocks, 256, smem, st>>>(inst, units, n_units, n_inst, nrhs, L_max, counters,
+                                                                err, spins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int *counter, int *err, int spins, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(counter, err, spins);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kernel_samples(double2 *samp, int n, KernelParams kp, cudaStream_t st)
 {
     dim3 grid((n + 127) / 128, n);
@@ -406,5 +558,12 @@ template cudaError_t launch_fft_rows_inv<double>(const double2 *, int, int, int,
                                                  cudaStream_t);
 template cudaError_t launch_build_mul<float>(const double2 *, int, const double *, float *, cudaStream_t);
 template cudaError_t launch_build_mul<double>(const double2 *, int, const double *, double *, cudaStream_t);
+
+template cudaError_t batch_fft_blocks<float>(int, int *);
+template cudaError_t batch_fft_blocks<double>(int, int *);
+template cudaError_t launch_batch_fft<float>(const BatchInst<float> *, const FftUnit *, int, int, int, int, int, int *,
+                                             int *, int, cudaStream_t);
+template cudaError_t launch_batch_fft<double>(const BatchInst<double> *, const FftUnit *, int, int, int, int, int,
+                                              int *, int *, int, cudaStream_t);
 
 }  // namespace fs

@@ -29,16 +29,13 @@ namespace fs {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_near64(int64_t N, const int *__restrict__ tgt_base,
-                                                const double2 *__restrict__ tgt_pos,
-                                                const double2 *__restrict__ src_pos, const int *__restrict__ src_start,
-                                                CellGrid cg, const double *__restrict__ q, NearParams<double> np,
-                                                double *__restrict__ phi_s, double *__restrict__ grad_s,
-                                                double *__restrict__ coinc)
+__device__ __forceinline__ void near64_target(int64_t k, const int *__restrict__ tgt_base,
+                                              const double2 *__restrict__ tgt_pos, const double2 *__restrict__ src_pos,
+                                              const int *__restrict__ src_start, const CellGrid &cg,
+                                              const double *__restrict__ q, const NearParams<double> &np,
+                                              double *__restrict__ phi_s, double *__restrict__ grad_s,
+                                              double *__restrict__ coinc)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= N)
-        return;
     const double2 X = tgt_pos[k];
     const int packed = tgt_base[k];
     const int c1 = base1(packed) / cg.cell, c2 = base2(packed) / cg.cell;
@@ -91,74 +88,157 @@ __global__ void __launch_bounds__(256) k_near64(int64_t N, const int *__restrict
     coinc[k] = qc;
 }
 
-// Forward correction at the targets: phi += q (G - T_I), grad += q c d, partial sums per
-// sub-cell row.
-template <int P> struct NearFwd {
-    static constexpr int kMinBlocks = 6;
+__global__ void __launch_bounds__(256) k_near64(int64_t N, const int *__restrict__ tgt_base,
+                                                const double2 *__restrict__ tgt_pos,
+                                                const double2 *__restrict__ src_pos, const int *__restrict__ src_start,
+                                                CellGrid cg, const double *__restrict__ q, NearParams<double> np,
+                                                double *__restrict__ phi_s, double *__restrict__ grad_s,
+                                                double *__restrict__ coinc)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < N)
+        near64_target(k, tgt_base, tgt_pos, src_pos, src_start, cg, q, np, phi_s, grad_s, coinc);
+}
+
+// Batched FP64 near field: block -> (instance, block of its targets), blockIdx.y = right-hand side.
+__global__ void __launch_bounds__(256) k_batch_near64(const BatchInst<double> *__restrict__ inst, BlockMap bm)
+{
+    const int i = bm.inst[blockIdx.x];
+    const BatchInst<double> &b = inst[i];
+    const int64_t k = (int64_t)(blockIdx.x - bm.first[i]) * blockDim.x + threadIdx.x;
+    const int64_t N = b.N;
+    if (k >= N)
+        return;
+    const int r = blockIdx.y;
+    near64_target(k, b.tgt_base, b.tgt_pos, b.src_pos, b.src_start, b.cg, b.q + (int64_t)r * b.M, b.np,
+                  b.phi_s + (int64_t)r * N, b.grad_s + 2 * (int64_t)r * N, b.coinc + (int64_t)r * N);
+}
+
+// Forward correction at the targets for R right-hand sides at once (the pair geometry, the
+// log and the gradient coefficient are shared): phi += q (G - T_I), grad += q c d.  With one
+// right-hand side the sums are split into partial sums per sub-cell row; with several the
+// registers go to the extra accumulators instead.  Right-hand side r reads q + r q_stride
+// and writes at r n_stride.
+template <int P, int R> struct NearFwd {
+    static constexpr int kMinBlocks = R == 1 ? 6 : 4;
+    static constexpr bool kRows = R == 1;
     const float *__restrict__ q;
     float *__restrict__ phi_s;
     float *__restrict__ grad_s;
     float *__restrict__ coinc;
-    float qj;
-    float phi[2], gx[2], gy[2], qc[2], rphi[2], rgx[2], rgy[2];
+    int64_t q_stride, n_stride;
+    float qj[R];
+    float phi[R][2], gx[R][2], gy[R][2], qc[R][2];
+    float rphi[kRows ? R : 1][2], rgx[kRows ? R : 1][2], rgy[kRows ? R : 1][2];
+
+    __device__ __forceinline__ float &acc_phi(int r, int t) { return kRows ? rphi[0][t] : phi[r][t]; }
+    __device__ __forceinline__ float &acc_gx(int r, int t) { return kRows ? rgx[0][t] : gx[r][t]; }
+    __device__ __forceinline__ float &acc_gy(int r, int t) { return kRows ? rgy[0][t] : gy[r][t]; }
 
     __device__ __forceinline__ void init()
     {
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
-            phi[t] = gx[t] = gy[t] = qc[t] = 0.f;
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                phi[r][t] = gx[r][t] = gy[r][t] = qc[r][t] = 0.f;
     }
-    __device__ __forceinline__ void load(int j) { qj = __ldg(q + j); }
+    __device__ __forceinline__ void load(int j)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            qj[r] = __ldg(q + r * q_stride + j);
+    }
     __device__ __forceinline__ void coincident(const NearParams<float> &np, int t)
     {
-        rphi[t] -= qj * np.beta[0];   // G(0) := 0 removes the far field's T_I(0)
-        qc[t] += qj;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            acc_phi(r, t) -= qj[r] * np.beta[0];   // G(0) := 0 removes the far field's T_I(0)
+            qc[r][t] += qj[r];
+        }
     }
     __device__ __forceinline__ void pair(const NearParams<float> &np, int t, float r2, float dx, float dy)
     {
-        const float qm = r2 < np.eps2 ? qj : 0.f;
+        const bool in = r2 < np.eps2;
         const float w = r2 * np.inv_eps2;
         const float coef = np.rcoef * ipow<P - 1>(w - 1.f) * rcp_approx(w);
-        rphi[t] = fmaf(qm, near_f<P>(np, w), rphi[t]);
-        const float tq = qm * coef;
-        rgx[t] = fmaf(tq, dx, rgx[t]);
-        rgy[t] = fmaf(tq, dy, rgy[t]);
+        const float val = near_f<P>(np, w);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float qm = in ? qj[r] : 0.f;
+            acc_phi(r, t) = fmaf(qm, val, acc_phi(r, t));
+            const float tq = qm * coef;
+            acc_gx(r, t) = fmaf(tq, dx, acc_gx(r, t));
+            acc_gy(r, t) = fmaf(tq, dy, acc_gy(r, t));
+        }
     }
     __device__ __forceinline__ void row_begin()
     {
+        if constexpr (kRows) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
-            rphi[t] = rgx[t] = rgy[t] = 0.f;
+            for (int t = 0; t < 2; ++t)
+                rphi[0][t] = rgx[0][t] = rgy[0][t] = 0.f;
+        }
     }
     __device__ __forceinline__ void row_end()
     {
+        if constexpr (kRows) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            phi[t] += rphi[t];
-            gx[t] += rgx[t];
-            gy[t] += rgy[t];
+            for (int t = 0; t < 2; ++t) {
+                phi[0][t] += rphi[0][t];
+                gx[0][t] += rgx[0][t];
+                gy[0][t] += rgy[0][t];
+            }
         }
     }
     __device__ __forceinline__ void store(int t, int64_t k)
     {
-        phi_s[k] += phi[t];
-        grad_s[2 * k] += gx[t];
-        grad_s[2 * k + 1] += gy[t];
-        coinc[k] = qc[t];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t kk = k + r * n_stride;
+            phi_s[kk] += phi[r][t];
+            grad_s[2 * kk] += gx[r][t];
+            grad_s[2 * kk + 1] += gy[r][t];
+            coinc[kk] = qc[r][t];
+        }
     }
 };
 
-template <typename real>
-__global__ void k_unpermute(int64_t N, const real *__restrict__ phi_s, const real *__restrict__ grad_s,
-                            const real *__restrict__ coinc, const int *__restrict__ perm, double shift,
-                            const double *__restrict__ q_sum, double s, void *__restrict__ phi_out,
-                            void *__restrict__ H_out, int out_is_f64)
+// Batched FP32 near field: one warp per item (first target, count, instance); all R
+// right-hand sides in one traversal.  The instance's constants live in registers rather than
+// in the constant bank, hence one block fewer per SM than the single-plan kernel for R = 1.
+template <int P, int R>
+__global__ void __launch_bounds__(128, NearFwd<P, R>::kMinBlocks - (R == 1 ? 1 : 0)) k_batch_near32(int64_t n_items,
+                                                                               const int4 *__restrict__ items,
+                                                                               const BatchInst<float> *__restrict__ inst)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= N)
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_items)
         return;
+    const int4 it = items[warp];
+    const BatchInst<float> &b = inst[it.z];
+    const NearSides sd{b.tgt_base, b.tgt_hi, b.tgt_lo, b.src_hi, b.src_lo, b.src_start};
+    const CellGrid cg = b.cg;
+    const NearParams<float> np = b.np;
+    NearFwd<P, R> op;
+    op.q = b.q;
+    op.phi_s = b.phi_s;
+    op.grad_s = b.grad_s;
+    op.coinc = b.coinc;
+    op.q_stride = b.M;
+    op.n_stride = b.N;
+    near_traverse(make_int2(it.x, it.y), lane, sd, cg, np, op);
+}
+
+template <typename real>
+__device__ __forceinline__ void unpermute_point(int64_t k, const real *__restrict__ phi_s,
+                                                const real *__restrict__ grad_s, const real *__restrict__ coinc,
+                                                const int *__restrict__ perm, double shift, double q_sum, double s,
+                                                void *__restrict__ phi_out, void *__restrict__ H_out, int out_is_f64)
+{
     const int64_t i = perm[k];
-    const double phi = (double)phi_s[k] + shift * (q_sum[0] - (double)coinc[k]);
+    const double phi = (double)phi_s[k] + shift * (q_sum - (double)coinc[k]);
     const double hx = -s * (double)grad_s[2 * k];
     const double hy = -s * (double)grad_s[2 * k + 1];
     if (out_is_f64) {
@@ -176,6 +256,37 @@ __global__ void k_unpermute(int64_t N, const real *__restrict__ phi_s, const rea
             ((float *)H_out)[2 * i + 1] = (float)hy;
         }
     }
+}
+
+template <typename real>
+__global__ void k_unpermute(int64_t N, const real *__restrict__ phi_s, const real *__restrict__ grad_s,
+                            const real *__restrict__ coinc, const int *__restrict__ perm, double shift,
+                            const double *__restrict__ q_sum, double s, void *__restrict__ phi_out,
+                            void *__restrict__ H_out, int out_is_f64)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < N)
+        unpermute_point(k, phi_s, grad_s, coinc, perm, shift, q_sum[0], s, phi_out, H_out, out_is_f64);
+}
+
+// Batched output: block -> (instance, block of its targets), blockIdx.y = right-hand side;
+// writes the caller's (nrhs, N) and (nrhs, N, 2) buffers of each instance.
+template <typename real>
+__global__ void k_batch_unpermute(const BatchInst<real> *__restrict__ inst, const BatchIO *__restrict__ io,
+                                  BlockMap bm, int out_is_f64)
+{
+    const int i = bm.inst[blockIdx.x];
+    const BatchInst<real> &b = inst[i];
+    const int64_t k = (int64_t)(blockIdx.x - bm.first[i]) * blockDim.x + threadIdx.x;
+    const int64_t N = b.N;
+    if (k >= N)
+        return;
+    const int r = blockIdx.y;
+    const size_t osz = out_is_f64 ? 8 : 4;
+    void *po = io[i].phi ? (unsigned char *)io[i].phi + (size_t)r * N * osz : nullptr;
+    void *ho = io[i].H ? (unsigned char *)io[i].H + (size_t)r * N * 2 * osz : nullptr;
+    unpermute_point(k, b.phi_s + (int64_t)r * N, b.grad_s + 2 * (int64_t)r * N, b.coinc + (int64_t)r * N,
+                    b.tgt_perm, b.shift, b.q_sum[r], b.s, po, ho, out_is_f64);
 }
 
 }  // namespace
@@ -198,11 +309,13 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
 {
     const NearSides sd{tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start};
     return with_degree(np.p, [&](auto pc) {
-        NearFwd<decltype(pc)::value> op{};
+        NearFwd<decltype(pc)::value, 1> op{};
         op.q = q;
         op.phi_s = phi_s;
         op.grad_s = grad_s;
         op.coinc = coinc;
+        op.q_stride = 0;
+        op.n_stride = 0;
         return launch_near_warp(n_items, items, sd, cg, np, op, st);
     });
 }
@@ -223,5 +336,47 @@ template cudaError_t launch_unpermute<float>(int64_t, const float *, const float
                                              double, const double *, double, void *, void *, int, cudaStream_t);
 template cudaError_t launch_unpermute<double>(int64_t, const double *, const double *, const double *, const int *,
                                               double, const double *, double, void *, void *, int, cudaStream_t);
+
+cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchInst<float> *inst, int p, int nrhs,
+                                cudaStream_t st)
+{
+    if (n_items <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_items + 3) / 4);
+    return with_degree(p, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        switch (nrhs) {
+        case 1: k_batch_near32<P, 1><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
+        case 2: k_batch_near32<P, 2><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
+        case 3: k_batch_near32<P, 3><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
+        case 4: k_batch_near32<P, 4><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_batch_near64(const BatchInst<double> *inst, BlockMap bm, int blocks, int nrhs, cudaStream_t st)
+{
+    if (blocks <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    k_batch_near64<<<dim3((unsigned)blocks, (unsigned)nrhs), 256, 0, st>>>(inst, bm);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_batch_unpermute(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks, int nrhs,
+                                   int out_is_f64, cudaStream_t st)
+{
+    if (blocks <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    k_batch_unpermute<real><<<dim3((unsigned)blocks, (unsigned)nrhs), 256, 0, st>>>(inst, io, bm, out_is_f64);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_batch_unpermute<float>(const BatchInst<float> *, const BatchIO *, BlockMap, int, int, int,
+                                                   cudaStream_t);
+template cudaError_t launch_batch_unpermute<double>(const BatchInst<double> *, const BatchIO *, BlockMap, int, int,
+                                                    int, cudaStream_t);
 
 }  // namespace fs

@@ -18,6 +18,8 @@
 // compensation tile, so the tile holds a double-FP32 sum.  At the end the warp
 // tiles are summed and added to the grid with global atomics (tiles overlap by
 // 2m-1 lines).
+#include <type_traits>
+
 #include "internal.h"
 
 namespace fs {
@@ -27,11 +29,10 @@ namespace {
 template <typename real> using real2_t = typename Cplx<real>::type;
 
 template <typename real, int M2, bool KAHAN>
-__global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
-                                                              const int *__restrict__ base,
-                                                              const real2_t<real> *__restrict__ frac,
-                                                              const real *__restrict__ q, Window<real> w, WindowPoly wp,
-                                                              real *__restrict__ grid, int pitch, int n_a)
+__device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid &cg, const int *__restrict__ base,
+                                            const real2_t<real> *__restrict__ frac, const real *__restrict__ q,
+                                            const Window<real> &w, const WindowPoly &wp, real *__restrict__ grid,
+                                            int pitch, int n_a)
 {
     constexpr int m = M2 / 2;
     constexpr int TAPS = M2 * M2;
@@ -50,7 +51,6 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *
         for (int i = threadIdx.x; i < M2 * (kPolyD + 1); i += blockDim.x)
             poly[i] = wp.c[i / (kPolyD + 1)][i % (kPolyD + 1)];
     }
-    const SpreadItem it = items[blockIdx.x];
     const int t1 = it.tile / cg.n_t, t2 = it.tile - (it.tile / cg.n_t) * cg.n_t;
     const int o1 = t1 * TG - (m - 1), o2 = t2 * TG - (m - 1);
     for (int i = lane; i < PP * PLANES; i += 32)
@@ -136,6 +136,29 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *
     }
 }
 
+template <typename real, int M2, bool KAHAN>
+__global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
+                                                              const int *__restrict__ base,
+                                                              const real2_t<real> *__restrict__ frac,
+                                                              const real *__restrict__ q, Window<real> w, WindowPoly wp,
+                                                              real *__restrict__ grid, int pitch, int n_a)
+{
+    spread_item<real, M2, KAHAN>(items[blockIdx.x], cg, base, frac, q, w, wp, grid, pitch, n_a);
+}
+
+// Batched spreading: items carry their instance in `pad`; blockIdx.y = right-hand side.
+template <typename real, int M2, bool KAHAN>
+__global__ void __launch_bounds__(kSpreadWarps * 32) k_batch_spread(const SpreadItem *__restrict__ items,
+                                                                    const BatchInst<real> *__restrict__ inst,
+                                                                    Window<real> w, WindowPoly wp)
+{
+    const SpreadItem it = items[blockIdx.x];
+    const BatchInst<real> &b = inst[it.pad];
+    const int r = blockIdx.y;
+    spread_item<real, M2, KAHAN>(it, b.cg, b.src_base, (const real2_t<real> *)b.src_frac, b.q + (int64_t)r * b.M, w,
+                                 wp, b.grid + (int64_t)r * b.grid_stride, b.pitch, b.n_a);
+}
+
 // In FP32 with m >= 5 the derivative sums are formed against a reference tap:
 // the window's periodisation sum_k psi(x - k) is flat (to ~1e-9 relative for
 // m = 5, ~1e-11 for m = 6), so sum_k psi'(x - k) vanishes to that level and
@@ -144,16 +167,13 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *
 // m <= 4 the periodisation is flat only to ~1e-7, no better than FP32 rounding,
 // so those widths (and the FP64 path) sum directly.
 template <typename real, int M2>
-__global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict__ base,
-                                                const real2_t<real> *__restrict__ frac, Window<real> w, WindowPoly wp,
-                                                const real *__restrict__ grid, int pitch, real n_os,
-                                                real *__restrict__ phi_s, real *__restrict__ grad_s)
+__device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ base,
+                                             const real2_t<real> *__restrict__ frac, const Window<real> &w,
+                                             const WindowPoly &wp, const real *__restrict__ grid, int pitch, real n_os,
+                                             real *__restrict__ phi_s, real *__restrict__ grad_s)
 {
     constexpr int m = M2 / 2;
     constexpr bool kRef = sizeof(real) == 4 && m >= 5;
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= N)
-        return;
     const int packed = base[k];
     const real2_t<real> f = frac[k];
     real w1[M2], d1[M2], w2[M2], d2[M2];
@@ -202,6 +222,34 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
     phi_s[k] = phi;
     grad_s[2 * k] = n_os * g1;
     grad_s[2 * k + 1] = n_os * g2;
+}
+
+template <typename real, int M2>
+__global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict__ base,
+                                                const real2_t<real> *__restrict__ frac, Window<real> w, WindowPoly wp,
+                                                const real *__restrict__ grid, int pitch, real n_os,
+                                                real *__restrict__ phi_s, real *__restrict__ grad_s)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < N)
+        interp_point<real, M2>(k, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s);
+}
+
+// Batched interpolation: block -> (instance, block of its targets), blockIdx.y = right-hand side.
+template <typename real, int M2>
+__global__ void __launch_bounds__(256) k_batch_interp(const BatchInst<real> *__restrict__ inst, BlockMap bm,
+                                                      Window<real> w, WindowPoly wp)
+{
+    const int i = bm.inst[blockIdx.x];
+    const BatchInst<real> &b = inst[i];
+    const int64_t k = (int64_t)(blockIdx.x - bm.first[i]) * blockDim.x + threadIdx.x;
+    const int64_t N = b.N;
+    if (k >= N)
+        return;
+    const int r = blockIdx.y;
+    interp_point<real, M2>(k, b.tgt_base, (const real2_t<real> *)b.tgt_frac, w, wp,
+                           b.grid + (int64_t)r * b.grid_stride, b.pitch, (real)b.L, b.phi_s + (int64_t)r * N,
+                           b.grad_s + 2 * (int64_t)r * N);
 }
 
 // Adjoint spreading at the targets: each point carries a monopole c and a dipole d (2-vector)
@@ -567,5 +615,86 @@ template cudaError_t launch_interp<float>(int64_t, int, const int *, const void 
 template cudaError_t launch_interp<double>(int64_t, int, const int *, const void *, Window<double>,
                                            const WindowPoly &, const double *, int, double, double *, double *,
                                            cudaStream_t);
+
+namespace {
+
+// Calls f(std::integral_constant<int, 2m>) for the window half-width m in 2..8.
+template <class F> cudaError_t with_width(int m, F &&f)
+{
+    switch (m) {
+    case 2: return f(std::integral_constant<int, 4>{});
+    case 3: return f(std::integral_constant<int, 6>{});
+    case 4: return f(std::integral_constant<int, 8>{});
+    case 5: return f(std::integral_constant<int, 10>{});
+    case 6: return f(std::integral_constant<int, 12>{});
+    case 7: return f(std::integral_constant<int, 14>{});
+    case 8: return f(std::integral_constant<int, 16>{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename real> size_t batch_spread_smem(int M2, int max_tile, bool comp)
+{
+    const int P = max_tile + M2 - 1;
+    return (size_t)kSpreadWarps * P * P * sizeof(real) * (comp ? 2 : 1) + sizeof(float) * M2 * (kPolyD + 1);
+}
+
+}  // namespace
+
+// Raises the dynamic shared memory limit of the batched spreading kernel (outside graph capture).
+template <typename real> cudaError_t prepare_batch_spread(int m, int max_tile, bool kahan)
+{
+    const bool comp = kahan && sizeof(real) == 4;
+    return with_width(m, [&](auto mc) {
+        constexpr int M2 = decltype(mc)::value;
+        const int smem = (int)batch_spread_smem<real>(M2, max_tile, comp);
+        return comp ? cudaFuncSetAttribute(k_batch_spread<real, M2, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                    : cudaFuncSetAttribute(k_batch_spread<real, M2, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+}
+
+template <typename real>
+cudaError_t launch_batch_spread(const SpreadItem *items, int n_items, int nrhs, const BatchInst<real> *inst, int m,
+                                int max_tile, Window<real> w, const WindowPoly &wp, bool kahan, cudaStream_t st)
+{
+    if (n_items <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    const bool comp = kahan && sizeof(real) == 4;
+    return with_width(m, [&](auto mc) {
+        constexpr int M2 = decltype(mc)::value;
+        const size_t smem = batch_spread_smem<real>(M2, max_tile, comp);
+        const dim3 grid((unsigned)n_items, (unsigned)nrhs);
+        if (comp)
+            k_batch_spread<real, M2, true><<<grid, kSpreadWarps * 32, smem, st>>>(items, inst, w, wp);
+        else
+            k_batch_spread<real, M2, false><<<grid, kSpreadWarps * 32, smem, st>>>(items, inst, w, wp);
+        return cudaGetLastError();
+    });
+}
+
+template <typename real>
+cudaError_t launch_batch_interp(const BatchInst<real> *inst, BlockMap bm, int blocks, int nrhs, int m,
+                                Window<real> w, const WindowPoly &wp, cudaStream_t st)
+{
+    if (blocks <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    return with_width(m, [&](auto mc) {
+        constexpr int M2 = decltype(mc)::value;
+        k_batch_interp<real, M2><<<dim3((unsigned)blocks, (unsigned)nrhs), 256, 0, st>>>(inst, bm, w, wp);
+        return cudaGetLastError();
+    });
+}
+
+#define FS_INST(real)                                                                                          \
+    template cudaError_t prepare_batch_spread<real>(int, int, bool);                                           \
+    template cudaError_t launch_batch_spread<real>(const SpreadItem *, int, int, const BatchInst<real> *, int, \
+                                                   int, Window<real>, const WindowPoly &, bool, cudaStream_t); \
+    template cudaError_t launch_batch_interp<real>(const BatchInst<real> *, BlockMap, int, int, int,           \
+                                                   Window<real>, const WindowPoly &, cudaStream_t);
+FS_INST(float)
+FS_INST(double)
+#undef FS_INST
 
 }  // namespace fs

@@ -1,0 +1,186 @@
+// Plan object of the FEM-NFFT fast summation and the host helpers shared by the plan
+// entry points (femnfft.cu) and the batched solves (batch.cu).  Private to the library.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/femnfft.h"
+#include "internal.h"
+
+namespace fs {
+
+// Records msg as the calling thread's last error and returns st.
+fs_status fail(fs_status st, const std::string &msg);
+
+constexpr int kStages = 8;
+constexpr int kSpreadChunk = 512;   // sources per spreading work item
+
+}  // namespace fs
+
+#define FS_CUDA(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fs::fail(FS_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_));       \
+    } while (0)
+
+#define FS_TRY(expr)                                                                                    \
+    do {                                                                                                \
+        fs_status s_ = (expr);                                                                          \
+        if (s_ != FS_OK)                                                                                \
+            return s_;                                                                                  \
+    } while (0)
+
+struct fs_plan {
+    // parameters
+    int precision = 32;
+    int n = 0, n_os = 0, m = 0, p = 0;
+    double sigma = 0, eps_I = 0, eps_B = 0, s = 1.0;
+    int64_t M = 0, N = 0;
+    int window_lo = 0, n_a = 0, pitch = 0, ld = 0;
+    fs::CellGrid cg{};
+    int n_keys = 0;
+    unsigned flags = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool kahan = true;
+    fs::KernelParams kp{};
+    double beta[fs::kMaxP] = {0};
+    fs::WindowPoly wpoly{};               // FP32 window polynomials (per tap)
+    // device memory
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    int *status = nullptr;
+    int *src_perm = nullptr, *tgt_perm = nullptr;
+    int *src_base = nullptr, *tgt_base = nullptr;
+    void *src_frac = nullptr, *tgt_frac = nullptr;
+    double2 *src_pos = nullptr, *tgt_pos = nullptr;
+    float2 *src_pos32 = nullptr, *tgt_pos32 = nullptr;
+    float2 *src_lo32 = nullptr, *tgt_lo32 = nullptr;
+    int *src_start = nullptr, *tgt_start = nullptr;
+    fs::SpreadItem *items = nullptr;
+    int n_items = 0;
+    fs::SpreadItem *tgt_items = nullptr;  // adjoint: spreading at the targets
+    int n_tgt_items = 0;
+    // adjoint workspace (allocated by the first fs_adjoint call)
+    void *adj_c = nullptr, *adj_dn = nullptr, *adj_df = nullptr;
+    void *adj_a = nullptr, *adj_ga = nullptr, *adj_cg = nullptr, *adj_hess = nullptr;
+    double *adj_gsum = nullptr;
+    int2 *near_items = nullptr;       // FP32 near field: (first target, count <= 64) per warp
+    int64_t n_near_items = 0;
+    std::vector<int2> near_items_h;   // host copies (merged into batch work lists)
+    std::vector<int64_t> near_work_h; // estimated pair work per near item
+    std::vector<fs::SpreadItem> items_h;
+    int2 *src_near_items = nullptr;   // FP32 adjoint near field: (first source, count <= 64) per warp
+    int64_t n_src_near_items = 0;
+    void *mul = nullptr, *tw = nullptr;
+    void *grid = nullptr, *spec = nullptr;
+    void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
+    // charges
+    void *q_sorted = nullptr;
+    double *q_sum = nullptr;
+    int nrhs = 0, nrhs_cap = 0;
+    // FEM
+    bool is_fem = false;
+    int64_t Nv = 0, Nt = 0, Ne = 0;
+    const double2 *nodes = nullptr;   // caller's (valid while the plan is used)
+    int *tris = nullptr, *bedges = nullptr;
+    double2 *fem_src = nullptr;
+    double *q_canon = nullptr;
+    int64_t q_canon_cap = 0;
+    // host staging for fs_solve_host
+    void *d_q_stage = nullptr, *d_phi_stage = nullptr, *d_H_stage = nullptr;
+    size_t q_stage_bytes = 0, phi_stage_bytes = 0, H_stage_bytes = 0;
+    // stats
+    int64_t near_pairs = 0, near_pairs_fp64 = 0;
+    // timing
+    cudaEvent_t ev[fs::kStages + 1] = {};
+    cudaEvent_t ev_q0 = nullptr, ev_q1 = nullptr;
+    bool events = false;
+
+    template <typename T> fs_status alloc(T **out, size_t count)
+    {
+        *out = nullptr;
+        if (count == 0)
+            count = 1;
+        void *p_ = nullptr;
+        const size_t nbytes = count * sizeof(T);
+        cudaError_t e = cudaMalloc(&p_, nbytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fs::fail(FS_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed: " +
+                                       cudaGetErrorString(e));
+        }
+        allocs.push_back(p_);
+        bytes += (int64_t)nbytes;
+        *out = static_cast<T *>(p_);
+        return FS_OK;
+    }
+    fs_status alloc_bytes(void **out, size_t nbytes)
+    {
+        unsigned char *p_ = nullptr;
+        FS_TRY(alloc(&p_, nbytes));
+        *out = p_;
+        return FS_OK;
+    }
+    void release(void *ptr)
+    {
+        if (!ptr)
+            return;
+        auto it = std::find(allocs.begin(), allocs.end(), ptr);
+        if (it != allocs.end()) {
+            cudaFree(ptr);
+            allocs.erase(it);
+        }
+    }
+    size_t rsize() const { return precision == 64 ? 8 : 4; }
+};
+
+namespace fs {
+
+// Validates the parameters and builds the plan (binning, tables, items) on its stream.
+fs_status plan_create_common(const double *src, int64_t M, const double *tgt, int64_t N, int n_grid,
+                             double sigma_os, int m, double eps_I, const fs_opts *opts, fs_plan *pl);
+// Waits for the plan's stream and frees everything it owns.
+void plan_destroy(fs_plan *pl);
+
+template <typename real> inline Window<real> make_window(const fs_plan *pl)
+{
+    const double b = kPi * (2.0 - 1.0 / pl->sigma);
+    const double m = pl->m;
+    Window<real> w;
+    w.m = (real)m;
+    w.m2 = (real)(m * m);
+    w.b = (real)b;
+    w.bm = (real)(b * m);
+    w.S = (real)(m * b / (1.0 - std::exp(-2.0 * b * m)));
+    return w;
+}
+
+template <typename real> inline NearParams<real> make_near(const fs_plan *pl)
+{
+    NearParams<real> np{};
+    np.p = pl->p;
+    np.eps2 = (real)(pl->eps_I * pl->eps_I);
+    np.inv_eps2 = (real)(1.0 / (pl->eps_I * pl->eps_I));
+    np.close2 = (real)((pl->eps_I / 8.0) * (pl->eps_I / 8.0));
+    np.hcell = (real)((double)pl->cg.cell / pl->n_os);
+    for (int k = 0; k < pl->p; ++k)
+        np.beta[k] = (real)pl->beta[k];
+    for (int k = 1; k < pl->p; ++k)
+        np.dbeta[k - 1] = (real)(2.0 * k * pl->beta[k] / (pl->eps_I * pl->eps_I));
+    // T_I - k(eps_I) vanishes at r = eps_I; and since k - T_I has a zero of order p there, the
+    // gradient numerator R(w) = -(1/2pi) - sum_k 2k beta_k w^k (degree p-1) is c (w-1)^(p-1).
+    const double k_eps = -std::log(pl->eps_I) / (2.0 * kPi);
+    for (int k = 0; k < pl->p; ++k)
+        np.pbeta[k] = (real)(k == 0 ? pl->beta[0] - k_eps : pl->beta[k]);
+    // R(w) = c (w-1)^(p-1) with R(0) = -(1/2pi) gives c = (-1)^p / (2pi), independent of beta
+    np.rcoef = (real)(((pl->p % 2 == 0) ? 1.0 : -1.0) / (2.0 * kPi * pl->eps_I * pl->eps_I));
+    return np;
+}
+
+}  // namespace fs
