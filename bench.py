@@ -147,8 +147,8 @@ def algorithmic_bytes(info, n_points):
 # the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
 # reports null until it is re-captured).
 NEAR_TRAFFIC = {
-    # profiles/k_near32_mixture_2p19.md: 28.13 MB at 2^19 points, scaled by the point count
-    "ca94ec2142a597bb983867d936f3b5d2cd8baabefba22c0dc5fb0c1c2c07d9c0": 2 * 28.13e6,
+    # profiles/dram_per_kernel_mixture_2p19.md: 28.32 MB per launch at 2^19 points, scaled by the point count
+    "32515a4cd552d4b658f598db3b5ef8c6080ea3b59d3452088532dca387fed6e2": 2 * 28.32e6,
 }
 
 
@@ -165,6 +165,120 @@ def near_flops_per_pair(p):
     # FP32 near-pair work: difference + r^2 (7), w (1), P(w) Horner (2(p-1)), (w-1)^(p-1) (p-1 + 1),
     # log and reciprocal (2 MUFU, counted 1 each), value and coefficient (4), three accumulations (6)
     return 7 + 1 + 2 * (p - 1) + p + 2 + 4 + 6
+
+
+BATCH_WORKLOAD = ("batch_c4: 64 instances, N_i = floor(2^U(11,19)) uniform points in the r<=0.25 disc "
+                  "(sources = targets), 3 charge vectors each; n_i = clamp(2^ceil(log2 sqrt N_i), 128, 1024), "
+                  "sigma=2, m=5, eps_I=6/n_i, p=6; FP32, autotuned cell/tile")
+ADJ_WORKLOAD = ("uniform_c3: N = M = 2^18 uniform points in the r<=0.25 disc (sources = targets), "
+                "n=512 (oversampled 1024^2), m=5, eps_I=6/512, p=6; FP32")
+
+
+def measure_batch(pkg, dev, steps, warmup, flush):
+    """Graph replays of the batched solve against the 192 solves one plan at a time."""
+    import torch
+    from paper_0807_2387_gb300 import workloads as W
+    cases = W.batch_c4()
+    pts = [torch.tensor(c["src"], device=dev) for c in cases]
+    q = [torch.tensor(c["q"], device=dev, dtype=torch.float32) for c in cases]
+    total = sum(len(c["src"]) for c in cases)
+    t0 = time.perf_counter()
+    b = pkg.FastSumBatch([(p, p, c["n"], c["eps_I"]) for p, c in zip(pts, cases)], 2.0, 5, 3, precision=32,
+                         flags=pkg.FS_FLAG_AUTOTUNE)
+    create_s = time.perf_counter() - t0
+    phi, H = b.outputs()
+    for _ in range(warmup):
+        b.eval_into(q, phi, H)
+    b.sync()
+
+    def timed(fn):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            z.record()
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(z))
+        return statistics.mean(ms)
+
+    t_batch = timed(lambda: b.eval_into(q, phi, H))
+    b.sync()
+    plans = [b.plan(i) for i in range(len(cases))]
+    outs = [(torch.empty(len(c["src"]), device=dev), torch.empty((len(c["src"]), 2), device=dev)) for c in cases]
+
+    def sequential():
+        for i, pl in enumerate(plans):
+            for r in range(3):
+                pkg.fs_set_charges(pl.handle, q[i][r], 1)
+                pkg.fs_eval_field(pl.handle, outs[i][0], outs[i][1])
+
+    sequential()
+    t_seq = timed(sequential)
+    # accuracy on the largest instance against its FP64 plan
+    i = max(range(len(cases)), key=lambda k: len(cases[k]["src"]))
+    c = cases[i]
+    fs64 = pkg.FastSum(pts[i], pts[i], c["n"], 2.0, 5, c["eps_I"], precision=64)
+    fs64.set_charges(q[i].double())
+    p64, h64 = fs64.field(dtype=torch.float64)
+    fs64.sync()
+    fs64.close()
+    e_phi = float(torch.linalg.norm(phi[i].double() - p64) / torch.linalg.norm(p64))
+    e_H = float(torch.linalg.norm(H[i].double() - h64) / torch.linalg.norm(h64))
+    info = b.info
+    b.close()
+    return {"workload": BATCH_WORKLOAD, "total_points": total, "point_solves_per_step": 3 * total,
+            "value": 3 * total / (t_batch / 1e3), "unit": "point-solves/s", "ms_per_replay": round(t_batch, 4),
+            "sequential_ms": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / t_batch, 3),
+            "sequential": "192 x (fs_set_charges + fs_eval_field) on the same instance plans",
+            "launches_per_replay": 7, "memsets_per_replay": 3, "fft_blocks": info["fft_blocks"],
+            "create_s_with_autotune": round(create_s, 3),
+            "largest_instance_vs_fp64": {"phi_rel_l2": e_phi, "H_rel_l2": e_H}}
+
+
+def measure_adjoint(pkg, dev, steps, warmup, flush):
+    """Forward (charges + field) and backward (fs_adjoint for dq, dy, dx) on the 2^18-point disc."""
+    import torch
+    from paper_0807_2387_gb300 import workloads as W
+    c = W.uniform_c3()
+    pts = torch.tensor(c["src"], device=dev)
+    q = torch.tensor(c["q"], device=dev)
+    w = torch.tensor(c["w"], device=dev)
+    out = {}
+    res = {}
+    for prec in (32, 64):
+        fs = pkg.FastSum(pts, pts, c["n"], c["sigma"], c["m"], c["eps_I"], precision=prec)
+        fs.set_charges(q)
+        phi, H = fs.field(dtype=torch.float64)
+        gphi, gH = 0.5 * q, 2.0 * w[:, None] * H       # L = 1/2 sum q phi + sum w |H|^2
+        for _ in range(warmup if prec == 32 else 1):
+            r = fs.adjoint(gphi, gH, want_q=True, want_src=True, want_tgt=True, dtype=torch.float64)
+        fs.sync()
+        res[prec] = [t.double() for t in r]
+        if prec == 32:
+            tf, tb = [], []
+            for _ in range(steps):
+                flush.zero_()
+                a, m_, z = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record()
+                fs.set_charges(q)
+                fs.field(dtype=torch.float64)
+                m_.record()
+                fs.adjoint(gphi, gH, want_q=True, want_src=True, want_tgt=True, dtype=torch.float64)
+                z.record()
+                torch.cuda.synchronize(dev)
+                tf.append(a.elapsed_time(m_))
+                tb.append(m_.elapsed_time(z))
+            out["forward_ms"] = round(statistics.mean(tf), 4)
+            out["adjoint_ms"] = round(statistics.mean(tb), 4)
+        fs.close()
+    errs = {k: float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for k, a, b in
+            zip(("dq", "dsrc", "dtgt"), res[32], res[64])}
+    n = len(c["src"])
+    return {"workload": ADJ_WORKLOAD, "loss": "1/2 sum q phi + sum w |H|^2", **out,
+            "value": n / ((out["forward_ms"] + out["adjoint_ms"]) / 1e3), "unit": "points/s (forward + backward)",
+            "fp32_vs_fp64_adjoint_rel_l2": errs}
 
 
 def run_ours(args):
@@ -283,7 +397,7 @@ def run_ours(args):
         traffic, sha = near_traffic()
         if args.traffic is not None:
             traffic = args.traffic
-        roof = {"kernel": "k_near32<8>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
+        roof = {"kernel": f"k_near_warp<NearFwd<{info['p']},1>>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
                 "kernel_source_sha256": sha[:16],
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
@@ -297,6 +411,12 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.quick and not args.no_cpu:
         cpu, _ = cpu_baseline(work, args.cpu_targets)
+
+    # the batched workload and the adjoint (one GPU; untimed by the headline value)
+    batch = adj = None
+    if world == 1 and not args.quick and not args.no_extra:
+        batch = measure_batch(pkg, dev, max(3, args.steps // 4), 3, flush)
+        adj = measure_adjoint(pkg, dev, max(3, args.steps // 4), 3, flush)
 
     if world > 1:
         dist.barrier()
@@ -313,11 +433,22 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": KERNELS_PER_STEP * args.steps,
             "near_pairs": info["near_pairs"], "near_pairs_fp64": info["near_pairs_fp64"],
             "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src},
+            "batch_c4": batch, "adjoint_c3": adj,
         }
         print(json.dumps(out))
     fs.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_only(args):
+    import torch
+    import paper_0807_2387_gb300 as pkg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    fn = measure_batch if args.only == "batch" else measure_adjoint
+    print(json.dumps(fn(pkg, dev, args.steps, args.warmup, flush)))
 
 
 def run_reference(args):
@@ -355,6 +486,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU baseline (profiling runs)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--only", choices=("batch", "adjoint"), default=None,
+                    help="run only the batched or the adjoint measurement and print its JSON object")
     ap.add_argument("--cpu-targets", type=int, default=32768)
     ap.add_argument("--ref-targets", type=int, default=64)
     ap.add_argument("--points", type=int, default=1 << 20,
@@ -366,6 +500,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
 
