@@ -110,6 +110,20 @@ def dist_env():
     return world, rank, local
 
 
+def job_throughput(local_ms, units_per_rank, steps, world, device=None):
+    """Whole-job throughput of a weak-scaled run: every rank processed `units_per_rank` per
+    step; the job's time is the slowest rank's (all-reduce MAX over the process group when
+    world > 1).  Returns (max total ms, units per second over all ranks)."""
+    total = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total, units_per_rank * steps * world / (total / 1e3)
+
+
 def cpu_baseline(work, targets: int, seed: int = 17):
     """Oracle O1 (plain FP64 direct sum) on `targets` random targets against all sources."""
     from oracle import direct as D
@@ -330,14 +344,9 @@ def run_ours(args):
                 stage_ms[s] += v
         torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = job_throughput(sum(a.elapsed_time(b) for a, b in ev), n_pts, args.steps, world, dev)
     fs.sync()
     ms_step = total_ms / args.steps
-    value = n_pts * args.steps * world / (total_ms / 1e3)
     stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
 
     # accuracy of this FP32 run against the FP64 GPU path (untimed)
