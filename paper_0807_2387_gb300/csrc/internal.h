@@ -39,6 +39,7 @@ template <typename real> struct NearParams {
     real beta[kMaxP];      // T_I coefficients in w = (r/eps_I)^2
     real dbeta[kMaxP];     // coefficients of T_I'(r)/r in w: 2k beta_k / eps_I^2 (index k-1)
     real pbeta[kMaxP];     // P(w) = T_I - k(eps_I): beta with beta_0 - k(eps_I), so P(1) = 0
+    real nptilde[kMaxP];   // -Ptilde(w) with P(w) = (w - 1) Ptilde(w): degree p - 2 (index < p - 1)
     real rcoef;            // (-1)^p / (2 pi eps_I^2): (k' - T_I')(r)/r = rcoef (w - 1)^(p-1) / w
     int p;
 };

@@ -215,74 +215,72 @@ __global__ void __launch_bounds__(256) k_near_hess64(int64_t N, const int *__res
 }
 
 // Hessian at the targets (FP32 warp items, own = targets, other = sources, d = x - y):
-// grad += q c d, Hess += q (c I + (2 c' / eps_I^2) d d^T).
+// grad += q c d, Hess += q (c I + (2 c' / eps_I^2) d d^T), with c = rc c^ and c' = rc c'^;
+// the sums over pairs are of the hatted forms and rc, 2 / eps_I^2 are applied at the store.
+// For p >= 3 clamping w to 1 masks pairs beyond eps_I (c^ and c'^ vanish there); below, the
+// charge is masked.
 template <int P> struct NearHess32 {
     static constexpr int kMinBlocks = 5;
+    static constexpr bool kClamp = P >= 3;
     const float *__restrict__ q;
     float *__restrict__ grad_s;
     float *__restrict__ hess_s;
-    float two_over_eps2, hess0;
+    float rcoef, two_over_eps2, self_c;   // self_c = Hess T_I(0) / rc
     float qj;
-    float gx[2], gy[2], hxx[2], hxy[2], hyy[2];
+    float2 gx, gy, sI, sxx, sxy, syy;
 
-    __device__ __forceinline__ void init()
-    {
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-            gx[t] = gy[t] = hxx[t] = hxy[t] = hyy[t] = 0.f;
-    }
+    __device__ __forceinline__ void init() { gx = gy = sI = sxx = sxy = syy = f2(0.f); }
     __device__ __forceinline__ void load(int j) { qj = __ldg(q + j); }
-    __device__ __forceinline__ void coincident(const NearParams<float> &, int t)
+    __device__ __forceinline__ void coincident(const NearParams<float> &, int t) { add_comp(sI, t, -qj * self_c); }
+    __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
-        hxx[t] -= qj * hess0;
-        hyy[t] -= qj * hess0;
-    }
-    __device__ __forceinline__ void pair(const NearParams<float> &np, int t, float r2, float dx, float dy)
-    {
-        const bool in = r2 < np.eps2;
-        float c, cp;
-        near_c_cp<P>(np, in ? r2 * np.inv_eps2 : 0.5f, c, cp);
-        const float qm = in ? qj : 0.f;
-        const float qc = qm * c, k = qm * two_over_eps2 * cp;
-        gx[t] = fmaf(qc, dx, gx[t]);
-        gy[t] = fmaf(qc, dy, gy[t]);
-        const float kx = k * dx;
-        hxx[t] += fmaf(kx, dx, qc);
-        hxy[t] = fmaf(kx, dy, hxy[t]);
-        hyy[t] += fmaf(k * dy, dy, qc);
+        float2 w = mul2(r2, f2(np.inv_eps2));
+        if constexpr (kClamp)
+            w = min1(w);
+        float2 c, cp;
+        near_c_cp2<P>(w, c, cp);
+        float2 qq = f2(qj);
+        if constexpr (!kClamp)
+            qq = select2(r2, np.eps2, qq);
+        const float2 qc = mul2(qq, c), k = mul2(qq, cp);
+        gx = fma2(qc, dx, gx);
+        gy = fma2(qc, dy, gy);
+        sI = add2(sI, qc);
+        const float2 kx = mul2(k, dx);
+        sxx = fma2(kx, dx, sxx);
+        sxy = fma2(kx, dy, sxy);
+        syy = fma2(mul2(k, dy), dy, syy);
     }
     __device__ __forceinline__ void row_begin() {}
     __device__ __forceinline__ void row_end() {}
     __device__ __forceinline__ void store(int t, int64_t k)
     {
-        grad_s[2 * k] += gx[t];
-        grad_s[2 * k + 1] += gy[t];
-        hess_s[3 * k] += hxx[t];
-        hess_s[3 * k + 1] += hxy[t];
-        hess_s[3 * k + 2] += hyy[t];
+        const float i0 = comp(sI, t);
+        grad_s[2 * k] += rcoef * comp(gx, t);
+        grad_s[2 * k + 1] += rcoef * comp(gy, t);
+        hess_s[3 * k] += rcoef * fmaf(two_over_eps2, comp(sxx, t), i0);
+        hess_s[3 * k + 1] += rcoef * two_over_eps2 * comp(sxy, t);
+        hess_s[3 * k + 2] += rcoef * fmaf(two_over_eps2, comp(syy, t), i0);
     }
 };
 
 // Adjoint potential at the sources (FP32 warp items, own = sources, other = targets,
-// d = y - x = -D):  A += gphi f - (dn . d) c,  grad_y A += c (gphi d - dn) - (2 c' / eps_I^2)(dn . d) d.
+// d = y - x = -D):  A += gphi f - (dn . d) c,  grad_y A += c (gphi d - dn) - (2 c' / eps_I^2)(dn . d) d,
+// with the hatted c^, c'^ summed and rc, 2 / eps_I^2 applied at the store.
 template <int P> struct NearAdj32 {
     static constexpr int kMinBlocks = 5;
+    static constexpr bool kClamp = P >= 3;
     const float *__restrict__ cw;
     const float2 *__restrict__ dnw;
     float *__restrict__ a_s;
     float *__restrict__ ga_s;
     float *__restrict__ cg_s;
-    float two_over_eps2, hess0;
+    float rcoef, two_over_eps2, self_c;   // self_c = Hess T_I(0) / rc
     float gp;
     float2 dn;
-    float A[2], gax[2], gay[2], gco[2];
+    float2 af, ac, gxc, gyc, gxk, gyk, gco;
 
-    __device__ __forceinline__ void init()
-    {
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-            A[t] = gax[t] = gay[t] = gco[t] = 0.f;
-    }
+    __device__ __forceinline__ void init() { af = ac = gxc = gyc = gxk = gyk = gco = f2(0.f); }
     __device__ __forceinline__ void load(int i)
     {
         gp = __ldg(cw + i);
@@ -290,33 +288,42 @@ template <int P> struct NearAdj32 {
     }
     __device__ __forceinline__ void coincident(const NearParams<float> &np, int t)
     {
-        A[t] -= gp * np.beta[0];
-        gco[t] += gp;
-        gax[t] = fmaf(hess0, dn.x, gax[t]);
-        gay[t] = fmaf(hess0, dn.y, gay[t]);
+        add_comp(af, t, -gp * np.beta[0]);
+        add_comp(gco, t, gp);
+        add_comp(gxc, t, self_c * dn.x);
+        add_comp(gyc, t, self_c * dn.y);
     }
-    __device__ __forceinline__ void pair(const NearParams<float> &np, int t, float r2, float dx, float dy)
+    __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
-        const bool in = r2 < np.eps2;
-        const float w = in ? r2 * np.inv_eps2 : 0.5f;
-        float c, cp;
-        near_c_cp<P>(np, w, c, cp);
-        const float f = near_f<P>(np, w);
-        const float g = in ? gp : 0.f, n1 = in ? dn.x : 0.f, n2 = in ? dn.y : 0.f;
-        const float dD = fmaf(n1, dx, n2 * dy);
-        A[t] = fmaf(g, f, fmaf(-dD, c, A[t]));
-        const float k = two_over_eps2 * cp * dD;
-        gax[t] += fmaf(c, fmaf(g, dx, -n1), -k * dx);
-        gay[t] += fmaf(c, fmaf(g, dy, -n2), -k * dy);
+        float2 w = mul2(r2, f2(np.inv_eps2));
+        if constexpr (kClamp)
+            w = min1(w);
+        float2 c, cp;
+        near_c_cp2<P>(w, c, cp);
+        const float2 f = near_f2<P>(np, w);
+        float2 g = f2(gp), n1 = f2(dn.x), n2 = f2(dn.y);
+        if constexpr (!kClamp) {
+            g = select2(r2, np.eps2, g);
+            n1 = select2(r2, np.eps2, n1);
+            n2 = select2(r2, np.eps2, n2);
+        }
+        const float2 dD = fma2(n1, dx, mul2(n2, dy));
+        af = fma2(g, f, af);
+        ac = fma2(dD, c, ac);
+        gxc = fma2(c, fma2(g, dx, mul2(f2(-1.f), n1)), gxc);
+        gyc = fma2(c, fma2(g, dy, mul2(f2(-1.f), n2)), gyc);
+        const float2 k = mul2(cp, dD);
+        gxk = fma2(k, dx, gxk);
+        gyk = fma2(k, dy, gyk);
     }
     __device__ __forceinline__ void row_begin() {}
     __device__ __forceinline__ void row_end() {}
     __device__ __forceinline__ void store(int t, int64_t k)
     {
-        a_s[k] += A[t];
-        ga_s[2 * k] += gax[t];
-        ga_s[2 * k + 1] += gay[t];
-        cg_s[k] = gco[t];
+        a_s[k] += fmaf(-rcoef, comp(ac, t), comp(af, t));
+        ga_s[2 * k] += rcoef * fmaf(-two_over_eps2, comp(gxk, t), comp(gxc, t));
+        ga_s[2 * k + 1] += rcoef * fmaf(-two_over_eps2, comp(gyk, t), comp(gyc, t));
+        cg_s[k] = comp(gco, t);
     }
 };
 
@@ -431,8 +438,9 @@ cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src
         op.a_s = a_s;
         op.ga_s = ga_s;
         op.cg_s = cg_s;
+        op.rcoef = np.rcoef;
         op.two_over_eps2 = 2.f * np.inv_eps2;
-        op.hess0 = self_hessian(np);
+        op.self_c = self_hessian(np) / np.rcoef;
         return launch_near_warp(n_items, items, sd, cg, np, op, st);
     });
 }
@@ -448,8 +456,9 @@ cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tg
         op.q = q;
         op.grad_s = grad_s;
         op.hess_s = hess_s;
+        op.rcoef = np.rcoef;
         op.two_over_eps2 = 2.f * np.inv_eps2;
-        op.hess0 = self_hessian(np);
+        op.self_c = self_hessian(np) / np.rcoef;
         return launch_near_warp(n_items, items, sd, cg, np, op, st);
     });
 }

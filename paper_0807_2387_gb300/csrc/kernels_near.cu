@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(256) k_batch_near64(const BatchInst<double> *_
 }
 
 // Forward correction at the targets for R right-hand sides at once (the pair geometry, the
-// log and the gradient coefficient are shared): phi += q (G - T_I), grad += q c d.  With one
+// log and the gradient coefficient are shared): phi += q f, grad += q c d, with the lane's
+// two targets as packed pairs and the factor rc of c applied once at the store.  With one
 // right-hand side the sums are split into partial sums per sub-cell row; with several the
 // registers go to the extra accumulators instead.  Right-hand side r reads q + r q_stride
 // and writes at r n_stride.
@@ -127,21 +128,20 @@ template <int P, int R> struct NearFwd {
     float *__restrict__ grad_s;
     float *__restrict__ coinc;
     int64_t q_stride, n_stride;
+    float rcoef;
     float qj[R];
-    float phi[R][2], gx[R][2], gy[R][2], qc[R][2];
-    float rphi[kRows ? R : 1][2], rgx[kRows ? R : 1][2], rgy[kRows ? R : 1][2];
+    float2 phi[R], gx[R], gy[R], qc[R];
+    float2 rphi[kRows ? R : 1], rgx[kRows ? R : 1], rgy[kRows ? R : 1];
 
-    __device__ __forceinline__ float &acc_phi(int r, int t) { return kRows ? rphi[0][t] : phi[r][t]; }
-    __device__ __forceinline__ float &acc_gx(int r, int t) { return kRows ? rgx[0][t] : gx[r][t]; }
-    __device__ __forceinline__ float &acc_gy(int r, int t) { return kRows ? rgy[0][t] : gy[r][t]; }
+    __device__ __forceinline__ float2 &acc_phi(int r) { return kRows ? rphi[0] : phi[r]; }
+    __device__ __forceinline__ float2 &acc_gx(int r) { return kRows ? rgx[0] : gx[r]; }
+    __device__ __forceinline__ float2 &acc_gy(int r) { return kRows ? rgy[0] : gy[r]; }
 
     __device__ __forceinline__ void init()
     {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-                phi[r][t] = gx[r][t] = gy[r][t] = qc[r][t] = 0.f;
+            phi[r] = gx[r] = gy[r] = qc[r] = f2(0.f);
     }
     __device__ __forceinline__ void load(int j)
     {
@@ -153,42 +153,41 @@ template <int P, int R> struct NearFwd {
     {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            acc_phi(r, t) -= qj[r] * np.beta[0];   // G(0) := 0 removes the far field's T_I(0)
-            qc[r][t] += qj[r];
+            add_comp(acc_phi(r), t, -qj[r] * np.beta[0]);   // G(0) := 0 removes the far field's T_I(0)
+            add_comp(qc[r], t, qj[r]);
         }
     }
-    __device__ __forceinline__ void pair(const NearParams<float> &np, int t, float r2, float dx, float dy)
+    __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
-        const bool in = r2 < np.eps2;
-        const float w = r2 * np.inv_eps2;
-        const float coef = np.rcoef * ipow<P - 1>(w - 1.f) * rcp_approx(w);
-        const float val = near_f<P>(np, w);
+        float2 w = mul2(r2, f2(np.inv_eps2));
+        if constexpr (P >= 2)
+            w = min1(w);                                  // f(1) = 0 and (w - 1)^(p-1) = 0: masked
+        const float2 val = near_f2<P>(np, w);
+        float2 coef = rcp_2(w);
+        if constexpr (P >= 2)
+            coef = mul2(ipow2<P - 1>(add2(w, f2(-1.f))), coef);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float qm = in ? qj[r] : 0.f;
-            acc_phi(r, t) = fmaf(qm, val, acc_phi(r, t));
-            const float tq = qm * coef;
-            acc_gx(r, t) = fmaf(tq, dx, acc_gx(r, t));
-            acc_gy(r, t) = fmaf(tq, dy, acc_gy(r, t));
+            float2 qq = f2(qj[r]);
+            if constexpr (P == 1)
+                qq = select2(r2, np.eps2, qq);
+            acc_phi(r) = fma2(qq, val, acc_phi(r));
+            const float2 tq = mul2(qq, coef);
+            acc_gx(r) = fma2(tq, dx, acc_gx(r));
+            acc_gy(r) = fma2(tq, dy, acc_gy(r));
         }
     }
     __device__ __forceinline__ void row_begin()
     {
-        if constexpr (kRows) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-                rphi[0][t] = rgx[0][t] = rgy[0][t] = 0.f;
-        }
+        if constexpr (kRows)
+            rphi[0] = rgx[0] = rgy[0] = f2(0.f);
     }
     __device__ __forceinline__ void row_end()
     {
         if constexpr (kRows) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                phi[0][t] += rphi[0][t];
-                gx[0][t] += rgx[0][t];
-                gy[0][t] += rgy[0][t];
-            }
+            phi[0] = add2(phi[0], rphi[0]);
+            gx[0] = add2(gx[0], rgx[0]);
+            gy[0] = add2(gy[0], rgy[0]);
         }
     }
     __device__ __forceinline__ void store(int t, int64_t k)
@@ -196,10 +195,10 @@ template <int P, int R> struct NearFwd {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int64_t kk = k + r * n_stride;
-            phi_s[kk] += phi[r][t];
-            grad_s[2 * kk] += gx[r][t];
-            grad_s[2 * kk + 1] += gy[r][t];
-            coinc[kk] = qc[r][t];
+            phi_s[kk] += comp(phi[r], t);
+            grad_s[2 * kk] += rcoef * comp(gx[r], t);
+            grad_s[2 * kk + 1] += rcoef * comp(gy[r], t);
+            coinc[kk] = comp(qc[r], t);
         }
     }
 };
@@ -228,6 +227,7 @@ __global__ void __launch_bounds__(128, NearFwd<P, R>::kMinBlocks - (R == 1 ? 1 :
     op.coinc = b.coinc;
     op.q_stride = b.M;
     op.n_stride = b.N;
+    op.rcoef = np.rcoef;
     near_traverse(make_int2(it.x, it.y), lane, sd, cg, np, op);
 }
 
@@ -316,6 +316,7 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
         op.coinc = coinc;
         op.q_stride = 0;
         op.n_stride = 0;
+        op.rcoef = np.rcoef;
         return launch_near_warp(n_items, items, sd, cg, np, op, st);
     });
 }

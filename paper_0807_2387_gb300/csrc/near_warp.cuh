@@ -20,6 +20,12 @@
 //     c'(w)     = dc/dw = rc (w - 1)^(p-2) ((p - 2) w + 1) / w^2
 // (the (p-1)-fold root at w = 1 keeps c free of cancellation near r = eps_I), so
 // grad f = c d and Hess f = c I + (2 c' / eps_I^2) d d^T for d = own - other.
+//
+// The two points of a lane meet the same other point, so their arithmetic is done as
+// packed pairs (Blackwell's two-wide FP32 add, multiply and fma: one instruction for
+// both).  Pairs beyond eps_I are masked without a select where the forms allow it:
+// with w clamped to 1, P(w) = (w - 1) Ptilde(w) and (w - 1)^(p-1) vanish exactly, as
+// does log2(1).
 #pragma once
 
 #include <type_traits>
@@ -82,29 +88,70 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// f(w) = G - T_I of one pair.
-template <int P> __device__ __forceinline__ float near_f(const NearParams<float> &np, float w)
+// ---- packed pairs of FP32 values (x: the lane's first point, y: its second)
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 min1(float2 w) { return make_float2(fminf(w.x, 1.f), fminf(w.y, 1.f)); }
+__device__ __forceinline__ float2 lg2_2(float2 w) { return make_float2(lg2_approx(w.x), lg2_approx(w.y)); }
+__device__ __forceinline__ float2 rcp_2(float2 w) { return make_float2(rcp_approx(w.x), rcp_approx(w.y)); }
+__device__ __forceinline__ float2 select2(float2 r2, float eps2, float2 v)
 {
-    float pw = np.pbeta[P - 1];
-#pragma unroll
-    for (int i = P - 2; i >= 0; --i)
-        pw = fmaf(pw, w, np.pbeta[i]);
-    const float c_ln = -0.69314718055994531f / (4.0f * 3.14159265358979324f);   // -(ln 2) / (4 pi)
-    return fmaf(c_ln, lg2_approx(w), -pw);
+    return make_float2(r2.x < eps2 ? v.x : 0.f, r2.y < eps2 ? v.y : 0.f);
+}
+__device__ __forceinline__ float comp(float2 v, int t) { return t == 0 ? v.x : v.y; }
+__device__ __forceinline__ void add_comp(float2 &v, int t, float a)
+{
+    if (t == 0)
+        v.x += a;
+    else
+        v.y += a;
 }
 
-// c(w) and c'(w) of one pair (the 1 / eps_I^2 of c is in rc).
-template <int P> __device__ __forceinline__ void near_c_cp(const NearParams<float> &np, float w, float &c, float &cp)
+template <int E> __device__ __forceinline__ float2 ipow2(float2 x)
 {
-    const float rw = rcp_approx(w);
-    if constexpr (P == 1) {
-        c = np.rcoef * rw;
-        cp = -c * rw;
+    if constexpr (E == 0) {
+        return f2(1.f);
+    } else if constexpr (E == 1) {
+        return x;
     } else {
-        const float om = w - 1.f;
-        const float base = np.rcoef * ipow<P - 2>(om) * rw;
-        c = base * om;
-        cp = base * fmaf((float)(P - 2), w, 1.f) * rw;
+        const float2 h = ipow2<E / 2>(x);
+        if constexpr (E % 2 == 0)
+            return mul2(h, h);
+        else
+            return mul2(mul2(h, h), x);
+    }
+}
+
+// f = G - T_I at w (clamped to <= 1 by the caller for p >= 2, where f(1) = 0 exactly).
+template <int P> __device__ __forceinline__ float2 near_f2(const NearParams<float> &np, float2 w)
+{
+    const float c_ln = -0.69314718055994531f / (4.0f * 3.14159265358979324f);   // -(ln 2) / (4 pi)
+    if constexpr (P == 1) {
+        return fma2(f2(c_ln), lg2_2(w), f2(-np.pbeta[0]));
+    } else {
+        float2 t = f2(np.nptilde[P - 2]);
+#pragma unroll
+        for (int i = P - 3; i >= 0; --i)
+            t = fma2(t, w, f2(np.nptilde[i]));
+        return fma2(f2(c_ln), lg2_2(w), mul2(add2(w, f2(-1.f)), t));   // c_ln log2 w - (w - 1) Ptilde(w)
+    }
+}
+
+// c / rc = (w - 1)^(p-1) / w and c' / rc = (w - 1)^(p-2) ((p - 2) w + 1) / w^2 (rc applied by the caller).
+template <int P> __device__ __forceinline__ void near_c_cp2(float2 w, float2 &c, float2 &cp)
+{
+    const float2 rw = rcp_2(w);
+    if constexpr (P == 1) {
+        c = rw;
+        cp = mul2(f2(-1.f), mul2(rw, rw));
+    } else {
+        const float2 om = add2(w, f2(-1.f));
+        const float2 base = mul2(ipow2<P - 2>(om), rw);
+        c = mul2(base, om);
+        cp = mul2(mul2(base, fma2(f2((float)(P - 2)), w, f2(1.f))), rw);
     }
 }
 
@@ -117,10 +164,56 @@ struct NearSides {
     const int *oth_start;
 };
 
+// Sources of one sub-cell [j0, j1) against the lane's two points (X, Y: packed x and y
+// coordinates shifted by the cell step).  With CLOSE, pairs closer than eps_I/8 refine their
+// difference exactly (taken warp-uniformly when any lane needs it) and coincident pairs are
+// reported to the operation; without, the sub-cell is known to hold no such pair.
+template <bool CLOSE, class Op>
+__device__ __forceinline__ void near_run(int j0, int j1, const NearSides &sd, const NearParams<float> &np, float2 X,
+                                         float2 Y, const float2 (&xh)[2], const float2 (&xl)[2], float offx,
+                                         float offy, Op &op)
+{
+    for (int j = j0; j < j1; ++j) {
+        const float2 yh = __ldg(sd.oth_hi + j);
+        op.load(j);
+        float2 dx = add2(X, f2(-yh.x));
+        float2 dy = add2(Y, f2(-yh.y));
+        float2 r2 = fma2(dy, dy, mul2(dx, dx));
+        if constexpr (CLOSE) {
+            const bool c0 = r2.x < np.close2, c1 = r2.y < np.close2;
+            if (__any_sync(0xffffffffu, c0 || c1)) {
+                const float2 yl = __ldg(sd.oth_lo + j);
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (t == 0 ? c0 : c1) {
+                        const float ex = refine_diff(xh[t].x, yh.x, offx, xl[t].x, yl.x);
+                        const float ey = refine_diff(xh[t].y, yh.y, offy, xl[t].y, yl.y);
+                        float e2 = ex * ex + ey * ey;
+                        if (ex == 0.f && ey == 0.f) {
+                            op.coincident(np, t);
+                            e2 = np.eps2;                 // masked out: w = 1
+                        }
+                        if (t == 0) {
+                            dx.x = ex;
+                            dy.x = ey;
+                            r2.x = e2;
+                        } else {
+                            dx.y = ex;
+                            dy.y = ey;
+                            r2.y = e2;
+                        }
+                    }
+                }
+            }
+        }
+        op.pair2(np, r2, dx, dy);
+    }
+}
+
 // One warp work item.  Op provides: init(), load(j) (the other point's weights),
-// coincident(np, t), pair(np, t, r2, dx, dy) (masked by r2 < eps_I^2), row_begin(),
-// row_end() (partial sums per sub-cell row), store(t, k).  No lane-divergent branch:
-// the close-pair refinement is taken warp-uniformly when any lane needs it.
+// coincident(np, t) (slot t = 0, 1 coincides with the current other point), pair2(np, r2,
+// dx, dy) (both slots packed; pairs with r2 >= eps_I^2 must contribute nothing),
+// row_begin(), row_end() (partial sums per sub-cell row), store(t, k).
 template <class Op>
 __device__ __forceinline__ void near_traverse(int2 item, int lane, const NearSides &sd, const CellGrid &cg,
                                               const NearParams<float> &np, Op &op)
@@ -163,16 +256,15 @@ __device__ __forceinline__ void near_traverse(int2 item, int lane, const NearSid
             xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
     const float reach = eps + ginv;               // eps_I plus one grid line for rounding of positions
     const float reach2 = reach * reach;
+    const float close_reach = sqrtf(np.close2) + ginv;
+    const float close_reach2 = close_reach * close_reach;
     const int cx0 = max(0, (int)floorf((tx0 - reach) / h)), cx1 = min(cg.n_c - 1, (int)floorf((tx1 + reach) / h));
     const int cy0 = max(0, (int)floorf((ty0 - reach) / h)), cy1 = min(cg.n_c - 1, (int)floorf((ty1 + reach) / h));
     op.init();
     for (int ex = cx0; ex <= cx1; ++ex) {
         const float offx = (float)(c1 - ex) * h;
         const float sx0 = (float)ex * h;
-        float2 xs[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-            xs[t].x = xh[t].x + offx;
+        const float2 X = make_float2(xh[0].x + offx, xh[1].x + offx);
         for (int s1 = 0; s1 < kSubEdge; ++s1) {
             // gap between this sub-cell row and the points' box (warp-uniform)
             const float lo = sx0 + (float)cg.sub_first(s1) * ginv, hi = sx0 + (float)cg.sub_first(s1 + 1) * ginv;
@@ -183,50 +275,21 @@ __device__ __forceinline__ void near_traverse(int2 item, int lane, const NearSid
             for (int ey = cy0; ey <= cy1; ++ey) {
                 const float offy = (float)(c2 - ey) * h;
                 const float sy0 = (float)ey * h;
-#pragma unroll
-                for (int t = 0; t < 2; ++t)
-                    xs[t].y = xh[t].y + offy;
+                const float2 Y = make_float2(xh[0].y + offy, xh[1].y + offy);
                 const int kbase = cg.key(ex, ey) * kSub;
                 for (int s2 = 0; s2 < kSubEdge; ++s2) {
                     const float ylo = sy0 + (float)cg.sub_first(s2) * ginv;
                     const float yhi = sy0 + (float)cg.sub_first(s2 + 1) * ginv;
                     const float gapy = fmaxf(0.f, fmaxf(ylo - ty1, ty0 - yhi));
-                    if (gapx * gapx + gapy * gapy > reach2)
+                    const float gap2 = gapx * gapx + gapy * gapy;
+                    if (gap2 > reach2)
                         continue;                 // no point of this warp is within eps_I of the sub-cell
                     const int sub = morton_sub(s1, s2);
-                    const int end = sd.oth_start[kbase + sub + 1];
-                    for (int j = sd.oth_start[kbase + sub]; j < end; ++j) {
-                        const float2 yh = __ldg(sd.oth_hi + j);
-                        op.load(j);
-                        // xs = xh + (cell step): one subtraction per coordinate
-                        float dx[2], dy[2], r2[2];
-                        bool close = false;
-#pragma unroll
-                        for (int t = 0; t < 2; ++t) {
-                            dx[t] = xs[t].x - yh.x;
-                            dy[t] = xs[t].y - yh.y;
-                            r2[t] = dx[t] * dx[t] + dy[t] * dy[t];
-                            close |= r2[t] < np.close2;
-                        }
-                        if (__any_sync(0xffffffffu, close)) {
-                            const float2 yl = __ldg(sd.oth_lo + j);
-#pragma unroll
-                            for (int t = 0; t < 2; ++t) {
-                                if (r2[t] < np.close2) {
-                                    dx[t] = refine_diff(xh[t].x, yh.x, offx, xl[t].x, yl.x);
-                                    dy[t] = refine_diff(xh[t].y, yh.y, offy, xl[t].y, yl.y);
-                                    r2[t] = dx[t] * dx[t] + dy[t] * dy[t];
-                                    if (dx[t] == 0.f && dy[t] == 0.f) {
-                                        op.coincident(np, t);
-                                        r2[t] = np.eps2;   // masked out below
-                                    }
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int t = 0; t < 2; ++t)
-                            op.pair(np, t, r2[t], dx[t], dy[t]);
-                    }
+                    const int j0 = sd.oth_start[kbase + sub], j1 = sd.oth_start[kbase + sub + 1];
+                    if (gap2 < close_reach2)
+                        near_run<true>(j0, j1, sd, np, X, Y, xh, xl, offx, offy, op);
+                    else
+                        near_run<false>(j0, j1, sd, np, X, Y, xh, xl, offx, offy, op);
                 }
             }
             op.row_end();

@@ -178,6 +178,17 @@ template <typename real> inline NearParams<real> make_near(const fs_plan *pl)
     const double k_eps = -std::log(pl->eps_I) / (2.0 * kPi);
     for (int k = 0; k < pl->p; ++k)
         np.pbeta[k] = (real)(k == 0 ? pl->beta[0] - k_eps : pl->beta[k]);
+    // synthetic division of P by (w - 1): Ptilde_{p-2} = a_{p-1}, Ptilde_k = a_{k+1} + Ptilde_{k+1}
+    // (the remainder P(1) vanishes in exact arithmetic and is dropped)
+    {
+        double a[kMaxP] = {0}, t[kMaxP] = {0};
+        for (int k = 0; k < pl->p; ++k)
+            a[k] = k == 0 ? pl->beta[0] - k_eps : pl->beta[k];
+        for (int k = pl->p - 2; k >= 0; --k)
+            t[k] = a[k + 1] + (k + 1 <= pl->p - 2 ? t[k + 1] : 0.0);
+        for (int k = 0; k + 1 < pl->p; ++k)
+            np.nptilde[k] = (real)(-t[k]);
+    }
     // R(w) = c (w-1)^(p-1) with R(0) = -(1/2pi) gives c = (-1)^p / (2pi), independent of beta
     np.rcoef = (real)(((pl->p % 2 == 0) ? 1.0 : -1.0) / (2.0 * kPi * pl->eps_I * pl->eps_I));
     return np;
