@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_batch_near64(const BatchInst<double> *_
 // registers go to the extra accumulators instead.  Right-hand side r reads q + r q_stride
 // and writes at r n_stride.
 template <int P, int R> struct NearFwd {
-    static constexpr int kMinBlocks = R == 1 ? 6 : 4;
+    static constexpr int kMinBlocks = R == 1 ? 5 : 4;
     static constexpr bool kRows = R == 1;
     const float *__restrict__ q;
     float *__restrict__ phi_s;
@@ -204,10 +204,9 @@ template <int P, int R> struct NearFwd {
 };
 
 // Batched FP32 near field: one warp per item (first target, count, instance); all R
-// right-hand sides in one traversal.  The instance's constants live in registers rather than
-// in the constant bank, hence one block fewer per SM than the single-plan kernel for R = 1.
+// right-hand sides in one traversal.
 template <int P, int R>
-__global__ void __launch_bounds__(128, NearFwd<P, R>::kMinBlocks - (R == 1 ? 1 : 0)) k_batch_near32(int64_t n_items,
+__global__ void __launch_bounds__(128, NearFwd<P, R>::kMinBlocks) k_batch_near32(int64_t n_items,
                                                                                const int4 *__restrict__ items,
                                                                                const BatchInst<float> *__restrict__ inst)
 {

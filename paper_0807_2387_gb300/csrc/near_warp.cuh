@@ -173,6 +173,7 @@ __device__ __forceinline__ void near_run(int j0, int j1, const NearSides &sd, co
                                          float2 Y, const float2 (&xh)[2], const float2 (&xl)[2], float offx,
                                          float offy, Op &op)
 {
+#pragma unroll 2
     for (int j = j0; j < j1; ++j) {
         const float2 yh = __ldg(sd.oth_hi + j);
         op.load(j);
@@ -254,9 +255,12 @@ __device__ __forceinline__ void near_traverse(int2 item, int lane, const NearSid
     for (int t = 0; t < 2; ++t)
         if (!valid[t])
             xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
-    const float reach = eps + ginv;               // eps_I plus one grid line for rounding of positions
+    // culling radii: eps_I (and eps_I / 8) plus a margin that covers the FP32 rounding of the
+    // box and sub-cell bounds (~1e-7 torus units) a hundred times over
+    const float margin = 1e-4f * eps + 1e-5f;
+    const float reach = eps + margin;
     const float reach2 = reach * reach;
-    const float close_reach = sqrtf(np.close2) + ginv;
+    const float close_reach = sqrtf(np.close2) + margin;
     const float close_reach2 = close_reach * close_reach;
     const int cx0 = max(0, (int)floorf((tx0 - reach) / h)), cx1 = min(cg.n_c - 1, (int)floorf((tx1 + reach) / h));
     const int cy0 = max(0, (int)floorf((ty0 - reach) / h)), cy1 = min(cg.n_c - 1, (int)floorf((ty1 + reach) / h));
