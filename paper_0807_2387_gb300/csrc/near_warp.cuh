@@ -173,7 +173,7 @@ __device__ __forceinline__ void near_run(int j0, int j1, const NearSides &sd, co
                                          float2 Y, const float2 (&xh)[2], const float2 (&xl)[2], float offx,
                                          float offy, Op &op)
 {
-#pragma unroll 2
+#pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         const float2 yh = __ldg(sd.oth_hi + j);
         op.load(j);
