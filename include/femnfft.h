@@ -285,9 +285,10 @@ typedef struct {
  * opts.tile_cells, if set, to every instance).  With FS_FLAG_AUTOTUNE (and cell,
  * tile_cells left 0) each class of instances - same n_grid, m, sigma, p,
  * precision and rounded log2 of N and of M - gets the near-field cell (1, 1.5 or
- * 2 times the narrowest) and spreading tile (about 16, 32 or 64 grid lines) that
- * evaluated fastest on the class's first instance; choices are cached for the
- * process.
+ * 2 times the narrowest) and spreading tile (about 16, 32 or 64 grid lines, if its
+ * shared-memory tile stays within 56 KB so that four spreading CTAs fit per SM)
+ * that evaluated fastest on the class's first instance; choices are cached for
+ * the process.
  *  inst   [host] count descriptors; the point arrays are read during the call only
  *  nrhs   1..4 charge vectors per instance
  * Returns FS_EINVAL (bad argument; instances with different p), FS_ENOMEM, FS_ECUDA.

@@ -29,6 +29,7 @@ using namespace fs;
 namespace {
 
 constexpr int kPointBlock = 256;   // threads (= points) per block of the per-point batched kernels
+constexpr size_t kMaxTileSmem = 56 * 1024;   // spreading tiles of tuned batches: >= 4 CTAs per SM
 constexpr int kMaxRhs = 4;
 
 struct GraphEntry {
@@ -132,8 +133,9 @@ fs_status time_candidate(const fs_instance &in, double sigma, int m, const fs_op
 }
 
 // Picks (tile_cells, cell) for the class of `in`: near-field cells of 1, 1.5 and 2 times the
-// narrowest admissible width, tiles of about 16, 32 and 64 grid lines, timed on the instance
-// itself with constant charges (the work is independent of the charge values).
+// narrowest admissible width, tiles of about 16, 32 and 64 grid lines whose spreading tile
+// fits in kMaxTileSmem, timed on the instance itself with constant charges (the work is
+// independent of the charge values).
 fs_status tune_instance(const fs_instance &in, double sigma, int m, const fs_opts &base, int *tile_cells, int *cell)
 {
     const int L = (int)std::lround(sigma * in.n_grid);
@@ -172,6 +174,13 @@ fs_status tune_instance(const fs_instance &in, double sigma, int m, const fs_opt
             tiles.push_back(std::max(1, (int)std::lround((double)tg / c)));
         tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
         for (int t : tiles) {
+            // a batch sizes the spreading kernel's shared memory for its largest tile, so tiles
+            // that would leave fewer than four CTAs per SM are not candidates
+            const int P = t * c + 2 * m - 1;
+            const size_t rsz = probe.precision == 64 ? 8 : 4;
+            const int planes = (probe.precision != 64 && !(probe.flags & FS_FLAG_NO_KAHAN)) ? 2 : 1;
+            if ((size_t)kSpreadWarps * P * P * rsz * planes > kMaxTileSmem)
+                continue;
             fs_opts o = probe;
             o.cell = c;
             o.tile_cells = t;

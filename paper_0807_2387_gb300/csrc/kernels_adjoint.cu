@@ -268,7 +268,7 @@ template <int P> struct NearHess32 {
 // d = y - x = -D):  A += gphi f - (dn . d) c,  grad_y A += c (gphi d - dn) - (2 c' / eps_I^2)(dn . d) d,
 // with the hatted c^, c'^ summed and rc, 2 / eps_I^2 applied at the store.
 template <int P> struct NearAdj32 {
-    static constexpr int kMinBlocks = 5;
+    static constexpr int kMinBlocks = 4;
     static constexpr bool kClamp = P >= 3;
     const float *__restrict__ cw;
     const float2 *__restrict__ dnw;
