@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(256) k_near_hess64(int64_t N, const int *__res
 // charge is masked.
 template <int P> struct NearHess32 {
     static constexpr int kMinBlocks = 5;
+    static constexpr int kUnroll = 2;
     static constexpr bool kClamp = P >= 3;
     const float *__restrict__ q;
     float *__restrict__ grad_s;
@@ -269,6 +270,7 @@ template <int P> struct NearHess32 {
 // with the hatted c^, c'^ summed and rc, 2 / eps_I^2 applied at the store.
 template <int P> struct NearAdj32 {
     static constexpr int kMinBlocks = 4;
+    static constexpr int kUnroll = 2;
     static constexpr bool kClamp = P >= 3;
     const float *__restrict__ cw;
     const float2 *__restrict__ dnw;

@@ -120,8 +120,11 @@ __global__ void __launch_bounds__(256) k_batch_near64(const BatchInst<double> *_
 // right-hand side the sums are split into partial sums per sub-cell row; with several the
 // registers go to the extra accumulators instead.  Right-hand side r reads q + r q_stride
 // and writes at r n_stride.
-template <int P, int R> struct NearFwd {
-    static constexpr int kMinBlocks = R == 1 ? 5 : 4;
+template <int P, int R, bool BATCH = false> struct NearFwd {
+    // the batched kernel holds the instance's constants in registers (the single-plan one reads
+    // them from the constant bank), so it gets more registers and less unrolling
+    static constexpr int kMinBlocks = (R == 1 && !BATCH) ? 5 : 4;
+    static constexpr int kUnroll = (R == 1 && !BATCH) ? 4 : (R >= 4 ? 1 : 2);
     static constexpr bool kRows = R == 1;
     const float *__restrict__ q;
     float *__restrict__ phi_s;
@@ -206,7 +209,7 @@ template <int P, int R> struct NearFwd {
 // Batched FP32 near field: one warp per item (first target, count, instance); all R
 // right-hand sides in one traversal.
 template <int P, int R>
-__global__ void __launch_bounds__(128, NearFwd<P, R>::kMinBlocks) k_batch_near32(int64_t n_items,
+__global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_near32(int64_t n_items,
                                                                                const int4 *__restrict__ items,
                                                                                const BatchInst<float> *__restrict__ inst)
 {
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(128, NearFwd<P, R>::kMinBlocks) k_batch_near32
     const NearSides sd{b.tgt_base, b.tgt_hi, b.tgt_lo, b.src_hi, b.src_lo, b.src_start};
     const CellGrid cg = b.cg;
     const NearParams<float> np = b.np;
-    NearFwd<P, R> op;
+    NearFwd<P, R, true> op;
     op.q = b.q;
     op.phi_s = b.phi_s;
     op.grad_s = b.grad_s;

@@ -173,7 +173,7 @@ __device__ __forceinline__ void near_run(int j0, int j1, const NearSides &sd, co
                                          float2 Y, const float2 (&xh)[2], const float2 (&xl)[2], float offx,
                                          float offy, Op &op)
 {
-#pragma unroll 4
+#pragma unroll(Op::kUnroll)
     for (int j = j0; j < j1; ++j) {
         const float2 yh = __ldg(sd.oth_hi + j);
         op.load(j);
@@ -211,7 +211,8 @@ __device__ __forceinline__ void near_run(int j0, int j1, const NearSides &sd, co
     }
 }
 
-// One warp work item.  Op provides: init(), load(j) (the other point's weights),
+// One warp work item.  Op provides kMinBlocks (launch bound), kUnroll (unrolling of the
+// per-source loop), init(), load(j) (the other point's weights),
 // coincident(np, t) (slot t = 0, 1 coincides with the current other point), pair2(np, r2,
 // dx, dy) (both slots packed; pairs with r2 >= eps_I^2 must contribute nothing),
 // row_begin(), row_end() (partial sums per sub-cell row), store(t, k).
