@@ -162,7 +162,7 @@ def algorithmic_bytes(info, n_points):
 # reports null until it is re-captured).
 NEAR_TRAFFIC = {
     # profiles/dram_per_kernel_mixture_2p19.md: 28.32 MB per launch at 2^19 points, scaled by the point count
-    "32515a4cd552d4b658f598db3b5ef8c6080ea3b59d3452088532dca387fed6e2": 2 * 28.32e6,
+    "9fd32b6a234f72e689b7bea3198e855167cd383a9565fa3de5862ffba4f03738": 2 * 28.32e6,
 }
 
 
