@@ -523,18 +523,27 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     FS_TRY(pl->alloc_bytes(&pl->grad_s, (size_t)std::max<int64_t>(N, 1) * 2 * sizeof(real)));
     FS_TRY(pl->alloc_bytes(&pl->coinc, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
 
-    // near-field pair statistics (FP64 distances)
+    // near-field pair statistics: the FP32 path counts with its own traversal (the pairs its
+    // near-field kernel evaluates), the FP64 path with FP64 distances
     {
         unsigned long long *cnt = nullptr;
-        FS_TRY(pl->alloc(&cnt, 2));
-        FS_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
-        FS_CUDA(launch_near_count(pl->tgt_pos, pl->tgt_base, N, pl->src_pos, pl->src_start, pl->cg, eps_I * eps_I,
-                                  (eps_I / 8) * (eps_I / 8), cnt, st));
-        unsigned long long h[2] = {0, 0};
-        FS_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+        FS_TRY(pl->alloc(&cnt, 2 * kNearCountSlots));
+        FS_CUDA(cudaMemsetAsync(cnt, 0, 2 * kNearCountSlots * sizeof(unsigned long long), st));
+        if constexpr (sizeof(real) == 4)
+            FS_CUDA(launch_near_count32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
+                                        pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, make_near<float>(pl), cnt,
+                                        st));
+        else
+            FS_CUDA(launch_near_count(pl->tgt_pos, pl->tgt_base, N, pl->src_pos, pl->src_start, pl->cg,
+                                      eps_I * eps_I, (eps_I / 8) * (eps_I / 8), cnt, st));
+        std::vector<unsigned long long> h(2 * kNearCountSlots, 0);
+        FS_CUDA(cudaMemcpyAsync(h.data(), cnt, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         FS_CUDA(cudaStreamSynchronize(st));
-        pl->near_pairs = (int64_t)h[0];
-        pl->near_pairs_fp64 = (int64_t)h[1];
+        pl->near_pairs = pl->near_pairs_fp64 = 0;
+        for (int i = 0; i < kNearCountSlots; ++i) {
+            pl->near_pairs += (int64_t)h[2 * i];
+            pl->near_pairs_fp64 += (int64_t)h[2 * i + 1];
+        }
         pl->release(cnt);
     }
 

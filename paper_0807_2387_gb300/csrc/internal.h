@@ -183,6 +183,12 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
                           const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                           CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,
                           cudaStream_t st);
+// plan-time pair statistics over the FP32 near-field items: counts[2 s] (r < eps_I) and
+// counts[2 s + 1] (r < eps_I / 8) for s < kNearCountSlots, to be summed
+constexpr int kNearCountSlots = 64;
+cudaError_t launch_near_count32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                                const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
+                                CellGrid cg, NearParams<float> np, unsigned long long *counts, cudaStream_t st);
 template <typename real>
 cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, const real *coinc,
                              const int *perm, double shift, const double *q_sum, double s, void *phi_out,

@@ -206,6 +206,42 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
     }
 };
 
+// Plan-time statistics: pairs with r < eps_I and with r < eps_I / 8 (coincident pairs
+// included), counted by the same traversal and the same FP32 differences as the field
+// kernel.  Each lane adds its counts to one of kCountSlots counter pairs (summed on the host).
+static_assert(kNearCountSlots == 64, "counter slots");
+constexpr int kCountSlots = kNearCountSlots;
+struct NearCount {
+    static constexpr int kMinBlocks = 6;
+    static constexpr int kUnroll = 2;
+    unsigned long long *__restrict__ counts;   // 2 * kCountSlots
+    unsigned n_near, n_close;
+
+    __device__ __forceinline__ void init() { n_near = n_close = 0; }
+    __device__ __forceinline__ void load(int) {}
+    __device__ __forceinline__ void coincident(const NearParams<float> &, int)
+    {
+        ++n_near;
+        ++n_close;
+    }
+    __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2, float2)
+    {
+        n_near += (r2.x < np.eps2 ? 1u : 0u) + (r2.y < np.eps2 ? 1u : 0u);
+        n_close += (r2.x < np.close2 ? 1u : 0u) + (r2.y < np.close2 ? 1u : 0u);
+    }
+    __device__ __forceinline__ void row_begin() {}
+    __device__ __forceinline__ void row_end() {}
+    __device__ __forceinline__ void store(int t, int64_t)
+    {
+        // both slots' counts are in the lane's totals (an idle slot never lands within eps_I)
+        if (t == 0) {
+            const int slot = threadIdx.x & (kCountSlots - 1);
+            atomicAdd(&counts[2 * slot], (unsigned long long)n_near);
+            atomicAdd(&counts[2 * slot + 1], (unsigned long long)n_close);
+        }
+    }
+};
+
 // Batched FP32 near field: one warp per item (first target, count, instance); all R
 // right-hand sides in one traversal.
 template <int P, int R>
@@ -339,6 +375,16 @@ template cudaError_t launch_unpermute<float>(int64_t, const float *, const float
                                              double, const double *, double, void *, void *, int, cudaStream_t);
 template cudaError_t launch_unpermute<double>(int64_t, const double *, const double *, const double *, const int *,
                                               double, const double *, double, void *, void *, int, cudaStream_t);
+
+cudaError_t launch_near_count32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
+                                const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
+                                CellGrid cg, NearParams<float> np, unsigned long long *counts, cudaStream_t st)
+{
+    const NearSides sd{tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start};
+    NearCount op{};
+    op.counts = counts;
+    return launch_near_warp(n_items, items, sd, cg, np, op, st);
+}
 
 cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchInst<float> *inst, int p, int nrhs,
                                 cudaStream_t st)

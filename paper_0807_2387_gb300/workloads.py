@@ -97,6 +97,47 @@ def ring_mesh(rng: np.random.Generator, rings: int, jitter: float = 0.2):
     return nodes, np.ascontiguousarray(tri[keep].astype(np.int32))
 
 
+def annulus_mesh(rng: np.random.Generator, rings: int, r_in: float = 0.5, r_out: float = 1.0,
+                 jitter: float = 0.2):
+    """P1 mesh of the annulus r_in <= r <= r_out (a cylinder with a bore), Delaunay-triangulated.
+
+    Rings k = 0..rings at radius r_in + k h (h = (r_out - r_in) / rings), each with
+    round(2 pi r / h) nodes; interior rings are jittered by at most ``jitter`` * h
+    radially and angularly, the two boundary rings are exact.  Triangles whose centroid
+    lies in the bore are dropped, so both boundaries are the ring polygons.
+
+    Returns (nodes (Nv,2) f64, tris (Nt,3) int32, counter-clockwise).
+    """
+    from scipy.spatial import Delaunay  # host-side mesh generation only
+
+    h = (r_out - r_in) / rings
+    pts = []
+    for k in range(rings + 1):
+        rad = r_in + k * h
+        cnt = max(6, int(round(2.0 * np.pi * rad / h)))
+        th = 2.0 * np.pi * (np.arange(cnt) + 0.5 * (k % 2)) / cnt
+        r = np.full(cnt, rad)
+        if 0 < k < rings:
+            r = r + jitter * h * rng.uniform(-1.0, 1.0, cnt)
+            th = th + jitter * h * rng.uniform(-1.0, 1.0, cnt) / rad
+        pts.append(np.stack([r * np.cos(th), r * np.sin(th)], axis=1))
+    nodes = np.concatenate(pts, axis=0)
+    tri = Delaunay(nodes).simplices.astype(np.int64)
+    a, b, c = nodes[tri[:, 0]], nodes[tri[:, 1]], nodes[tri[:, 2]]
+    centroid = (a + b + c) / 3.0
+    signed = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    flip = signed < 0
+    tri[flip, 1], tri[flip, 2] = tri[flip, 2].copy(), tri[flip, 1].copy()
+    keep = (np.abs(signed) > 1e-14 * h * h) & (np.hypot(centroid[:, 0], centroid[:, 1]) > r_in)
+    return nodes, np.ascontiguousarray(tri[keep].astype(np.int32))
+
+
+def magic_cylinder_magnetisation(nodes: np.ndarray) -> np.ndarray:
+    """M = (cos 2t, sin 2t) at polar angle t: the magic cylinder of the paper's second test."""
+    t = np.arctan2(nodes[:, 1], nodes[:, 0])
+    return np.stack([np.cos(2.0 * t), np.sin(2.0 * t)], axis=1)
+
+
 def uniform_magnetisation(nodes: np.ndarray) -> np.ndarray:
     """M = (1, 0) at every node."""
     m = np.zeros_like(nodes)

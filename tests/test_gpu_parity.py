@@ -334,3 +334,77 @@ def test_stage_times(pkg):
     t = fs.stage_times()
     assert len(t) == 8 and all(v >= 0 for v in t.values()) and sum(t.values()) > 0
     fs.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_magic_cylinder_fem_nfft_tracks_direct(pkg, precision):
+    """The paper's second test (its Table 2): on an annulus mesh magnetised at angle 2t the
+    FEM-NFFT potential at the nodes misses the closed form x log(r / r_out) by FEM-direct's
+    error within the tables' few percent, and the bore field from the GPU's quadrature charges
+    is log(r_out / r_in) x-hat up to the discretisation error."""
+    import math
+    from oracle import direct as D
+    from oracle import fem
+    from paper_0807_2387_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    nodes, tris = W.annulus_mesh(np.random.default_rng(3), 12)
+    mag = W.magic_cylinder_magnetisation(nodes)
+    mag_t = torch.tensor(mag, device=dev)
+    fs = pkg.FastSum.fem(torch.tensor(nodes, device=dev), torch.tensor(tris, device=dev), 128, 2.0, 6, 6 / 128,
+                         precision=precision)
+    fs.set_magnetization(mag_t)
+    phi, _ = fs.field(dtype=torch.float64)
+    src = fs.sources()
+    q = fs.fem_charges(mag_t)
+    fs.sync()
+    phi = phi.cpu().numpy()
+    src_o = fem.quadrature_points(nodes, tris)
+    q_o = fem.assemble_charges(nodes, tris, mag)
+    assert rel(src.cpu().numpy(), src_o) <= 1e-14
+    assert rel(q.cpu().numpy(), q_o) <= 1e-13
+    phi_d = D.direct_sum(nodes, src_o, q_o, field=False)
+    exact = nodes[:, 0] * np.log(np.hypot(nodes[:, 0], nodes[:, 1]))
+    err_d = np.sqrt(np.mean((phi_d - exact) ** 2)) / 2.0       # (M_s L)^-1 RMS, L = diameter = 2
+    err_f = np.sqrt(np.mean((phi - exact) ** 2)) / 2.0
+    assert 0.95 < err_f / err_d < 1.05, (err_f, err_d)
+    rng = np.random.default_rng(1)
+    rad = 0.4 * 0.5 * np.sqrt(rng.random(300))
+    ang = 2 * np.pi * rng.random(300)
+    tb = np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+    bore = pkg.FastSum(src, torch.tensor(tb, device=dev), 128, 2.0, 6, 6 / 128, precision=precision)
+    bore.set_charges(q)
+    _, Hb = bore.field(dtype=torch.float64)
+    bore.sync()
+    Hb = Hb.cpu().numpy()
+    _, H_d = D.direct_sum(tb, src_o, q_o)
+    assert rel(Hb, H_d) <= 1e-4
+    assert np.max(np.abs(Hb - np.array([math.log(2.0), 0.0]))) < 1e-3
+    bore.close()
+    fs.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_near_pair_counts_match_oracle_search(pkg, precision):
+    """fs_plan_info's pair statistics (r < eps_I and r < eps_I / 8, coincident pairs included)
+    against the oracle's FP64 k-d tree search: exact for the FP64 count; the FP32 count uses the
+    FP32 near-field traversal and may differ only for pairs within FP32 rounding of the radius."""
+    from oracle import fastsum as F
+    from oracle import kernel as K
+    from paper_0807_2387_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    case = W.small_case(77, 3000, 2500, n=64, m=4, eps_I=4 / 64, coincident=False)
+    # a few coincident and near-coincident pairs
+    tgt = case["tgt"].copy()
+    tgt[:20] = case["src"][:20]
+    tgt[20:40] = case["src"][20:40] + 1e-7
+    par = K.make_params(case["n"], case["sigma"], case["m"], case["eps_I"], None)
+    s = F.torus_scale(case["src"], tgt, par)
+    ii, _, _, r2 = F.near_pairs(s * tgt, s * case["src"], par.eps_I)
+    n_near, n_close = len(ii), int(np.sum(r2 < (par.eps_I / 8) ** 2))
+    fs = pkg.FastSum(torch.tensor(case["src"], device=dev), torch.tensor(tgt, device=dev), case["n"], case["sigma"],
+                     case["m"], case["eps_I"], precision=precision)
+    info = fs.info
+    fs.close()
+    tol = 0 if precision == 64 else 2
+    assert abs(info["near_pairs"] - n_near) <= tol, (info["near_pairs"], n_near)
+    assert abs(info["near_pairs_fp64"] - n_close) <= tol, (info["near_pairs_fp64"], n_close)

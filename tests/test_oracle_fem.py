@@ -12,6 +12,8 @@
 * the boundary-edge extraction against an independent count.
 """
 
+import math
+
 import numpy as np
 import pytest
 
@@ -127,3 +129,36 @@ def test_fast_summation_error_tracks_direct_as_in_tables():
     assert 0.95 < err_f / err_d < 1.05
     # errors in the range the paper reports for meshes of this size (tens to hundreds of ppm)
     assert 10e-6 < err_d < 1000e-6
+
+
+def _magic_potential(nodes, r_out=1.0):
+    """Closed form inside the magnet of the magic cylinder M = (cos 2t, sin 2t), r_in <= r <= r_out:
+    phi = f(r) cos t with f'' + f'/r - f/r^2 = 2/r (rho = -div M = -2 cos t / r), continuity of phi
+    and jumps of H_r by M_r at both surfaces give f = r log(r / r_out), i.e. phi = x log(r / r_out);
+    in the bore phi = x log(r_in / r_out), so H = log(r_out / r_in) x-hat there, and 0 outside."""
+    r = np.hypot(nodes[:, 0], nodes[:, 1])
+    return nodes[:, 0] * np.log(r / r_out)
+
+
+def test_magic_cylinder_fem_direct_closed_form():
+    """The paper's second test case on annulus meshes: FEM-direct at the nodes converges to the
+    closed form, the bore field to log(r_out / r_in) at second order, with errors of the size
+    the paper's Table 2 reports (174 ppm at 1192 nodes)."""
+    errs, bore = [], []
+    rng = np.random.default_rng(1)
+    rad = 0.4 * 0.5 * np.sqrt(rng.random(200))
+    ang = 2 * np.pi * rng.random(200)
+    tb = np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+    for rings in (6, 12, 24):
+        nodes, tris = W.annulus_mesh(np.random.default_rng(3), rings)
+        src = fem.quadrature_points(nodes, tris)
+        q = fem.assemble_charges(nodes, tris, W.magic_cylinder_magnetisation(nodes))
+        assert abs(q.sum()) < 1e-12
+        phi = D.direct_sum(nodes, src, q, field=False)
+        errs.append(np.sqrt(np.mean((phi - _magic_potential(nodes)) ** 2)) / 2.0)   # M_s = 1, L = 2
+        _, H = D.direct_sum(tb, src, q)
+        bore.append(np.max(np.abs(H - np.array([math.log(2.0), 0.0]))))
+    assert errs[0] > errs[1] > errs[2]
+    assert 100e-6 < errs[1] < 400e-6          # 1471 nodes (the paper: 174 ppm at 1192, 95.8 at 2091)
+    assert bore[0] / bore[1] > 3.5 and bore[1] / bore[2] > 3.5
+    assert bore[2] < 2e-4
