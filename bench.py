@@ -295,6 +295,59 @@ def measure_adjoint(pkg, dev, steps, warmup, flush):
             "fp32_vs_fp64_adjoint_rel_l2": errs}
 
 
+FEM_WORKLOAD = ("mesh_disc_c1: unit-disc P1 mesh, 129 rings (50,311 nodes, ~100k triangles; targets = nodes, "
+                "sources = 3 points per triangle + 2 per boundary edge), n=512 (oversampled 1024^2), m=6, "
+                "eps_I=6/512, p=6; FP32; a rotating uniform magnetisation, a new M every step")
+
+
+def measure_fem_loop(pkg, dev, steps, warmup, flush):
+    """Time loop on one FEM plan: per step fs_set_magnetization (assembly fused with the gather)
+    + fs_eval_field, with M(t) = (cos a_t, sin a_t) at every node."""
+    import torch
+    from paper_0807_2387_gb300 import workloads as W
+    c = W.mesh_disc_c1()
+    nodes = torch.tensor(c["nodes"], device=dev)
+    fs = pkg.FastSum.fem(nodes, torch.tensor(c["tris"], device=dev), c["n"], c["sigma"], c["m"], c["eps_I"],
+                         precision=32)
+    mags = []
+    for k in range(steps + warmup):
+        m = torch.zeros_like(nodes)
+        m[:, 0], m[:, 1] = math.cos(0.1 * k), math.sin(0.1 * k)
+        mags.append(m)
+    n = fs.info["n_tgt"]
+    phi = torch.empty(n, dtype=torch.float32, device=dev)
+    H = torch.empty((n, 2), dtype=torch.float32, device=dev)
+
+    def step(m):
+        pkg.fs_set_magnetization(fs.handle, m, 1)
+        pkg.fs_eval_field(fs.handle, phi, H)
+
+    for k in range(warmup):
+        step(mags[k])
+    fs.sync()
+    ms = []
+    for k in range(warmup, warmup + steps):
+        flush.zero_()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(mags[k])
+        z.record()
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(z))
+    fs.sync()
+    ang = 0.1 * (warmup + steps - 1)
+    xy = nodes.double()
+    exact = 0.5 * (math.cos(ang) * xy[:, 0] + math.sin(ang) * xy[:, 1])
+    inner = torch.hypot(xy[:, 0], xy[:, 1]) < 1 - 5.0 / 129
+    err = float(torch.max(torch.abs(phi.double()[inner] - exact[inner])))
+    info = fs.info
+    fs.close()
+    t = statistics.mean(ms)
+    return {"workload": FEM_WORKLOAD, "nodes": n, "sources": info["n_src"], "ms_per_step": round(t, 4),
+            "value": 1e3 / t, "unit": "time steps/s (fs_set_magnetization + fs_eval_field)",
+            "interior_phi_max_err_vs_closed_form": err}
+
+
 def measure_cufft(dev, n_os, steps, flush):
     """cuFFT (through torch.fft) R2C + C2R of the full n_os x n_os FP32 grid, for comparison with
     the pruned hand-written transform (which reads the active window only and keeps I_n)."""
@@ -441,7 +494,7 @@ def run_ours(args):
         cpu, _ = cpu_baseline(work, args.cpu_targets)
 
     # the batched workload and the adjoint (one GPU; untimed by the headline value)
-    batch = adj = fftcmp = None
+    batch = adj = fftcmp = femloop = None
     if world == 1 and not args.quick:
         ours = stage_ms["fft_rows_fwd"] + stage_ms["fft_cols_mul"] + stage_ms["fft_rows_inv"]
         fftcmp = {"cufft_r2c_c2r_full_grid_ms": round(measure_cufft(dev, info["n_os"], 10, flush), 4),
@@ -451,6 +504,7 @@ def run_ours(args):
     if world == 1 and not args.quick and not args.no_extra:
         batch = measure_batch(pkg, dev, max(3, args.steps // 4), 3, flush)
         adj = measure_adjoint(pkg, dev, max(3, args.steps // 4), 3, flush)
+        femloop = measure_fem_loop(pkg, dev, max(5, args.steps), 3, flush)
 
     if world > 1:
         dist.barrier()
@@ -467,7 +521,7 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": KERNELS_PER_STEP * args.steps,
             "near_pairs": info["near_pairs"], "near_pairs_fp64": info["near_pairs_fp64"],
             "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src},
-            "batch_c4": batch, "adjoint_c3": adj, "fft_comparison": fftcmp,
+            "batch_c4": batch, "adjoint_c3": adj, "fem_time_loop_c1": femloop, "fft_comparison": fftcmp,
         }
         print(json.dumps(out))
     fs.close()
@@ -483,6 +537,8 @@ def run_only(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     if args.only == "batch":
         out = measure_batch(pkg, dev, args.steps, args.warmup, flush, args.instances)
+    elif args.only == "fem":
+        out = measure_fem_loop(pkg, dev, args.steps, args.warmup, flush)
     else:
         out = measure_adjoint(pkg, dev, args.steps, args.warmup, flush)
     print(json.dumps(out))
@@ -524,7 +580,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU baseline (profiling runs)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", choices=("batch", "adjoint"), default=None,
+    ap.add_argument("--only", choices=("batch", "adjoint", "fem"), default=None,
                     help="run only the batched or the adjoint measurement and print its JSON object")
     ap.add_argument("--instances", type=int, default=64,
                     help="instances of the batched workload with --only batch (the first K of the 64)")

@@ -148,8 +148,12 @@ fs_status fs_set_charges(fs_plan *plan, const void *q, fs_dtype dtype, int nrhs)
  * FEM plans only: charges from nodal magnetisation (kernel (a), Eq. (2)):
  * rho_T = -div M constant per P1 triangle, q = rho_T |T| / 3 per triangle
  * point; sigma = M(t).n_e along boundary edges (outward unit normal, M linear
- * along the edge), q = sigma |e| / 2 per edge point.
- *  mag [device] (nrhs, Nv, 2) float64.
+ * along the edge), q = sigma |e| / 2 per edge point.  The charges are computed
+ * (in FP64) straight into the plan's cell order in one kernel, so a time loop
+ * (one plan, a new M every step) costs one pass over the sources per step.
+ * The first call (or one with more vectors than before) allocates the plan's
+ * charge storage.
+ *  mag [device] (nrhs, Nv, 2) float64, 16-byte aligned.
  */
 fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs);
 
@@ -161,9 +165,9 @@ fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs);
  * memory budget or an external arena, and time-stepping loops that must not
  * stall on the allocator every step.
  *
- * The intermediate charges (nrhs x M doubles, which fs_set_magnetization keeps in
- * memory it allocates on first use) live instead in one static device array of
- * 2^19 doubles (4 MiB) inside the library.  Every GPU that loads the library
+ * It passes through intermediate charges in source order (nrhs x M doubles, as
+ * fs_fem_charges writes them); these live in one static device array of 2^19
+ * doubles (4 MiB) inside the library.  Every GPU that loads the library
  * holds that array until the process exits.
  *  - nrhs * M above 524288 is rejected with FS_EINVAL.
  *  - The plan's charge storage must already hold nrhs vectors, reserved by an

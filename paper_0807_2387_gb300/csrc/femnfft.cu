@@ -595,9 +595,9 @@ void plan_destroy(fs_plan *pl)
 
 namespace {
 
-template <typename real> fs_status set_charges_t(fs_plan *pl, const void *q, fs_dtype dtype, int nrhs)
+// Sorted-charge storage for nrhs vectors (kept when large enough).
+template <typename real> fs_status reserve_charges(fs_plan *pl, int nrhs)
 {
-    cudaStream_t st = pl->stream;
     if (nrhs > pl->nrhs_cap) {
         pl->release(pl->q_sorted);
         pl->release(pl->q_sum);
@@ -607,6 +607,13 @@ template <typename real> fs_status set_charges_t(fs_plan *pl, const void *q, fs_
         FS_TRY(pl->alloc(&pl->q_sum, nrhs));
         pl->nrhs_cap = nrhs;
     }
+    return FS_OK;
+}
+
+template <typename real> fs_status set_charges_t(fs_plan *pl, const void *q, fs_dtype dtype, int nrhs)
+{
+    cudaStream_t st = pl->stream;
+    FS_TRY(reserve_charges<real>(pl, nrhs));
     pl->nrhs = nrhs;
     if (pl->events)
         FS_CUDA(cudaEventRecord(pl->ev_q0, st));
@@ -949,14 +956,29 @@ fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs)
         return fail(FS_EINVAL, "not a FEM plan");
     if (!mag || nrhs < 1 || nrhs > 65535)
         return fail(FS_EINVAL, "bad magnetisation arguments");
-    if ((int64_t)nrhs * plan->M > plan->q_canon_cap) {
-        plan->release(plan->q_canon);
-        plan->q_canon = nullptr;
-        FS_TRY(plan->alloc(&plan->q_canon, (size_t)nrhs * plan->M));
-        plan->q_canon_cap = (int64_t)nrhs * plan->M;
-    }
-    FS_TRY(fs_fem_charges(plan, mag, plan->q_canon, nrhs));
-    return fs_set_charges(plan, plan->q_canon, FS_F64, nrhs);
+    if ((reinterpret_cast<uintptr_t>(mag) & 15u) != 0)
+        return fail(FS_EINVAL, "magnetisation must be 16-byte aligned (read as (Mx, My) pairs)");
+    // assembly fused with the gather: the charges go straight into cell order
+    cudaStream_t st = plan->stream;
+    if (plan->precision == 64)
+        FS_TRY(reserve_charges<double>(plan, nrhs));
+    else
+        FS_TRY(reserve_charges<float>(plan, nrhs));
+    plan->nrhs = nrhs;
+    if (plan->events)
+        FS_CUDA(cudaEventRecord(plan->ev_q0, st));
+    FS_CUDA(cudaMemsetAsync(plan->q_sum, 0, sizeof(double) * nrhs, st));
+    if (plan->precision == 64)
+        FS_CUDA(launch_fem_charges_sorted<double>(plan->nodes, plan->tris, plan->Nt, plan->bedges, (const double2 *)mag,
+                                                  plan->Nv, nrhs, plan->src_perm, plan->M, (double *)plan->q_sorted,
+                                                  plan->q_sum, st));
+    else
+        FS_CUDA(launch_fem_charges_sorted<float>(plan->nodes, plan->tris, plan->Nt, plan->bedges, (const double2 *)mag,
+                                                 plan->Nv, nrhs, plan->src_perm, plan->M, (float *)plan->q_sorted,
+                                                 plan->q_sum, st));
+    if (plan->events)
+        FS_CUDA(cudaEventRecord(plan->ev_q1, st));
+    return FS_OK;
 }
 
 fs_status fs_fem_sources(fs_plan *plan, double *src_out)

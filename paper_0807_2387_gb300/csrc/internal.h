@@ -228,5 +228,10 @@ cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt
 cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
                                int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, double *q,
                                int64_t M, cudaStream_t st);
+// charges of perm's sources in cell order (q_sorted, stride M per rhs) and their sums (q_sum, zeroed)
+template <typename real>
+cudaError_t launch_fem_charges_sorted(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
+                                      const double2 *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
+                                      real *q_sorted, double *q_sum, cudaStream_t st);
 
 }  // namespace fs

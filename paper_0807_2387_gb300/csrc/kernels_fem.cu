@@ -10,7 +10,9 @@
 // q = (M(t) . n_e) |e| / 2, n_e the outward unit normal (pointing away from
 // `third`) and M(t) = (1-t) M_lo + t M_hi.
 //
-// Source order: 3 per triangle (triangle-major), then 2 per boundary edge.
+// Source order: 3 per triangle (triangle-major), then 2 per boundary edge.  For a time loop
+// (one plan, many M(t)) the assembly is fused with the gather into cell order
+// (k_fem_charges_sorted), so a magnetisation becomes sorted charges in one pass.
 #include "internal.h"
 
 namespace fs {
@@ -39,6 +41,38 @@ __global__ void k_fem_sources(const double2 *__restrict__ nodes, const int *__re
     }
 }
 
+// Charge of one triangle point: rho_T |T| / 3 (the same for its three points).
+__device__ __forceinline__ double triangle_charge(const double2 *__restrict__ nodes, const int *__restrict__ tris,
+                                                  int64_t t, const double2 *__restrict__ mg)
+{
+    const int ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
+    const double2 pa = nodes[ia], pb = nodes[ib], pc = nodes[ic];
+    const double two_a = (pb.x - pa.x) * (pc.y - pa.y) - (pb.y - pa.y) * (pc.x - pa.x);
+    const double2 ma = mg[ia], mb = mg[ib], mc = mg[ic];
+    // sum_k M_k . (rotated opposite edge), divided by 2A
+    const double div = (ma.x * (pb.y - pc.y) + ma.y * (pc.x - pb.x) + mb.x * (pc.y - pa.y) + mb.y * (pa.x - pc.x) +
+                        mc.x * (pa.y - pb.y) + mc.y * (pb.x - pa.x)) / two_a;
+    return -div * fabs(two_a) / 6.0;
+}
+
+// Charge of Gauss point g (0: t = 1/2 - 1/(2 sqrt 3), 1: t = 1/2 + 1/(2 sqrt 3)) of boundary edge e.
+__device__ __forceinline__ double edge_charge(const double2 *__restrict__ nodes, const int *__restrict__ bedges,
+                                              int64_t e, int g, const double2 *__restrict__ mg)
+{
+    const int i0 = bedges[3 * e], i1 = bedges[3 * e + 1], i3 = bedges[3 * e + 2];
+    const double2 p0 = nodes[i0], p1 = nodes[i1], p3 = nodes[i3];
+    const double tx = p1.x - p0.x, ty = p1.y - p0.y;
+    const double len = sqrt(tx * tx + ty * ty);
+    double nx = ty / len, ny = -tx / len;
+    if (nx * (p3.x - p0.x) + ny * (p3.y - p0.y) > 0.0) {
+        nx = -nx;
+        ny = -ny;
+    }
+    const double2 m0 = mg[i0], m1 = mg[i1];
+    const double t = g == 0 ? kGaussLo : kGaussHi;
+    return (((1.0 - t) * m0.x + t * m1.x) * nx + ((1.0 - t) * m0.y + t * m1.y) * ny) * len * 0.5;
+}
+
 __global__ void k_fem_charges(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
                               const int *__restrict__ bedges, int64_t Ne, const double2 *__restrict__ mag, int64_t Nv,
                               double *__restrict__ q, int64_t M)
@@ -48,33 +82,49 @@ __global__ void k_fem_charges(const double2 *__restrict__ nodes, const int *__re
     const double2 *mg = mag + (int64_t)r * Nv;
     double *qr = q + (int64_t)r * M;
     if (i < Nt) {
-        const int ia = tris[3 * i], ib = tris[3 * i + 1], ic = tris[3 * i + 2];
-        const double2 pa = nodes[ia], pb = nodes[ib], pc = nodes[ic];
-        const double two_a = (pb.x - pa.x) * (pc.y - pa.y) - (pb.y - pa.y) * (pc.x - pa.x);
-        const double2 ma = mg[ia], mb = mg[ib], mc = mg[ic];
-        // sum_k M_k . (rotated opposite edge), divided by 2A
-        const double div = (ma.x * (pb.y - pc.y) + ma.y * (pc.x - pb.x) + mb.x * (pc.y - pa.y) + mb.y * (pa.x - pc.x) +
-                            mc.x * (pa.y - pb.y) + mc.y * (pb.x - pa.x)) / two_a;
-        const double qt = -div * fabs(two_a) / 6.0;
+        const double qt = triangle_charge(nodes, tris, i, mg);
         qr[3 * i] = qt;
         qr[3 * i + 1] = qt;
         qr[3 * i + 2] = qt;
     } else if (i < Nt + Ne) {
         const int64_t e = i - Nt;
-        const int i0 = bedges[3 * e], i1 = bedges[3 * e + 1], i3 = bedges[3 * e + 2];
-        const double2 p0 = nodes[i0], p1 = nodes[i1], p3 = nodes[i3];
-        const double tx = p1.x - p0.x, ty = p1.y - p0.y;
-        const double len = sqrt(tx * tx + ty * ty);
-        double nx = ty / len, ny = -tx / len;
-        if (nx * (p3.x - p0.x) + ny * (p3.y - p0.y) > 0.0) {
-            nx = -nx;
-            ny = -ny;
-        }
-        const double2 m0 = mg[i0], m1 = mg[i1];
         const int64_t o = 3 * Nt + 2 * e;
-        const double tl = kGaussLo, th = kGaussHi;
-        qr[o] = (((1.0 - tl) * m0.x + tl * m1.x) * nx + ((1.0 - tl) * m0.y + tl * m1.y) * ny) * len * 0.5;
-        qr[o + 1] = (((1.0 - th) * m0.x + th * m1.x) * nx + ((1.0 - th) * m0.y + th * m1.y) * ny) * len * 0.5;
+        qr[o] = edge_charge(nodes, bedges, e, 0, mg);
+        qr[o + 1] = edge_charge(nodes, bedges, e, 1, mg);
+    }
+}
+
+// Charges straight into cell order (the assembly fused with the gather of fs_set_charges):
+// sorted source k is canonical source perm[k], whose charge is computed from the nodal M in
+// FP64 and stored in the plan's precision; the block sums go to q_sum.
+template <typename real>
+__global__ void k_fem_charges_sorted(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
+                                     const int *__restrict__ bedges, const double2 *__restrict__ mag, int64_t Nv,
+                                     const int *__restrict__ perm, int64_t M, real *__restrict__ q_sorted,
+                                     double *__restrict__ q_sum)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    const double2 *mg = mag + (int64_t)r * Nv;
+    double v = 0.0;
+    if (k < M) {
+        const int64_t i = perm[k];
+        v = i < 3 * Nt ? triangle_charge(nodes, tris, i / 3, mg)
+                       : edge_charge(nodes, bedges, (i - 3 * Nt) / 2, (int)((i - 3 * Nt) % 2), mg);
+        q_sorted[(int64_t)r * M + k] = (real)v;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0)
+            atomicAdd(&q_sum[r], v);
     }
 }
 
@@ -100,5 +150,24 @@ cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt
     k_fem_charges<<<grid, 256, 0, st>>>(nodes, tris, Nt, bedges, Ne, mag, Nv, q, M);
     return cudaGetLastError();
 }
+
+template <typename real>
+cudaError_t launch_fem_charges_sorted(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
+                                      const double2 *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
+                                      real *q_sorted, double *q_sum, cudaStream_t st)
+{
+    if (M <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)((M + 255) / 256), nrhs);
+    k_fem_charges_sorted<real><<<grid, 256, 0, st>>>(nodes, tris, Nt, bedges, mag, Nv, perm, M, q_sorted, q_sum);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fem_charges_sorted<float>(const double2 *, const int *, int64_t, const int *,
+                                                      const double2 *, int64_t, int, const int *, int64_t, float *,
+                                                      double *, cudaStream_t);
+template cudaError_t launch_fem_charges_sorted<double>(const double2 *, const int *, int64_t, const int *,
+                                                       const double2 *, int64_t, int, const int *, int64_t, double *,
+                                                       double *, cudaStream_t);
 
 }  // namespace fs

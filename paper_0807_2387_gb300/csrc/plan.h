@@ -90,8 +90,6 @@ struct fs_plan {
     const double2 *nodes = nullptr;   // caller's (valid while the plan is used)
     int *tris = nullptr, *bedges = nullptr;
     double2 *fem_src = nullptr;
-    double *q_canon = nullptr;
-    int64_t q_canon_cap = 0;
     // host staging for fs_solve_host
     void *d_q_stage = nullptr, *d_phi_stage = nullptr, *d_H_stage = nullptr;
     size_t q_stage_bytes = 0, phi_stage_bytes = 0, H_stage_bytes = 0;
