@@ -21,6 +21,9 @@ computation of magnetostatic fields by Non-uniform Fast Fourier Transforms"):
   correction and the rescale to physical units.
 * ``fem``     P1 charge assembly of Eq. (2): rho = -div M at triangle
   quadrature points and sigma = M.n at boundary-edge Gauss points.
+* ``fastsum3`` the paper's stated next step, the 3D kernel G = 1/(4 pi r):
+  O1 direct sum, O2 and O3 fast sums and the near field with the same
+  regularisation and window steps in three dimensions.
 
 Readings of points the paper leaves open are listed in the repository's
 design notes; each function's docstring states the one it uses.
