@@ -342,6 +342,48 @@ fs_status fs_batch_destroy(fs_batch *batch);
  */
 fs_status fs_wait_selftest(int spins);
 
+/*
+ * The 3D kernel G(r) = 1/(4 pi r): the paper names it (with tetrahedral P1 elements) as
+ * the next step, with the same pipeline in three dimensions.  A 3D plan evaluates
+ *
+ *     phi(x_i) = sum_{j : y_j != x_i} q_j / (4 pi |x_i - y_j|),   H = -grad phi,
+ *
+ * for points in R^3: frequencies l in I_n^3, an oversampled n_os^3 grid (only the
+ * active window cube around the scaled points is stored), the Kaiser-Bessel window in
+ * each coordinate, 1/r smoothed inside eps_I by the even polynomial T_I and flattened
+ * near |x| = 1/2 of the torus cube, and the near-field correction for pairs closer than
+ * eps_I (cells at least eps_I wide, the 27 around a target's).  The points are scaled by
+ * s = (1/4 - eps_B/2) / R_max; results are returned in physical units (phi = s phi~,
+ * H = -s^2 grad~ phi~).  Conventions as for the 2D plan; points are (x, y, z) triples.
+ */
+typedef struct fs3_plan fs3_plan;
+
+/*
+ *  src_xyz [device] (M, 3) float64;  tgt_xyz [device] (N, 3) float64 (may equal src_xyz)
+ *  n_grid  power of two in [4, 256];  sigma_os: n_os = sigma_os * n_grid a power of two in
+ *          (n_grid, 512];  m_window in [2, 5], below n_os / 4;  eps_I in (0, 1/4) torus units
+ *  opts    precision (32 | 64), p, eps_B, stream as for fs_plan_create; other fields ignored
+ * Returns FS_EINVAL, FS_EDOMAIN (a point beyond the admissible radius), FS_ENOMEM,
+ * FS_ECUDA.  Synchronising.
+ */
+fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xyz, int64_t N, int n_grid,
+                          double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out);
+
+/* nrhs charge vectors q [device] (nrhs, M) of dtype FS_F32 or FS_F64 (copied). */
+fs_status fs3_set_charges(fs3_plan *plan, const void *q, fs_dtype dtype, int nrhs);
+
+/* phi [device] (nrhs, N) or NULL;  H [device] (nrhs, N, 3) or NULL (not both);  FS_F32|FS_F64. */
+fs_status fs3_eval_field(fs3_plan *plan, void *phi, void *H, fs_dtype dtype);
+
+/* Wait for the plan's stream. */
+fs_status fs3_sync_status(fs3_plan *plan);
+
+/* The plan's facts (fields of the 2D plan that have no 3D meaning are zero). */
+fs_status fs3_plan_info(const fs3_plan *plan, fs_info *info);
+
+/* Release the plan (synchronises its stream first). */
+fs_status fs3_plan_destroy(fs3_plan *plan);
+
 /* Message for the last failing call on this host thread ("" if none). */
 const char *fs_last_error(void);
 

@@ -11,10 +11,12 @@ The functions ``fs_plan_create``, ``fs_plan_create_fem``, ``fs_set_charges``,
 ``fs_eval_potential``, ``fs_eval_field``, ``fs_solve_host``, ``fs_sync_status``,
 ``fs_plan_info``, ``fs_stage_times``, ``fs_plan_destroy``, ``fs_adjoint`` and the
 batch calls ``fs_batch_create``, ``fs_batch_eval``, ``fs_batch_sync_status``,
-``fs_batch_info``, ``fs_batch_plan``, ``fs_batch_destroy`` and
-``fs_wait_selftest`` mirror the C entry points one to one, taking torch tensors
-(or numpy arrays for host buffers).  ``FastSum`` wraps a plan and
-``FastSumBatch`` a batch with tensor-returning methods.
+``fs_batch_info``, ``fs_batch_plan``, ``fs_batch_destroy``,
+``fs_wait_selftest`` and the 3D calls ``fs3_plan_create``, ``fs3_set_charges``,
+``fs3_eval_field``, ``fs3_sync_status``, ``fs3_plan_info`` and
+``fs3_plan_destroy`` mirror the C entry points one to one, taking torch tensors
+(or numpy arrays for host buffers).  ``FastSum`` wraps a plan, ``FastSumBatch``
+a batch and ``FastSum3`` a 3D plan with tensor-returning methods.
 """
 
 from __future__ import annotations
@@ -30,7 +32,8 @@ __all__ = [
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path", "FastSumFn",
     "FS_FLAG_AUTOTUNE", "FastSumBatch", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status",
-    "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest",
+    "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest", "FastSum3", "fs3_plan_create",
+    "fs3_set_charges", "fs3_eval_field", "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
 ]
 
 
@@ -273,6 +276,43 @@ def fs_wait_selftest(spins):
     return int(load().fs_wait_selftest(int(spins)))
 
 
+def fs3_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts):
+    """src (M,3), tgt (N,3) float64 CUDA tensors -> 3D plan handle (kernel 1/(4 pi r))."""
+    torch = _torch()
+    handle = ctypes.c_void_p()
+    o = _opts(**opts)
+    check(load().fs3_plan_create(_dev_ptr(src, torch.float64, "src"), int(src.shape[0]),
+                                 _dev_ptr(tgt, torch.float64, "tgt"), int(tgt.shape[0]), int(n_grid), float(sigma_os),
+                                 int(m_window), float(eps_I), ctypes.byref(o), ctypes.byref(handle)), "fs3_plan_create")
+    return handle
+
+
+def fs3_set_charges(plan, q, nrhs=None):
+    nrhs = nrhs or (1 if q.dim() == 1 else int(q.shape[0]))
+    check(load().fs3_set_charges(plan, _dev_ptr(q, name="q"), _dtype_code(q.dtype), int(nrhs)), "fs3_set_charges")
+
+
+def fs3_eval_field(plan, phi, H):
+    ref = H if H is not None else phi
+    check(load().fs3_eval_field(plan, _dev_ptr(phi, name="phi"), _dev_ptr(H, name="H"), _dtype_code(ref.dtype)),
+          "fs3_eval_field")
+
+
+def fs3_sync_status(plan):
+    check(load().fs3_sync_status(plan), "fs3_sync_status")
+
+
+def fs3_plan_info(plan) -> dict:
+    info = FsInfo()
+    check(load().fs3_plan_info(plan, ctypes.byref(info)), "fs3_plan_info")
+    return info.as_dict()
+
+
+def fs3_plan_destroy(plan):
+    if plan:
+        check(load().fs3_plan_destroy(plan), "fs3_plan_destroy")
+
+
 STAGES = ("charges", "spread", "fft_rows_fwd", "fft_cols_mul", "fft_rows_inv", "interp", "near", "unpermute")
 
 
@@ -430,6 +470,50 @@ class FastSumBatch:
     def close(self):
         if getattr(self, "_h", None):
             fs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FastSum3:
+    """A 3D plan: phi(x_i) = sum_j q_j / (4 pi |x_i - y_j|), H = -grad phi.
+
+    ``FastSum3(src, tgt, n, sigma, m, eps_I, precision=32)`` with float64 CUDA tensors
+    of shape (M, 3) and (N, 3).
+    """
+
+    def __init__(self, src, tgt, n_grid, sigma_os=2.0, m_window=4, eps_I=None, **opts):
+        self._h = fs3_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
+        self.device = src.device
+        self.info = fs3_plan_info(self._h)
+        self.nrhs = 0
+
+    def set_charges(self, q):
+        self.nrhs = 1 if q.dim() == 1 else int(q.shape[0])
+        fs3_set_charges(self._h, q.contiguous(), self.nrhs)
+        return self
+
+    def field(self, dtype=None, with_phi=True):
+        torch = _torch()
+        dtype = dtype or (torch.float64 if self.info["precision"] == 64 else torch.float32)
+        n = self.info["n_tgt"]
+        phi = torch.empty((self.nrhs, n), dtype=dtype, device=self.device) if with_phi else None
+        H = torch.empty((self.nrhs, n, 3), dtype=dtype, device=self.device)
+        fs3_eval_field(self._h, phi, H)
+        if self.nrhs == 1:
+            return (phi[0] if with_phi else None), H[0]
+        return phi, H
+
+    def sync(self):
+        fs3_sync_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            fs3_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -19,7 +19,8 @@ EXPORTED = (
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "fs_last_error",
     "fs_version", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status", "fs_batch_info", "fs_batch_plan",
-    "fs_batch_destroy", "fs_wait_selftest",
+    "fs_batch_destroy", "fs_wait_selftest", "fs3_plan_create", "fs3_set_charges", "fs3_eval_field",
+    "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
 )
 
 
@@ -103,6 +104,12 @@ def load(path: str = LIB_PATH):
         "fs_batch_plan": [P, I32, PP],
         "fs_batch_destroy": [P],
         "fs_wait_selftest": [I32],
+        "fs3_plan_create": [P, I64, P, I64, I32, D, I32, D, ctypes.POINTER(FsOpts), PP],
+        "fs3_set_charges": [P, P, I32, I32],
+        "fs3_eval_field": [P, P, P, I32],
+        "fs3_sync_status": [P],
+        "fs3_plan_info": [P, ctypes.POINTER(FsInfo)],
+        "fs3_plan_destroy": [P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

@@ -37,8 +37,10 @@ namespace {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+}  // namespace
+
 // Modified Bessel function I_0 by its power series sum_k (x^2/4)^k / (k!)^2 (all terms positive).
-double bessel_i0(double x)
+double fs::bessel_i0(double x)
 {
     const double y = 0.25 * x * x;
     double term = 1.0, sum = 1.0;
@@ -50,6 +52,8 @@ double bessel_i0(double x)
     }
     return sum;
 }
+
+namespace {
 
 // Solve the p x p system that makes T_I(r) = sum_k beta_k (r/eps)^(2k) match k(r) = -(1/2pi) log r
 // and its first p-1 derivatives at r = eps (scaled variable u = r/eps; Gaussian elimination with
@@ -116,10 +120,11 @@ namespace {
 // function frac -> psi(frac + m - 1 - a) on [0, 1) is interpolated at kPolyD + 1 Chebyshev
 // points in FP64 and rewritten in monomials of t = frac - 1/2; the slope polynomial is its
 // exact derivative.
-void build_window_poly(const fs_plan *pl, WindowPoly *wp)
+}  // namespace
+
+void fs::build_window_poly(double sigma, int m, WindowPoly *wp)
 {
-    const double b = kPi * (2.0 - 1.0 / pl->sigma);
-    const int m = pl->m;
+    const double b = kPi * (2.0 - 1.0 / sigma);
     const int D = kPolyD, K = kPolyD + 1;
     auto psi = [&](double x) {
         const double t = (double)m * m - x * x;
@@ -166,6 +171,8 @@ void build_window_poly(const fs_plan *pl, WindowPoly *wp)
     }
     (void)D;
 }
+
+namespace {
 
 // Bin one point set: keys, counting sort, per-point records.
 template <typename real>
@@ -473,7 +480,7 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         pl->kp.k_half = std::log(2.0) * inv2pi;
     }
 
-    build_window_poly(pl, &pl->wpoly);
+    build_window_poly(pl->sigma, pl->m, &pl->wpoly);
 
     // binning
     FS_TRY(bin_points<real>(pl, src, M, &pl->src_perm, &pl->src_base, &pl->src_frac, &pl->src_pos, &pl->src_pos32,

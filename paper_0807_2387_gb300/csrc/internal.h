@@ -24,6 +24,7 @@ struct KernelParams {
     double eps_I;
     double eps_B;
     int p;
+    int dim;               // 3: k(r) = 1/(4 pi r); otherwise k(r) = -(1/2 pi) log r
     double beta[kMaxP];    // T_I(r) = sum_k beta_k (r/eps_I)^(2k)
     double tb_f0[kMaxP];   // eps_B^j k^(j)(1/2 - eps_B) / j!   (two-point Taylor data at the left end)
     double tb_binom[kMaxP];// C(p-1+i, i)
@@ -43,6 +44,49 @@ template <typename real> struct NearParams {
     real rcoef;            // (-1)^p / (2 pi eps_I^2): (k' - T_I')(r)/r = rcoef (w - 1)^(p-1) / w
     int p;
 };
+
+// ---- 3D kernel 1/(4 pi r) (kernels3d.cu; transform and coefficients in kernels_fft.cu)
+
+// Near-field cells of the 3D path: n_c^3 cubes of `cell` grid lines, key (c1 n_c + c2) n_c + c3.
+struct CellGrid3 {
+    int cell;
+    int n_c;
+    __host__ __device__ int key(int c1, int c2, int c3) const { return (c1 * n_c + c2) * n_c + c3; }
+    __host__ __device__ int n_keys() const { return n_c * n_c * n_c; }
+};
+
+cudaError_t launch_rmax3(const double *xyz, int64_t n, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_point_keys3(const double *xyz, int64_t n, double s, int n_os, int window_lo, int n_a, int m,
+                               CellGrid3 cg, int *key, int *count, int *status, cudaStream_t st);
+// pos: torus coordinates (n x 3, FP64); frac (n x 3); base: window grid lines packed 10 bits each;
+// pos32 (FP32 path, else null): offsets from the point's cell corner
+template <typename real>
+cudaError_t launch_gather_points3(const double *xyz, const int *perm, int64_t n, double s, int n_os, int window_lo,
+                                  int n_a, int m, int cell, double *pos, real *frac, int *base, float4 *pos32,
+                                  int *status, cudaStream_t st);
+template <typename real>
+cudaError_t launch_spread3(int64_t M, int m, const int *base, const real *frac, const real *q, Window<real> w,
+                           const WindowPoly &wp, real *grid, int n_a, cudaStream_t st);
+template <typename real>
+cudaError_t launch_interp3(int64_t N, int m, const int *base, const real *frac, Window<real> w, const WindowPoly &wp,
+                           const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, cudaStream_t st);
+template <typename real>
+cudaError_t launch_near3(int64_t N, const int *tgt_base, const double *tgt_pos, const float4 *tgt_p32,
+                         const double *src_pos, const float4 *src_p32, const int *src_start, CellGrid3 cg,
+                         const real *q, NearParams<real> np, real *phi_s, real *grad_s, cudaStream_t st);
+template <typename real>
+cudaError_t launch_unpermute3(int64_t N, const real *phi_s, const real *grad_s, const int *perm, double s,
+                              void *phi_out, void *H_out, int out_f64, cudaStream_t st);
+// five-pass transform with the multiply on the n_a^3 window (spec1: n_a x (n/2+1) x n_a,
+// spec2: n_a x (n/2+1) x (n+1) complex)
+template <typename real>
+cudaError_t launch_fft3(real *grid, int n_a, int L, int n, typename Cplx<real>::type *spec1,
+                        typename Cplx<real>::type *spec2, const real *mul3, const typename Cplx<real>::type *tw,
+                        cudaStream_t st);
+// FP64 samples of K_R on the n^3 frequency grid, their 3D FFT (samp, tmp: n^3 each) and the
+// multiplier (n/2+1) x (n+1) x (n+1) in the plan's precision
+cudaError_t launch_coeffs3(double2 *samp, double2 *tmp, int n, KernelParams kp, const double2 *tw64,
+                           const double *c_tab, void *mul3, int real_is_f64, cudaStream_t st);
 
 // ---- batched solves: one launch per stage over all instances and right-hand sides
 

@@ -315,6 +315,167 @@ __global__ void k_wait_selftest(const int *counter, int *err, int spins)
     block_wait_geq(counter, 1, err, spins);
 }
 
+__device__ double kr_sample(double r, const KernelParams &kp);
+
+// ---- 3D transform on the active window cube g[z][y][x] (x fastest, edge n_a), the five
+// passes of the 2D transform with a third axis:
+//   A  x rows -> half spectra, per z plane (rows_fwd_unit): spec1[z][l1][y], l1 in [0, n/2]
+//   B  y lines forward, keeping l2 in [-n/2, n/2]:         spec2[z][l1][l2 + n/2]
+//   C  z lines: forward FFT, multiply by mul3[l1][l2][l3], inverse FFT, window rows kept
+//   D  y lines inverse (bins l2 in [-n/2, n/2]) ->          spec1[z][l1][y]
+//   E  Hermitian-extended inverse of x rows per plane (rows_inv_unit)
+// The multiplier carries the weights that make the real part of the sum over I_n^3 exact.
+
+template <typename real>
+__global__ void k_fft3_x_fwd(const real *__restrict__ grid, int n_a, int L, int n_half, cplx<real> *__restrict__ spec1,
+                             const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    const int64_t z = blockIdx.y;
+    rows_fwd_unit<real>(blockIdx.x, grid + z * n_a * n_a, n_a, n_a, L, n_half,
+                        spec1 + z * (int64_t)(n_half + 1) * n_a, n_a, tw, a, a + L);
+}
+
+template <typename real>
+__global__ void k_fft3_y_fwd(const cplx<real> *__restrict__ spec1, int n_a, int L, int n,
+                             cplx<real> *__restrict__ spec2, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    const int h = n / 2;
+    const int64_t line = (int64_t)blockIdx.y * (h + 1) + blockIdx.x;   // (z, l1)
+    const cplx<real> *in = spec1 + line * n_a;
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        cplx<real> v;
+        v.x = v.y = real(0);
+        if (r < n_a)
+            v = in[r];
+        a[r] = v;
+    }
+    __syncthreads();
+    const cplx<real> *F = fft_line<real, false>(a, a + L, L, tw);
+    cplx<real> *out = spec2 + line * (n + 1);
+    for (int k = threadIdx.x; k <= n; k += blockDim.x)
+        out[k] = F[(k - h + L) & (L - 1)];
+}
+
+template <typename real>
+__global__ void k_fft3_z(cplx<real> *__restrict__ spec2, int n_a, int L, int n, const real *__restrict__ mul3,
+                         const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    cplx<real> *b = a + L;
+    const int h = n / 2;
+    const int k2 = blockIdx.x, l1 = blockIdx.y;
+    const int64_t stride = (int64_t)(h + 1) * (n + 1);
+    cplx<real> *col = spec2 + (int64_t)l1 * (n + 1) + k2;
+    for (int z = threadIdx.x; z < L; z += blockDim.x) {
+        cplx<real> v;
+        v.x = v.y = real(0);
+        if (z < n_a)
+            v = col[z * stride];
+        a[z] = v;
+    }
+    __syncthreads();
+    cplx<real> *F = fft_line<real, false>(a, b, L, tw);
+    cplx<real> *other = (F == a) ? b : a;
+    const real *mrow = mul3 + ((int64_t)l1 * (n + 1) + k2) * (n + 1);
+    for (int k3 = threadIdx.x; k3 < L; k3 += blockDim.x) {
+        const int l3 = k3 < L / 2 ? k3 : k3 - L;
+        cplx<real> v = F[k3];
+        const real f = (l3 >= -h && l3 <= h) ? mrow[l3 + h] : real(0);
+        v.x *= f;
+        v.y *= f;
+        F[k3] = v;
+    }
+    __syncthreads();
+    const cplx<real> *G = fft_line<real, true>(F, other, L, tw);
+    for (int z = threadIdx.x; z < n_a; z += blockDim.x)
+        col[z * stride] = G[z];
+}
+
+template <typename real>
+__global__ void k_fft3_y_inv(const cplx<real> *__restrict__ spec2, int n_a, int L, int n,
+                             cplx<real> *__restrict__ spec1, const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    const int h = n / 2;
+    const int64_t line = (int64_t)blockIdx.y * (h + 1) + blockIdx.x;   // (z, l1)
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        cplx<real> v;
+        v.x = v.y = real(0);
+        a[r] = v;
+    }
+    __syncthreads();
+    const cplx<real> *in = spec2 + line * (n + 1);
+    for (int k = threadIdx.x; k <= n; k += blockDim.x)
+        a[(k - h + L) & (L - 1)] = in[k];
+    __syncthreads();
+    const cplx<real> *G = fft_line<real, true>(a, a + L, L, tw);
+    cplx<real> *out = spec1 + line * n_a;
+    for (int y = threadIdx.x; y < n_a; y += blockDim.x)
+        out[y] = G[y];
+}
+
+template <typename real>
+__global__ void k_fft3_x_inv(const cplx<real> *__restrict__ spec1, int n_a, int L, int n_half, real *__restrict__ grid,
+                             const cplx<real> *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
+    const int64_t z = blockIdx.y;
+    rows_inv_unit<real, false>(blockIdx.x, spec1 + z * (int64_t)(n_half + 1) * n_a, n_a, n_a, L, n_half,
+                               grid + z * n_a * n_a, n_a, tw, a, a + L);
+}
+
+// out[(i3 n + i1) n + i2] = in[(i1 n + i2) n + i3]: the middle axis becomes the fastest.
+__global__ void k_rotate3_c64(const double2 *__restrict__ in, double2 *__restrict__ out, int n)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)n * n * n;
+    if (t >= total)
+        return;
+    const int i3 = (int)(t % n), i2 = (int)((t / n) % n), i1 = (int)(t / ((int64_t)n * n));
+    out[((int64_t)i3 * n + i1) * n + i2] = in[t];
+}
+
+__global__ void k_kernel_samples3(double2 *__restrict__ samp, int n, KernelParams kp)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n * n)
+        return;
+    const int j3 = (int)(t % n), j2 = (int)((t / n) % n), j1 = (int)(t / ((int64_t)n * n));
+    const double x1 = (double)(j1 < n / 2 ? j1 : j1 - n) / n;
+    const double x2 = (double)(j2 < n / 2 ? j2 : j2 - n) / n;
+    const double x3 = (double)(j3 < n / 2 ? j3 : j3 - n) / n;
+    samp[t] = make_double2(kr_sample(sqrt(x1 * x1 + x2 * x2 + x3 * x3), kp), 0.0);
+}
+
+// mul3[l1][l2 + n/2][l3 + n/2] = V(l) b_l / (c(l1) c(l2) c(l3))^2 with V(l) = ([l in I_n^3] + [-l in I_n^3]) / 2.
+template <typename real>
+__global__ void k_build_mul3(const double2 *__restrict__ bhat, int n, const double *__restrict__ c_tab,
+                             real *__restrict__ mul3)
+{
+    const int h = n / 2;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)(h + 1) * (n + 1) * (n + 1);
+    if (t >= total)
+        return;
+    const int k3 = (int)(t % (n + 1)), k2 = (int)((t / (n + 1)) % (n + 1)), l1 = (int)(t / ((int64_t)(n + 1) * (n + 1)));
+    const int l2 = k2 - h, l3 = k3 - h;
+    auto in_I = [h](int l) { return l >= -h && l <= h - 1; };
+    auto in_negI = [h](int l) { return l >= -h + 1 && l <= h; };
+    const double v = 0.5 * ((in_I(l1) && in_I(l2) && in_I(l3) ? 1.0 : 0.0) +
+                            (in_negI(l1) && in_negI(l2) && in_negI(l3) ? 1.0 : 0.0));
+    const int m1 = l1 % n, m2 = ((l2 % n) + n) % n, m3 = ((l3 % n) + n) % n;
+    const double b = bhat[((int64_t)m1 * n + m2) * n + m3].x / ((double)n * n * n);
+    const double c1 = c_tab[l1], c2 = c_tab[l2 < 0 ? -l2 : l2], c3 = c_tab[l3 < 0 ? -l3 : l3];
+    mul3[t] = (real)(v * b / (c1 * c1 * c2 * c2 * c3 * c3));
+}
+
 // ---- FP64 coefficients b_l
 
 __device__ double kr_sample(double r, const KernelParams &kp)
@@ -328,7 +489,7 @@ __device__ double kr_sample(double r, const KernelParams &kp)
         return acc;
     }
     if (r <= 0.5 - kp.eps_B)
-        return -log(r) * inv2pi;
+        return kp.dim == 3 ? 1.0 / (4.0 * kPi * r) : -log(r) * inv2pi;
     if (r <= 0.5) {
         // two-point Taylor form on v in [0, 1]:
         //   sum_j f0_j v^j (1-v)^p S_{p-1-j}(v) + k(1/2) v^p S_{p-1}(1-v),  S_k(x) = sum_{i<=k} C(p-1+i,i) x^i
@@ -513,6 +674,50 @@ cudaError_t launch_wait_selftest(int *counter, int *err, int spins, cudaStream_t
     return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_fft3(real *grid, int n_a, int L, int n, cplx<real> *spec1, cplx<real> *spec2, const real *mul3,
+                        const cplx<real> *tw, cudaStream_t st)
+{
+    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    cudaError_t e;
+    if ((e = set_smem(k_fft3_x_fwd<real>, smem)) != cudaSuccess || (e = set_smem(k_fft3_y_fwd<real>, smem)) != cudaSuccess ||
+        (e = set_smem(k_fft3_z<real>, smem)) != cudaSuccess || (e = set_smem(k_fft3_y_inv<real>, smem)) != cudaSuccess ||
+        (e = set_smem(k_fft3_x_inv<real>, smem)) != cudaSuccess)
+        return e;
+    const int h = n / 2, thr = fft_threads<real>(L);
+    k_fft3_x_fwd<real><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(grid, n_a, L, h, spec1, tw);
+    k_fft3_y_fwd<real><<<dim3(h + 1, n_a), thr, smem, st>>>(spec1, n_a, L, n, spec2, tw);
+    k_fft3_z<real><<<dim3(n + 1, h + 1), thr, smem, st>>>(spec2, n_a, L, n, mul3, tw);
+    k_fft3_y_inv<real><<<dim3(h + 1, n_a), thr, smem, st>>>(spec2, n_a, L, n, spec1, tw);
+    k_fft3_x_inv<real><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(spec1, n_a, L, h, grid, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coeffs3(double2 *samp, double2 *tmp, int n, KernelParams kp, const double2 *tw64,
+                           const double *c_tab, void *mul3, int real_is_f64, cudaStream_t st)
+{
+    const int64_t total = (int64_t)n * n * n;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_kernel_samples3<<<blocks, 256, 0, st>>>(samp, n, kp);
+    cudaError_t e = launch_fft_lines_c64(samp, n * n, n, tw64, st);
+    if (e != cudaSuccess)
+        return e;
+    k_rotate3_c64<<<blocks, 256, 0, st>>>(samp, tmp, n);
+    if ((e = launch_fft_lines_c64(tmp, n * n, n, tw64, st)) != cudaSuccess)
+        return e;
+    k_rotate3_c64<<<blocks, 256, 0, st>>>(tmp, samp, n);
+    if ((e = launch_fft_lines_c64(samp, n * n, n, tw64, st)) != cudaSuccess)
+        return e;
+    const int h = n / 2;
+    const int64_t mt = (int64_t)(h + 1) * (n + 1) * (n + 1);
+    const unsigned mb = (unsigned)((mt + 255) / 256);
+    if (real_is_f64)
+        k_build_mul3<double><<<mb, 256, 0, st>>>(samp, n, c_tab, (double *)mul3);
+    else
+        k_build_mul3<float><<<mb, 256, 0, st>>>(samp, n, c_tab, (float *)mul3);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kernel_samples(double2 *samp, int n, KernelParams kp, cudaStream_t st)
 {
     dim3 grid((n + 127) / 128, n);
@@ -565,5 +770,10 @@ template cudaError_t launch_batch_fft<float>(const BatchInst<float> *, const Fft
                                              int *, int, cudaStream_t);
 template cudaError_t launch_batch_fft<double>(const BatchInst<double> *, const FftUnit *, int, int, int, int, int,
                                               int *, int *, int, cudaStream_t);
+
+template cudaError_t launch_fft3<float>(float *, int, int, int, float2 *, float2 *, const float *, const float2 *,
+                                        cudaStream_t);
+template cudaError_t launch_fft3<double>(double *, int, int, int, double2 *, double2 *, const double *,
+                                         const double2 *, cudaStream_t);
 
 }  // namespace fs

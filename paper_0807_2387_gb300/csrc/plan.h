@@ -140,16 +140,22 @@ struct fs_plan {
 
 namespace fs {
 
+// Modified Bessel function I_0 (power series, FP64).
+double bessel_i0(double x);
+// Per-tap polynomial form of the normalised Kaiser-Bessel window (FP32 kernels) for
+// oversampling sigma and half-width m.
+void build_window_poly(double sigma, int m, WindowPoly *wp);
+
 // Validates the parameters and builds the plan (binning, tables, items) on its stream.
 fs_status plan_create_common(const double *src, int64_t M, const double *tgt, int64_t N, int n_grid,
                              double sigma_os, int m, double eps_I, const fs_opts *opts, fs_plan *pl);
 // Waits for the plan's stream and frees everything it owns.
 void plan_destroy(fs_plan *pl);
 
-template <typename real> inline Window<real> make_window(const fs_plan *pl)
+template <typename real> inline Window<real> make_window(double sigma, int m_window)
 {
-    const double b = kPi * (2.0 - 1.0 / pl->sigma);
-    const double m = pl->m;
+    const double b = kPi * (2.0 - 1.0 / sigma);
+    const double m = m_window;
     Window<real> w;
     w.m = (real)m;
     w.m2 = (real)(m * m);
@@ -157,6 +163,11 @@ template <typename real> inline Window<real> make_window(const fs_plan *pl)
     w.bm = (real)(b * m);
     w.S = (real)(m * b / (1.0 - std::exp(-2.0 * b * m)));
     return w;
+}
+
+template <typename real> inline Window<real> make_window(const fs_plan *pl)
+{
+    return make_window<real>(pl->sigma, pl->m);
 }
 
 template <typename real> inline NearParams<real> make_near(const fs_plan *pl)

@@ -97,6 +97,13 @@ def ring_mesh(rng: np.random.Generator, rings: int, jitter: float = 0.2):
     return nodes, np.ascontiguousarray(tri[keep].astype(np.int32))
 
 
+def uniform_ball(rng: np.random.Generator, count: int, radius: float = 0.25) -> np.ndarray:
+    """count points uniform in the ball |x| <= radius of R^3 (direction Gaussian, r = R u^(1/3))."""
+    v = rng.standard_normal((count, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    return v * radius * rng.random(count)[:, None] ** (1.0 / 3.0)
+
+
 def annulus_mesh(rng: np.random.Generator, rings: int, r_in: float = 0.5, r_out: float = 1.0,
                  jitter: float = 0.2):
     """P1 mesh of the annulus r_in <= r <= r_out (a cylinder with a bore), Delaunay-triangulated.
