@@ -348,6 +348,55 @@ def measure_fem_loop(pkg, dev, steps, warmup, flush):
             "interior_phi_max_err_vs_closed_form": err}
 
 
+BALL_WORKLOAD = ("uniform_ball_3d: 2^18 sources + 2^18 targets uniform in the radius-0.25 ball, charges "
+                 "N(0,1); kernel 1/(4 pi r); n=128 (oversampled 256^3), m=4, eps_I=3/128, p=3; FP32")
+
+
+def measure_3d(pkg, dev, steps, warmup, flush, count=1 << 18):
+    """3D plan (fs3_*): per step fs3_set_charges + fs3_eval_field (phi and H)."""
+    import torch
+    from paper_0807_2387_gb300 import workloads as W
+    rng = np.random.default_rng(11)
+    src = torch.tensor(W.uniform_ball(rng, count, 0.25), device=dev)
+    tgt = torch.tensor(W.uniform_ball(rng, count, 0.25), device=dev)
+    q = torch.tensor(rng.standard_normal(count), device=dev)
+    t0 = time.perf_counter()
+    fs = pkg.FastSum3(src, tgt, 128, 2.0, 4, 3 / 128, precision=32)
+    plan_s = time.perf_counter() - t0
+    phi = torch.empty(count, dtype=torch.float32, device=dev)
+    H = torch.empty((count, 3), dtype=torch.float32, device=dev)
+
+    def step():
+        pkg.fs3_set_charges(fs._h, q, 1)
+        pkg.fs3_eval_field(fs._h, phi, H)
+
+    for _ in range(warmup):
+        step()
+    fs.sync()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        z.record()
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(z))
+    fs.sync()
+    fs64 = pkg.FastSum3(src, tgt, 128, 2.0, 4, 3 / 128, precision=64)
+    fs64.set_charges(q)
+    p64, h64 = fs64.field(dtype=torch.float64)
+    fs64.sync()
+    fs64.close()
+    err = {"phi_rel_l2": float(torch.linalg.norm(phi.double() - p64) / torch.linalg.norm(p64)),
+           "H_rel_l2": float(torch.linalg.norm(H.double() - h64) / torch.linalg.norm(h64))}
+    info = fs.info
+    fs.close()
+    t = statistics.mean(ms)
+    return {"workload": BALL_WORKLOAD, "ms_per_step": round(t, 4), "value": count / (t / 1e3), "unit": "points/s",
+            "plan_s": round(plan_s, 3), "window_n": info["window_n"], "fp32_vs_fp64": err}
+
+
 def measure_cufft(dev, n_os, steps, flush):
     """cuFFT (through torch.fft) R2C + C2R of the full n_os x n_os FP32 grid, for comparison with
     the pruned hand-written transform (which reads the active window only and keeps I_n)."""
@@ -494,7 +543,7 @@ def run_ours(args):
         cpu, _ = cpu_baseline(work, args.cpu_targets)
 
     # the batched workload and the adjoint (one GPU; untimed by the headline value)
-    batch = adj = fftcmp = femloop = None
+    batch = adj = fftcmp = femloop = ball3d = None
     if world == 1 and not args.quick:
         ours = stage_ms["fft_rows_fwd"] + stage_ms["fft_cols_mul"] + stage_ms["fft_rows_inv"]
         fftcmp = {"cufft_r2c_c2r_full_grid_ms": round(measure_cufft(dev, info["n_os"], 10, flush), 4),
@@ -505,6 +554,7 @@ def run_ours(args):
         batch = measure_batch(pkg, dev, max(3, args.steps // 4), 3, flush)
         adj = measure_adjoint(pkg, dev, max(3, args.steps // 4), 3, flush)
         femloop = measure_fem_loop(pkg, dev, max(5, args.steps), 3, flush)
+        ball3d = measure_3d(pkg, dev, max(5, args.steps // 2), 3, flush)
 
     if world > 1:
         dist.barrier()
@@ -521,7 +571,8 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": KERNELS_PER_STEP * args.steps,
             "near_pairs": info["near_pairs"], "near_pairs_fp64": info["near_pairs_fp64"],
             "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src},
-            "batch_c4": batch, "adjoint_c3": adj, "fem_time_loop_c1": femloop, "fft_comparison": fftcmp,
+            "batch_c4": batch, "adjoint_c3": adj, "fem_time_loop_c1": femloop, "kernel_3d": ball3d,
+            "fft_comparison": fftcmp,
         }
         print(json.dumps(out))
     fs.close()
@@ -539,6 +590,8 @@ def run_only(args):
         out = measure_batch(pkg, dev, args.steps, args.warmup, flush, args.instances)
     elif args.only == "fem":
         out = measure_fem_loop(pkg, dev, args.steps, args.warmup, flush)
+    elif args.only == "3d":
+        out = measure_3d(pkg, dev, args.steps, args.warmup, flush)
     else:
         out = measure_adjoint(pkg, dev, args.steps, args.warmup, flush)
     print(json.dumps(out))
@@ -580,7 +633,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU baseline (profiling runs)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", choices=("batch", "adjoint", "fem"), default=None,
+    ap.add_argument("--only", choices=("batch", "adjoint", "fem", "3d"), default=None,
                     help="run only the batched or the adjoint measurement and print its JSON object")
     ap.add_argument("--instances", type=int, default=64,
                     help="instances of the batched workload with --only batch (the first K of the 64)")
