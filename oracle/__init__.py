@@ -24,6 +24,8 @@ computation of magnetostatic fields by Non-uniform Fast Fourier Transforms"):
 * ``fastsum3`` the paper's stated next step, the 3D kernel G = 1/(4 pi r):
   O1 direct sum, O2 and O3 fast sums and the near field with the same
   regularisation and window steps in three dimensions.
+* ``fem3``    the 3D charge assembly: P1 tetrahedra (rho = -div M, 4 points
+  each) and boundary triangles (sigma = M.n, 3 points each).
 
 Readings of points the paper leaves open are listed in the repository's
 design notes; each function's docstring states the one it uses.

@@ -104,6 +104,43 @@ def uniform_ball(rng: np.random.Generator, count: int, radius: float = 0.25) -> 
     return v * radius * rng.random(count)[:, None] ** (1.0 / 3.0)
 
 
+def cube_tet_mesh(rng: np.random.Generator, k: int, half: float = 1.0, jitter: float = 0.1):
+    """P1 tetrahedral mesh of the cube [-half, half]^3: k^3 sub-cubes of side h = 2 half / k, each cut
+    into the 6 tetrahedra along its main diagonal (for each ordering of the axes, the path
+    000 -> one axis -> two axes -> 111), which is conforming across sub-cubes.  Interior nodes are
+    jittered by at most ``jitter`` * h per coordinate; boundary nodes are exact, so the mesh is the
+    cube itself.
+
+    Returns (nodes (Nv,3) f64, tets (Nt,4) int32, every tetrahedron positively oriented).
+    """
+    h = 2.0 * half / k
+    g = np.arange(k + 1)
+    ii, jj, kk = np.meshgrid(g, g, g, indexing="ij")
+    idx = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
+    nodes = -half + h * idx.astype(float)
+    inner = np.all((idx > 0) & (idx < k), axis=1)
+    nodes[inner] += jitter * h * rng.uniform(-1.0, 1.0, (int(inner.sum()), 3))
+
+    def nid(a, b, c):
+        return (a * (k + 1) + b) * (k + 1) + c
+
+    c0 = np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), axis=-1).reshape(-1, 3)
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        v = [c0.copy()]
+        for ax in perm:
+            nxt = v[-1].copy()
+            nxt[:, ax] += 1
+            v.append(nxt)
+        tets.append(np.stack([nid(*w.T) for w in v], axis=1))
+    tets = np.concatenate(tets).astype(np.int64)
+    x = nodes[tets]
+    det = np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]], axis=2))
+    flip = det < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    return nodes, np.ascontiguousarray(tets.astype(np.int32))
+
+
 def annulus_mesh(rng: np.random.Generator, rings: int, r_in: float = 0.5, r_out: float = 1.0,
                  jitter: float = 0.2):
     """P1 mesh of the annulus r_in <= r <= r_out (a cylinder with a bore), Delaunay-triangulated.
