@@ -369,6 +369,40 @@ typedef struct fs3_plan fs3_plan;
 fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xyz, int64_t N, int n_grid,
                           double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out);
 
+/*
+ * Create a plan for a P1 tetrahedral mesh: the charge quadrature of Eq. (2) with d = 3
+ * (the paper's next step; the 3D rule is this library's reading).  Targets are the Nv
+ * nodes; sources are the quadrature points, in this order: 4 points per tetrahedron at
+ * barycentric (a, b, b, b) and its permutations, a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20
+ * (tetrahedron-major, the weight a on its node 0, 1, 2, 3 in turn), then 3 points per
+ * boundary face at barycentric (2/3, 1/6, 1/6) and permutations (faces used by one
+ * tetrahedron only, sorted by their ascending node triple i0 < i1 < i2, the weight 2/3 on
+ * i0, i1, i2 in turn).  Tetrahedra of either orientation are accepted.
+ *
+ *  nodes [device] (Nv, 3) float64, kept by reference: it must outlive the plan
+ *  tets  [device] (Nt, 4) int32 node indices (copied)
+ *  Other arguments as fs3_plan_create.  FS_EINVAL for an index out of range, a repeated
+ *  node, a face shared by more than two tetrahedra, or more than 2^31 - 1 sources.
+ */
+fs_status fs3_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tets, int64_t Nt, int n_grid,
+                              double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out);
+
+/*
+ * Tetrahedral plans only: charges from the nodal magnetisation, computed in FP64 straight
+ * into the plan's cell order: rho_T = -div M constant per P1 tetrahedron, q = rho_T |T| / 4
+ * per tetrahedron point; sigma = M.n_F on boundary faces (outward unit normal, M linear on
+ * the face), q = sigma |F| / 3 per face point.
+ *  mag [device] (nrhs, Nv, 3) float64.
+ */
+fs_status fs3_set_magnetization(fs3_plan *plan, const double *mag, int nrhs);
+
+/* Tetrahedral plans only: the assembly alone, in source order.
+ *  mag [device] (nrhs, Nv, 3) float64;  q_out [device] (nrhs, M) float64. */
+fs_status fs3_fem_charges(fs3_plan *plan, const double *mag, double *q_out, int nrhs);
+
+/* Tetrahedral plans only: the quadrature points [device] (M, 3) float64, in source order. */
+fs_status fs3_fem_sources(fs3_plan *plan, double *src_out);
+
 /* nrhs charge vectors q [device] (nrhs, M) of dtype FS_F32 or FS_F64 (copied). */
 fs_status fs3_set_charges(fs3_plan *plan, const void *q, fs_dtype dtype, int nrhs);
 
@@ -378,7 +412,9 @@ fs_status fs3_eval_field(fs3_plan *plan, void *phi, void *H, fs_dtype dtype);
 /* Wait for the plan's stream. */
 fs_status fs3_sync_status(fs3_plan *plan);
 
-/* The plan's facts (fields of the 2D plan that have no 3D meaning are zero). */
+/* The plan's facts (fields of the 2D plan that have no 3D meaning are zero; for a
+ * tetrahedral plan n_nodes, n_tris and n_bedges count nodes, tetrahedra and boundary
+ * faces). */
 fs_status fs3_plan_info(const fs3_plan *plan, fs_info *info);
 
 /* Release the plan (synchronises its stream first). */

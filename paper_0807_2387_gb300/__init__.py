@@ -34,6 +34,7 @@ __all__ = [
     "FS_FLAG_AUTOTUNE", "FastSumBatch", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status",
     "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest", "FastSum3", "fs3_plan_create",
     "fs3_set_charges", "fs3_eval_field", "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
+    "fs3_plan_create_fem", "fs3_set_magnetization", "fs3_fem_charges", "fs3_fem_sources",
 ]
 
 
@@ -287,6 +288,36 @@ def fs3_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts):
     return handle
 
 
+def fs3_plan_create_fem(nodes, tets, n_grid, sigma_os, m_window, eps_I, **opts):
+    """nodes (Nv,3) float64, tets (Nt,4) int32 CUDA tensors -> 3D plan (sources = quadrature points)."""
+    torch = _torch()
+    handle = ctypes.c_void_p()
+    o = _opts(**opts)
+    check(load().fs3_plan_create_fem(_dev_ptr(nodes, torch.float64, "nodes"), int(nodes.shape[0]),
+                                     _dev_ptr(tets, torch.int32, "tets"), int(tets.shape[0]), int(n_grid),
+                                     float(sigma_os), int(m_window), float(eps_I), ctypes.byref(o),
+                                     ctypes.byref(handle)), "fs3_plan_create_fem")
+    return handle
+
+
+def fs3_set_magnetization(plan, mag, nrhs=None):
+    torch = _torch()
+    nrhs = nrhs or (1 if mag.dim() == 2 else int(mag.shape[0]))
+    check(load().fs3_set_magnetization(plan, _dev_ptr(mag, torch.float64, "mag"), int(nrhs)), "fs3_set_magnetization")
+
+
+def fs3_fem_charges(plan, mag, q_out, nrhs=None):
+    torch = _torch()
+    nrhs = nrhs or (1 if mag.dim() == 2 else int(mag.shape[0]))
+    check(load().fs3_fem_charges(plan, _dev_ptr(mag, torch.float64, "mag"), _dev_ptr(q_out, torch.float64, "q_out"),
+                                 int(nrhs)), "fs3_fem_charges")
+
+
+def fs3_fem_sources(plan, src_out):
+    torch = _torch()
+    check(load().fs3_fem_sources(plan, _dev_ptr(src_out, torch.float64, "src_out")), "fs3_fem_sources")
+
+
 def fs3_set_charges(plan, q, nrhs=None):
     nrhs = nrhs or (1 if q.dim() == 1 else int(q.shape[0]))
     check(load().fs3_set_charges(plan, _dev_ptr(q, name="q"), _dtype_code(q.dtype), int(nrhs)), "fs3_set_charges")
@@ -483,14 +514,45 @@ class FastSum3:
     """A 3D plan: phi(x_i) = sum_j q_j / (4 pi |x_i - y_j|), H = -grad phi.
 
     ``FastSum3(src, tgt, n, sigma, m, eps_I, precision=32)`` with float64 CUDA tensors
-    of shape (M, 3) and (N, 3).
+    of shape (M, 3) and (N, 3); ``FastSum3.fem(nodes, tets, ...)`` for a P1 tetrahedral
+    mesh (targets = nodes, sources = quadrature points).
     """
 
-    def __init__(self, src, tgt, n_grid, sigma_os=2.0, m_window=4, eps_I=None, **opts):
-        self._h = fs3_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
-        self.device = src.device
+    def __init__(self, src=None, tgt=None, n_grid=None, sigma_os=2.0, m_window=4, eps_I=None, _handle=None,
+                 **opts):
+        if _handle is None:
+            self._h = fs3_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
+            self.device = src.device
+        else:
+            self._h = _handle
         self.info = fs3_plan_info(self._h)
         self.nrhs = 0
+
+    @classmethod
+    def fem(cls, nodes, tets, n_grid, sigma_os=2.0, m_window=4, eps_I=None, **opts):
+        h = fs3_plan_create_fem(nodes, tets, n_grid, sigma_os, m_window, eps_I, **opts)
+        obj = cls(_handle=h)
+        obj.device = nodes.device
+        obj._nodes = nodes            # the plan reads the caller's node array
+        return obj
+
+    def set_magnetization(self, mag):
+        self.nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+        fs3_set_magnetization(self._h, mag.contiguous(), self.nrhs)
+        return self
+
+    def fem_charges(self, mag):
+        torch = _torch()
+        nrhs = 1 if mag.dim() == 2 else int(mag.shape[0])
+        out = torch.empty((nrhs, self.info["n_src"]), dtype=torch.float64, device=self.device)
+        fs3_fem_charges(self._h, mag.contiguous(), out, nrhs)
+        return out[0] if mag.dim() == 2 else out
+
+    def sources(self):
+        torch = _torch()
+        out = torch.empty((self.info["n_src"], 3), dtype=torch.float64, device=self.device)
+        fs3_fem_sources(self._h, out)
+        return out
 
     def set_charges(self, q):
         self.nrhs = 1 if q.dim() == 1 else int(q.shape[0])

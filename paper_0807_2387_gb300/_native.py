@@ -20,7 +20,8 @@ EXPORTED = (
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "fs_last_error",
     "fs_version", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status", "fs_batch_info", "fs_batch_plan",
     "fs_batch_destroy", "fs_wait_selftest", "fs3_plan_create", "fs3_set_charges", "fs3_eval_field",
-    "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
+    "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy", "fs3_plan_create_fem", "fs3_set_magnetization",
+    "fs3_fem_charges", "fs3_fem_sources",
 )
 
 
@@ -110,6 +111,10 @@ def load(path: str = LIB_PATH):
         "fs3_sync_status": [P],
         "fs3_plan_info": [P, ctypes.POINTER(FsInfo)],
         "fs3_plan_destroy": [P],
+        "fs3_plan_create_fem": [P, I64, P, I64, I32, D, I32, D, ctypes.POINTER(FsOpts), PP],
+        "fs3_set_magnetization": [P, P, I32],
+        "fs3_fem_charges": [P, P, P, I32],
+        "fs3_fem_sources": [P, P],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

@@ -277,5 +277,14 @@ template <typename real>
 cudaError_t launch_fem_charges_sorted(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
                                       const double2 *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
                                       real *q_sorted, double *q_sum, cudaStream_t st);
+// tetrahedra: nodes (Nv, 3), tets (Nt, 4), faces (Nf, 4) = (i0 < i1 < i2, fourth node), mag (nrhs, Nv, 3)
+cudaError_t launch_fem3_sources(const double *nodes, const int *tets, int64_t Nt, const int *faces, int64_t Nf,
+                                double *src, cudaStream_t st);
+cudaError_t launch_fem3_charges(const double *nodes, const int *tets, int64_t Nt, const int *faces,
+                                const double *mag, int64_t Nv, int nrhs, double *q, int64_t M, cudaStream_t st);
+template <typename real>
+cudaError_t launch_fem3_charges_sorted(const double *nodes, const int *tets, int64_t Nt, const int *faces,
+                                       const double *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
+                                       real *q_sorted, double *q_sum, cudaStream_t st);
 
 }  // namespace fs

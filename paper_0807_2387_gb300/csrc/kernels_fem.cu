@@ -128,7 +128,188 @@ __global__ void k_fem_charges_sorted(const double2 *__restrict__ nodes, const in
     }
 }
 
+// ---------------------------------------------------------------- tetrahedra (d = 3)
+//
+// The same quadrature with d = 3.  M linear in a P1 tetrahedron (nodes x0..x3) has
+// div M = sum_{k=1..3} (M_k - M_0) . grad la_k with grad la_k the rows of J^-1,
+// J = [u v w] = [x1 - x0, x2 - x0, x3 - x0]:  J^-1 = [v x w; w x u; u x v] / det J.
+// Four points at barycentric (a, b, b, b) and permutations, a = (5 + 3 sqrt 5)/20,
+// b = (5 - sqrt 5)/20, carry q = -div M |T| / 4 each (|T| = |det J| / 6).  Each boundary
+// face (nodes i0 < i1 < i2 used by one tetrahedron; `opp` its fourth node) carries three
+// points at barycentric (2/3, 1/6, 1/6) and permutations with q = (M . n_F) |F| / 3,
+// n_F the outward unit normal (pointing away from opp).
+// Source order: 4 per tetrahedron (tetrahedron-major), then 3 per boundary face.
+
+constexpr double kTetA = 0.58541019662496845446137605030969143;   // (5 + 3 sqrt 5) / 20
+constexpr double kTetB = 0.13819660112501051517954131656343619;   // (5 - sqrt 5) / 20
+
+struct V3 {
+    double x, y, z;
+};
+
+__device__ __forceinline__ V3 ld3(const double *__restrict__ a, int64_t i)
+{
+    return V3{a[3 * i], a[3 * i + 1], a[3 * i + 2]};
+}
+__device__ __forceinline__ V3 sub3(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double dot3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross3(V3 a, V3 b)
+{
+    return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+__global__ void k_fem3_sources(const double *__restrict__ nodes, const int *__restrict__ tets, int64_t Nt,
+                               const int *__restrict__ faces, int64_t Nf, double *__restrict__ src)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < Nt) {
+        V3 p[4];
+        for (int k = 0; k < 4; ++k)
+            p[k] = ld3(nodes, tets[4 * i + k]);
+        const V3 sum{p[0].x + p[1].x + p[2].x + p[3].x, p[0].y + p[1].y + p[2].y + p[3].y,
+                     p[0].z + p[1].z + p[2].z + p[3].z};
+        for (int k = 0; k < 4; ++k) {
+            double *o = src + 3 * (4 * i + k);
+            o[0] = kTetB * sum.x + (kTetA - kTetB) * p[k].x;
+            o[1] = kTetB * sum.y + (kTetA - kTetB) * p[k].y;
+            o[2] = kTetB * sum.z + (kTetA - kTetB) * p[k].z;
+        }
+    } else if (i < Nt + Nf) {
+        const int64_t f = i - Nt;
+        V3 p[3];
+        for (int k = 0; k < 3; ++k)
+            p[k] = ld3(nodes, faces[4 * f + k]);
+        const V3 sum{p[0].x + p[1].x + p[2].x, p[0].y + p[1].y + p[2].y, p[0].z + p[1].z + p[2].z};
+        for (int k = 0; k < 3; ++k) {
+            double *o = src + 3 * (4 * Nt + 3 * f + k);
+            o[0] = sum.x / 6.0 + 0.5 * p[k].x;
+            o[1] = sum.y / 6.0 + 0.5 * p[k].y;
+            o[2] = sum.z / 6.0 + 0.5 * p[k].z;
+        }
+    }
+}
+
+// Charge of each of the four points of tetrahedron t: -div M |T| / 4.
+__device__ __forceinline__ double tet_charge(const double *__restrict__ nodes, const int *__restrict__ tets,
+                                             int64_t t, const double *__restrict__ mg)
+{
+    const int i0 = tets[4 * t], i1 = tets[4 * t + 1], i2 = tets[4 * t + 2], i3 = tets[4 * t + 3];
+    const V3 x0 = ld3(nodes, i0);
+    const V3 u = sub3(ld3(nodes, i1), x0), v = sub3(ld3(nodes, i2), x0), w = sub3(ld3(nodes, i3), x0);
+    const V3 m0 = ld3(mg, i0);
+    const V3 vw = cross3(v, w), wu = cross3(w, u), uv = cross3(u, v);
+    const double det = dot3(u, vw);
+    // div M * det = sum_k (M_k - M_0) . (row k of adj J); q = -div M |det| / 24
+    const double num = dot3(sub3(ld3(mg, i1), m0), vw) + dot3(sub3(ld3(mg, i2), m0), wu) +
+                       dot3(sub3(ld3(mg, i3), m0), uv);
+    return det > 0.0 ? -num / 24.0 : num / 24.0;
+}
+
+// Charge of point k (the 2/3 weight on node k) of boundary face f: (M . n_F) |F| / 3.
+__device__ __forceinline__ double face_charge(const double *__restrict__ nodes, const int *__restrict__ faces,
+                                              int64_t f, int k, const double *__restrict__ mg)
+{
+    const int i0 = faces[4 * f], i1 = faces[4 * f + 1], i2 = faces[4 * f + 2], io = faces[4 * f + 3];
+    const V3 p0 = ld3(nodes, i0);
+    const V3 c = cross3(sub3(ld3(nodes, i1), p0), sub3(ld3(nodes, i2), p0));   // |c| = 2 |F|
+    const double sgn = dot3(c, sub3(ld3(nodes, io), p0)) > 0.0 ? -1.0 : 1.0;   // outward
+    const int ik = k == 0 ? i0 : (k == 1 ? i1 : i2);
+    const V3 ma = ld3(mg, i0), mb = ld3(mg, i1), mc = ld3(mg, i2), mk = ld3(mg, ik);
+    const V3 mp{(ma.x + mb.x + mc.x) / 6.0 + 0.5 * mk.x, (ma.y + mb.y + mc.y) / 6.0 + 0.5 * mk.y,
+                (ma.z + mb.z + mc.z) / 6.0 + 0.5 * mk.z};
+    // (M . c/|c|) (|c|/2) / 3 = M . c / 6
+    return sgn * dot3(mp, c) / 6.0;
+}
+
+__device__ __forceinline__ double fem3_point_charge(const double *__restrict__ nodes, const int *__restrict__ tets,
+                                                    int64_t Nt, const int *__restrict__ faces, int64_t i,
+                                                    const double *__restrict__ mg)
+{
+    if (i < 4 * Nt)
+        return tet_charge(nodes, tets, i >> 2, mg);
+    const int64_t j = i - 4 * Nt;
+    return face_charge(nodes, faces, j / 3, (int)(j % 3), mg);
+}
+
+__global__ void k_fem3_charges(const double *__restrict__ nodes, const int *__restrict__ tets, int64_t Nt,
+                               const int *__restrict__ faces, const double *__restrict__ mag, int64_t Nv,
+                               double *__restrict__ q, int64_t M)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i < M)
+        q[(int64_t)r * M + i] = fem3_point_charge(nodes, tets, Nt, faces, i, mag + (int64_t)r * 3 * Nv);
+}
+
+// 3D assembly fused with the gather into cell order (as k_fem_charges_sorted).
+template <typename real>
+__global__ void k_fem3_charges_sorted(const double *__restrict__ nodes, const int *__restrict__ tets, int64_t Nt,
+                                      const int *__restrict__ faces, const double *__restrict__ mag, int64_t Nv,
+                                      const int *__restrict__ perm, int64_t M, real *__restrict__ q_sorted,
+                                      double *__restrict__ q_sum)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    double v = 0.0;
+    if (k < M) {
+        v = fem3_point_charge(nodes, tets, Nt, faces, perm[k], mag + (int64_t)r * 3 * Nv);
+        q_sorted[(int64_t)r * M + k] = (real)v;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0)
+            atomicAdd(&q_sum[r], v);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_fem3_sources(const double *nodes, const int *tets, int64_t Nt, const int *faces, int64_t Nf,
+                                double *src, cudaStream_t st)
+{
+    const int64_t n = Nt + Nf;
+    if (n <= 0)
+        return cudaSuccess;
+    k_fem3_sources<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nodes, tets, Nt, faces, Nf, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fem3_charges(const double *nodes, const int *tets, int64_t Nt, const int *faces,
+                                const double *mag, int64_t Nv, int nrhs, double *q, int64_t M, cudaStream_t st)
+{
+    if (M <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)((M + 255) / 256), nrhs);
+    k_fem3_charges<<<grid, 256, 0, st>>>(nodes, tets, Nt, faces, mag, Nv, q, M);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_fem3_charges_sorted(const double *nodes, const int *tets, int64_t Nt, const int *faces,
+                                       const double *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
+                                       real *q_sorted, double *q_sum, cudaStream_t st)
+{
+    if (M <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)((M + 255) / 256), nrhs);
+    k_fem3_charges_sorted<real><<<grid, 256, 0, st>>>(nodes, tets, Nt, faces, mag, Nv, perm, M, q_sorted, q_sum);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fem3_charges_sorted<float>(const double *, const int *, int64_t, const int *,
+                                                       const double *, int64_t, int, const int *, int64_t, float *,
+                                                       double *, cudaStream_t);
+template cudaError_t launch_fem3_charges_sorted<double>(const double *, const int *, int64_t, const int *,
+                                                        const double *, int64_t, int, const int *, int64_t,
+                                                        double *, double *, cudaStream_t);
 
 cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges, int64_t Ne,
                                double2 *src, cudaStream_t st)

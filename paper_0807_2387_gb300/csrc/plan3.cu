@@ -38,6 +38,12 @@ struct fs3_plan {
     void *q_sorted = nullptr;
     double *q_sum = nullptr;
     int nrhs = 0, nrhs_cap = 0;
+    // tetrahedral FEM plans: sources are the quadrature points, targets the nodes
+    bool is_fem = false;
+    int64_t Nv = 0, Nt = 0, Nf = 0;
+    const double *nodes = nullptr;
+    int *tets = nullptr, *faces = nullptr;
+    double *fem_src = nullptr;
 
     template <typename T> fs_status alloc(T **out, size_t count)
     {
@@ -296,17 +302,84 @@ fs_status plan3_init(fs3_plan *pl, const double *src, int64_t M, const double *t
     return FS_OK;
 }
 
-template <typename real> fs_status set_charges3_t(fs3_plan *pl, const void *q, fs_dtype dtype, int nrhs)
+// Boundary faces (used by one tetrahedron) as (i0 < i1 < i2, fourth node), sorted by the triple.
+fs_status boundary_faces3(const std::vector<int> &tets, int64_t Nt, int64_t Nv, std::vector<int> &out)
+{
+    struct F {
+        int a, b, c, opp;
+    };
+    std::vector<F> f;
+    f.reserve(4 * (size_t)Nt);
+    for (int64_t t = 0; t < Nt; ++t) {
+        const int *v = &tets[4 * t];
+        for (int k = 0; k < 4; ++k)
+            if (v[k] < 0 || v[k] >= Nv)
+                return fail(FS_EINVAL, "tetrahedron node index out of range");
+        for (int i = 0; i < 4; ++i)
+            for (int j = i + 1; j < 4; ++j)
+                if (v[i] == v[j])
+                    return fail(FS_EINVAL, "degenerate tetrahedron (repeated node)");
+        for (int skip = 0; skip < 4; ++skip) {
+            int w[3], n = 0;
+            for (int k = 0; k < 4; ++k)
+                if (k != skip)
+                    w[n++] = v[k];
+            std::sort(w, w + 3);
+            f.push_back(F{w[0], w[1], w[2], v[skip]});
+        }
+    }
+    auto key_less = [](const F &x, const F &y) {
+        return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : x.c < y.c);
+    };
+    std::sort(f.begin(), f.end(), key_less);
+    out.clear();
+    size_t i = 0;
+    while (i < f.size()) {
+        size_t j = i + 1;
+        while (j < f.size() && f[j].a == f[i].a && f[j].b == f[i].b && f[j].c == f[i].c)
+            ++j;
+        if (j - i == 1) {
+            out.push_back(f[i].a);
+            out.push_back(f[i].b);
+            out.push_back(f[i].c);
+            out.push_back(f[i].opp);
+        } else if (j - i > 2) {
+            return fail(FS_EINVAL, "non-manifold mesh: a face is shared by more than two tetrahedra");
+        }
+        i = j;
+    }
+    return FS_OK;
+}
+
+template <typename real> fs_status reserve_charges3(fs3_plan *pl, int nrhs)
 {
     if (nrhs > pl->nrhs_cap) {
         pl->release(pl->q_sorted);
         pl->release(pl->q_sum);
+        pl->q_sorted = nullptr;
+        pl->q_sum = nullptr;
         real *qs = nullptr;
         FS_TRY(pl->alloc(&qs, (size_t)std::max<int64_t>(pl->M, 1) * nrhs));
         pl->q_sorted = qs;
         FS_TRY(pl->alloc(&pl->q_sum, nrhs));
         pl->nrhs_cap = nrhs;
     }
+    return FS_OK;
+}
+
+template <typename real> fs_status set_magnetization3_t(fs3_plan *pl, const double *mag, int nrhs)
+{
+    FS_TRY(reserve_charges3<real>(pl, nrhs));
+    pl->nrhs = nrhs;
+    FS_CUDA(cudaMemsetAsync(pl->q_sum, 0, sizeof(double) * nrhs, pl->stream));
+    FS_CUDA(launch_fem3_charges_sorted<real>(pl->nodes, pl->tets, pl->Nt, pl->faces, mag, pl->Nv, nrhs, pl->src_perm,
+                                             pl->M, (real *)pl->q_sorted, pl->q_sum, pl->stream));
+    return FS_OK;
+}
+
+template <typename real> fs_status set_charges3_t(fs3_plan *pl, const void *q, fs_dtype dtype, int nrhs)
+{
+    FS_TRY(reserve_charges3<real>(pl, nrhs));
     pl->nrhs = nrhs;
     FS_CUDA(cudaMemsetAsync(pl->q_sum, 0, sizeof(double) * nrhs, pl->stream));
     FS_CUDA(launch_gather_charges<real>(q, dtype == FS_F64, pl->src_perm, pl->M, nrhs, (real *)pl->q_sorted,
@@ -353,21 +426,12 @@ void plan3_free(fs3_plan *pl)
     delete pl;
 }
 
-}  // namespace
-
-extern "C" {
-
-fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xyz, int64_t N, int n_grid,
-                          double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out)
+// Validate the grid parameters and options shared by the point and mesh entry points.
+fs_status plan3_new(int n_grid, double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out)
 {
-    if (!out)
-        return fail(FS_EINVAL, "null output pointer");
-    *out = nullptr;
     fs_opts o{};
     if (opts)
         o = *opts;
-    if (M < 0 || N < 0 || (M > 0 && !src_xyz) || (N > 0 && !tgt_xyz))
-        return fail(FS_EINVAL, "bad point arrays");
     if (!is_pow2(n_grid) || n_grid < 4 || n_grid > 256)
         return fail(FS_EINVAL, "n_grid must be a power of two in [4, 256]");
     const double nos = sigma_os * n_grid;
@@ -384,7 +448,9 @@ fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xy
         return fail(FS_EINVAL, "p must be in [1, 16] (0 = default)");
     if (o.eps_B < 0.0 || o.eps_B >= 0.25 || std::isnan(o.eps_B))
         return fail(FS_EINVAL, "eps_B must be in (0, 1/4) (0 = default)");
-    fs3_plan *pl = new fs3_plan;
+    fs3_plan *pl = new (std::nothrow) fs3_plan;
+    if (!pl)
+        return fail(FS_ENOMEM, "host allocation failed");
     pl->precision = o.precision == 64 ? 64 : 32;
     pl->n = n_grid;
     pl->n_os = n_os;
@@ -393,9 +459,27 @@ fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xy
     pl->eps_I = eps_I;
     pl->eps_B = o.eps_B > 0.0 ? o.eps_B : eps_I;
     pl->p = o.p > 0 ? o.p : std::max(2, (int)std::lround(n_grid * eps_I));
+    pl->stream = (cudaStream_t)o.stream;
+    *out = pl;
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xyz, int64_t N, int n_grid,
+                          double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out)
+{
+    if (!out)
+        return fail(FS_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (M < 0 || N < 0 || (M > 0 && !src_xyz) || (N > 0 && !tgt_xyz))
+        return fail(FS_EINVAL, "bad point arrays");
+    fs3_plan *pl = nullptr;
+    FS_TRY(plan3_new(n_grid, sigma_os, m_window, eps_I, opts, &pl));
     pl->M = M;
     pl->N = N;
-    pl->stream = (cudaStream_t)o.stream;
     const fs_status s = pl->precision == 64 ? plan3_init<double>(pl, src_xyz, M, tgt_xyz, N)
                                             : plan3_init<float>(pl, src_xyz, M, tgt_xyz, N);
     if (s != FS_OK) {
@@ -403,6 +487,91 @@ fs_status fs3_plan_create(const double *src_xyz, int64_t M, const double *tgt_xy
         return s;
     }
     *out = pl;
+    return FS_OK;
+}
+
+fs_status fs3_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tets, int64_t Nt, int n_grid,
+                              double sigma_os, int m_window, double eps_I, const fs_opts *opts, fs3_plan **out)
+{
+    if (!out)
+        return fail(FS_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (Nv <= 0 || Nt <= 0 || !nodes || !tets)
+        return fail(FS_EINVAL, "a mesh needs nodes and tetrahedra");
+    if (Nv > (int64_t)INT32_MAX || 4 * Nt + 12 * Nt > (int64_t)INT32_MAX)
+        return fail(FS_EINVAL, "mesh too large");
+    fs3_plan *pl = nullptr;
+    FS_TRY(plan3_new(n_grid, sigma_os, m_window, eps_I, opts, &pl));
+    auto body = [&]() -> fs_status {
+        cudaStream_t st = pl->stream;
+        std::vector<int> h_tets(4 * (size_t)Nt), h_faces;
+        FS_CUDA(cudaMemcpyAsync(h_tets.data(), tets, sizeof(int) * 4 * Nt, cudaMemcpyDeviceToHost, st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        FS_TRY(boundary_faces3(h_tets, Nt, Nv, h_faces));
+        pl->is_fem = true;
+        pl->Nv = Nv;
+        pl->Nt = Nt;
+        pl->Nf = (int64_t)h_faces.size() / 4;
+        pl->nodes = nodes;
+        FS_TRY(pl->alloc(&pl->tets, h_tets.size()));
+        FS_TRY(pl->alloc(&pl->faces, std::max<size_t>(h_faces.size(), 1)));
+        FS_CUDA(cudaMemcpyAsync(pl->tets, h_tets.data(), sizeof(int) * h_tets.size(), cudaMemcpyHostToDevice, st));
+        if (!h_faces.empty())
+            FS_CUDA(cudaMemcpyAsync(pl->faces, h_faces.data(), sizeof(int) * h_faces.size(), cudaMemcpyHostToDevice,
+                                    st));
+        const int64_t Ms = 4 * Nt + 3 * pl->Nf;
+        FS_TRY(pl->alloc(&pl->fem_src, 3 * (size_t)Ms));
+        FS_CUDA(launch_fem3_sources(nodes, pl->tets, Nt, pl->faces, pl->Nf, pl->fem_src, st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        pl->M = Ms;
+        pl->N = Nv;
+        return pl->precision == 64 ? plan3_init<double>(pl, pl->fem_src, Ms, nodes, Nv)
+                                   : plan3_init<float>(pl, pl->fem_src, Ms, nodes, Nv);
+    };
+    const fs_status s = body();
+    if (s != FS_OK) {
+        plan3_free(pl);
+        return s;
+    }
+    *out = pl;
+    return FS_OK;
+}
+
+fs_status fs3_set_magnetization(fs3_plan *plan, const double *mag, int nrhs)
+{
+    if (!plan)
+        return fail(FS_EINVAL, "null plan");
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!mag || nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "bad magnetisation arguments");
+    return plan->precision == 64 ? set_magnetization3_t<double>(plan, mag, nrhs)
+                                 : set_magnetization3_t<float>(plan, mag, nrhs);
+}
+
+fs_status fs3_fem_charges(fs3_plan *plan, const double *mag, double *q_out, int nrhs)
+{
+    if (!plan)
+        return fail(FS_EINVAL, "null plan");
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!mag || !q_out || nrhs < 1 || nrhs > 65535)
+        return fail(FS_EINVAL, "bad magnetisation/charge arguments");
+    FS_CUDA(launch_fem3_charges(plan->nodes, plan->tets, plan->Nt, plan->faces, mag, plan->Nv, nrhs, q_out, plan->M,
+                                plan->stream));
+    return FS_OK;
+}
+
+fs_status fs3_fem_sources(fs3_plan *plan, double *src_out)
+{
+    if (!plan)
+        return fail(FS_EINVAL, "null plan");
+    if (!plan->is_fem)
+        return fail(FS_EINVAL, "not a FEM plan");
+    if (!src_out)
+        return fail(FS_EINVAL, "null output");
+    FS_CUDA(cudaMemcpyAsync(src_out, plan->fem_src, sizeof(double) * 3 * plan->M, cudaMemcpyDeviceToDevice,
+                            plan->stream));
     return FS_OK;
 }
 
@@ -457,6 +626,10 @@ fs_status fs3_plan_info(const fs3_plan *plan, fs_info *info)
     info->cell = plan->cg.cell;
     info->cells_per_dim = plan->cg.n_c;
     info->workspace_bytes = plan->bytes;
+    info->is_fem = plan->is_fem;
+    info->n_nodes = plan->Nv;
+    info->n_tris = plan->Nt;
+    info->n_bedges = plan->Nf;
     return FS_OK;
 }
 
