@@ -179,7 +179,7 @@ fs_status tune_instance(const fs_instance &in, double sigma, int m, const fs_opt
             const int P = t * c + 2 * m - 1;
             const size_t rsz = probe.precision == 64 ? 8 : 4;
             const int planes = (probe.precision != 64 && !(probe.flags & FS_FLAG_NO_KAHAN)) ? 2 : 1;
-            if ((size_t)kSpreadWarps * P * P * rsz * planes > kMaxTileSmem)
+            if ((size_t)kSpreadWarps * P * spread_pitch(P, 2 * m) * rsz * planes > kMaxTileSmem)
                 continue;
             fs_opts o = probe;
             o.cell = c;

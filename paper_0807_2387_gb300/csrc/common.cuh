@@ -178,6 +178,77 @@ template <int DEG> __device__ __forceinline__ float poly_eval(const float *c, fl
     return acc;
 }
 
+// Spreading tiles in shared memory: a warp's tile holds `rows` x `rows` grid lines at a row
+// pitch q >= rows.  The M2 x M2 taps of one source sit at offsets a q + b (a, b < M2) from the
+// source's corner; tap (a, b) lies on bank (a q + b) mod 32 relative to the corner.  Dealing the
+// taps to lanes by bank makes every read and write of a source conflict-free, provided no bank
+// holds more than ceil(M2^2 / 32) taps: spread_pitch picks the smallest such q (q = M2 mod 32
+// always qualifies, since the offsets a M2 + b are then consecutive, so q < rows + 32).
+__host__ __device__ __forceinline__ int spread_taps_on_bank(int bank, int q, int M2)
+{
+    int c = 0;
+    for (int a = 0; a < M2; ++a)
+        c += (((bank - a * q) % 32 + 32) % 32) < M2 ? 1 : 0;
+    return c;
+}
+
+inline int spread_pitch(int rows, int M2)
+{
+    const int per = (M2 * M2 + 31) / 32;
+    for (int q = rows; q < rows + 32; ++q) {
+        int worst = 0;
+        for (int bank = 0; bank < 32; ++bank)
+            worst = worst > spread_taps_on_bank(bank, q, M2) ? worst : spread_taps_on_bank(bank, q, M2);
+        if (worst <= per)
+            return q;
+    }
+    return rows;   // not reached
+}
+
+// The same choice made by one warp, each lane counting its own bank.
+__device__ __forceinline__ int spread_pitch_warp(int rows, int M2, int lane)
+{
+    const int per = (M2 * M2 + 31) / 32;
+    for (int q = rows; q < rows + 32; ++q)
+        if (__reduce_max_sync(0xffffffffu, spread_taps_on_bank(lane, q, M2)) <= per)
+            return q;
+    return rows;   // not reached
+}
+
+// This lane's taps for pitch q: slot i holds the i-th row a (ascending) whose tap on this lane's
+// bank exists, b = (lane - a q) mod 32 < M2.  Slots beyond the count are marked invalid.
+template <int M2, int PER>
+__device__ __forceinline__ void spread_lane_taps(int lane, int q, int (&ta)[PER], int (&tb)[PER], int (&toff)[PER],
+                                                 unsigned &valid)
+{
+    int g = 0;
+    valid = 0u;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        ta[i] = 0;
+        tb[i] = 0;
+    }
+#pragma unroll
+    for (int a = 0; a < M2; ++a) {
+        const int b = ((lane - a * q) % 32 + 32) % 32;
+        if (b < M2) {
+#pragma unroll
+            for (int i = 0; i < PER; ++i)
+                if (g == i) {
+                    ta[i] = a;
+                    tb[i] = b;
+                }
+            ++g;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        toff[i] = ta[i] * q + tb[i];
+        if (i < g)
+            valid |= 1u << i;
+    }
+}
+
 // Point record fields in cell-sorted order.
 //   base: packed (b1 | b2 << 16), b = floor(u), u = n_os (s x + 1/2) - window_lo
 //   frac: u - b in [0, 1), per dimension

@@ -433,7 +433,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     int T = o.tile_cells > 0 ? o.tile_cells : std::max(1, (int)std::lround(16.0 / cell));
     auto smem_for = [&](int t) {
         const int P = t * cell + 2 * m - 1;
-        return (size_t)kSpreadWarps * P * P * sizeof(real) * ((pl->kahan && sizeof(real) == 4) ? 2 : 1) +
+        return (size_t)kSpreadWarps * P * spread_pitch(P, 2 * m) * sizeof(real) *
+                   ((pl->kahan && sizeof(real) == 4) ? 2 : 1) +
                sizeof(float) * 2 * m * (kPolyD + 1);
     };
     while (T > 1 && smem_for(T) > 160 * 1024)

@@ -18,6 +18,7 @@
 // compensation tile, so the tile holds a double-FP32 sum.  At the end the warp
 // tiles are summed and added to the grid with global atomics (tiles overlap by
 // 2m-1 lines).
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
@@ -42,8 +43,9 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
     extern __shared__ unsigned char smem_raw[];
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const int PP = P * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Q = spread_pitch_warp(P, M2, lane);   // row pitch: bank-conflict-free taps
+    const int PP = P * Q;                             // one plane of a warp tile
     real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
     // FP32 window polynomials, one row per tap, after the warp tiles (taps differ across lanes)
     float *poly = reinterpret_cast<float *>(reinterpret_cast<real *>(smem_raw) + (size_t)kSpreadWarps * PP * PLANES);
@@ -56,19 +58,20 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
     for (int i = lane; i < PP * PLANES; i += 32)
         acc[i] = real(0);
     __syncthreads();
-    // this lane's taps: t = lane + 32 i -> (a, b) = (t / 2m, t % 2m)
-    int toff[PER];
-    int ta[PER], tb[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int t = lane + 32 * i;
-        ta[i] = t < TAPS ? t / M2 : 0;
-        tb[i] = t < TAPS ? t - (t / M2) * M2 : 0;
-        toff[i] = ta[i] * P + tb[i];
-    }
+    // this lane's taps: those on its shared-memory bank (spread_lane_taps)
+    int toff[PER], ta[PER], tb[PER];
+    unsigned valid;
+    spread_lane_taps<M2, PER>(lane, Q, ta, tb, toff, valid);
     const bool first = lane < M2;
     const int jw = first ? lane : lane - M2;
-    const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
+    // the lane's window polynomial (FP32 path), held in registers for the whole item
+    float pc[kPolyD + 1];
+    {
+        const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
+#pragma unroll
+        for (int k = 0; k <= kPolyD; ++k)
+            pc[k] = kPoly ? prow[k] : 0.f;
+    }
     const int end = it.start + it.count;
     int j = it.start + warp;
     // software pipeline: the next source's record is in flight while this one is spread
@@ -93,26 +96,37 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
         if (lane < 2 * M2) {
             const real fr = first ? f.x : f.y;
             if constexpr (kPoly)
-                wv = poly_eval<kPolyD>(prow, (float)fr - 0.5f);
+                wv = poly_eval<kPolyD>(pc, (float)fr - 0.5f);
             else
                 wv = kb_value<real>(w, fr, m - 1 - jw);
             if (!first)
                 wv *= qj;
         }
-        real *corner = acc + (base1(packed) - m + 1 - o1) * P + (base2(packed) - m + 1 - o2);
+        real *corner = acc + (base1(packed) - m + 1 - o1) * Q + (base2(packed) - m + 1 - o2);
+        // A lane's taps of one source are distinct cells (and distinct from the other lanes'),
+        // so every read of this source is issued before any write: one shared-memory latency
+        // per source instead of one per tap.
+        real v[PER], old[PER], cmp[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const real w1 = __shfl_sync(0xffffffffu, wv, ta[i]);
             const real w2 = __shfl_sync(0xffffffffu, wv, M2 + tb[i]);
-            if (lane + 32 * i < TAPS) {
+            v[i] = w1 * w2;
+            if ((valid >> i) & 1u) {
+                old[i] = corner[toff[i]];
+                if (KAHAN)
+                    cmp[i] = corner[toff[i] + PP];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            if ((valid >> i) & 1u) {
                 real *cell = corner + toff[i];
-                const real v = w1 * w2;
-                const real old = *cell;
-                const real s = old + v;
+                const real s = old[i] + v[i];
                 *cell = s;
                 if (KAHAN) {
-                    const real bb = s - old;
-                    cell[PP] += (old - (s - bb)) + (v - bb);
+                    const real bb = s - old[i];
+                    cell[PP] = cmp[i] + ((old[i] - (s - bb)) + (v[i] - bb));
                 }
             }
         }
@@ -120,16 +134,16 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
     }
     __syncthreads();
     const real *base_tile = reinterpret_cast<const real *>(smem_raw);
-    for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, c = i - (i / P) * P;
         real v = real(0);
 #pragma unroll
         for (int ww = 0; ww < kSpreadWarps; ++ww) {
-            const real *tile = base_tile + (size_t)ww * PP * PLANES;
-            v += tile[i];
+            const real *tile = base_tile + (size_t)ww * PP * PLANES + r * Q + c;
+            v += tile[0];
             if (KAHAN)
-                v += tile[i + PP];
+                v += tile[PP];
         }
-        const int r = i / P, c = i - (i / P) * P;
         const int g1 = o1 + r, g2 = o2 + c;
         if (v != real(0) && g1 >= 0 && g1 < n_a && g2 >= 0 && g2 < n_a)
             atomicAdd(grid + (int64_t)g1 * pitch + g2, v);
@@ -273,8 +287,9 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread_dip(const SpreadIt
     extern __shared__ unsigned char smem_raw[];
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const int PP = P * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Q = spread_pitch_warp(P, M2, lane);   // row pitch: bank-conflict-free taps
+    const int PP = P * Q;                             // one plane of a warp tile
     real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
     float *poly = reinterpret_cast<float *>(reinterpret_cast<real *>(smem_raw) + (size_t)kSpreadWarps * PP * PLANES);
     if (kPoly) {
@@ -290,17 +305,21 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread_dip(const SpreadIt
         acc[i] = real(0);
     __syncthreads();
     int toff[PER], ta[PER], tb[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int t = lane + 32 * i;
-        ta[i] = t < TAPS ? t / M2 : 0;
-        tb[i] = t < TAPS ? t - (t / M2) * M2 : 0;
-        toff[i] = ta[i] * P + tb[i];
-    }
+    unsigned valid;
+    spread_lane_taps<M2, PER>(lane, Q, ta, tb, toff, valid);
     const bool first = lane < M2;
     const int jw = first ? lane : lane - M2;
-    const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
-    const float *drow = poly + M2 * (kPolyD + 1) + (lane < 2 * M2 ? jw : 0) * kPolyD;
+    float pc[kPolyD + 1], pd[kPolyD];   // the lane's value and slope polynomials, in registers
+    {
+        const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
+        const float *drow = poly + M2 * (kPolyD + 1) + (lane < 2 * M2 ? jw : 0) * kPolyD;
+#pragma unroll
+        for (int k = 0; k <= kPolyD; ++k)
+            pc[k] = kPoly ? prow[k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kPolyD; ++k)
+            pd[k] = kPoly ? drow[k] : 0.f;
+    }
     for (int j = it.start + warp; j < it.start + it.count; j += kSpreadWarps) {
         const int packed = base[j];
         const real2_t<real> f = frac[j];
@@ -310,28 +329,36 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread_dip(const SpreadIt
         if (lane < 2 * M2) {
             const real fr = first ? f.x : f.y;
             if constexpr (kPoly) {
-                wv = poly_eval<kPolyD>(prow, (float)fr - 0.5f);
-                wd = poly_eval<kPolyD - 1>(drow, (float)fr - 0.5f);
+                wv = poly_eval<kPolyD>(pc, (float)fr - 0.5f);
+                wd = poly_eval<kPolyD - 1>(pd, (float)fr - 0.5f);
             } else {
                 kb_value_slope<real>(w, fr, m - 1 - jw, wv, wd);
             }
         }
-        real *corner = acc + (base1(packed) - m + 1 - o1) * P + (base2(packed) - m + 1 - o2);
+        real *corner = acc + (base1(packed) - m + 1 - o1) * Q + (base2(packed) - m + 1 - o2);
+        real v[PER], old[PER], cmp[PER];     // reads before writes, as in spread_item
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const real w1 = __shfl_sync(0xffffffffu, wv, ta[i]);
             const real d1 = __shfl_sync(0xffffffffu, wd, ta[i]);
             const real w2 = __shfl_sync(0xffffffffu, wv, M2 + tb[i]);
             const real d2 = __shfl_sync(0xffffffffu, wd, M2 + tb[i]);
-            if (lane + 32 * i < TAPS) {
+            v[i] = w2 * (c * w1 + d.x * d1) + d.y * w1 * d2;
+            if ((valid >> i) & 1u) {
+                old[i] = corner[toff[i]];
+                if (KAHAN)
+                    cmp[i] = corner[toff[i] + PP];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            if ((valid >> i) & 1u) {
                 real *cell = corner + toff[i];
-                const real v = w2 * (c * w1 + d.x * d1) + d.y * w1 * d2;
-                const real old = *cell;
-                const real s = old + v;
+                const real s = old[i] + v[i];
                 *cell = s;
                 if (KAHAN) {
-                    const real bb = s - old;
-                    cell[PP] += (old - (s - bb)) + (v - bb);
+                    const real bb = s - old[i];
+                    cell[PP] = cmp[i] + ((old[i] - (s - bb)) + (v[i] - bb));
                 }
             }
         }
@@ -339,16 +366,16 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread_dip(const SpreadIt
     }
     __syncthreads();
     const real *base_tile = reinterpret_cast<const real *>(smem_raw);
-    for (int i = threadIdx.x; i < PP; i += blockDim.x) {
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, cc = i - (i / P) * P;
         real v = real(0);
 #pragma unroll
         for (int ww = 0; ww < kSpreadWarps; ++ww) {
-            const real *tile = base_tile + (size_t)ww * PP * PLANES;
-            v += tile[i];
+            const real *tile = base_tile + (size_t)ww * PP * PLANES + r * Q + cc;
+            v += tile[0];
             if (KAHAN)
-                v += tile[i + PP];
+                v += tile[PP];
         }
-        const int r = i / P, cc = i - (i / P) * P;
         const int g1 = o1 + r, g2 = o2 + cc;
         if (v != real(0) && g1 >= 0 && g1 < n_a && g2 >= 0 && g2 < n_a)
             atomicAdd(grid + (int64_t)g1 * pitch + g2, v);
@@ -438,7 +465,7 @@ cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const in
 {
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const size_t smem = (size_t)kSpreadWarps * P * P * sizeof(real) * (kahan ? 2 : 1) +
+    const size_t smem = (size_t)kSpreadWarps * P * spread_pitch(P, M2) * sizeof(real) * (kahan ? 2 : 1) +
                         sizeof(float) * M2 * (kPolyD + 1);
     const real2_t<real> *fr = (const real2_t<real> *)frac;
     if (kahan) {
@@ -474,7 +501,7 @@ cudaError_t spread_dip_m(const SpreadItem *items, int n_items, CellGrid cg, cons
 {
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const size_t smem = (size_t)kSpreadWarps * P * P * sizeof(real) * (kahan ? 2 : 1) +
+    const size_t smem = (size_t)kSpreadWarps * P * spread_pitch(P, M2) * sizeof(real) * (kahan ? 2 : 1) +
                         sizeof(float) * M2 * (2 * kPolyD + 1);
     const real2_t<real> *fr = (const real2_t<real> *)frac;
     const real2_t<real> *dd = (const real2_t<real> *)dq;
@@ -633,10 +660,15 @@ template <class F> cudaError_t with_width(int m, F &&f)
     }
 }
 
+// Instances have tiles of up to max_tile grid lines; a tile of r <= P rows takes r x
+// spread_pitch(r) words per plane, which is below P^2 <= P x spread_pitch(P) unless r > P - 32.
 template <typename real> size_t batch_spread_smem(int M2, int max_tile, bool comp)
 {
     const int P = max_tile + M2 - 1;
-    return (size_t)kSpreadWarps * P * P * sizeof(real) * (comp ? 2 : 1) + sizeof(float) * M2 * (kPolyD + 1);
+    size_t words = 0;
+    for (int r = P > 32 ? P - 32 : 1; r <= P; ++r)
+        words = std::max(words, (size_t)r * spread_pitch(r, M2));
+    return (size_t)kSpreadWarps * words * sizeof(real) * (comp ? 2 : 1) + sizeof(float) * M2 * (kPolyD + 1);
 }
 
 }  // namespace
