@@ -47,33 +47,64 @@ template <typename real> struct NearParams {
 
 // ---- 3D kernel 1/(4 pi r) (kernels3d.cu; transform and coefficients in kernels_fft.cu)
 
-// Near-field cells of the 3D path: n_c^3 cubes of `cell` grid lines, key (c1 n_c + c2) n_c + c3.
+// Near-field cells of the 3D path: n_c^3 cubes of `cell` grid lines, cell key
+// (c1 n_c + c2) n_c + c3.  Points are sorted by cell and, inside a cell, by sub-cell (sub^3
+// cubes, Morton order): sort key = cell key x sub^3 + Morton index, so the points of cell K
+// occupy the sorted range [start[K sub^3], start[(K + 1) sub^3]).
 struct CellGrid3 {
     int cell;
     int n_c;
+    int sub;   // sub-cells per cell edge: 1, 2 or 4
     __host__ __device__ int key(int c1, int c2, int c3) const { return (c1 * n_c + c2) * n_c + c3; }
-    __host__ __device__ int n_keys() const { return n_c * n_c * n_c; }
+    __host__ __device__ int n_cells() const { return n_c * n_c * n_c; }
+    __host__ __device__ int sub3() const { return sub * sub * sub; }
+    __host__ __device__ int n_keys() const { return n_cells() * sub3(); }
+};
+
+// FP32 3D near field (distances in units of eps_I, w = |d|^2 / eps_I^2):
+//   f(w)       = c1 w^(-1/2) - P(w),             c1 = 1 / (4 pi eps_I), P(w) = T_I = sum beta_k w^k
+//   grad_x f   = -(1/eps_I) (c1 w^(-3/2) + 2 P'(w)) d,   d in units of eps_I
+struct Near3Params {
+    float H;               // cell edge / eps_I (>= 1)
+    float reach2;          // squared culling radius, 1 plus a rounding margin
+    float c1;              // 1 / (4 pi eps_I)
+    float inv_eps;         // 1 / eps_I
+    float beta0;           // T_I(0), removed for coincident pairs (G(0) := 0)
+    float nbeta[kMaxP];    // -beta_k
+    float dbeta2[kMaxP];   // 2 P'(w) = sum dbeta2_k w^k, dbeta2_k = 2 (k + 1) beta_{k+1}
+    int p;
 };
 
 cudaError_t launch_rmax3(const double *xyz, int64_t n, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_point_keys3(const double *xyz, int64_t n, double s, int n_os, int window_lo, int n_a, int m,
                                CellGrid3 cg, int *key, int *count, int *status, cudaStream_t st);
 // pos: torus coordinates (n x 3, FP64); frac (n x 3); base: window grid lines packed 10 bits each;
-// pos32 (FP32 path, else null): offsets from the point's cell corner
+// pos32 (FP32 path, else null): offsets from the point's cell corner in units of eps_I (times inv_eps)
 template <typename real>
 cudaError_t launch_gather_points3(const double *xyz, const int *perm, int64_t n, double s, int n_os, int window_lo,
-                                  int n_a, int m, int cell, double *pos, real *frac, int *base, float4 *pos32,
-                                  int *status, cudaStream_t st);
+                                  int n_a, int m, int cell, double inv_eps, double *pos, real *frac, int *base,
+                                  float4 *pos32, int *status, cudaStream_t st);
 template <typename real>
 cudaError_t launch_spread3(int64_t M, int m, const int *base, const real *frac, const real *q, Window<real> w,
                            const WindowPoly &wp, real *grid, int n_a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_interp3(int64_t N, int m, const int *base, const real *frac, Window<real> w, const WindowPoly &wp,
                            const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, cudaStream_t st);
-template <typename real>
-cudaError_t launch_near3(int64_t N, const int *tgt_base, const double *tgt_pos, const float4 *tgt_p32,
-                         const double *src_pos, const float4 *src_p32, const int *src_start, CellGrid3 cg,
-                         const real *q, NearParams<real> np, real *phi_s, real *grad_s, cudaStream_t st);
+// FP64 near field, thread per target over the 27 cells around its own
+cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,
+                             const int *src_start, CellGrid3 cg, const double *q, NearParams<double> np,
+                             double *phi_s, double *grad_s, cudaStream_t st);
+// FP32 near field over warp items {first target, count <= 64} of one cell each (sorted order);
+// coincident pairs (equal FP32 offsets) are listed per target in coinc_start / coinc_src
+cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_base, const float4 *tgt_p32,
+                              const float4 *src_p32, const float *q, const int *src_start, CellGrid3 cg,
+                              const Near3Params &np, const int *coinc_start, const int *coinc_src, float *phi_s,
+                              float *grad_s, cudaStream_t st);
+// per target: count of sources with the same FP32 offsets in the same cell (coinc_src null), or
+// their sorted indices from coinc_start (coinc_src given)
+cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const float4 *tgt_p32, const float4 *src_p32,
+                               const int *src_start, CellGrid3 cg, int *count, const int *coinc_start, int *coinc_src,
+                               cudaStream_t st);
 template <typename real>
 cudaError_t launch_unpermute3(int64_t N, const real *phi_s, const real *grad_s, const int *perm, double s,
                               void *phi_out, void *H_out, int out_f64, cudaStream_t st);

@@ -15,7 +15,7 @@
 //   output       phi = s phi~, H = -s^2 grad~ phi~ (1/r is homogeneous of degree -1).
 // Grid layout: g[z][y][x], x fastest, edge n_a (the active window); a point's base grid
 // line per coordinate is packed into 10 bits each.
-#include "internal.h"
+#include "near_warp.cuh"
 
 namespace fs {
 
@@ -64,20 +64,28 @@ __global__ void k_point_keys3(const double *__restrict__ xyz, int64_t n, double 
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n)
         return;
-    double f;
-    const int b1 = grid_line3(xyz[3 * k], s, n_os, window_lo, m, n_a, f, status);
-    const int b2 = grid_line3(xyz[3 * k + 1], s, n_os, window_lo, m, n_a, f, status);
-    const int b3 = grid_line3(xyz[3 * k + 2], s, n_os, window_lo, m, n_a, f, status);
-    const int kk = cg.key(b1 / cg.cell, b2 / cg.cell, b3 / cg.cell);
+    int b[3], sc[3];
+    for (int d = 0; d < 3; ++d) {
+        double f;
+        b[d] = grid_line3(xyz[3 * k + d], s, n_os, window_lo, m, n_a, f, status);
+        // sub-cell from the offset inside the cell, (b mod cell + frac) / cell in [0, 1)
+        const int sidx = (int)(((double)(b[d] % cg.cell) + f) * cg.sub / cg.cell);
+        sc[d] = sidx < cg.sub ? sidx : cg.sub - 1;
+    }
+    int morton = 0;
+    for (int bit = 0; bit < 2; ++bit)
+        morton |= (((sc[2] >> bit) & 1) << (3 * bit)) | (((sc[1] >> bit) & 1) << (3 * bit + 1)) |
+                  (((sc[0] >> bit) & 1) << (3 * bit + 2));
+    const int kk = cg.key(b[0] / cg.cell, b[1] / cg.cell, b[2] / cg.cell) * cg.sub3() + morton;
     key[k] = kk;
     atomicAdd(&count[kk], 1);
 }
 
 template <typename real>
 __global__ void k_gather_points3(const double *__restrict__ xyz, const int *__restrict__ perm, int64_t n, double s,
-                                 int n_os, int window_lo, int n_a, int m, int cell, double *__restrict__ pos,
-                                 real *__restrict__ frac, int *__restrict__ base, float4 *__restrict__ pos32,
-                                 int *status)
+                                 int n_os, int window_lo, int n_a, int m, int cell, double inv_eps,
+                                 double *__restrict__ pos, real *__restrict__ frac, int *__restrict__ base,
+                                 float4 *__restrict__ pos32, int *status)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n)
@@ -92,11 +100,11 @@ __global__ void k_gather_points3(const double *__restrict__ xyz, const int *__re
     }
     base[k] = b[0] | (b[1] << 10) | (b[2] << 20);
     if (pos32) {
-        // offset from the lower corner of the point's cell, torus units
+        // offset from the lower corner of the point's cell, in units of eps_I
         float o[3];
         for (int d = 0; d < 3; ++d) {
             const double corner = (double)((b[d] / cell) * cell + window_lo) / n_os - 0.5;
-            o[d] = (float)(s * xyz[3 * i + d] - corner);
+            o[d] = (float)((s * xyz[3 * i + d] - corner) * inv_eps);
         }
         pos32[k] = make_float4(o[0], o[1], o[2], 0.f);
     }
@@ -194,74 +202,53 @@ __global__ void __launch_bounds__(256) k_interp3(int64_t N, const int *__restric
     grad_s[3 * k + 2] = n_os * gz;
 }
 
-// Near-field correction at target k (thread per target) over the 27 cells around its cell.
-template <typename real>
-__global__ void __launch_bounds__(256) k_near3(int64_t N, const int *__restrict__ tgt_base,
-                                               const double *__restrict__ tgt_pos, const float4 *__restrict__ tgt_p32,
-                                               const double *__restrict__ src_pos, const float4 *__restrict__ src_p32,
-                                               const int *__restrict__ src_start, CellGrid3 cg,
-                                               const real *__restrict__ q, NearParams<real> np,
-                                               real *__restrict__ phi_s, real *__restrict__ grad_s)
+// FP64 near-field correction at target k (thread per target) over the 27 cells around its cell.
+__global__ void __launch_bounds__(256) k_near3_f64(int64_t N, const int *__restrict__ tgt_base,
+                                                   const double *__restrict__ tgt_pos,
+                                                   const double *__restrict__ src_pos,
+                                                   const int *__restrict__ src_start, CellGrid3 cg,
+                                                   const double *__restrict__ q, NearParams<double> np,
+                                                   double *__restrict__ phi_s, double *__restrict__ grad_s)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= N)
         return;
     const int packed = tgt_base[k];
     const int c1 = b3x(packed) / cg.cell, c2 = b3y(packed) / cg.cell, c3 = b3z(packed) / cg.cell;
-    real xt[3];
-    if constexpr (sizeof(real) == 4) {
-        const float4 p = tgt_p32[k];
-        xt[0] = p.x;
-        xt[1] = p.y;
-        xt[2] = p.z;
-    } else {
-        for (int d = 0; d < 3; ++d)
-            xt[d] = tgt_pos[3 * k + d];
-    }
-    const real inv4pi = real(1.0 / (4.0 * kPi));
-    real phi = 0, g0 = 0, g1 = 0, g2 = 0;
+    const double xt0 = tgt_pos[3 * k], xt1 = tgt_pos[3 * k + 1], xt2 = tgt_pos[3 * k + 2];
+    const double inv4pi = 1.0 / (4.0 * kPi);
+    const int S3 = cg.sub3();
+    double phi = 0, g0 = 0, g1 = 0, g2 = 0;
     for (int e1 = max(c1 - 1, 0); e1 <= min(c1 + 1, cg.n_c - 1); ++e1)
         for (int e2 = max(c2 - 1, 0); e2 <= min(c2 + 1, cg.n_c - 1); ++e2)
             for (int e3 = max(c3 - 1, 0); e3 <= min(c3 + 1, cg.n_c - 1); ++e3) {
                 const int key = cg.key(e1, e2, e3);
-                // FP32 offsets are relative to the cell corners: add the cell step
-                const real o1 = sizeof(real) == 4 ? (real)(c1 - e1) * np.hcell : real(0);
-                const real o2 = sizeof(real) == 4 ? (real)(c2 - e2) * np.hcell : real(0);
-                const real o3 = sizeof(real) == 4 ? (real)(c3 - e3) * np.hcell : real(0);
-                const int end = src_start[key + 1];
-                for (int j = src_start[key]; j < end; ++j) {
-                    real dx, dy, dz;
-                    if constexpr (sizeof(real) == 4) {
-                        const float4 p = __ldg(src_p32 + j);
-                        dx = (xt[0] - p.x) + o1;
-                        dy = (xt[1] - p.y) + o2;
-                        dz = (xt[2] - p.z) + o3;
-                    } else {
-                        dx = xt[0] - src_pos[3 * j];
-                        dy = xt[1] - src_pos[3 * j + 1];
-                        dz = xt[2] - src_pos[3 * j + 2];
-                    }
-                    const real r2 = dx * dx + dy * dy + dz * dz;
+                const int end = src_start[(key + 1) * S3];
+                for (int j = src_start[key * S3]; j < end; ++j) {
+                    const double dx = xt0 - src_pos[3 * j];
+                    const double dy = xt1 - src_pos[3 * j + 1];
+                    const double dz = xt2 - src_pos[3 * j + 2];
+                    const double r2 = dx * dx + dy * dy + dz * dz;
                     if (!(r2 < np.eps2))
                         continue;
-                    const real qj = q[j];
-                    if (r2 == real(0)) {
+                    const double qj = q[j];
+                    if (r2 == 0.0) {
                         phi -= qj * np.beta[0];
                         continue;
                     }
-                    const real u2 = r2 * np.inv_eps2;
-                    real t = np.beta[np.p - 1];
+                    const double u2 = r2 * np.inv_eps2;
+                    double t = np.beta[np.p - 1];
                     for (int i = np.p - 2; i >= 0; --i)
                         t = t * u2 + np.beta[i];
-                    real tp = real(0);
+                    double tp = 0.0;
                     if (np.p > 1) {
                         tp = np.dbeta[np.p - 2];
                         for (int i = np.p - 3; i >= 0; --i)
                             tp = tp * u2 + np.dbeta[i];
                     }
-                    const real inv_r = real(1) / sqrt(r2);
-                    const real val = inv4pi * inv_r - t;
-                    const real coef = -inv4pi * inv_r * inv_r * inv_r - tp;
+                    const double inv_r = 1.0 / sqrt(r2);
+                    const double val = inv4pi * inv_r - t;
+                    const double coef = -inv4pi * inv_r * inv_r * inv_r - tp;
                     phi += qj * val;
                     g0 += qj * coef * dx;
                     g1 += qj * coef * dy;
@@ -272,6 +259,194 @@ __global__ void __launch_bounds__(256) k_near3(int64_t N, const int *__restrict_
     grad_s[3 * k] += g0;
     grad_s[3 * k + 1] += g1;
     grad_s[3 * k + 2] += g2;
+}
+
+// ---- FP32 near field: warp items, candidate lists, packed pairs
+//
+// A warp takes one item, at most 64 consecutive targets of one cell (two per lane; Morton
+// sub-cell order keeps them compact) and forms their bounding box.  Coordinates are offsets
+// from the target cell's corner in units of eps_I.  For each of the 27 cells around (skipping
+// cells beyond the culling radius of the box), the lanes read 32 sources at a time, keep those
+// within the culling radius of the box (ballot) and append them to the warp's candidate list
+// in shared memory, pre-broadcast as (x, x, y, y), (z, z, q, q).  The list is evaluated by
+// all lanes against both of their targets as packed FP32 pairs: no branch, pairs outside
+// 0 < w < 1 get charge 0 (an integer compare of the bits of w: 0 < w < 1 iff
+// bits(w) - 1 < bits(1) - 1 as unsigned), and coincident pairs (w = 0) are accounted from the
+// per-target lists built with the plan.
+constexpr int kNear3Warps = 4;
+constexpr int kNear3Cap = 256;   // candidate list entries per warp (32 B each)
+constexpr int kNear3Unroll = 2;
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// q if 0 < w < 1, else 0
+__device__ __forceinline__ float in_range(float w, float q)
+{
+    return (__float_as_uint(w) - 1u) < 0x3f7fffffu ? q : 0.f;
+}
+
+template <int P>
+__device__ __forceinline__ void near3_eval(const float4 (*list)[2], int n, float2 X, float2 Y, float2 Z,
+                                           const Near3Params &np, float2 &phi, float2 &gx, float2 &gy, float2 &gz)
+{
+    const float2 c1 = make_float2(np.c1, np.c1);
+#pragma unroll kNear3Unroll
+    for (int e = 0; e < n; ++e) {
+        const float4 A = list[e][0], B = list[e][1];
+        const float2 dx = __fadd2_rn(X, make_float2(-A.x, -A.y));
+        const float2 dy = __fadd2_rn(Y, make_float2(-A.z, -A.w));
+        const float2 dz = __fadd2_rn(Z, make_float2(-B.x, -B.y));
+        const float2 w = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const float2 qe = make_float2(in_range(w.x, B.z), in_range(w.y, B.w));
+        // w = 0 only for coincident pairs (charge 0 here): floor w so that w^-3/2 stays finite
+        // (distinct FP32 offsets of size ~1 give w >= ~1e-14, far above the floor)
+        const float2 rs = make_float2(rsqrt_approx(fmaxf(w.x, 1e-20f)), rsqrt_approx(fmaxf(w.y, 1e-20f)));
+        float2 t = make_float2(np.nbeta[P - 1], np.nbeta[P - 1]);
+#pragma unroll
+        for (int i = P - 2; i >= 0; --i)
+            t = __ffma2_rn(t, w, make_float2(np.nbeta[i], np.nbeta[i]));
+        float2 u = make_float2(0.f, 0.f);
+        if constexpr (P >= 2) {
+            u = make_float2(np.dbeta2[P - 2], np.dbeta2[P - 2]);
+#pragma unroll
+            for (int i = P - 3; i >= 0; --i)
+                u = __ffma2_rn(u, w, make_float2(np.dbeta2[i], np.dbeta2[i]));
+        }
+        const float2 val = __ffma2_rn(c1, rs, t);                                  // c1 w^-1/2 - P(w)
+        const float2 gc = __ffma2_rn(c1, __fmul2_rn(__fmul2_rn(rs, rs), rs), u);   // c1 w^-3/2 + 2 P'(w)
+        phi = __ffma2_rn(qe, val, phi);
+        const float2 qc = __fmul2_rn(qe, gc);
+        gx = __ffma2_rn(qc, dx, gx);
+        gy = __ffma2_rn(qc, dy, gy);
+        gz = __ffma2_rn(qc, dz, gz);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__restrict__ items, int n_items,
+                                                                 const int *__restrict__ tgt_base,
+                                                                 const float4 *__restrict__ tgt_p32,
+                                                                 const float4 *__restrict__ src_p32,
+                                                                 const float *__restrict__ q,
+                                                                 const int *__restrict__ src_start, CellGrid3 cg,
+                                                                 Near3Params np, const int *__restrict__ coinc_start,
+                                                                 const int *__restrict__ coinc_src,
+                                                                 float *__restrict__ phi_s, float *__restrict__ grad_s)
+{
+    __shared__ float4 lists[kNear3Warps][kNear3Cap][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = blockIdx.x * kNear3Warps + warp;
+    if (item >= n_items)
+        return;   // whole warp; the kernel has no block-wide barrier
+    float4(*list)[2] = lists[warp];
+    const int2 it = items[item];
+    const int first = it.x, count = it.y;
+    const bool va = lane < count, vb = lane + 32 < count;
+    const int ka = va ? first + lane : first, kb = vb ? first + 32 + lane : ka;
+    const float4 pa = tgt_p32[ka], pb = tgt_p32[kb];
+    const float2 X = make_float2(pa.x, pb.x), Y = make_float2(pa.y, pb.y), Z = make_float2(pa.z, pb.z);
+    const float lox = warp_min(fminf(pa.x, pb.x)), hix = warp_max(fmaxf(pa.x, pb.x));
+    const float loy = warp_min(fminf(pa.y, pb.y)), hiy = warp_max(fmaxf(pa.y, pb.y));
+    const float loz = warp_min(fminf(pa.z, pb.z)), hiz = warp_max(fmaxf(pa.z, pb.z));
+    const int packed = tgt_base[first];
+    const int c1 = b3x(packed) / cg.cell, c2 = b3y(packed) / cg.cell, c3 = b3z(packed) / cg.cell;
+    const int S3 = cg.sub3();
+    float2 phi = make_float2(0.f, 0.f), gx = phi, gy = phi, gz = phi;
+    int n = 0;
+    for (int e1 = max(c1 - 1, 0); e1 <= min(c1 + 1, cg.n_c - 1); ++e1) {
+        const float o1 = (float)(e1 - c1) * np.H;
+        const float bx = fmaxf(0.f, fmaxf(o1 - hix, lox - (o1 + np.H)));
+        for (int e2 = max(c2 - 1, 0); e2 <= min(c2 + 1, cg.n_c - 1); ++e2) {
+            const float o2 = (float)(e2 - c2) * np.H;
+            const float by = fmaxf(0.f, fmaxf(o2 - hiy, loy - (o2 + np.H)));
+            for (int e3 = max(c3 - 1, 0); e3 <= min(c3 + 1, cg.n_c - 1); ++e3) {
+                const float o3 = (float)(e3 - c3) * np.H;
+                const float bz = fmaxf(0.f, fmaxf(o3 - hiz, loz - (o3 + np.H)));
+                if (bx * bx + by * by + bz * bz >= np.reach2)
+                    continue;   // the whole cell is beyond reach of the box (warp-uniform)
+                const int key = cg.key(e1, e2, e3);
+                const int end = src_start[(key + 1) * S3];
+                for (int j0 = src_start[key * S3]; j0 < end; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool keep = false;
+                    float sx = 0.f, sy = 0.f, sz = 0.f, qj = 0.f;
+                    if (j < end) {
+                        const float4 sp = src_p32[j];
+                        qj = q[j];
+                        sx = sp.x + o1;
+                        sy = sp.y + o2;
+                        sz = sp.z + o3;
+                        const float dx = fmaxf(0.f, fmaxf(sx - hix, lox - sx));
+                        const float dy = fmaxf(0.f, fmaxf(sy - hiy, loy - sy));
+                        const float dz = fmaxf(0.f, fmaxf(sz - hiz, loz - sz));
+                        keep = dx * dx + dy * dy + dz * dz < np.reach2;
+                    }
+                    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const int at = n + __popc(mask & ((1u << lane) - 1u));
+                        list[at][0] = make_float4(sx, sx, sy, sy);
+                        list[at][1] = make_float4(sz, sz, qj, qj);
+                    }
+                    n += __popc(mask);
+                    if (n > kNear3Cap - 32) {
+                        __syncwarp();
+                        near3_eval<P>(list, n, X, Y, Z, np, phi, gx, gy, gz);
+                        n = 0;
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    near3_eval<P>(list, n, X, Y, Z, np, phi, gx, gy, gz);
+    // coincident pairs: G(0) := 0, so only -q T_I(0) remains of the far field's self term
+    const int kt[2] = {first + lane, first + 32 + lane};
+    const bool vt[2] = {va, vb};
+    const float ph[2] = {phi.x, phi.y}, ggx[2] = {gx.x, gx.y}, ggy[2] = {gy.x, gy.y}, ggz[2] = {gz.x, gz.y};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (!vt[t])
+            continue;
+        const int k = kt[t];
+        float self = 0.f;
+        for (int c = coinc_start[k]; c < coinc_start[k + 1]; ++c)
+            self += q[coinc_src[c]];
+        phi_s[k] += ph[t] - np.beta0 * self;
+        grad_s[3 * k] -= np.inv_eps * ggx[t];
+        grad_s[3 * k + 1] -= np.inv_eps * ggy[t];
+        grad_s[3 * k + 2] -= np.inv_eps * ggz[t];
+    }
+}
+
+// Coincident pairs: sources of the target's own cell with the same FP32 offsets.
+__global__ void k_coincident3(int64_t N, const int *__restrict__ tgt_base, const float4 *__restrict__ tgt_p32,
+                              const float4 *__restrict__ src_p32, const int *__restrict__ src_start, CellGrid3 cg,
+                              int *__restrict__ count, const int *__restrict__ coinc_start, int *__restrict__ coinc_src)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N)
+        return;
+    const int packed = tgt_base[k];
+    const int key = cg.key(b3x(packed) / cg.cell, b3y(packed) / cg.cell, b3z(packed) / cg.cell);
+    const float4 t = tgt_p32[k];
+    const int S3 = cg.sub3();
+    int c = 0, at = coinc_src ? coinc_start[k] : 0;
+    for (int j = src_start[key * S3]; j < src_start[(key + 1) * S3]; ++j) {
+        const float4 sp = src_p32[j];
+        if (sp.x == t.x && sp.y == t.y && sp.z == t.z) {
+            if (coinc_src)
+                coinc_src[at++] = j;
+            ++c;
+        }
+    }
+    if (!coinc_src)
+        count[k] = c;
 }
 
 template <typename real>
@@ -337,13 +512,13 @@ cudaError_t launch_point_keys3(const double *xyz, int64_t n, double s, int n_os,
 
 template <typename real>
 cudaError_t launch_gather_points3(const double *xyz, const int *perm, int64_t n, double s, int n_os, int window_lo,
-                                  int n_a, int m, int cell, double *pos, real *frac, int *base, float4 *pos32,
-                                  int *status, cudaStream_t st)
+                                  int n_a, int m, int cell, double inv_eps, double *pos, real *frac, int *base,
+                                  float4 *pos32, int *status, cudaStream_t st)
 {
     if (n <= 0)
         return cudaSuccess;
-    k_gather_points3<real><<<nblk(n, 256), 256, 0, st>>>(xyz, perm, n, s, n_os, window_lo, n_a, m, cell, pos, frac,
-                                                        base, pos32, status);
+    k_gather_points3<real><<<nblk(n, 256), 256, 0, st>>>(xyz, perm, n, s, n_os, window_lo, n_a, m, cell, inv_eps, pos,
+                                                        frac, base, pos32, status);
     return cudaGetLastError();
 }
 
@@ -376,15 +551,40 @@ cudaError_t launch_interp3(int64_t N, int m, const int *base, const real *frac, 
     });
 }
 
-template <typename real>
-cudaError_t launch_near3(int64_t N, const int *tgt_base, const double *tgt_pos, const float4 *tgt_p32,
-                         const double *src_pos, const float4 *src_p32, const int *src_start, CellGrid3 cg,
-                         const real *q, NearParams<real> np, real *phi_s, real *grad_s, cudaStream_t st)
+cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,
+                             const int *src_start, CellGrid3 cg, const double *q, NearParams<double> np,
+                             double *phi_s, double *grad_s, cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
-    k_near3<real><<<nblk(N, 256), 256, 0, st>>>(N, tgt_base, tgt_pos, tgt_p32, src_pos, src_p32, src_start, cg, q, np,
-                                               phi_s, grad_s);
+    k_near3_f64<<<nblk(N, 256), 256, 0, st>>>(N, tgt_base, tgt_pos, src_pos, src_start, cg, q, np, phi_s, grad_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_base, const float4 *tgt_p32,
+                              const float4 *src_p32, const float *q, const int *src_start, CellGrid3 cg,
+                              const Near3Params &np, const int *coinc_start, const int *coinc_src, float *phi_s,
+                              float *grad_s, cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_items + kNear3Warps - 1) / kNear3Warps);
+    return with_degree(np.p, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        k_near3_warp<P><<<blocks, kNear3Warps * 32, 0, st>>>(items, n_items, tgt_base, tgt_p32, src_p32, q, src_start,
+                                                              cg, np, coinc_start, coinc_src, phi_s, grad_s);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const float4 *tgt_p32, const float4 *src_p32,
+                               const int *src_start, CellGrid3 cg, int *count, const int *coinc_start, int *coinc_src,
+                               cudaStream_t st)
+{
+    if (N <= 0)
+        return cudaSuccess;
+    k_coincident3<<<nblk(N, 256), 256, 0, st>>>(N, tgt_base, tgt_p32, src_p32, src_start, cg, count, coinc_start,
+                                                coinc_src);
     return cudaGetLastError();
 }
 
@@ -400,16 +600,13 @@ cudaError_t launch_unpermute3(int64_t N, const real *phi_s, const real *grad_s, 
 
 #define FS_INST3(real)                                                                                            \
     template cudaError_t launch_gather_points3<real>(const double *, const int *, int64_t, double, int, int, int, \
-                                                     int, int, double *, real *, int *, float4 *, int *,          \
+                                                     int, int, double, double *, real *, int *, float4 *, int *,  \
                                                      cudaStream_t);                                               \
     template cudaError_t launch_spread3<real>(int64_t, int, const int *, const real *, const real *, Window<real>, \
                                               const WindowPoly &, real *, int, cudaStream_t);                     \
     template cudaError_t launch_interp3<real>(int64_t, int, const int *, const real *, Window<real>,               \
                                               const WindowPoly &, const real *, int, real, real *, real *,        \
                                               cudaStream_t);                                                      \
-    template cudaError_t launch_near3<real>(int64_t, const int *, const double *, const float4 *, const double *,  \
-                                            const float4 *, const int *, CellGrid3, const real *, NearParams<real>, \
-                                            real *, real *, cudaStream_t);                                        \
     template cudaError_t launch_unpermute3<real>(int64_t, const real *, const real *, const int *, double, void *, \
                                                  void *, int, cudaStream_t);
 FS_INST3(float)

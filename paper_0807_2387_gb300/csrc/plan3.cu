@@ -38,6 +38,10 @@ struct fs3_plan {
     void *q_sorted = nullptr;
     double *q_sum = nullptr;
     int nrhs = 0, nrhs_cap = 0;
+    // FP32 near field: warp items and the coincident-source lists of the targets
+    int2 *near_items = nullptr;
+    int n_near_items = 0;
+    int *coinc_start = nullptr, *coinc_src = nullptr;
     // tetrahedral FEM plans: sources are the quadrature points, targets the nodes
     bool is_fem = false;
     int64_t Nv = 0, Nt = 0, Nf = 0;
@@ -138,13 +142,14 @@ template <typename real> fs_status twiddles3(fs3_plan *pl, int L, void **out)
     return FS_OK;
 }
 
+fs_status near_setup3(fs3_plan *pl);
+
 template <typename real> NearParams<real> make_near3(const fs3_plan *pl)
 {
     NearParams<real> np{};
     np.p = pl->p;
     np.eps2 = (real)(pl->eps_I * pl->eps_I);
     np.inv_eps2 = (real)(1.0 / (pl->eps_I * pl->eps_I));
-    np.hcell = (real)((double)pl->cg.cell / pl->n_os);
     for (int k = 0; k < pl->p; ++k)
         np.beta[k] = (real)pl->kp.beta[k];
     for (int k = 1; k < pl->p; ++k)
@@ -181,7 +186,7 @@ fs_status bin3(fs3_plan *pl, const double *xyz, int64_t n, int **perm, int **bas
     FS_CUDA(cudaMemcpyAsync(fill, *start, sizeof(int) * ((size_t)n_keys + 1), cudaMemcpyDeviceToDevice, st));
     FS_CUDA(launch_scatter(key, n, fill, *perm, st));
     FS_CUDA(launch_gather_points3<real>(xyz, *perm, n, pl->s, pl->n_os, pl->window_lo, pl->n_a, pl->m, pl->cg.cell,
-                                        *pos, fr, *base, *p32, pl->status, st));
+                                        1.0 / pl->eps_I, *pos, fr, *base, *p32, pl->status, st));
     FS_CUDA(cudaStreamSynchronize(st));
     pl->release(key);
     pl->release(count);
@@ -222,6 +227,16 @@ fs_status plan3_init(fs3_plan *pl, const double *src, int64_t M, const double *t
     pl->n_a = n_a;
     pl->cg.cell = std::max(1, (int)std::ceil(pl->eps_I * L - 1e-9));
     pl->cg.n_c = (n_a + pl->cg.cell - 1) / pl->cg.cell;
+    // sub-cells (FP32 near field: compact warp items) while the sort keys stay below 2^24
+    pl->cg.sub = 1;
+    if (pl->precision == 32)
+        for (int sub : {4, 2})
+            if ((int64_t)pl->cg.n_c * pl->cg.n_c * pl->cg.n_c * sub * sub * sub <= (int64_t)1 << 24) {
+                pl->cg.sub = sub;
+                break;
+            }
+    if ((int64_t)pl->cg.n_c * pl->cg.n_c * pl->cg.n_c * pl->cg.sub3() > (int64_t)1 << 24)
+        return fail(FS_EINVAL, "too many near-field cells (eps_I too small for this grid)");
     FS_TRY(pl->alloc(&pl->status, 1));
     FS_CUDA(cudaMemset(pl->status, 0, sizeof(int)));
     FS_TRY(bin3<real>(pl, src, M, &pl->src_perm, &pl->src_base, &pl->src_frac, &pl->src_pos, &pl->src_p32,
@@ -232,6 +247,8 @@ fs_status plan3_init(fs3_plan *pl, const double *src, int64_t M, const double *t
     FS_CUDA(cudaMemcpy(&dev_status, pl->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (dev_status != 0)
         return fail(FS_EDOMAIN, "a point fell outside the admissible radius after scaling");
+    if (pl->precision == 32)
+        FS_TRY(near_setup3(pl));
     // kernel regularisation (FP64): T_I and the boundary form's data at 1/2 - eps_B
     KernelParams &kp = pl->kp;
     kp.eps_I = pl->eps_I;
@@ -300,6 +317,75 @@ fs_status plan3_init(fs3_plan *pl, const double *src, int64_t M, const double *t
     pl->phi_s = ph;
     pl->grad_s = gr;
     return FS_OK;
+}
+
+// FP32 near field: warp items (at most 64 consecutive targets of one cell, split evenly) and,
+// per target, the sources at exactly the same FP32 offsets (coincident pairs).
+fs_status near_setup3(fs3_plan *pl)
+{
+    cudaStream_t st = pl->stream;
+    if (pl->N > ((int64_t)1 << 24))
+        return fail(FS_EINVAL, "FP32 3D plans take at most 2^24 targets");
+    const int n_cells = pl->cg.n_cells(), S3 = pl->cg.sub3();
+    std::vector<int> start((size_t)pl->cg.n_keys() + 1);
+    FS_CUDA(cudaMemcpyAsync(start.data(), pl->tgt_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int2> items;
+    for (int c = 0; c < n_cells; ++c) {
+        const int a = start[(size_t)c * S3], b = start[(size_t)(c + 1) * S3];
+        const int cnt = b - a;
+        if (cnt <= 0)
+            continue;
+        const int pieces = (cnt + 63) / 64;
+        for (int k = 0; k < pieces; ++k) {
+            const int lo = a + (int)((int64_t)cnt * k / pieces), hi = a + (int)((int64_t)cnt * (k + 1) / pieces);
+            items.push_back(make_int2(lo, hi - lo));
+        }
+    }
+    pl->n_near_items = (int)items.size();
+    FS_TRY(pl->alloc(&pl->near_items, items.size()));
+    if (!items.empty())
+        FS_CUDA(cudaMemcpyAsync(pl->near_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                                st));
+    // coincident sources: count, scan, fill
+    const int64_t N = pl->N;
+    int *count = nullptr, *tmp = nullptr;
+    FS_TRY(pl->alloc(&count, (size_t)std::max<int64_t>(N, 1)));
+    FS_TRY(pl->alloc(&pl->coinc_start, (size_t)N + 1));
+    FS_TRY(pl->alloc(&tmp, (size_t)N / 4096 + 2));
+    FS_CUDA(cudaMemsetAsync(pl->coinc_start, 0, sizeof(int) * ((size_t)N + 1), st));
+    FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_p32, pl->src_p32, pl->src_start, pl->cg, count, nullptr,
+                               nullptr, st));
+    if (N > 0)
+        FS_CUDA(launch_exclusive_scan(count, pl->coinc_start, (int)N, tmp, st));
+    int total = 0;
+    FS_CUDA(cudaMemcpyAsync(&total, pl->coinc_start + N, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    FS_TRY(pl->alloc(&pl->coinc_src, (size_t)std::max(total, 1)));
+    if (total > 0)
+        FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_p32, pl->src_p32, pl->src_start, pl->cg, nullptr,
+                                   pl->coinc_start, pl->coinc_src, st));
+    FS_CUDA(cudaStreamSynchronize(st));
+    pl->release(count);
+    pl->release(tmp);
+    return FS_OK;
+}
+
+Near3Params make_near3_f32(const fs3_plan *pl)
+{
+    Near3Params np{};
+    const double eps = pl->eps_I;
+    np.p = pl->p;
+    np.H = (float)((double)pl->cg.cell / pl->n_os / eps);
+    np.reach2 = (float)((1.0 + 2e-4) * (1.0 + 2e-4));
+    np.c1 = (float)(1.0 / (4.0 * kPi * eps));
+    np.inv_eps = (float)(1.0 / eps);
+    np.beta0 = (float)pl->kp.beta[0];
+    for (int k = 0; k < pl->p; ++k)
+        np.nbeta[k] = (float)(-pl->kp.beta[k]);
+    for (int k = 0; k + 1 < pl->p; ++k)
+        np.dbeta2[k] = (float)(2.0 * (k + 1) * pl->kp.beta[k + 1]);
+    return np;
 }
 
 // Boundary faces (used by one tetrahedron) as (i0 < i1 < i2, fourth node), sorted by the triple.
@@ -392,7 +478,8 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
     using C = typename Cplx<real>::type;
     cudaStream_t st = pl->stream;
     const Window<real> w = make_window<real>(pl->sigma, pl->m);
-    const NearParams<real> np = make_near3<real>(pl);
+    const NearParams<double> np = make_near3<double>(pl);
+    const Near3Params np32 = sizeof(real) == 4 ? make_near3_f32(pl) : Near3Params{};
     const size_t osz = dtype == FS_F64 ? 8 : 4;
     const size_t cube = (size_t)pl->n_a * pl->n_a * pl->n_a;
     for (int r = 0; r < pl->nrhs; ++r) {
@@ -405,8 +492,13 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
         FS_CUDA(launch_interp3<real>(pl->N, pl->m, pl->tgt_base, (const real *)pl->tgt_frac, w, pl->wpoly,
                                      (const real *)pl->grid, pl->n_a, (real)pl->n_os, (real *)pl->phi_s,
                                      (real *)pl->grad_s, st));
-        FS_CUDA(launch_near3<real>(pl->N, pl->tgt_base, pl->tgt_pos, pl->tgt_p32, pl->src_pos, pl->src_p32,
-                                   pl->src_start, pl->cg, q, np, (real *)pl->phi_s, (real *)pl->grad_s, st));
+        if constexpr (sizeof(real) == 4)
+            FS_CUDA(launch_near3_warp(pl->near_items, pl->n_near_items, pl->tgt_base, pl->tgt_p32, pl->src_p32,
+                                      (const float *)q, pl->src_start, pl->cg, np32, pl->coinc_start, pl->coinc_src,
+                                      (float *)pl->phi_s, (float *)pl->grad_s, st));
+        else
+            FS_CUDA(launch_near3_f64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
+                                     (const double *)q, np, (double *)pl->phi_s, (double *)pl->grad_s, st));
         void *po = phi ? (unsigned char *)phi + (size_t)r * pl->N * osz : nullptr;
         void *ho = H ? (unsigned char *)H + (size_t)r * pl->N * 3 * osz : nullptr;
         FS_CUDA(launch_unpermute3<real>(pl->N, (const real *)pl->phi_s, (const real *)pl->grad_s, pl->tgt_perm, pl->s,
