@@ -152,6 +152,7 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
         for (int r = 0; r < R; ++r)
             qj[r] = __ldg(q + r * q_stride + j);
     }
+    __device__ __forceinline__ void set_q(float v) { qj[0] = v; }   // candidate-list traversal (R = 1)
     __device__ __forceinline__ void coincident(const NearParams<float> &np, int t)
     {
 #pragma unroll
@@ -355,7 +356,7 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
         op.q_stride = 0;
         op.n_stride = 0;
         op.rcoef = np.rcoef;
-        return launch_near_warp(n_items, items, sd, cg, np, op, st);
+        return launch_near_list(n_items, items, sd, cg, np, q, op, st);
     });
 }
 

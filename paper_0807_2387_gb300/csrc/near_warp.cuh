@@ -328,6 +328,228 @@ template <class Op> cudaError_t launch_near_warp(int64_t n_items, const int2 *it
     return cudaGetLastError();
 }
 
+// ---- candidate-list traversal (single-charge operations: the forward near field)
+//
+// The same items, boxes and sub-cell culling as near_traverse, but sources are not evaluated
+// where they are found.  The lanes read the sources of an accepted sub-cell 32 at a time,
+// test each against the box (ballot) and append those within reach to the warp's lists in
+// shared memory: "far" candidates (beyond eps_I/8 of the box: no pair can need the refined
+// difference) pre-shifted into the item's cell frame and negated, (-x, -x, -y, -y) with the
+// charge; "close" candidates with their hi and lo parts and the cell step, for the refined
+// path.  A list is evaluated when it fills and at the end: one shared broadcast load per
+// candidate, no per-source test or vote in the far loop.  Partial sums are kept per list
+// evaluation (op.row_begin / row_end).
+constexpr int kListCap = 256;    // far candidates per warp
+constexpr int kCloseCap = 64;    // close candidates per warp
+
+template <class Op>
+__device__ __forceinline__ void near_eval_far(const float4 *s_xy, const float *s_q, int n, float2 X, float2 Y,
+                                              const NearParams<float> &np, Op &op)
+{
+    op.row_begin();
+#pragma unroll(Op::kUnroll)
+    for (int e = 0; e < n; ++e) {
+        const float4 a = s_xy[e];
+        op.set_q(s_q[e]);
+        const float2 dx = add2(X, make_float2(a.x, a.y));
+        const float2 dy = add2(Y, make_float2(a.z, a.w));
+        op.pair2(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
+    }
+    op.row_end();
+}
+
+template <class Op>
+__device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float4 *s_cl, int n,
+                                                const float2 (&xh)[2], const float2 (&xl)[2],
+                                                const NearParams<float> &np, Op &op)
+{
+    op.row_begin();
+    for (int e = 0; e < n; ++e) {
+        const float4 c = s_cxy[e], l = s_cl[e];   // (yh.x, yh.y, offx, offy), (yl.x, yl.y, q, 0)
+        op.set_q(l.z);
+        float2 dx = make_float2(xh[0].x + c.z - c.x, xh[1].x + c.z - c.x);
+        float2 dy = make_float2(xh[0].y + c.w - c.y, xh[1].y + c.w - c.y);
+        float2 r2 = fma2(dy, dy, mul2(dx, dx));
+        const bool c0 = r2.x < np.close2, c1 = r2.y < np.close2;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (t == 0 ? c0 : c1) {
+                const float ex = refine_diff(xh[t].x, c.x, c.z, xl[t].x, l.x);
+                const float ey = refine_diff(xh[t].y, c.y, c.w, xl[t].y, l.y);
+                float e2 = ex * ex + ey * ey;
+                if (ex == 0.f && ey == 0.f) {
+                    op.coincident(np, t);
+                    e2 = np.eps2;                 // masked out: w = 1
+                }
+                if (t == 0) {
+                    dx.x = ex;
+                    dy.x = ey;
+                    r2.x = e2;
+                } else {
+                    dx.y = ex;
+                    dy.y = ey;
+                    r2.y = e2;
+                }
+            }
+        }
+        op.pair2(np, r2, dx, dy);
+    }
+    op.row_end();
+}
+
+template <class Op>
+__device__ __forceinline__ void near_traverse_list(int2 item, int lane, const NearSides &sd, const CellGrid &cg,
+                                                   const NearParams<float> &np, const float *__restrict__ q, Op &op,
+                                                   float4 *s_xy, float *s_q, float4 *s_cxy, float4 *s_cl)
+{
+    const float h = np.hcell, eps = sqrtf(np.eps2);
+    const float ginv = h / (float)cg.cell;
+    bool valid[2];
+    int64_t kt[2];
+    int cc1[2], cc2[2];
+    float2 xh[2], xl[2];
+    float tx0 = 3e38f, tx1 = -3e38f, ty0 = 3e38f, ty1 = -3e38f;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        valid[t] = lane + 32 * t < item.y;
+        kt[t] = item.x + lane + 32 * t;
+        const int64_t kk = valid[t] ? kt[t] : item.x;
+        const int packed = sd.own_base[kk];
+        cc1[t] = base1(packed) / cg.cell;
+        cc2[t] = base2(packed) / cg.cell;
+        xh[t] = sd.own_hi[kk];
+        xl[t] = sd.own_lo[kk];
+        if (valid[t]) {
+            const float ax = (float)cc1[t] * h + xh[t].x, ay = (float)cc2[t] * h + xh[t].y;
+            tx0 = fminf(tx0, ax);
+            tx1 = fmaxf(tx1, ax);
+            ty0 = fminf(ty0, ay);
+            ty1 = fmaxf(ty1, ay);
+        }
+    }
+    tx0 = warp_min(tx0);
+    tx1 = warp_max(tx1);
+    ty0 = warp_min(ty0);
+    ty1 = warp_max(ty1);
+    const int c1 = cc1[0], c2 = cc2[0];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (!valid[t])
+            xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
+    const float2 X = make_float2(xh[0].x, xh[1].x), Y = make_float2(xh[0].y, xh[1].y);
+    const float margin = 1e-4f * eps + 1e-5f;
+    const float reach = eps + margin;
+    const float reach2 = reach * reach;
+    const float close_reach = sqrtf(np.close2) + margin;
+    const float close_reach2 = close_reach * close_reach;
+    const int cx0 = max(0, (int)floorf((tx0 - reach) / h)), cx1 = min(cg.n_c - 1, (int)floorf((tx1 + reach) / h));
+    const int cy0 = max(0, (int)floorf((ty0 - reach) / h)), cy1 = min(cg.n_c - 1, (int)floorf((ty1 + reach) / h));
+    const unsigned below = (1u << lane) - 1u;
+    int nf = 0, nc = 0;
+    op.init();
+    for (int ex = cx0; ex <= cx1; ++ex) {
+        const float offx = (float)(c1 - ex) * h;
+        const float sx0 = (float)ex * h;
+        for (int s1 = 0; s1 < kSubEdge; ++s1) {
+            const float lo = sx0 + (float)cg.sub_first(s1) * ginv, hi = sx0 + (float)cg.sub_first(s1 + 1) * ginv;
+            const float gapx = fmaxf(0.f, fmaxf(lo - tx1, tx0 - hi));
+            if (gapx > reach || !(hi > lo))
+                continue;
+            for (int ey = cy0; ey <= cy1; ++ey) {
+                const float offy = (float)(c2 - ey) * h;
+                const float sy0 = (float)ey * h;
+                const int kbase = cg.key(ex, ey) * kSub;
+                for (int s2 = 0; s2 < kSubEdge; ++s2) {
+                    const float ylo = sy0 + (float)cg.sub_first(s2) * ginv;
+                    const float yhi = sy0 + (float)cg.sub_first(s2 + 1) * ginv;
+                    const float gapy = fmaxf(0.f, fmaxf(ylo - ty1, ty0 - yhi));
+                    if (gapx * gapx + gapy * gapy > reach2)
+                        continue;
+                    const int sub = morton_sub(s1, s2);
+                    const int j0 = sd.oth_start[kbase + sub], j1 = sd.oth_start[kbase + sub + 1];
+                    for (int jb = j0; jb < j1; jb += 32) {
+                        const int j = jb + lane;
+                        const bool in = j < j1;
+                        float2 yh = make_float2(0.f, 0.f);
+                        float qv = 0.f;
+                        if (in) {
+                            yh = __ldg(sd.oth_hi + j);
+                            qv = __ldg(q + j);
+                        }
+                        const float ax = sx0 + yh.x, ay = sy0 + yh.y;
+                        const float gx = fmaxf(0.f, fmaxf(ax - tx1, tx0 - ax));
+                        const float gy = fmaxf(0.f, fmaxf(ay - ty1, ty0 - ay));
+                        const float g2 = gx * gx + gy * gy;
+                        const bool keep = in && g2 <= reach2;
+                        const bool close = keep && g2 <= close_reach2;
+                        const unsigned mf = __ballot_sync(0xffffffffu, keep && !close);
+                        const unsigned mc = __ballot_sync(0xffffffffu, close);
+                        if (keep && !close) {
+                            const int at = nf + __popc(mf & below);
+                            const float nx = offx - yh.x, ny = offy - yh.y;   // -(source in the item's frame)
+                            s_xy[at] = make_float4(nx, nx, ny, ny);
+                            s_q[at] = qv;
+                        }
+                        if (close) {
+                            const int at = nc + __popc(mc & below);
+                            const float2 yl = __ldg(sd.oth_lo + j);
+                            s_cxy[at] = make_float4(yh.x, yh.y, offx, offy);
+                            s_cl[at] = make_float4(yl.x, yl.y, qv, 0.f);
+                        }
+                        nf += __popc(mf);
+                        nc += __popc(mc);
+                        if (nf > kListCap - 32) {
+                            __syncwarp();
+                            near_eval_far(s_xy, s_q, nf, X, Y, np, op);
+                            nf = 0;
+                            __syncwarp();
+                        }
+                        if (nc > kCloseCap - 32) {
+                            __syncwarp();
+                            near_eval_close(s_cxy, s_cl, nc, xh, xl, np, op);
+                            nc = 0;
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    near_eval_far(s_xy, s_q, nf, X, Y, np, op);
+    near_eval_close(s_cxy, s_cl, nc, xh, xl, np, op);
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (valid[t])
+            op.store(t, kt[t]);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(128, Op::kMinBlocks) k_near_list(int64_t n_items, const int2 *__restrict__ items,
+                                                                   NearSides sd, CellGrid cg, NearParams<float> np,
+                                                                   const float *__restrict__ q, Op op)
+{
+    __shared__ float4 s_xy[4][kListCap];
+    __shared__ float s_q[4][kListCap];
+    __shared__ float4 s_cxy[4][kCloseCap], s_cl[4][kCloseCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_items)
+        return;                                   // whole warp past the end; no block-wide barrier follows
+    near_traverse_list(items[warp], lane, sd, cg, np, q, op, s_xy[w], s_q[w], s_cxy[w], s_cl[w]);
+}
+
+template <class Op> cudaError_t launch_near_list(int64_t n_items, const int2 *items, const NearSides &sd, CellGrid cg,
+                                                 const NearParams<float> &np, const float *q, const Op &op,
+                                                 cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_items + 3) / 4);
+    k_near_list<Op><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, q, op);
+    return cudaGetLastError();
+}
+
 // Calls f(std::integral_constant<int, P>) for the expansion degree p in 1..16.
 template <class F> cudaError_t with_degree(int p, F &&f)
 {
