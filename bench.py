@@ -161,8 +161,8 @@ def algorithmic_bytes(info, n_points):
 # the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
 # reports null until it is re-captured).
 NEAR_TRAFFIC = {
-    # profiles/dram_per_kernel_mixture_2p19.md: 28.32 MB per launch at 2^19 points, scaled by the point count
-    "9fd32b6a234f72e689b7bea3198e855167cd383a9565fa3de5862ffba4f03738": 2 * 28.32e6,
+    # profiles/k_near_list_mixture_2p19.md: 27.81 MB per launch at 2^19 points, scaled by the point count
+    "f7b1b4ec50b85830c76f9d5a5afc9f14180bba19530ff44f8960dc9cbdb41020": 2 * (27809280 + 768),
 }
 
 
@@ -527,7 +527,7 @@ def run_ours(args):
         traffic, sha = near_traffic()
         if args.traffic is not None:
             traffic = args.traffic
-        roof = {"kernel": f"k_near_warp<NearFwd<{info['p']},1>>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
+        roof = {"kernel": f"k_near_list<NearFwd<{info['p']},1,0>>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
                 "kernel_source_sha256": sha[:16],
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",

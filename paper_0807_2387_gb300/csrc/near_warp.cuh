@@ -330,9 +330,11 @@ template <class Op> cudaError_t launch_near_warp(int64_t n_items, const int2 *it
 
 // ---- candidate-list traversal (single-charge operations: the forward near field)
 //
-// The same items, boxes and sub-cell culling as near_traverse, but sources are not evaluated
-// where they are found.  The lanes read the sources of an accepted sub-cell 32 at a time,
-// test each against the box (ballot) and append those within reach to the warp's lists in
+// The same items and boxes as near_traverse, but sources are not evaluated where they are
+// found.  The lanes read the sources of each neighbour cell within reach of the box 32 at a
+// time (a cell is one contiguous range: full chunks, where sub-cells would hold only a few
+// sources each), test each against the box (ballot) and append those within reach to the
+// warp's lists in
 // shared memory: "far" candidates (beyond eps_I/8 of the box: no pair can need the refined
 // difference) pre-shifted into the item's cell frame and negated, (-x, -x, -y, -y) with the
 // charge; "close" candidates with their hi and lo parts and the cell step, for the refined
@@ -403,7 +405,6 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                                                    float4 *s_xy, float *s_q, float4 *s_cxy, float4 *s_cl)
 {
     const float h = np.hcell, eps = sqrtf(np.eps2);
-    const float ginv = h / (float)cg.cell;
     bool valid[2];
     int64_t kt[2];
     int cc1[2], cc2[2];
@@ -447,70 +448,61 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
     const unsigned below = (1u << lane) - 1u;
     int nf = 0, nc = 0;
     op.init();
+    // whole neighbour cells (contiguous source ranges), read in full chunks of 32
     for (int ex = cx0; ex <= cx1; ++ex) {
         const float offx = (float)(c1 - ex) * h;
         const float sx0 = (float)ex * h;
-        for (int s1 = 0; s1 < kSubEdge; ++s1) {
-            const float lo = sx0 + (float)cg.sub_first(s1) * ginv, hi = sx0 + (float)cg.sub_first(s1 + 1) * ginv;
-            const float gapx = fmaxf(0.f, fmaxf(lo - tx1, tx0 - hi));
-            if (gapx > reach || !(hi > lo))
-                continue;
-            for (int ey = cy0; ey <= cy1; ++ey) {
-                const float offy = (float)(c2 - ey) * h;
-                const float sy0 = (float)ey * h;
-                const int kbase = cg.key(ex, ey) * kSub;
-                for (int s2 = 0; s2 < kSubEdge; ++s2) {
-                    const float ylo = sy0 + (float)cg.sub_first(s2) * ginv;
-                    const float yhi = sy0 + (float)cg.sub_first(s2 + 1) * ginv;
-                    const float gapy = fmaxf(0.f, fmaxf(ylo - ty1, ty0 - yhi));
-                    if (gapx * gapx + gapy * gapy > reach2)
-                        continue;
-                    const int sub = morton_sub(s1, s2);
-                    const int j0 = sd.oth_start[kbase + sub], j1 = sd.oth_start[kbase + sub + 1];
-                    for (int jb = j0; jb < j1; jb += 32) {
-                        const int j = jb + lane;
-                        const bool in = j < j1;
-                        float2 yh = make_float2(0.f, 0.f);
-                        float qv = 0.f;
-                        if (in) {
-                            yh = __ldg(sd.oth_hi + j);
-                            qv = __ldg(q + j);
-                        }
-                        const float ax = sx0 + yh.x, ay = sy0 + yh.y;
-                        const float gx = fmaxf(0.f, fmaxf(ax - tx1, tx0 - ax));
-                        const float gy = fmaxf(0.f, fmaxf(ay - ty1, ty0 - ay));
-                        const float g2 = gx * gx + gy * gy;
-                        const bool keep = in && g2 <= reach2;
-                        const bool close = keep && g2 <= close_reach2;
-                        const unsigned mf = __ballot_sync(0xffffffffu, keep && !close);
-                        const unsigned mc = __ballot_sync(0xffffffffu, close);
-                        if (keep && !close) {
-                            const int at = nf + __popc(mf & below);
-                            const float nx = offx - yh.x, ny = offy - yh.y;   // -(source in the item's frame)
-                            s_xy[at] = make_float4(nx, nx, ny, ny);
-                            s_q[at] = qv;
-                        }
-                        if (close) {
-                            const int at = nc + __popc(mc & below);
-                            const float2 yl = __ldg(sd.oth_lo + j);
-                            s_cxy[at] = make_float4(yh.x, yh.y, offx, offy);
-                            s_cl[at] = make_float4(yl.x, yl.y, qv, 0.f);
-                        }
-                        nf += __popc(mf);
-                        nc += __popc(mc);
-                        if (nf > kListCap - 32) {
-                            __syncwarp();
-                            near_eval_far(s_xy, s_q, nf, X, Y, np, op);
-                            nf = 0;
-                            __syncwarp();
-                        }
-                        if (nc > kCloseCap - 32) {
-                            __syncwarp();
-                            near_eval_close(s_cxy, s_cl, nc, xh, xl, np, op);
-                            nc = 0;
-                            __syncwarp();
-                        }
-                    }
+        const float gapx = fmaxf(0.f, fmaxf(sx0 - tx1, tx0 - (sx0 + h)));
+        for (int ey = cy0; ey <= cy1; ++ey) {
+            const float offy = (float)(c2 - ey) * h;
+            const float sy0 = (float)ey * h;
+            const float gapy = fmaxf(0.f, fmaxf(sy0 - ty1, ty0 - (sy0 + h)));
+            if (gapx * gapx + gapy * gapy > reach2)
+                continue;                           // the whole cell is beyond reach (warp-uniform)
+            const int kbase = cg.key(ex, ey) * kSub;
+            const int j0 = sd.oth_start[kbase], j1 = sd.oth_start[kbase + kSub];
+            for (int jb = j0; jb < j1; jb += 32) {
+                const int j = jb + lane;
+                const bool in = j < j1;
+                float2 yh = make_float2(0.f, 0.f);
+                float qv = 0.f;
+                if (in) {
+                    yh = __ldg(sd.oth_hi + j);
+                    qv = __ldg(q + j);
+                }
+                const float ax = sx0 + yh.x, ay = sy0 + yh.y;
+                const float gx = fmaxf(0.f, fmaxf(ax - tx1, tx0 - ax));
+                const float gy = fmaxf(0.f, fmaxf(ay - ty1, ty0 - ay));
+                const float g2 = gx * gx + gy * gy;
+                const bool keep = in && g2 <= reach2;
+                const bool close = keep && g2 <= close_reach2;
+                const unsigned mf = __ballot_sync(0xffffffffu, keep && !close);
+                const unsigned mc = __ballot_sync(0xffffffffu, close);
+                if (keep && !close) {
+                    const int at = nf + __popc(mf & below);
+                    const float nx = offx - yh.x, ny = offy - yh.y;   // -(source in the item's frame)
+                    s_xy[at] = make_float4(nx, nx, ny, ny);
+                    s_q[at] = qv;
+                }
+                if (close) {
+                    const int at = nc + __popc(mc & below);
+                    const float2 yl = __ldg(sd.oth_lo + j);
+                    s_cxy[at] = make_float4(yh.x, yh.y, offx, offy);
+                    s_cl[at] = make_float4(yl.x, yl.y, qv, 0.f);
+                }
+                nf += __popc(mf);
+                nc += __popc(mc);
+                if (nf > kListCap - 32) {
+                    __syncwarp();
+                    near_eval_far(s_xy, s_q, nf, X, Y, np, op);
+                    nf = 0;
+                    __syncwarp();
+                }
+                if (nc > kCloseCap - 32) {
+                    __syncwarp();
+                    near_eval_close(s_cxy, s_cl, nc, xh, xl, np, op);
+                    nc = 0;
+                    __syncwarp();
                 }
             }
         }
