@@ -161,8 +161,8 @@ def algorithmic_bytes(info, n_points):
 # the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
 # reports null until it is re-captured).
 NEAR_TRAFFIC = {
-    # profiles/k_near_list_mixture_2p19.md: 27.81 MB per launch at 2^19 points, scaled by the point count
-    "f7b1b4ec50b85830c76f9d5a5afc9f14180bba19530ff44f8960dc9cbdb41020": 2 * (27809280 + 768),
+    # profiles/k_near_list_mixture_2p19.md: 27.75 MB per launch at 2^19 points, scaled by the point count
+    "891f1e2b2f5ff3f8d581a01de39e9af44dac33a9c6fabc59c1be0e3a1899c7e4": 2 * (27749120 + 768),
 }
 
 

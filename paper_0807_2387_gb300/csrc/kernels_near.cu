@@ -152,7 +152,20 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
         for (int r = 0; r < R; ++r)
             qj[r] = __ldg(q + r * q_stride + j);
     }
-    __device__ __forceinline__ void set_q(float v) { qj[0] = v; }   // candidate-list traversal (R = 1)
+    // candidate-list traversal: the R charges of source j, and those of a listed candidate
+    static constexpr int kR = R;
+    __device__ __forceinline__ void fetch(int j, float (&v)[R]) const
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            v[r] = __ldg(q + r * q_stride + j);
+    }
+    __device__ __forceinline__ void set_q(const float *v)
+    {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            qj[r] = v[r];
+    }
     __device__ __forceinline__ void coincident(const NearParams<float> &np, int t)
     {
 #pragma unroll
@@ -244,7 +257,7 @@ struct NearCount {
 };
 
 // Batched FP32 near field: one warp per item (first target, count, instance); all R
-// right-hand sides in one traversal.
+// right-hand sides in one candidate-list traversal.
 template <int P, int R>
 __global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_near32(int64_t n_items,
                                                                                const int4 *__restrict__ items,
@@ -267,7 +280,9 @@ __global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_
     op.q_stride = b.M;
     op.n_stride = b.N;
     op.rcoef = np.rcoef;
-    near_traverse(make_int2(it.x, it.y), lane, sd, cg, np, op);
+    __shared__ NearLists<R> L;
+    const int w = threadIdx.x >> 5;
+    near_traverse_list(make_int2(it.x, it.y), lane, sd, cg, np, op, L.xy[w], L.q[w], L.cxy[w], L.cl[w], L.cq[w]);
 }
 
 template <typename real>
@@ -356,7 +371,7 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
         op.q_stride = 0;
         op.n_stride = 0;
         op.rcoef = np.rcoef;
-        return launch_near_list(n_items, items, sd, cg, np, q, op, st);
+        return launch_near_list(n_items, items, sd, cg, np, op, st);
     });
 }
 

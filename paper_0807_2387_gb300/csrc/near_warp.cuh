@@ -352,7 +352,7 @@ __device__ __forceinline__ void near_eval_far(const float4 *s_xy, const float *s
 #pragma unroll(Op::kUnroll)
     for (int e = 0; e < n; ++e) {
         const float4 a = s_xy[e];
-        op.set_q(s_q[e]);
+        op.set_q(s_q + e * Op::kR);
         const float2 dx = add2(X, make_float2(a.x, a.y));
         const float2 dy = add2(Y, make_float2(a.z, a.w));
         op.pair2(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
@@ -361,14 +361,15 @@ __device__ __forceinline__ void near_eval_far(const float4 *s_xy, const float *s
 }
 
 template <class Op>
-__device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float4 *s_cl, int n,
+__device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float2 *s_cl, const float *s_cq, int n,
                                                 const float2 (&xh)[2], const float2 (&xl)[2],
                                                 const NearParams<float> &np, Op &op)
 {
     op.row_begin();
     for (int e = 0; e < n; ++e) {
-        const float4 c = s_cxy[e], l = s_cl[e];   // (yh.x, yh.y, offx, offy), (yl.x, yl.y, q, 0)
-        op.set_q(l.z);
+        const float4 c = s_cxy[e];                // (yh.x, yh.y, offx, offy)
+        const float2 l = s_cl[e];                 // (yl.x, yl.y)
+        op.set_q(s_cq + e * Op::kR);
         float2 dx = make_float2(xh[0].x + c.z - c.x, xh[1].x + c.z - c.x);
         float2 dy = make_float2(xh[0].y + c.w - c.y, xh[1].y + c.w - c.y);
         float2 r2 = fma2(dy, dy, mul2(dx, dx));
@@ -401,9 +402,10 @@ __device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float
 
 template <class Op>
 __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const NearSides &sd, const CellGrid &cg,
-                                                   const NearParams<float> &np, const float *__restrict__ q, Op &op,
-                                                   float4 *s_xy, float *s_q, float4 *s_cxy, float4 *s_cl)
+                                                   const NearParams<float> &np, Op &op, float4 *s_xy, float *s_q,
+                                                   float4 *s_cxy, float2 *s_cl, float *s_cq)
 {
+    constexpr int R = Op::kR;
     const float h = np.hcell, eps = sqrtf(np.eps2);
     bool valid[2];
     int64_t kt[2];
@@ -465,10 +467,13 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                 const int j = jb + lane;
                 const bool in = j < j1;
                 float2 yh = make_float2(0.f, 0.f);
-                float qv = 0.f;
+                float qv[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    qv[r] = 0.f;
                 if (in) {
                     yh = __ldg(sd.oth_hi + j);
-                    qv = __ldg(q + j);
+                    op.fetch(j, qv);
                 }
                 const float ax = sx0 + yh.x, ay = sy0 + yh.y;
                 const float gx = fmaxf(0.f, fmaxf(ax - tx1, tx0 - ax));
@@ -482,13 +487,17 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                     const int at = nf + __popc(mf & below);
                     const float nx = offx - yh.x, ny = offy - yh.y;   // -(source in the item's frame)
                     s_xy[at] = make_float4(nx, nx, ny, ny);
-                    s_q[at] = qv;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        s_q[at * R + r] = qv[r];
                 }
                 if (close) {
                     const int at = nc + __popc(mc & below);
-                    const float2 yl = __ldg(sd.oth_lo + j);
                     s_cxy[at] = make_float4(yh.x, yh.y, offx, offy);
-                    s_cl[at] = make_float4(yl.x, yl.y, qv, 0.f);
+                    s_cl[at] = __ldg(sd.oth_lo + j);
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        s_cq[at * R + r] = qv[r];
                 }
                 nf += __popc(mf);
                 nc += __popc(mc);
@@ -500,7 +509,7 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                 }
                 if (nc > kCloseCap - 32) {
                     __syncwarp();
-                    near_eval_close(s_cxy, s_cl, nc, xh, xl, np, op);
+                    near_eval_close(s_cxy, s_cl, s_cq, nc, xh, xl, np, op);
                     nc = 0;
                     __syncwarp();
                 }
@@ -509,36 +518,42 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
     }
     __syncwarp();
     near_eval_far(s_xy, s_q, nf, X, Y, np, op);
-    near_eval_close(s_cxy, s_cl, nc, xh, xl, np, op);
+    near_eval_close(s_cxy, s_cl, s_cq, nc, xh, xl, np, op);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
         if (valid[t])
             op.store(t, kt[t]);
 }
 
+// Per-warp lists of a 4-warp block (R charges per candidate).
+template <int R> struct NearLists {
+    float4 xy[4][kListCap];
+    float q[4][kListCap * R];
+    float4 cxy[4][kCloseCap];
+    float2 cl[4][kCloseCap];
+    float cq[4][kCloseCap * R];
+};
+
 template <class Op>
 __global__ void __launch_bounds__(128, Op::kMinBlocks) k_near_list(int64_t n_items, const int2 *__restrict__ items,
                                                                    NearSides sd, CellGrid cg, NearParams<float> np,
-                                                                   const float *__restrict__ q, Op op)
+                                                                   Op op)
 {
-    __shared__ float4 s_xy[4][kListCap];
-    __shared__ float s_q[4][kListCap];
-    __shared__ float4 s_cxy[4][kCloseCap], s_cl[4][kCloseCap];
+    __shared__ NearLists<Op::kR> L;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (warp >= n_items)
         return;                                   // whole warp past the end; no block-wide barrier follows
-    near_traverse_list(items[warp], lane, sd, cg, np, q, op, s_xy[w], s_q[w], s_cxy[w], s_cl[w]);
+    near_traverse_list(items[warp], lane, sd, cg, np, op, L.xy[w], L.q[w], L.cxy[w], L.cl[w], L.cq[w]);
 }
 
 template <class Op> cudaError_t launch_near_list(int64_t n_items, const int2 *items, const NearSides &sd, CellGrid cg,
-                                                 const NearParams<float> &np, const float *q, const Op &op,
-                                                 cudaStream_t st)
+                                                 const NearParams<float> &np, const Op &op, cudaStream_t st)
 {
     if (n_items <= 0)
         return cudaSuccess;
     const unsigned blocks = (unsigned)((n_items + 3) / 4);
-    k_near_list<Op><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, q, op);
+    k_near_list<Op><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, op);
     return cudaGetLastError();
 }
 
