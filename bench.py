@@ -161,8 +161,8 @@ def algorithmic_bytes(info, n_points):
 # the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
 # reports null until it is re-captured).
 NEAR_TRAFFIC = {
-    # profiles/k_near_list_mixture_2p19.md: 27.75 MB per launch at 2^19 points, scaled by the point count
-    "891f1e2b2f5ff3f8d581a01de39e9af44dac33a9c6fabc59c1be0e3a1899c7e4": 2 * (27749120 + 768),
+    # profiles/k_near_list_mixture_2p19.md: 27.77 MB per launch at 2^19 points, scaled by the point count
+    "b329bc8abd3974da49bc4d2051818f73b45954ca6d3c846ff6dbf50c1314b203": 2 * (27765504 + 1024),
 }
 
 

@@ -231,7 +231,10 @@ template <int P> struct NearHess32 {
     float2 gx, gy, sI, sxx, sxy, syy;
 
     __device__ __forceinline__ void init() { gx = gy = sI = sxx = sxy = syy = f2(0.f); }
-    __device__ __forceinline__ void load(int j) { qj = __ldg(q + j); }
+    // candidate-list traversal: one value per other point (its charge)
+    static constexpr int kR = 1;
+    __device__ __forceinline__ void fetch(int j, float (&v)[1]) const { v[0] = __ldg(q + j); }
+    __device__ __forceinline__ void set_q(const float *v) { qj = v[0]; }
     __device__ __forceinline__ void coincident(const NearParams<float> &, int t) { add_comp(sI, t, -qj * self_c); }
     __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
@@ -283,10 +286,19 @@ template <int P> struct NearAdj32 {
     float2 af, ac, gxc, gyc, gxk, gyk, gco;
 
     __device__ __forceinline__ void init() { af = ac = gxc = gyc = gxk = gyk = gco = f2(0.f); }
-    __device__ __forceinline__ void load(int i)
+    // candidate-list traversal: three values per other point (gphi and the dipole dn)
+    static constexpr int kR = 3;
+    __device__ __forceinline__ void fetch(int i, float (&v)[3]) const
     {
-        gp = __ldg(cw + i);
-        dn = __ldg(dnw + i);
+        const float2 d = __ldg(dnw + i);
+        v[0] = __ldg(cw + i);
+        v[1] = d.x;
+        v[2] = d.y;
+    }
+    __device__ __forceinline__ void set_q(const float *v)
+    {
+        gp = v[0];
+        dn = make_float2(v[1], v[2]);
     }
     __device__ __forceinline__ void coincident(const NearParams<float> &np, int t)
     {
@@ -443,7 +455,7 @@ cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src
         op.rcoef = np.rcoef;
         op.two_over_eps2 = 2.f * np.inv_eps2;
         op.self_c = self_hessian(np) / np.rcoef;
-        return launch_near_warp(n_items, items, sd, cg, np, op, st);
+        return launch_near_list(n_items, items, sd, cg, np, op, st);
     });
 }
 
@@ -461,7 +473,7 @@ cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tg
         op.rcoef = np.rcoef;
         op.two_over_eps2 = 2.f * np.inv_eps2;
         op.self_c = self_hessian(np) / np.rcoef;
-        return launch_near_warp(n_items, items, sd, cg, np, op, st);
+        return launch_near_list(n_items, items, sd, cg, np, op, st);
     });
 }
 

@@ -146,12 +146,6 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
         for (int r = 0; r < R; ++r)
             phi[r] = gx[r] = gy[r] = qc[r] = f2(0.f);
     }
-    __device__ __forceinline__ void load(int j)
-    {
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            qj[r] = __ldg(q + r * q_stride + j);
-    }
     // candidate-list traversal: the R charges of source j, and those of a listed candidate
     static constexpr int kR = R;
     __device__ __forceinline__ void fetch(int j, float (&v)[R]) const
@@ -232,7 +226,9 @@ struct NearCount {
     unsigned n_near, n_close;
 
     __device__ __forceinline__ void init() { n_near = n_close = 0; }
-    __device__ __forceinline__ void load(int) {}
+    static constexpr int kR = 1;   // candidate-list traversal: no values per other point
+    __device__ __forceinline__ void fetch(int, float (&v)[1]) const { v[0] = 0.f; }
+    __device__ __forceinline__ void set_q(const float *) {}
     __device__ __forceinline__ void coincident(const NearParams<float> &, int)
     {
         ++n_near;
@@ -399,7 +395,7 @@ cudaError_t launch_near_count32(int64_t n_items, const int2 *items, const int *t
     const NearSides sd{tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start};
     NearCount op{};
     op.counts = counts;
-    return launch_near_warp(n_items, items, sd, cg, np, op, st);
+    return launch_near_list(n_items, items, sd, cg, np, op, st);
 }
 
 cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchInst<float> *inst, int p, int nrhs,

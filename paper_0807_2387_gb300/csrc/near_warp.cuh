@@ -1,17 +1,17 @@
 // Warp-cooperative FP32 near-field traversal, shared by the forward correction
-// (phi and grad phi at the targets), the Hessian of phi at the targets and the
-// adjoint potential at the sources.
+// (phi and grad phi at the targets; one or several charge vectors), the Hessian of phi at
+// the targets, the adjoint potential at the sources and the plan's pair statistics.
 //
 // A work item is at most 64 consecutive "own" points of one cell (two per lane),
-// sorted by cell and, inside a cell, by 8 x 8 sub-cell in Morton order.  The warp
-// forms the bounding box of its points and visits only the "other" side's
-// sub-cells whose distance to that box is below eps_I (a warp-uniform test per
-// sub-cell).  Each other point there is read once per warp (a broadcast load) and
-// evaluated by all 32 lanes with branch-free masked arithmetic.  Positions are
-// FP32 offsets from the cell corner stored as hi + lo; pairs closer than eps_I / 8
-// refine their difference with an exact TwoSum of the hi parts plus the lo parts,
-// so r keeps full FP32 relative accuracy for nearly coincident points, and exactly
-// coincident pairs are detected (G(0) := 0).
+// sorted by cell and, inside a cell, by 8 x 8 sub-cell in Morton order, so the item is
+// compact.  The warp forms the bounding box of its points, reads the "other" points of the
+// neighbour cells within eps_I of that box 32 at a time, keeps those within eps_I of the box
+// (ballot) and appends them to candidate lists in shared memory, which all 32 lanes then
+// evaluate with branch-free masked arithmetic against both of their points.  Positions are
+// FP32 offsets from the cell corner stored as hi + lo; candidates within eps_I / 8 of the box
+// go to a second list whose pairs closer than eps_I / 8 refine their difference with an exact
+// TwoSum of the hi parts plus the lo parts, so r keeps full FP32 relative accuracy for nearly
+// coincident points, and exactly coincident pairs are detected (G(0) := 0).
 //
 // With w = r^2 / eps_I^2 and f = G - T_I (T_I the inner polynomial of the
 // regularised kernel, p-fold contact with G at r = eps_I):
@@ -164,183 +164,22 @@ struct NearSides {
     const int *oth_start;
 };
 
-// Sources of one sub-cell [j0, j1) against the lane's two points (X, Y: packed x and y
-// coordinates shifted by the cell step).  With CLOSE, pairs closer than eps_I/8 refine their
-// difference exactly (taken warp-uniformly when any lane needs it) and coincident pairs are
-// reported to the operation; without, the sub-cell is known to hold no such pair.
-template <bool CLOSE, class Op>
-__device__ __forceinline__ void near_run(int j0, int j1, const NearSides &sd, const NearParams<float> &np, float2 X,
-                                         float2 Y, const float2 (&xh)[2], const float2 (&xl)[2], float offx,
-                                         float offy, Op &op)
-{
-#pragma unroll(Op::kUnroll)
-    for (int j = j0; j < j1; ++j) {
-        const float2 yh = __ldg(sd.oth_hi + j);
-        op.load(j);
-        float2 dx = add2(X, f2(-yh.x));
-        float2 dy = add2(Y, f2(-yh.y));
-        float2 r2 = fma2(dy, dy, mul2(dx, dx));
-        if constexpr (CLOSE) {
-            const bool c0 = r2.x < np.close2, c1 = r2.y < np.close2;
-            if (__any_sync(0xffffffffu, c0 || c1)) {
-                const float2 yl = __ldg(sd.oth_lo + j);
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    if (t == 0 ? c0 : c1) {
-                        const float ex = refine_diff(xh[t].x, yh.x, offx, xl[t].x, yl.x);
-                        const float ey = refine_diff(xh[t].y, yh.y, offy, xl[t].y, yl.y);
-                        float e2 = ex * ex + ey * ey;
-                        if (ex == 0.f && ey == 0.f) {
-                            op.coincident(np, t);
-                            e2 = np.eps2;                 // masked out: w = 1
-                        }
-                        if (t == 0) {
-                            dx.x = ex;
-                            dy.x = ey;
-                            r2.x = e2;
-                        } else {
-                            dx.y = ex;
-                            dy.y = ey;
-                            r2.y = e2;
-                        }
-                    }
-                }
-            }
-        }
-        op.pair2(np, r2, dx, dy);
-    }
-}
-
-// One warp work item.  Op provides kMinBlocks (launch bound), kUnroll (unrolling of the
-// per-source loop), init(), load(j) (the other point's weights),
-// coincident(np, t) (slot t = 0, 1 coincides with the current other point), pair2(np, r2,
-// dx, dy) (both slots packed; pairs with r2 >= eps_I^2 must contribute nothing),
-// row_begin(), row_end() (partial sums per sub-cell row), store(t, k).
-template <class Op>
-__device__ __forceinline__ void near_traverse(int2 item, int lane, const NearSides &sd, const CellGrid &cg,
-                                              const NearParams<float> &np, Op &op)
-{
-    const float h = np.hcell, eps = sqrtf(np.eps2);
-    const float ginv = h / (float)cg.cell;        // one grid line (1 / n_os)
-    bool valid[2];
-    int64_t kt[2];
-    int cc1[2], cc2[2];
-    float2 xh[2], xl[2];
-    float tx0 = 3e38f, tx1 = -3e38f, ty0 = 3e38f, ty1 = -3e38f;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        valid[t] = lane + 32 * t < item.y;
-        kt[t] = item.x + lane + 32 * t;
-        const int64_t kk = valid[t] ? kt[t] : item.x;
-        const int packed = sd.own_base[kk];
-        cc1[t] = base1(packed) / cg.cell;
-        cc2[t] = base2(packed) / cg.cell;
-        xh[t] = sd.own_hi[kk];
-        xl[t] = sd.own_lo[kk];
-        if (valid[t]) {
-            const float ax = (float)cc1[t] * h + xh[t].x, ay = (float)cc2[t] * h + xh[t].y;
-            tx0 = fminf(tx0, ax);
-            tx1 = fmaxf(tx1, ax);
-            ty0 = fminf(ty0, ay);
-            ty1 = fmaxf(ty1, ay);
-        }
-    }
-    // bounding box of the warp's points, in "cell * h + offset" coordinates
-    tx0 = warp_min(tx0);
-    tx1 = warp_max(tx1);
-    ty0 = warp_min(ty0);
-    ty1 = warp_max(ty1);
-    // all points of an item share one cell
-    const int c1 = cc1[0], c2 = cc2[0];
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-        if (!valid[t])
-            xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
-    // culling radii: eps_I (and eps_I / 8) plus a margin that covers the FP32 rounding of the
-    // box and sub-cell bounds (~1e-7 torus units) a hundred times over
-    const float margin = 1e-4f * eps + 1e-5f;
-    const float reach = eps + margin;
-    const float reach2 = reach * reach;
-    const float close_reach = sqrtf(np.close2) + margin;
-    const float close_reach2 = close_reach * close_reach;
-    const int cx0 = max(0, (int)floorf((tx0 - reach) / h)), cx1 = min(cg.n_c - 1, (int)floorf((tx1 + reach) / h));
-    const int cy0 = max(0, (int)floorf((ty0 - reach) / h)), cy1 = min(cg.n_c - 1, (int)floorf((ty1 + reach) / h));
-    op.init();
-    for (int ex = cx0; ex <= cx1; ++ex) {
-        const float offx = (float)(c1 - ex) * h;
-        const float sx0 = (float)ex * h;
-        const float2 X = make_float2(xh[0].x + offx, xh[1].x + offx);
-        for (int s1 = 0; s1 < kSubEdge; ++s1) {
-            // gap between this sub-cell row and the points' box (warp-uniform)
-            const float lo = sx0 + (float)cg.sub_first(s1) * ginv, hi = sx0 + (float)cg.sub_first(s1 + 1) * ginv;
-            const float gapx = fmaxf(0.f, fmaxf(lo - tx1, tx0 - hi));
-            if (gapx > reach || !(hi > lo))
-                continue;
-            op.row_begin();
-            for (int ey = cy0; ey <= cy1; ++ey) {
-                const float offy = (float)(c2 - ey) * h;
-                const float sy0 = (float)ey * h;
-                const float2 Y = make_float2(xh[0].y + offy, xh[1].y + offy);
-                const int kbase = cg.key(ex, ey) * kSub;
-                for (int s2 = 0; s2 < kSubEdge; ++s2) {
-                    const float ylo = sy0 + (float)cg.sub_first(s2) * ginv;
-                    const float yhi = sy0 + (float)cg.sub_first(s2 + 1) * ginv;
-                    const float gapy = fmaxf(0.f, fmaxf(ylo - ty1, ty0 - yhi));
-                    const float gap2 = gapx * gapx + gapy * gapy;
-                    if (gap2 > reach2)
-                        continue;                 // no point of this warp is within eps_I of the sub-cell
-                    const int sub = morton_sub(s1, s2);
-                    const int j0 = sd.oth_start[kbase + sub], j1 = sd.oth_start[kbase + sub + 1];
-                    if (gap2 < close_reach2)
-                        near_run<true>(j0, j1, sd, np, X, Y, xh, xl, offx, offy, op);
-                    else
-                        near_run<false>(j0, j1, sd, np, X, Y, xh, xl, offx, offy, op);
-                }
-            }
-            op.row_end();
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-        if (valid[t])
-            op.store(t, kt[t]);
-}
-
-template <class Op>
-__global__ void __launch_bounds__(128, Op::kMinBlocks) k_near_warp(int64_t n_items, const int2 *__restrict__ items,
-                                                                   NearSides sd, CellGrid cg, NearParams<float> np,
-                                                                   Op op)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (warp >= n_items)
-        return;                                   // whole warp past the end (warp-uniform)
-    near_traverse(items[warp], lane, sd, cg, np, op);
-}
-
-template <class Op> cudaError_t launch_near_warp(int64_t n_items, const int2 *items, const NearSides &sd, CellGrid cg,
-                                                 const NearParams<float> &np, const Op &op, cudaStream_t st)
-{
-    if (n_items <= 0)
-        return cudaSuccess;
-    const unsigned blocks = (unsigned)((n_items + 3) / 4);
-    k_near_warp<Op><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, op);
-    return cudaGetLastError();
-}
-
-// ---- candidate-list traversal (single-charge operations: the forward near field)
+// ---- candidate-list traversal
 //
-// The same items and boxes as near_traverse, but sources are not evaluated where they are
-// found.  The lanes read the sources of each neighbour cell within reach of the box 32 at a
-// time (a cell is one contiguous range: full chunks, where sub-cells would hold only a few
-// sources each), test each against the box (ballot) and append those within reach to the
-// warp's lists in
-// shared memory: "far" candidates (beyond eps_I/8 of the box: no pair can need the refined
-// difference) pre-shifted into the item's cell frame and negated, (-x, -x, -y, -y) with the
-// charge; "close" candidates with their hi and lo parts and the cell step, for the refined
-// path.  A list is evaluated when it fills and at the end: one shared broadcast load per
-// candidate, no per-source test or vote in the far loop.  Partial sums are kept per list
-// evaluation (op.row_begin / row_end).
+// The lanes read the other points of each neighbour cell within reach of the box 32 at a time
+// (a cell is one contiguous range, so the chunks are full, where sub-cells would hold only a
+// few points each), test each against the box (ballot) and append those within reach to the
+// warp's lists in shared memory: "far" candidates (beyond eps_I / 8 of the box: no pair can
+// need the refined difference) shifted into the item's cell frame and negated,
+// (-x, -x, -y, -y), with their Op::kR values (charges, or the adjoint's weights); "close"
+// candidates with their hi and lo parts and the cell step, for the refined path.  A list is
+// evaluated when it fills and at the end: one shared broadcast load per candidate and no
+// per-candidate test or vote in the far loop.  Partial sums are kept per list evaluation
+// (op.row_begin / row_end).  An Op provides kMinBlocks, kUnroll, kR, init(), fetch(j, v)
+// (the kR values of other point j), set_q(v) (those of the current candidate),
+// coincident(np, t) (slot t = 0, 1 coincides with it), pair2(np, r2, dx, dy) (both slots
+// packed; pairs with r2 >= eps_I^2 must contribute nothing), row_begin(), row_end() and
+// store(t, k).
 constexpr int kListCap = 256;    // far candidates per warp
 constexpr int kCloseCap = 64;    // close candidates per warp
 
