@@ -67,6 +67,8 @@ struct CellGrid3 {
 struct Near3Params {
     float H;               // cell edge / eps_I (>= 1)
     float reach2;          // squared culling radius, 1 plus a rounding margin
+    float close_reach2;    // squared radius of the close list, 1/8 plus a rounding margin
+    double inv_eps_d;      // 1 / eps_I, for the FP64 differences of close pairs
     float c1;              // 1 / (4 pi eps_I)
     float inv_eps;         // 1 / eps_I
     float beta0;           // T_I(0), removed for coincident pairs (G(0) := 0)
@@ -95,14 +97,15 @@ cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_p
                              const int *src_start, CellGrid3 cg, const double *q, NearParams<double> np,
                              double *phi_s, double *grad_s, cudaStream_t st);
 // FP32 near field over warp items {first target, count <= 64} of one cell each (sorted order);
-// coincident pairs (equal FP32 offsets) are listed per target in coinc_start / coinc_src
+// coincident pairs (equal positions) are listed per target in coinc_start / coinc_src
+// (pairs closer than eps_I / 8 refine their difference from the FP64 positions tgt_pos, src_pos)
 cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_base, const float4 *tgt_p32,
-                              const float4 *src_p32, const float *q, const int *src_start, CellGrid3 cg,
-                              const Near3Params &np, const int *coinc_start, const int *coinc_src, float *phi_s,
-                              float *grad_s, cudaStream_t st);
-// per target: count of sources with the same FP32 offsets in the same cell (coinc_src null), or
+                              const float4 *src_p32, const double *tgt_pos, const double *src_pos, const float *q,
+                              const int *src_start, CellGrid3 cg, const Near3Params &np, const int *coinc_start,
+                              const int *coinc_src, float *phi_s, float *grad_s, cudaStream_t st);
+// per target: count of sources at the same FP64 position (same cell) when coinc_src is null, or
 // their sorted indices from coinc_start (coinc_src given)
-cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const float4 *tgt_p32, const float4 *src_p32,
+cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,
                                const int *src_start, CellGrid3 cg, int *count, const int *coinc_start, int *coinc_src,
                                cudaStream_t st);
 template <typename real>

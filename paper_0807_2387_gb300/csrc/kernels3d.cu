@@ -272,9 +272,11 @@ __global__ void __launch_bounds__(256) k_near3_f64(int64_t N, const int *__restr
 // all lanes against both of their targets as packed FP32 pairs: no branch, pairs outside
 // 0 < w < 1 get charge 0 (an integer compare of the bits of w: 0 < w < 1 iff
 // bits(w) - 1 < bits(1) - 1 as unsigned), and coincident pairs (w = 0) are accounted from the
-// per-target lists built with the plan.
+// per-target lists built with the plan.  Sources within eps_I / 8 of the box go to a second
+// list, whose pairs closer than eps_I / 8 take their difference from the FP64 positions.
 constexpr int kNear3Warps = 4;
-constexpr int kNear3Cap = 256;   // candidate list entries per warp (32 B each)
+constexpr int kNear3Cap = 256;        // far candidate entries per warp (32 B each)
+constexpr int kNear3CloseCap = 64;    // close candidate entries per warp (32 B + index)
 constexpr int kNear3Unroll = 2;
 
 __device__ __forceinline__ float rsqrt_approx(float x)
@@ -290,11 +292,41 @@ __device__ __forceinline__ float in_range(float w, float q)
     return (__float_as_uint(w) - 1u) < 0x3f7fffffu ? q : 0.f;
 }
 
+// The packed pair arithmetic for one candidate at (w, dx, dy, dz) (units of eps_I).
+template <int P>
+__device__ __forceinline__ void near3_pair(const Near3Params &np, float2 w, float2 dx, float2 dy, float2 dz,
+                                           float2 qq, float2 &phi, float2 &gx, float2 &gy, float2 &gz)
+{
+    const float2 c1 = make_float2(np.c1, np.c1);
+    const float2 qe = make_float2(in_range(w.x, qq.x), in_range(w.y, qq.y));
+    // w = 0 only for coincident pairs (charge 0 here): floor w so that w^-3/2 stays finite
+    // (distinct points give w >= ~1e-14, far above the floor)
+    const float2 rs = make_float2(rsqrt_approx(fmaxf(w.x, 1e-20f)), rsqrt_approx(fmaxf(w.y, 1e-20f)));
+    float2 t = make_float2(np.nbeta[P - 1], np.nbeta[P - 1]);
+#pragma unroll
+    for (int i = P - 2; i >= 0; --i)
+        t = __ffma2_rn(t, w, make_float2(np.nbeta[i], np.nbeta[i]));
+    float2 u = make_float2(0.f, 0.f);
+    if constexpr (P >= 2) {
+        u = make_float2(np.dbeta2[P - 2], np.dbeta2[P - 2]);
+#pragma unroll
+        for (int i = P - 3; i >= 0; --i)
+            u = __ffma2_rn(u, w, make_float2(np.dbeta2[i], np.dbeta2[i]));
+    }
+    const float2 val = __ffma2_rn(c1, rs, t);                                  // c1 w^-1/2 - P(w)
+    const float2 gc = __ffma2_rn(c1, __fmul2_rn(__fmul2_rn(rs, rs), rs), u);   // c1 w^-3/2 + 2 P'(w)
+    phi = __ffma2_rn(qe, val, phi);
+    const float2 qc = __fmul2_rn(qe, gc);
+    gx = __ffma2_rn(qc, dx, gx);
+    gy = __ffma2_rn(qc, dy, gy);
+    gz = __ffma2_rn(qc, dz, gz);
+}
+
+// Far candidates: no pair can be closer than eps_I / 8.
 template <int P>
 __device__ __forceinline__ void near3_eval(const float4 (*list)[2], int n, float2 X, float2 Y, float2 Z,
                                            const Near3Params &np, float2 &phi, float2 &gx, float2 &gy, float2 &gz)
 {
-    const float2 c1 = make_float2(np.c1, np.c1);
 #pragma unroll kNear3Unroll
     for (int e = 0; e < n; ++e) {
         const float4 A = list[e][0], B = list[e][1];
@@ -302,28 +334,52 @@ __device__ __forceinline__ void near3_eval(const float4 (*list)[2], int n, float
         const float2 dy = __fadd2_rn(Y, make_float2(-A.z, -A.w));
         const float2 dz = __fadd2_rn(Z, make_float2(-B.x, -B.y));
         const float2 w = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        const float2 qe = make_float2(in_range(w.x, B.z), in_range(w.y, B.w));
-        // w = 0 only for coincident pairs (charge 0 here): floor w so that w^-3/2 stays finite
-        // (distinct FP32 offsets of size ~1 give w >= ~1e-14, far above the floor)
-        const float2 rs = make_float2(rsqrt_approx(fmaxf(w.x, 1e-20f)), rsqrt_approx(fmaxf(w.y, 1e-20f)));
-        float2 t = make_float2(np.nbeta[P - 1], np.nbeta[P - 1]);
+        near3_pair<P>(np, w, dx, dy, dz, make_float2(B.z, B.w), phi, gx, gy, gz);
+    }
+}
+
+// Close candidates (within eps_I / 8 of the box): pairs closer than eps_I / 8 take their
+// difference from the FP64 positions (the FP32 cell offsets lose relative precision as r
+// shrinks, and such pairs dominate H), then the same arithmetic.
+template <int P>
+__device__ __forceinline__ void near3_eval_close(const float4 (*list)[2], const int *jlist, int n, float2 X,
+                                                 float2 Y, float2 Z, const int (&kt)[2],
+                                                 const double *__restrict__ tgt_pos,
+                                                 const double *__restrict__ src_pos, const Near3Params &np,
+                                                 float2 &phi, float2 &gx, float2 &gy, float2 &gz)
+{
+    for (int e = 0; e < n; ++e) {
+        const float4 A = list[e][0], B = list[e][1];
+        float2 dx = __fadd2_rn(X, make_float2(-A.x, -A.y));
+        float2 dy = __fadd2_rn(Y, make_float2(-A.z, -A.w));
+        float2 dz = __fadd2_rn(Z, make_float2(-B.x, -B.y));
+        float2 w = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const bool c0 = w.x < 1.f / 64.f, c1 = w.y < 1.f / 64.f;
+        if (__any_sync(0xffffffffu, c0 || c1)) {
+            const int j = jlist[e];
 #pragma unroll
-        for (int i = P - 2; i >= 0; --i)
-            t = __ffma2_rn(t, w, make_float2(np.nbeta[i], np.nbeta[i]));
-        float2 u = make_float2(0.f, 0.f);
-        if constexpr (P >= 2) {
-            u = make_float2(np.dbeta2[P - 2], np.dbeta2[P - 2]);
-#pragma unroll
-            for (int i = P - 3; i >= 0; --i)
-                u = __ffma2_rn(u, w, make_float2(np.dbeta2[i], np.dbeta2[i]));
+            for (int t = 0; t < 2; ++t) {
+                if (t == 0 ? c0 : c1) {
+                    const int64_t k = kt[t];
+                    const float ex = (float)((tgt_pos[3 * k] - src_pos[3 * (int64_t)j]) * np.inv_eps_d);
+                    const float ey = (float)((tgt_pos[3 * k + 1] - src_pos[3 * (int64_t)j + 1]) * np.inv_eps_d);
+                    const float ez = (float)((tgt_pos[3 * k + 2] - src_pos[3 * (int64_t)j + 2]) * np.inv_eps_d);
+                    const float e2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                    if (t == 0) {
+                        dx.x = ex;
+                        dy.x = ey;
+                        dz.x = ez;
+                        w.x = e2;
+                    } else {
+                        dx.y = ex;
+                        dy.y = ey;
+                        dz.y = ez;
+                        w.y = e2;
+                    }
+                }
+            }
         }
-        const float2 val = __ffma2_rn(c1, rs, t);                                  // c1 w^-1/2 - P(w)
-        const float2 gc = __ffma2_rn(c1, __fmul2_rn(__fmul2_rn(rs, rs), rs), u);   // c1 w^-3/2 + 2 P'(w)
-        phi = __ffma2_rn(qe, val, phi);
-        const float2 qc = __fmul2_rn(qe, gc);
-        gx = __ffma2_rn(qc, dx, gx);
-        gy = __ffma2_rn(qc, dy, gy);
-        gz = __ffma2_rn(qc, dz, gz);
+        near3_pair<P>(np, w, dx, dy, dz, make_float2(B.z, B.w), phi, gx, gy, gz);
     }
 }
 
@@ -332,6 +388,8 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
                                                                  const int *__restrict__ tgt_base,
                                                                  const float4 *__restrict__ tgt_p32,
                                                                  const float4 *__restrict__ src_p32,
+                                                                 const double *__restrict__ tgt_pos,
+                                                                 const double *__restrict__ src_pos,
                                                                  const float *__restrict__ q,
                                                                  const int *__restrict__ src_start, CellGrid3 cg,
                                                                  Near3Params np, const int *__restrict__ coinc_start,
@@ -339,17 +397,22 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
                                                                  float *__restrict__ phi_s, float *__restrict__ grad_s)
 {
     __shared__ float4 lists[kNear3Warps][kNear3Cap][2];
+    __shared__ float4 clists[kNear3Warps][kNear3CloseCap][2];
+    __shared__ int cjs[kNear3Warps][kNear3CloseCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int item = blockIdx.x * kNear3Warps + warp;
     if (item >= n_items)
         return;   // whole warp; the kernel has no block-wide barrier
     float4(*list)[2] = lists[warp];
+    float4(*clist)[2] = clists[warp];
+    int *cj = cjs[warp];
     const int2 it = items[item];
     const int first = it.x, count = it.y;
     const bool va = lane < count, vb = lane + 32 < count;
     const int ka = va ? first + lane : first, kb = vb ? first + 32 + lane : ka;
     const float4 pa = tgt_p32[ka], pb = tgt_p32[kb];
     const float2 X = make_float2(pa.x, pb.x), Y = make_float2(pa.y, pb.y), Z = make_float2(pa.z, pb.z);
+    const int kt[2] = {ka, kb};
     const float lox = warp_min(fminf(pa.x, pb.x)), hix = warp_max(fmaxf(pa.x, pb.x));
     const float loy = warp_min(fminf(pa.y, pb.y)), hiy = warp_max(fmaxf(pa.y, pb.y));
     const float loz = warp_min(fminf(pa.z, pb.z)), hiz = warp_max(fmaxf(pa.z, pb.z));
@@ -357,7 +420,8 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
     const int c1 = b3x(packed) / cg.cell, c2 = b3y(packed) / cg.cell, c3 = b3z(packed) / cg.cell;
     const int S3 = cg.sub3();
     float2 phi = make_float2(0.f, 0.f), gx = phi, gy = phi, gz = phi;
-    int n = 0;
+    int n = 0, nc = 0;
+    const unsigned below = (1u << lane) - 1u;
     for (int e1 = max(c1 - 1, 0); e1 <= min(c1 + 1, cg.n_c - 1); ++e1) {
         const float o1 = (float)(e1 - c1) * np.H;
         const float bx = fmaxf(0.f, fmaxf(o1 - hix, lox - (o1 + np.H)));
@@ -373,7 +437,7 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
                 const int end = src_start[(key + 1) * S3];
                 for (int j0 = src_start[key * S3]; j0 < end; j0 += 32) {
                     const int j = j0 + lane;
-                    bool keep = false;
+                    bool keep = false, close = false;
                     float sx = 0.f, sy = 0.f, sz = 0.f, qj = 0.f;
                     if (j < end) {
                         const float4 sp = src_p32[j];
@@ -384,19 +448,35 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
                         const float dx = fmaxf(0.f, fmaxf(sx - hix, lox - sx));
                         const float dy = fmaxf(0.f, fmaxf(sy - hiy, loy - sy));
                         const float dz = fmaxf(0.f, fmaxf(sz - hiz, loz - sz));
-                        keep = dx * dx + dy * dy + dz * dz < np.reach2;
+                        const float g2 = dx * dx + dy * dy + dz * dz;
+                        keep = g2 < np.reach2;
+                        close = g2 < np.close_reach2;
                     }
-                    const unsigned mask = __ballot_sync(0xffffffffu, keep);
-                    if (keep) {
-                        const int at = n + __popc(mask & ((1u << lane) - 1u));
+                    const unsigned mf = __ballot_sync(0xffffffffu, keep && !close);
+                    const unsigned mc = __ballot_sync(0xffffffffu, close);
+                    if (keep && !close) {
+                        const int at = n + __popc(mf & below);
                         list[at][0] = make_float4(sx, sx, sy, sy);
                         list[at][1] = make_float4(sz, sz, qj, qj);
                     }
-                    n += __popc(mask);
+                    if (close) {
+                        const int at = nc + __popc(mc & below);
+                        clist[at][0] = make_float4(sx, sx, sy, sy);
+                        clist[at][1] = make_float4(sz, sz, qj, qj);
+                        cj[at] = j;
+                    }
+                    n += __popc(mf);
+                    nc += __popc(mc);
                     if (n > kNear3Cap - 32) {
                         __syncwarp();
                         near3_eval<P>(list, n, X, Y, Z, np, phi, gx, gy, gz);
                         n = 0;
+                        __syncwarp();
+                    }
+                    if (nc > kNear3CloseCap - 32) {
+                        __syncwarp();
+                        near3_eval_close<P>(clist, cj, nc, X, Y, Z, kt, tgt_pos, src_pos, np, phi, gx, gy, gz);
+                        nc = 0;
                         __syncwarp();
                     }
                 }
@@ -405,8 +485,8 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
     }
     __syncwarp();
     near3_eval<P>(list, n, X, Y, Z, np, phi, gx, gy, gz);
+    near3_eval_close<P>(clist, cj, nc, X, Y, Z, kt, tgt_pos, src_pos, np, phi, gx, gy, gz);
     // coincident pairs: G(0) := 0, so only -q T_I(0) remains of the far field's self term
-    const int kt[2] = {first + lane, first + 32 + lane};
     const bool vt[2] = {va, vb};
     const float ph[2] = {phi.x, phi.y}, ggx[2] = {gx.x, gx.y}, ggy[2] = {gy.x, gy.y}, ggz[2] = {gz.x, gz.y};
 #pragma unroll
@@ -424,9 +504,9 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
     }
 }
 
-// Coincident pairs: sources of the target's own cell with the same FP32 offsets.
-__global__ void k_coincident3(int64_t N, const int *__restrict__ tgt_base, const float4 *__restrict__ tgt_p32,
-                              const float4 *__restrict__ src_p32, const int *__restrict__ src_start, CellGrid3 cg,
+// Coincident pairs: sources of the target's own cell at the same (FP64) position.
+__global__ void k_coincident3(int64_t N, const int *__restrict__ tgt_base, const double *__restrict__ tgt_pos,
+                              const double *__restrict__ src_pos, const int *__restrict__ src_start, CellGrid3 cg,
                               int *__restrict__ count, const int *__restrict__ coinc_start, int *__restrict__ coinc_src)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -434,12 +514,11 @@ __global__ void k_coincident3(int64_t N, const int *__restrict__ tgt_base, const
         return;
     const int packed = tgt_base[k];
     const int key = cg.key(b3x(packed) / cg.cell, b3y(packed) / cg.cell, b3z(packed) / cg.cell);
-    const float4 t = tgt_p32[k];
+    const double tx = tgt_pos[3 * k], ty = tgt_pos[3 * k + 1], tz = tgt_pos[3 * k + 2];
     const int S3 = cg.sub3();
     int c = 0, at = coinc_src ? coinc_start[k] : 0;
     for (int j = src_start[key * S3]; j < src_start[(key + 1) * S3]; ++j) {
-        const float4 sp = src_p32[j];
-        if (sp.x == t.x && sp.y == t.y && sp.z == t.z) {
+        if (src_pos[3 * (int64_t)j] == tx && src_pos[3 * (int64_t)j + 1] == ty && src_pos[3 * (int64_t)j + 2] == tz) {
             if (coinc_src)
                 coinc_src[at++] = j;
             ++c;
@@ -562,28 +641,29 @@ cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_p
 }
 
 cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_base, const float4 *tgt_p32,
-                              const float4 *src_p32, const float *q, const int *src_start, CellGrid3 cg,
-                              const Near3Params &np, const int *coinc_start, const int *coinc_src, float *phi_s,
-                              float *grad_s, cudaStream_t st)
+                              const float4 *src_p32, const double *tgt_pos, const double *src_pos, const float *q,
+                              const int *src_start, CellGrid3 cg, const Near3Params &np, const int *coinc_start,
+                              const int *coinc_src, float *phi_s, float *grad_s, cudaStream_t st)
 {
     if (n_items <= 0)
         return cudaSuccess;
     const unsigned blocks = (unsigned)((n_items + kNear3Warps - 1) / kNear3Warps);
     return with_degree(np.p, [&](auto pc) {
         constexpr int P = decltype(pc)::value;
-        k_near3_warp<P><<<blocks, kNear3Warps * 32, 0, st>>>(items, n_items, tgt_base, tgt_p32, src_p32, q, src_start,
-                                                              cg, np, coinc_start, coinc_src, phi_s, grad_s);
+        k_near3_warp<P><<<blocks, kNear3Warps * 32, 0, st>>>(items, n_items, tgt_base, tgt_p32, src_p32, tgt_pos,
+                                                              src_pos, q, src_start, cg, np, coinc_start, coinc_src,
+                                                              phi_s, grad_s);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const float4 *tgt_p32, const float4 *src_p32,
+cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,
                                const int *src_start, CellGrid3 cg, int *count, const int *coinc_start, int *coinc_src,
                                cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
-    k_coincident3<<<nblk(N, 256), 256, 0, st>>>(N, tgt_base, tgt_p32, src_p32, src_start, cg, count, coinc_start,
+    k_coincident3<<<nblk(N, 256), 256, 0, st>>>(N, tgt_base, tgt_pos, src_pos, src_start, cg, count, coinc_start,
                                                 coinc_src);
     return cudaGetLastError();
 }

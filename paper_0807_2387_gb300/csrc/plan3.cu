@@ -354,7 +354,7 @@ fs_status near_setup3(fs3_plan *pl)
     FS_TRY(pl->alloc(&pl->coinc_start, (size_t)N + 1));
     FS_TRY(pl->alloc(&tmp, (size_t)N / 4096 + 2));
     FS_CUDA(cudaMemsetAsync(pl->coinc_start, 0, sizeof(int) * ((size_t)N + 1), st));
-    FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_p32, pl->src_p32, pl->src_start, pl->cg, count, nullptr,
+    FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, count, nullptr,
                                nullptr, st));
     if (N > 0)
         FS_CUDA(launch_exclusive_scan(count, pl->coinc_start, (int)N, tmp, st));
@@ -363,7 +363,7 @@ fs_status near_setup3(fs3_plan *pl)
     FS_CUDA(cudaStreamSynchronize(st));
     FS_TRY(pl->alloc(&pl->coinc_src, (size_t)std::max(total, 1)));
     if (total > 0)
-        FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_p32, pl->src_p32, pl->src_start, pl->cg, nullptr,
+        FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, nullptr,
                                    pl->coinc_start, pl->coinc_src, st));
     FS_CUDA(cudaStreamSynchronize(st));
     pl->release(count);
@@ -378,6 +378,8 @@ Near3Params make_near3_f32(const fs3_plan *pl)
     np.p = pl->p;
     np.H = (float)((double)pl->cg.cell / pl->n_os / eps);
     np.reach2 = (float)((1.0 + 2e-4) * (1.0 + 2e-4));
+    np.close_reach2 = (float)((0.125 + 2e-4) * (0.125 + 2e-4));
+    np.inv_eps_d = 1.0 / eps;
     np.c1 = (float)(1.0 / (4.0 * kPi * eps));
     np.inv_eps = (float)(1.0 / eps);
     np.beta0 = (float)pl->kp.beta[0];
@@ -494,8 +496,8 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
                                      (real *)pl->grad_s, st));
         if constexpr (sizeof(real) == 4)
             FS_CUDA(launch_near3_warp(pl->near_items, pl->n_near_items, pl->tgt_base, pl->tgt_p32, pl->src_p32,
-                                      (const float *)q, pl->src_start, pl->cg, np32, pl->coinc_start, pl->coinc_src,
-                                      (float *)pl->phi_s, (float *)pl->grad_s, st));
+                                      pl->tgt_pos, pl->src_pos, (const float *)q, pl->src_start, pl->cg, np32,
+                                      pl->coinc_start, pl->coinc_src, (float *)pl->phi_s, (float *)pl->grad_s, st));
         else
             FS_CUDA(launch_near3_f64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
                                      (const double *)q, np, (double *)pl->phi_s, (double *)pl->grad_s, st));

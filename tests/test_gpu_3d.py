@@ -1,7 +1,8 @@
 """GPU 3D plans (kernel 1/(4 pi r)) through the C ABI against the 3D oracle.
 
 * FP64 path vs oracle O3 (same algorithm in FP64): relative L2 <= 1e-12 for phi and H.
-* FP32 path vs FP64 path: relative L2 <= 2e-5 for phi and H.
+* FP32 path vs FP64 path: relative L2 <= 5e-6 for phi and H (pairs closer than eps_I / 8 take
+  their difference from the FP64 positions; without that H alone was off by ~1e-5).
 * Against the direct sum O1: the approximation error of the method (regularisation of
   1/r and window), which decreases with p.
 """
@@ -74,8 +75,8 @@ def test_3d_fp32_matches_fp64(pkg, seed, ns, nt, n, m, eps, coinc):
     src, tgt, q = case3(seed, ns, nt, coinc)
     phi64, H64, _ = gpu3(pkg, src, tgt, q, n, m, eps, 64)
     phi32, H32, _ = gpu3(pkg, src, tgt, q, n, m, eps, 32)
-    assert rel(phi32, phi64) <= 2e-5, rel(phi32, phi64)
-    assert rel(H32, H64) <= 2e-5, rel(H32, H64)
+    assert rel(phi32, phi64) <= 5e-6, rel(phi32, phi64)
+    assert rel(H32, H64) <= 5e-6, rel(H32, H64)
 
 
 def test_3d_approximation_error_against_direct_sum(pkg):
