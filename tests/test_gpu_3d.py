@@ -117,3 +117,25 @@ def test_3d_empty_sources_and_invalid_arguments(pkg):
         with pytest.raises(pkg.FastSumError) as e:
             pkg.FastSum3(t, t, *args)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 5e-6)])
+def test_3d_dense_pile_overflows_candidate_lists(pkg, precision, tol):
+    """600 sources within eps_I/20 of one point plus a sparse background: the close list (pairs below
+    eps_I/8, refined from the FP64 positions) refills many times; coincident targets included."""
+    from oracle import fastsum3 as F3
+    from oracle import kernel as K
+    rng = np.random.default_rng(18)
+    eps = 4 / 32
+    pile = 0.05 + rng.normal(0.0, eps / 80, (600, 3))
+    bg = rng.uniform(-0.15, 0.15, (300, 3))
+    src = np.concatenate([pile, bg])
+    tgt = np.concatenate([pile[:120], pile[:40] + 1e-7, rng.uniform(-0.15, 0.15, (80, 3))])
+    q = rng.standard_normal(len(src))
+    phi, H, _ = gpu3(pkg, src, tgt, q, 32, 4, eps, 64)
+    if precision == 64:
+        phi_o, H_o = F3.fast_sum3(src, tgt, q, K.make_params(32, 2.0, 4, eps), "nfft")
+    else:
+        phi_o, H_o = phi, H
+        phi, H, _ = gpu3(pkg, src, tgt, q, 32, 4, eps, 32)
+    assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))

@@ -437,3 +437,19 @@ def test_time_loop_fused_magnetisation(pkg, precision, tol):
         exact = 0.5 * (math.cos(a) * nodes[:, 0] + math.sin(a) * nodes[:, 1])
         assert np.max(np.abs(phi.cpu().numpy()[inner] - exact[inner])) < 5e-4
     fs.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 2e-5)])
+def test_dense_pile_overflows_candidate_lists(pkg, precision, tol):
+    """800 sources within eps_I/20 of one point plus a sparse background: every warp item there sees
+    hundreds of close candidates (the close list refills many times) and many far ones."""
+    rng = np.random.default_rng(17)
+    eps = 4 / 64
+    pile = 0.03 + rng.normal(0.0, eps / 80, (800, 2))
+    bg = rng.uniform(-0.2, 0.2, (400, 2))
+    src = np.concatenate([pile, bg])
+    tgt = np.concatenate([pile[:150], pile[:50] + 1e-7, rng.uniform(-0.2, 0.2, (100, 2))])
+    case = dict(src=src, tgt=tgt, q=rng.standard_normal(len(src)), n=64, sigma=2.0, m=5, eps_I=eps)
+    phi, H, _ = gpu_field(pkg, case, precision)
+    phi_o, H_o = oracle_field(case)
+    assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))
