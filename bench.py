@@ -348,6 +348,68 @@ def measure_fem_loop(pkg, dev, steps, warmup, flush):
             "interior_phi_max_err_vs_closed_form": err}
 
 
+FEM3_WORKLOAD = ("cube_tet_mesh: the cube [-1,1]^3 as 40^3 sub-cubes of 6 P1 tetrahedra (68,921 nodes, 384,000 "
+                 "tetrahedra; targets = nodes, sources = 4 points per tetrahedron + 3 per boundary face), interior "
+                 "nodes jittered by 0.1 h; kernel 1/(4 pi r); n=128 (oversampled 256^3), m=4, eps_I=3/128, p=3; FP32; "
+                 "M(t) = (cos a_t + x/5, sin a_t + y/5, 0.3), a new M every step")
+
+
+def measure_fem3_loop(pkg, dev, steps, warmup, flush):
+    """Time loop on one tetrahedral plan: per step fs3_set_magnetization + fs3_eval_field."""
+    import torch
+    from paper_0807_2387_gb300 import workloads as W
+    nodes_h, tets_h = W.cube_tet_mesh(np.random.default_rng(12), 40, 1.0, 0.1)
+    nodes = torch.tensor(nodes_h, device=dev)
+    tets = torch.tensor(tets_h, device=dev)
+    t0 = time.perf_counter()
+    fs = pkg.FastSum3.fem(nodes, tets, 128, 2.0, 4, 3 / 128, precision=32)
+    plan_s = time.perf_counter() - t0
+
+    def mag(k):
+        m = torch.empty_like(nodes)
+        m[:, 0] = math.cos(0.1 * k) + 0.2 * nodes[:, 0]
+        m[:, 1] = math.sin(0.1 * k) + 0.2 * nodes[:, 1]
+        m[:, 2] = 0.3
+        return m
+
+    mags = [mag(k) for k in range(steps + warmup)]
+    n = fs.info["n_tgt"]
+    phi = torch.empty(n, dtype=torch.float32, device=dev)
+    H = torch.empty((n, 3), dtype=torch.float32, device=dev)
+
+    def step(m):
+        pkg.fs3_set_magnetization(fs._h, m, 1)
+        pkg.fs3_eval_field(fs._h, phi, H)
+
+    for k in range(warmup):
+        step(mags[k])
+    fs.sync()
+    ms = []
+    for k in range(warmup, warmup + steps):
+        flush.zero_()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(mags[k])
+        z.record()
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(z))
+    fs.sync()
+    last = mags[warmup + steps - 1]
+    fs64 = pkg.FastSum3.fem(nodes, tets, 128, 2.0, 4, 3 / 128, precision=64)
+    fs64.set_magnetization(last)
+    p64, h64 = fs64.field(dtype=torch.float64)
+    fs64.sync()
+    fs64.close()
+    err = {"phi_rel_l2": float(torch.linalg.norm(phi.double() - p64) / torch.linalg.norm(p64)),
+           "H_rel_l2": float(torch.linalg.norm(H.double() - h64) / torch.linalg.norm(h64))}
+    info = fs.info
+    fs.close()
+    t = statistics.mean(ms)
+    return {"workload": FEM3_WORKLOAD, "nodes": n, "sources": info["n_src"], "ms_per_step": round(t, 4),
+            "value": 1e3 / t, "unit": "time steps/s (fs3_set_magnetization + fs3_eval_field)",
+            "plan_s": round(plan_s, 3), "fp32_vs_fp64": err}
+
+
 BALL_WORKLOAD = ("uniform_ball_3d: 2^18 sources + 2^18 targets uniform in the radius-0.25 ball, charges "
                  "N(0,1); kernel 1/(4 pi r); n=128 (oversampled 256^3), m=4, eps_I=3/128, p=3; FP32")
 
@@ -543,7 +605,7 @@ def run_ours(args):
         cpu, _ = cpu_baseline(work, args.cpu_targets)
 
     # the batched workload and the adjoint (one GPU; untimed by the headline value)
-    batch = adj = fftcmp = femloop = ball3d = None
+    batch = adj = fftcmp = femloop = ball3d = fem3 = None
     if world == 1 and not args.quick:
         ours = stage_ms["fft_rows_fwd"] + stage_ms["fft_cols_mul"] + stage_ms["fft_rows_inv"]
         fftcmp = {"cufft_r2c_c2r_full_grid_ms": round(measure_cufft(dev, info["n_os"], 10, flush), 4),
@@ -555,6 +617,7 @@ def run_ours(args):
         adj = measure_adjoint(pkg, dev, max(3, args.steps // 4), 3, flush)
         femloop = measure_fem_loop(pkg, dev, max(5, args.steps), 3, flush)
         ball3d = measure_3d(pkg, dev, max(5, args.steps // 2), 3, flush)
+        fem3 = measure_fem3_loop(pkg, dev, max(5, args.steps // 2), 3, flush)
 
     if world > 1:
         dist.barrier()
@@ -572,6 +635,7 @@ def run_ours(args):
             "near_pairs": info["near_pairs"], "near_pairs_fp64": info["near_pairs_fp64"],
             "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src},
             "batch_c4": batch, "adjoint_c3": adj, "fem_time_loop_c1": femloop, "kernel_3d": ball3d,
+            "fem3_time_loop": fem3,
             "fft_comparison": fftcmp,
         }
         print(json.dumps(out))
@@ -592,6 +656,8 @@ def run_only(args):
         out = measure_fem_loop(pkg, dev, args.steps, args.warmup, flush)
     elif args.only == "3d":
         out = measure_3d(pkg, dev, args.steps, args.warmup, flush)
+    elif args.only == "fem3":
+        out = measure_fem3_loop(pkg, dev, args.steps, args.warmup, flush)
     else:
         out = measure_adjoint(pkg, dev, args.steps, args.warmup, flush)
     print(json.dumps(out))
@@ -633,7 +699,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip accuracy, e2e and CPU baseline (profiling runs)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint measurements")
-    ap.add_argument("--only", choices=("batch", "adjoint", "fem", "3d"), default=None,
+    ap.add_argument("--only", choices=("batch", "adjoint", "fem", "3d", "fem3"), default=None,
                     help="run only the batched or the adjoint measurement and print its JSON object")
     ap.add_argument("--instances", type=int, default=64,
                     help="instances of the batched workload with --only batch (the first K of the 64)")

@@ -103,6 +103,14 @@ cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_bas
                               const float4 *src_p32, const double *tgt_pos, const double *src_pos, const float *q,
                               const int *src_start, CellGrid3 cg, const Near3Params &np, const int *coinc_start,
                               const int *coinc_src, float *phi_s, float *grad_s, cudaStream_t st);
+// Source-major FP32 near field (many more sources than targets): items of at most 64 sources of
+// one cell; phi and grad phi are added to the targets with atomics, then the coincident pairs'
+// -q T_I(0) when any_coincident
+cudaError_t launch_near3_src(const int2 *items, int n_items, const int *src_base, const float4 *src_p32,
+                             const float4 *tgt_p32, const double *tgt_pos, const double *src_pos, const float *q,
+                             const int *tgt_start, CellGrid3 cg, const Near3Params &np, int64_t N,
+                             const int *coinc_start, const int *coinc_src, bool any_coincident, float *phi_s,
+                             float *grad_s, cudaStream_t st);
 // per target: count of sources at the same FP64 position (same cell) when coinc_src is null, or
 // their sorted indices from coinc_start (coinc_src given)
 cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,

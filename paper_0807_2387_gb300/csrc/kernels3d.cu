@@ -504,6 +504,186 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
     }
 }
 
+// ---- FP32 near field, source-major (plans with many more sources than targets: FEM meshes,
+// where every node meets the quadrature points of several elements)
+//
+// Target items hold only the few targets of a cell, so their box is the whole cell and most
+// candidates lie beyond eps_I of most targets.  Here a warp takes an item of at most 64 sources
+// of one cell (compact: Morton sub-cell order) and keeps them in shared memory as packed pairs;
+// it reads the targets of the 27 cells around 32 at a time, keeps those within eps_I of the
+// sources' box (ballot) in a list (those within eps_I / 8 of the box in a second one), and
+// each lane then takes one listed target and sums the item's sources on it, two per packed
+// operation, adding phi and grad phi to the target with atomics.  Pairs closer than eps_I / 8
+// take their difference from the FP64 positions, as in k_near3_warp; coincident pairs are
+// removed by k_coincident3_apply.
+constexpr int kSrcListCap = 128;
+
+template <int P, bool CLOSE>
+__device__ __forceinline__ void near3_src_eval(const float4 (*spairs)[2], const float4 *tlist, int n, int first,
+                                               int count, float dummy, const double *__restrict__ tgt_pos,
+                                               const double *__restrict__ src_pos, const Near3Params &np,
+                                               float *__restrict__ phi_s, float *__restrict__ grad_s, int lane)
+{
+    for (int base = 0; base < n; base += 32) {
+        const int e = base + lane;
+        const bool valid = e < n;
+        const float4 T = valid ? tlist[e] : make_float4(dummy, dummy, dummy, 0.f);
+        const int k = __float_as_int(T.w);
+        const float2 X = make_float2(T.x, T.x), Y = make_float2(T.y, T.y), Z = make_float2(T.z, T.z);
+        float2 phi = make_float2(0.f, 0.f), gx = phi, gy = phi, gz = phi;
+#pragma unroll 2
+        for (int i = 0; i < 32; ++i) {
+            const float4 A = spairs[i][0], B = spairs[i][1];   // (xa, xb, ya, yb), (za, zb, qa, qb)
+            float2 dx = __fadd2_rn(X, make_float2(-A.x, -A.y));
+            float2 dy = __fadd2_rn(Y, make_float2(-A.z, -A.w));
+            float2 dz = __fadd2_rn(Z, make_float2(-B.x, -B.y));
+            float2 w = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            if constexpr (CLOSE) {
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    // (idle source slots, i + 32 t >= count, carry charge 0 and are not refined)
+                    if (valid && i + 32 * t < count && (t == 0 ? w.x : w.y) < 1.f / 64.f) {
+                        const int64_t j = first + i + 32 * t;
+                        const float ex = (float)((tgt_pos[3 * (int64_t)k] - src_pos[3 * j]) * np.inv_eps_d);
+                        const float ey = (float)((tgt_pos[3 * (int64_t)k + 1] - src_pos[3 * j + 1]) * np.inv_eps_d);
+                        const float ez = (float)((tgt_pos[3 * (int64_t)k + 2] - src_pos[3 * j + 2]) * np.inv_eps_d);
+                        const float e2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                        if (t == 0) {
+                            dx.x = ex;
+                            dy.x = ey;
+                            dz.x = ez;
+                            w.x = e2;
+                        } else {
+                            dx.y = ex;
+                            dy.y = ey;
+                            dz.y = ez;
+                            w.y = e2;
+                        }
+                    }
+                }
+            }
+            near3_pair<P>(np, w, dx, dy, dz, make_float2(B.z, B.w), phi, gx, gy, gz);
+        }
+        if (valid) {
+            atomicAdd(phi_s + k, phi.x + phi.y);
+            atomicAdd(grad_s + 3 * (int64_t)k, -np.inv_eps * (gx.x + gx.y));
+            atomicAdd(grad_s + 3 * (int64_t)k + 1, -np.inv_eps * (gy.x + gy.y));
+            atomicAdd(grad_s + 3 * (int64_t)k + 2, -np.inv_eps * (gz.x + gz.y));
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kNear3Warps * 32) k_near3_src(const int2 *__restrict__ items, int n_items,
+                                                                const int *__restrict__ src_base,
+                                                                const float4 *__restrict__ src_p32,
+                                                                const float4 *__restrict__ tgt_p32,
+                                                                const double *__restrict__ tgt_pos,
+                                                                const double *__restrict__ src_pos,
+                                                                const float *__restrict__ q,
+                                                                const int *__restrict__ tgt_start, CellGrid3 cg,
+                                                                Near3Params np, float *__restrict__ phi_s,
+                                                                float *__restrict__ grad_s)
+{
+    __shared__ float4 spairs_all[kNear3Warps][32][2];
+    __shared__ float4 flist_all[kNear3Warps][kSrcListCap];
+    __shared__ float4 clist_all[kNear3Warps][kSrcListCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = blockIdx.x * kNear3Warps + warp;
+    if (item >= n_items)
+        return;   // whole warp; the kernel has no block-wide barrier
+    float4(*spairs)[2] = spairs_all[warp];
+    float4 *flist = flist_all[warp], *clist = clist_all[warp];
+    const int2 it = items[item];
+    const int first = it.x, count = it.y;
+    const bool va = lane < count, vb = lane + 32 < count;
+    const float4 pa = src_p32[va ? first + lane : first], pb = src_p32[vb ? first + 32 + lane : first];
+    spairs[lane][0] = make_float4(pa.x, pb.x, pa.y, pb.y);
+    spairs[lane][1] = make_float4(pa.z, pb.z, va ? q[first + lane] : 0.f, vb ? q[first + 32 + lane] : 0.f);
+    const float lox = warp_min(fminf(pa.x, pb.x)), hix = warp_max(fmaxf(pa.x, pb.x));
+    const float loy = warp_min(fminf(pa.y, pb.y)), hiy = warp_max(fmaxf(pa.y, pb.y));
+    const float loz = warp_min(fminf(pa.z, pb.z)), hiz = warp_max(fmaxf(pa.z, pb.z));
+    const float dummy = fminf(lox, fminf(loy, loz)) - 3.f;   // idle lanes: every pair beyond eps_I
+    __syncwarp();
+    const int packed = src_base[first];
+    const int c1 = b3x(packed) / cg.cell, c2 = b3y(packed) / cg.cell, c3 = b3z(packed) / cg.cell;
+    const int S3 = cg.sub3();
+    const unsigned below = (1u << lane) - 1u;
+    int nf = 0, nc = 0;
+    for (int e1 = max(c1 - 1, 0); e1 <= min(c1 + 1, cg.n_c - 1); ++e1) {
+        const float o1 = (float)(e1 - c1) * np.H;
+        const float bx = fmaxf(0.f, fmaxf(o1 - hix, lox - (o1 + np.H)));
+        for (int e2 = max(c2 - 1, 0); e2 <= min(c2 + 1, cg.n_c - 1); ++e2) {
+            const float o2 = (float)(e2 - c2) * np.H;
+            const float by = fmaxf(0.f, fmaxf(o2 - hiy, loy - (o2 + np.H)));
+            for (int e3 = max(c3 - 1, 0); e3 <= min(c3 + 1, cg.n_c - 1); ++e3) {
+                const float o3 = (float)(e3 - c3) * np.H;
+                const float bz = fmaxf(0.f, fmaxf(o3 - hiz, loz - (o3 + np.H)));
+                if (bx * bx + by * by + bz * bz >= np.reach2)
+                    continue;
+                const int key = cg.key(e1, e2, e3);
+                const int end = tgt_start[(key + 1) * S3];
+                for (int j0 = tgt_start[key * S3]; j0 < end; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool keep = false, close = false;
+                    float tx = 0.f, ty = 0.f, tz = 0.f;
+                    if (j < end) {
+                        const float4 tp = tgt_p32[j];
+                        tx = tp.x + o1;
+                        ty = tp.y + o2;
+                        tz = tp.z + o3;
+                        const float dx = fmaxf(0.f, fmaxf(tx - hix, lox - tx));
+                        const float dy = fmaxf(0.f, fmaxf(ty - hiy, loy - ty));
+                        const float dz = fmaxf(0.f, fmaxf(tz - hiz, loz - tz));
+                        const float g2 = dx * dx + dy * dy + dz * dz;
+                        keep = g2 < np.reach2;
+                        close = g2 < np.close_reach2;
+                    }
+                    const unsigned mf = __ballot_sync(0xffffffffu, keep && !close);
+                    const unsigned mc = __ballot_sync(0xffffffffu, close);
+                    if (keep && !close)
+                        flist[nf + __popc(mf & below)] = make_float4(tx, ty, tz, __int_as_float(j));
+                    if (close)
+                        clist[nc + __popc(mc & below)] = make_float4(tx, ty, tz, __int_as_float(j));
+                    nf += __popc(mf);
+                    nc += __popc(mc);
+                    if (nf > kSrcListCap - 32) {
+                        __syncwarp();
+                        near3_src_eval<P, false>(spairs, flist, nf, first, count, dummy, tgt_pos, src_pos, np, phi_s, grad_s,
+                                                 lane);
+                        nf = 0;
+                        __syncwarp();
+                    }
+                    if (nc > kSrcListCap - 32) {
+                        __syncwarp();
+                        near3_src_eval<P, true>(spairs, clist, nc, first, count, dummy, tgt_pos, src_pos, np, phi_s, grad_s,
+                                                lane);
+                        nc = 0;
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    near3_src_eval<P, false>(spairs, flist, nf, first, count, dummy, tgt_pos, src_pos, np, phi_s, grad_s, lane);
+    near3_src_eval<P, true>(spairs, clist, nc, first, count, dummy, tgt_pos, src_pos, np, phi_s, grad_s, lane);
+}
+
+// Coincident pairs for the source-major kernel: phi -= T_I(0) (sum of the coincident charges).
+__global__ void k_coincident3_apply(int64_t N, const int *__restrict__ coinc_start, const int *__restrict__ coinc_src,
+                                    const float *__restrict__ q, float beta0, float *__restrict__ phi_s)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N)
+        return;
+    float self = 0.f;
+    for (int c = coinc_start[k]; c < coinc_start[k + 1]; ++c)
+        self += q[coinc_src[c]];
+    if (self != 0.f)
+        phi_s[k] -= beta0 * self;
+}
+
 // Coincident pairs: sources of the target's own cell at the same (FP64) position.
 __global__ void k_coincident3(int64_t N, const int *__restrict__ tgt_base, const double *__restrict__ tgt_pos,
                               const double *__restrict__ src_pos, const int *__restrict__ src_start, CellGrid3 cg,
@@ -655,6 +835,30 @@ cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_bas
                                                               phi_s, grad_s);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_near3_src(const int2 *items, int n_items, const int *src_base, const float4 *src_p32,
+                             const float4 *tgt_p32, const double *tgt_pos, const double *src_pos, const float *q,
+                             const int *tgt_start, CellGrid3 cg, const Near3Params &np, int64_t N,
+                             const int *coinc_start, const int *coinc_src, bool any_coincident, float *phi_s,
+                             float *grad_s, cudaStream_t st)
+{
+    if (n_items > 0) {
+        const unsigned blocks = (unsigned)((n_items + kNear3Warps - 1) / kNear3Warps);
+        cudaError_t e = with_degree(np.p, [&](auto pc) {
+            constexpr int P = decltype(pc)::value;
+            k_near3_src<P><<<blocks, kNear3Warps * 32, 0, st>>>(items, n_items, src_base, src_p32, tgt_p32, tgt_pos,
+                                                                 src_pos, q, tgt_start, cg, np, phi_s, grad_s);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (any_coincident && N > 0) {
+        k_coincident3_apply<<<nblk(N, 256), 256, 0, st>>>(N, coinc_start, coinc_src, q, np.beta0, phi_s);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_coincident3(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,

@@ -41,6 +41,11 @@ struct fs3_plan {
     // FP32 near field: warp items and the coincident-source lists of the targets
     int2 *near_items = nullptr;
     int n_near_items = 0;
+    // source-major near field (many more sources than targets): items over the sources
+    bool src_major = false;
+    int2 *src_items = nullptr;
+    int n_src_items = 0;
+    int n_coinc = 0;
     int *coinc_start = nullptr, *coinc_src = nullptr;
     // tetrahedral FEM plans: sources are the quadrature points, targets the nodes
     bool is_fem = false;
@@ -327,26 +332,36 @@ fs_status near_setup3(fs3_plan *pl)
     if (pl->N > ((int64_t)1 << 24))
         return fail(FS_EINVAL, "FP32 3D plans take at most 2^24 targets");
     const int n_cells = pl->cg.n_cells(), S3 = pl->cg.sub3();
-    std::vector<int> start((size_t)pl->cg.n_keys() + 1);
-    FS_CUDA(cudaMemcpyAsync(start.data(), pl->tgt_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost, st));
-    FS_CUDA(cudaStreamSynchronize(st));
-    std::vector<int2> items;
-    for (int c = 0; c < n_cells; ++c) {
-        const int a = start[(size_t)c * S3], b = start[(size_t)(c + 1) * S3];
-        const int cnt = b - a;
-        if (cnt <= 0)
-            continue;
-        const int pieces = (cnt + 63) / 64;
-        for (int k = 0; k < pieces; ++k) {
-            const int lo = a + (int)((int64_t)cnt * k / pieces), hi = a + (int)((int64_t)cnt * (k + 1) / pieces);
-            items.push_back(make_int2(lo, hi - lo));
+    // the sorted points of each cell, split evenly into pieces of at most 64
+    auto make_items = [&](const int *dev_start, int2 **out, int *n_out) -> fs_status {
+        std::vector<int> start((size_t)pl->cg.n_keys() + 1);
+        FS_CUDA(cudaMemcpyAsync(start.data(), dev_start, sizeof(int) * start.size(), cudaMemcpyDeviceToHost, st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        std::vector<int2> items;
+        for (int c = 0; c < n_cells; ++c) {
+            const int a = start[(size_t)c * S3], b = start[(size_t)(c + 1) * S3];
+            const int cnt = b - a;
+            if (cnt <= 0)
+                continue;
+            const int pieces = (cnt + 63) / 64;
+            for (int k = 0; k < pieces; ++k) {
+                const int lo = a + (int)((int64_t)cnt * k / pieces), hi = a + (int)((int64_t)cnt * (k + 1) / pieces);
+                items.push_back(make_int2(lo, hi - lo));
+            }
         }
-    }
-    pl->n_near_items = (int)items.size();
-    FS_TRY(pl->alloc(&pl->near_items, items.size()));
-    if (!items.empty())
-        FS_CUDA(cudaMemcpyAsync(pl->near_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
-                                st));
+        *n_out = (int)items.size();
+        FS_TRY(pl->alloc(out, items.size()));
+        if (!items.empty())
+            FS_CUDA(cudaMemcpyAsync(*out, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+        return FS_OK;
+    };
+    // targets much sparser than sources (FEM meshes): items over the sources instead, whose boxes
+    // stay small where a cell's few targets would span the whole cell
+    pl->src_major = pl->N > 0 && pl->M >= 3 * pl->N;
+    if (pl->src_major)
+        FS_TRY(make_items(pl->src_start, &pl->src_items, &pl->n_src_items));
+    else
+        FS_TRY(make_items(pl->tgt_start, &pl->near_items, &pl->n_near_items));
     // coincident sources: count, scan, fill
     const int64_t N = pl->N;
     int *count = nullptr, *tmp = nullptr;
@@ -361,6 +376,7 @@ fs_status near_setup3(fs3_plan *pl)
     int total = 0;
     FS_CUDA(cudaMemcpyAsync(&total, pl->coinc_start + N, sizeof(int), cudaMemcpyDeviceToHost, st));
     FS_CUDA(cudaStreamSynchronize(st));
+    pl->n_coinc = total;
     FS_TRY(pl->alloc(&pl->coinc_src, (size_t)std::max(total, 1)));
     if (total > 0)
         FS_CUDA(launch_coincident3(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, nullptr,
@@ -494,10 +510,18 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
         FS_CUDA(launch_interp3<real>(pl->N, pl->m, pl->tgt_base, (const real *)pl->tgt_frac, w, pl->wpoly,
                                      (const real *)pl->grid, pl->n_a, (real)pl->n_os, (real *)pl->phi_s,
                                      (real *)pl->grad_s, st));
-        if constexpr (sizeof(real) == 4)
-            FS_CUDA(launch_near3_warp(pl->near_items, pl->n_near_items, pl->tgt_base, pl->tgt_p32, pl->src_p32,
-                                      pl->tgt_pos, pl->src_pos, (const float *)q, pl->src_start, pl->cg, np32,
-                                      pl->coinc_start, pl->coinc_src, (float *)pl->phi_s, (float *)pl->grad_s, st));
+        if constexpr (sizeof(real) == 4) {
+            if (pl->src_major)
+                FS_CUDA(launch_near3_src(pl->src_items, pl->n_src_items, pl->src_base, pl->src_p32, pl->tgt_p32,
+                                         pl->tgt_pos, pl->src_pos, (const float *)q, pl->tgt_start, pl->cg, np32,
+                                         pl->N, pl->coinc_start, pl->coinc_src, pl->n_coinc > 0, (float *)pl->phi_s,
+                                         (float *)pl->grad_s, st));
+            else
+                FS_CUDA(launch_near3_warp(pl->near_items, pl->n_near_items, pl->tgt_base, pl->tgt_p32, pl->src_p32,
+                                          pl->tgt_pos, pl->src_pos, (const float *)q, pl->src_start, pl->cg, np32,
+                                          pl->coinc_start, pl->coinc_src, (float *)pl->phi_s, (float *)pl->grad_s,
+                                          st));
+        }
         else
             FS_CUDA(launch_near3_f64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
                                      (const double *)q, np, (double *)pl->phi_s, (double *)pl->grad_s, st));
