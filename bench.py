@@ -175,6 +175,25 @@ def near_traffic():
     return NEAR_TRAFFIC.get(sha), sha
 
 
+def on_chip_bound_ms(info, stage, sm_mhz=2070.0):
+    """Lower bound of a grid stage that is not HBM-bound, from its on-chip work (None if not modelled).
+
+    spread: per source, ceil((2m)^2 / 32) tap iterations of 4 shared-memory accesses (value and
+    compensation, read and write) and 2 weight shuffles, at one warp-wide MIO operation per SM
+    and cycle.  interp: per target, (2m)^2 taps x (1 load + 3 FMA) + 4 (2m) window polynomials
+    of degree 12, at 128 FP32 lanes per SM and cycle.
+    """
+    m2 = 2 * info["m"]
+    f = sm_mhz * 1e6
+    if stage == "spread":
+        per_src = -(-m2 * m2 // 32) * (4 + 2)
+        return 1e3 * info["n_src"] * per_src / (152 * f)
+    if stage == "interp":
+        per_tgt = m2 * m2 * 4 + 4 * m2 * 12
+        return 1e3 * info["n_tgt"] * per_tgt / (152 * 128 * f)
+    return None
+
+
 def near_flops_per_pair(p):
     # FP32 near-pair work: difference + r^2 (7), w (1), P(w) Horner (2(p-1)), (w-1)^(p-1) (p-1 + 1),
     # log and reciprocal (2 MUFU, counted 1 each), value and coefficient (4), three accumulations (6)
@@ -580,6 +599,10 @@ def run_ours(args):
         stages[s] = {"ms": round(t, 5), "algorithmic_bytes": abytes[s],
                      "GB_per_s": round(gbs, 1) if gbs else None,
                      "frac_hbm": round(gbs / hbm, 4) if gbs else None}
+        lb = on_chip_bound_ms(info, s)
+        if lb is not None and t > 0:
+            stages[s]["on_chip_bound_ms"] = round(lb, 5)
+            stages[s]["frac_of_on_chip_bound"] = round(lb / t, 4)
     dominant = max(STAGES, key=lambda s: stage_ms[s])
     if dominant == "near":
         fpp = near_flops_per_pair(info["p"])
