@@ -136,15 +136,29 @@ __global__ void __launch_bounds__(256) k_spread3(int64_t M, const int *__restric
                 wv *= q[j];
         }
         const int x0 = b3x(packed) - m + 1, y0 = b3y(packed) - m + 1, z0 = b3z(packed) - m + 1;
+        if constexpr (M2 == 8) {
+            // t = lane + 32 i: tx = lane % 8 for every i, ty takes two values (i even / odd) and
+            // tz = i / 2, so 11 shuffles serve the 16 taps of a lane
+            const real vx = __shfl_sync(0xffffffffu, wv, lane & 7);
+            const real vxy0 = vx * __shfl_sync(0xffffffffu, wv, 8 + (lane >> 3));
+            const real vxy1 = vx * __shfl_sync(0xffffffffu, wv, 12 + (lane >> 3));
+            real* row = grid + ((int64_t)z0 * n_a + (y0 + (lane >> 3))) * n_a + (x0 + (lane & 7));
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int t = lane + 32 * i;
-            const int tx = t % M2, ty = (t / M2) % M2, tz = t / (M2 * M2);
-            const real vx = __shfl_sync(0xffffffffu, wv, tx);
-            const real vy = __shfl_sync(0xffffffffu, wv, M2 + ty);
-            const real vz = __shfl_sync(0xffffffffu, wv, 2 * M2 + (tz < M2 ? tz : 0));
-            if (t < TAPS)
-                atomicAdd(grid + ((int64_t)(z0 + tz) * n_a + (y0 + ty)) * n_a + (x0 + tx), vx * vy * vz);
+            for (int i = 0; i < 16; ++i) {
+                const real vz = __shfl_sync(0xffffffffu, wv, 16 + (i >> 1));
+                atomicAdd(row + ((int64_t)(i >> 1) * n_a + 4 * (i & 1)) * n_a, ((i & 1) ? vxy1 : vxy0) * vz);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int t = lane + 32 * i;
+                const int tx = t % M2, ty = (t / M2) % M2, tz = t / (M2 * M2);
+                const real vx = __shfl_sync(0xffffffffu, wv, tx);
+                const real vy = __shfl_sync(0xffffffffu, wv, M2 + ty);
+                const real vz = __shfl_sync(0xffffffffu, wv, 2 * M2 + (tz < M2 ? tz : 0));
+                if (t < TAPS)
+                    atomicAdd(grid + ((int64_t)(z0 + tz) * n_a + (y0 + ty)) * n_a + (x0 + tx), vx * vy * vz);
+            }
         }
     }
 }
