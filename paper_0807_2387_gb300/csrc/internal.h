@@ -89,6 +89,12 @@ cudaError_t launch_gather_points3(const double *xyz, const int *perm, int64_t n,
 template <typename real>
 cudaError_t launch_spread3(int64_t M, int m, const int *base, const real *frac, const real *q, Window<real> w,
                            const WindowPoly &wp, real *grid, int n_a, cudaStream_t st);
+// FP32 spreading through warp-private shared tiles with compensation; items {first source,
+// count <= kSpread3ItemMax} of one cell each.  spread3_tile_smem is 0 when the tiles do not fit.
+constexpr int kSpread3ItemMax = 1024;
+size_t spread3_tile_smem(int cell, int m);
+cudaError_t launch_spread3_tile(const int2 *items, int n_items, int m, int cell, const int *base, const float *frac,
+                                const float *q, const WindowPoly &wp, float *grid, int n_a, cudaStream_t st);
 template <typename real>
 cudaError_t launch_interp3(int64_t N, int m, const int *base, const real *frac, Window<real> w, const WindowPoly &wp,
                            const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, cudaStream_t st);

@@ -41,6 +41,11 @@ struct fs3_plan {
     // FP32 near field: warp items and the coincident-source lists of the targets
     int2 *near_items = nullptr;
     int n_near_items = 0;
+    // FP32 spreading through warp-private shared tiles: items of at most kSpread3ItemMax sources
+    // of one cell (plans whose tiles fit in shared memory)
+    bool spread_tiles = false;
+    int2 *spread_items = nullptr;
+    int n_spread_items = 0;
     // source-major near field (many more sources than targets): items over the sources
     bool src_major = false;
     int2 *src_items = nullptr;
@@ -357,6 +362,25 @@ fs_status near_setup3(fs3_plan *pl)
     };
     // targets much sparser than sources (FEM meshes): items over the sources instead, whose boxes
     // stay small where a cell's few targets would span the whole cell
+    // spreading items: the sources of each cell in pieces of at most kSpread3ItemMax
+    pl->spread_tiles = spread3_tile_smem(pl->cg.cell, pl->m) > 0;
+    if (pl->spread_tiles) {
+        std::vector<int> sstart((size_t)pl->cg.n_keys() + 1);
+        FS_CUDA(cudaMemcpyAsync(sstart.data(), pl->src_start, sizeof(int) * sstart.size(), cudaMemcpyDeviceToHost,
+                                st));
+        FS_CUDA(cudaStreamSynchronize(st));
+        std::vector<int2> sitems;
+        for (int c = 0; c < n_cells; ++c) {
+            const int a = sstart[(size_t)c * S3], b = sstart[(size_t)(c + 1) * S3];
+            for (int lo = a; lo < b; lo += kSpread3ItemMax)
+                sitems.push_back(make_int2(lo, std::min(kSpread3ItemMax, b - lo)));
+        }
+        pl->n_spread_items = (int)sitems.size();
+        FS_TRY(pl->alloc(&pl->spread_items, sitems.size()));
+        if (!sitems.empty())
+            FS_CUDA(cudaMemcpyAsync(pl->spread_items, sitems.data(), sizeof(int2) * sitems.size(),
+                                    cudaMemcpyHostToDevice, st));
+    }
     pl->src_major = pl->N > 0 && pl->M >= 3 * pl->N;
     if (pl->src_major)
         FS_TRY(make_items(pl->src_start, &pl->src_items, &pl->n_src_items));
@@ -503,8 +527,13 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
     for (int r = 0; r < pl->nrhs; ++r) {
         const real *q = (const real *)pl->q_sorted + (int64_t)r * pl->M;
         FS_CUDA(cudaMemsetAsync(pl->grid, 0, cube * sizeof(real), st));
-        FS_CUDA(launch_spread3<real>(pl->M, pl->m, pl->src_base, (const real *)pl->src_frac, q, w, pl->wpoly,
-                                     (real *)pl->grid, pl->n_a, st));
+        if (sizeof(real) == 4 && pl->spread_tiles)
+            FS_CUDA(launch_spread3_tile(pl->spread_items, pl->n_spread_items, pl->m, pl->cg.cell, pl->src_base,
+                                        (const float *)pl->src_frac, (const float *)q, pl->wpoly, (float *)pl->grid,
+                                        pl->n_a, st));
+        else
+            FS_CUDA(launch_spread3<real>(pl->M, pl->m, pl->src_base, (const real *)pl->src_frac, q, w, pl->wpoly,
+                                         (real *)pl->grid, pl->n_a, st));
         FS_CUDA(launch_fft3<real>((real *)pl->grid, pl->n_a, pl->n_os, pl->n, (C *)pl->spec1, (C *)pl->spec2,
                                   (const real *)pl->mul, (const C *)pl->tw, st));
         FS_CUDA(launch_interp3<real>(pl->N, pl->m, pl->tgt_base, (const real *)pl->tgt_frac, w, pl->wpoly,
