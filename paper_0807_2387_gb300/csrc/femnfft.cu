@@ -516,9 +516,16 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
             FS_CUDA(cudaMemcpy(*dst, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
     }
 
-    if (pl->precision == 32)
+    if (pl->precision == 32) {
         FS_TRY(build_near_items(pl, pl->tgt_start, pl->src_start, &pl->near_items, &pl->n_near_items,
                                 &pl->near_items_h, &pl->near_work_h));
+        // FEM plans (several quadrature points around every node): a cell holds few targets, so a
+        // target item's box would span the whole cell; the forward near field then runs over
+        // items of sources, whose boxes stay small
+        pl->src_major = N > 0 && M >= 3 * N;
+        if (pl->src_major)
+            FS_TRY(build_near_items(pl, pl->src_start, pl->tgt_start, &pl->src_near_items, &pl->n_src_near_items));
+    }
 
     // coefficient table and FFT twiddles
     FS_TRY(coefficients<real>(pl));
@@ -667,11 +674,19 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
                                     (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[5], st));
-        if constexpr (sizeof(real) == 4)
-            FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
-                                  pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q, np,
-                                  (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc, st));
-        else
+        if constexpr (sizeof(real) == 4) {
+            if (pl->src_major) {
+                FS_CUDA(cudaMemsetAsync(pl->coinc, 0, sizeof(float) * (size_t)std::max<int64_t>(pl->N, 1), st));
+                FS_CUDA(launch_near_src32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
+                                          pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
+                                          (const float *)q, np, (float *)pl->phi_s, (float *)pl->grad_s,
+                                          (float *)pl->coinc, st));
+            } else {
+                FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
+                                      pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q, np,
+                                      (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc, st));
+            }
+        } else
             FS_CUDA(launch_near64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
                                   (const double *)q, np, (double *)pl->phi_s, (double *)pl->grad_s,
                                   (double *)pl->coinc, st));
@@ -771,7 +786,7 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
         FS_TRY(pl->alloc_bytes(&pl->adj_cg, (size_t)std::max<int64_t>(M, 1) * sizeof(real)));
         FS_TRY(pl->alloc_bytes(&pl->adj_hess, (size_t)std::max<int64_t>(N, 1) * 3 * sizeof(real)));
         FS_TRY(pl->alloc(&pl->adj_gsum, 1));
-        if (pl->precision == 32)
+        if (pl->precision == 32 && !pl->src_near_items)
             FS_TRY(build_near_items(pl, pl->src_start, pl->tgt_start, &pl->src_near_items, &pl->n_src_near_items));
     }
     const Window<real> w = make_window<real>(pl);

@@ -275,6 +275,12 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
                           const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                           CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,
                           cudaStream_t st);
+// source-major variant for plans with many more sources than targets: items (first source,
+// count <= 64) per warp; phi_s, grad_s and coinc (zeroed by the caller) receive atomic adds
+cudaError_t launch_near_src32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,
+                              const float2 *src_lo, const float2 *tgt_hi, const float2 *tgt_lo, const int *tgt_start,
+                              CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s,
+                              float *coinc, cudaStream_t st);
 // plan-time pair statistics over the FP32 near-field items: counts[2 s] (r < eps_I) and
 // counts[2 s + 1] (r < eps_I / 8) for s < kNearCountSlots, to be summed
 constexpr int kNearCountSlots = 64;

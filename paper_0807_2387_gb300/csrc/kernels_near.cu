@@ -371,6 +371,22 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
     });
 }
 
+cudaError_t launch_near_src32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,
+                              const float2 *src_lo, const float2 *tgt_hi, const float2 *tgt_lo, const int *tgt_start,
+                              CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s,
+                              float *coinc, cudaStream_t st)
+{
+    if (n_items <= 0)
+        return cudaSuccess;
+    const NearSides sd{src_base, src_hi, src_lo, tgt_hi, tgt_lo, tgt_start};
+    const unsigned blocks = (unsigned)((n_items + 3) / 4);
+    return with_degree(np.p, [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        k_near_src32<P><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, q, phi_s, grad_s, coinc);
+        return cudaGetLastError();
+    });
+}
+
 template <typename real>
 cudaError_t launch_unpermute(int64_t N, const real *phi_s, const real *grad_s, const real *coinc, const int *perm,
                              double shift, const double *q_sum, double s, void *phi_out, void *H_out, int out_is_f64,

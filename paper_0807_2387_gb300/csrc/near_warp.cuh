@@ -396,6 +396,192 @@ template <class Op> cudaError_t launch_near_list(int64_t n_items, const int2 *it
     return cudaGetLastError();
 }
 
+// ---- source-major forward near field (FP32), for plans with many more sources than targets
+//
+// FEM plans put several quadrature points around every node, so a cell holds few targets and
+// a target item's box spans the whole cell.  Here a warp takes an item of at most 64 sources
+// of one cell (compact) and keeps them in shared memory as packed pairs; it reads the targets
+// of the neighbour cells within eps_I of the sources' box 32 at a time, lists those within
+// reach (a second list for those within eps_I / 8 of the box), and each lane then takes one
+// listed target and sums the item's sources on it, two per packed operation; phi, grad phi and
+// the coincident charge are added to the target with atomics.  Close pairs are refined from
+// the hi and lo parts exactly as in the target-major traversal.
+constexpr int kSrcMajorCap = 128;   // listed targets per warp and list
+
+template <int P>
+__device__ __forceinline__ void near_src_pair(const NearParams<float> &np, float2 r2, float2 dx, float2 dy,
+                                              float2 q2, float2 &phi, float2 &gx, float2 &gy)
+{
+    float2 w = mul2(r2, f2(np.inv_eps2));
+    if constexpr (P >= 2)
+        w = min1(w);                                      // f(1) = 0 and (w - 1)^(p-1) = 0: masked
+    const float2 val = near_f2<P>(np, w);
+    float2 coef = rcp_2(w);
+    if constexpr (P >= 2)
+        coef = mul2(ipow2<P - 1>(add2(w, f2(-1.f))), coef);
+    if constexpr (P == 1)
+        q2 = select2(r2, np.eps2, q2);
+    phi = fma2(q2, val, phi);
+    const float2 tq = mul2(q2, coef);
+    gx = fma2(tq, dx, gx);
+    gy = fma2(tq, dy, gy);
+}
+
+// One round per 32 listed targets.  Far entries: (x, y) in the item's frame and the target
+// index; close entries: (hi x, hi y, lo x, lo y) and (cell step x, cell step y, index).
+template <int P, bool CLOSE>
+__device__ __forceinline__ void near_src_eval(const float4 *s_hi, const float4 *s_lo, const float2 *s_q,
+                                              const float4 *ta, const float4 *tb, int n, int lane,
+                                              const NearParams<float> &np, float rcoef, float *__restrict__ phi_s,
+                                              float *__restrict__ grad_s, float *__restrict__ coinc)
+{
+    for (int base = 0; base < n; base += 32) {
+        const int e = base + lane;
+        const bool valid = e < n;
+        const float4 A = valid ? ta[e] : make_float4(1e6f, 1e6f, 0.f, 0.f);
+        const float4 B = (CLOSE && valid) ? tb[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int k = __float_as_int(CLOSE ? B.z : A.z);
+        // frame position of the target (close entries carry hi parts and the cell step)
+        const float tx = CLOSE ? A.x + B.x : A.x, ty = CLOSE ? A.y + B.y : A.y;
+        const float2 X = f2(tx), Y = f2(ty);
+        float2 phi = f2(0.f), gx = f2(0.f), gy = f2(0.f);
+        float cq = 0.f;
+#pragma unroll 2
+        for (int i = 0; i < 32; ++i) {
+            const float4 sh = s_hi[i];                    // (xa, xb, ya, yb)
+            float2 q2 = s_q[i];
+            float2 dx = add2(X, make_float2(-sh.x, -sh.y));
+            float2 dy = add2(Y, make_float2(-sh.z, -sh.w));
+            float2 r2 = fma2(dy, dy, mul2(dx, dx));
+            if constexpr (CLOSE) {
+                const float4 sl = s_lo[i];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (valid && (t == 0 ? r2.x : r2.y) < np.close2) {
+                        const float ex = refine_diff(A.x, t == 0 ? sh.x : sh.y, B.x, A.z, t == 0 ? sl.x : sl.y);
+                        const float ey = refine_diff(A.y, t == 0 ? sh.z : sh.w, B.y, A.w, t == 0 ? sl.z : sl.w);
+                        float e2 = ex * ex + ey * ey;
+                        if (ex == 0.f && ey == 0.f) {             // coincident: G(0) := 0
+                            const float qs = t == 0 ? q2.x : q2.y;
+                            add_comp(phi, t, -qs * np.beta[0]);
+                            cq += qs;
+                            e2 = np.eps2;                          // masked out: w = 1
+                        }
+                        if (t == 0) {
+                            dx.x = ex;
+                            dy.x = ey;
+                            r2.x = e2;
+                        } else {
+                            dx.y = ex;
+                            dy.y = ey;
+                            r2.y = e2;
+                        }
+                    }
+                }
+            }
+            near_src_pair<P>(np, r2, dx, dy, q2, phi, gx, gy);
+        }
+        if (valid) {
+            atomicAdd(phi_s + k, phi.x + phi.y);
+            atomicAdd(grad_s + 2 * (int64_t)k, rcoef * (gx.x + gx.y));
+            atomicAdd(grad_s + 2 * (int64_t)k + 1, rcoef * (gy.x + gy.y));
+            if (CLOSE && cq != 0.f)
+                atomicAdd(coinc + k, cq);
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_near_src32(int64_t n_items, const int2 *__restrict__ items, NearSides sd,
+                                                    CellGrid cg, NearParams<float> np, const float *__restrict__ q,
+                                                    float *__restrict__ phi_s, float *__restrict__ grad_s,
+                                                    float *__restrict__ coinc)
+{
+    __shared__ float4 s_hi_all[4][32], s_lo_all[4][32];
+    __shared__ float2 s_q_all[4][32];
+    __shared__ float4 far_all[4][kSrcMajorCap], ca_all[4][kSrcMajorCap], cb_all[4][kSrcMajorCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= n_items)
+        return;                                   // whole warp past the end; no block-wide barrier follows
+    float4 *s_hi = s_hi_all[w], *s_lo = s_lo_all[w], *far = far_all[w], *ca = ca_all[w], *cb = cb_all[w];
+    float2 *s_q = s_q_all[w];
+    const int2 item = items[warp];
+    // the item's sources (own side): slots a = lane, b = lane + 32; idle slots copy the first
+    // source with charge 0
+    const bool va = lane < item.y, vb = lane + 32 < item.y;
+    const int64_t ja = va ? item.x + lane : item.x, jb = vb ? item.x + 32 + lane : item.x;
+    const float2 ha = sd.own_hi[ja], hb = sd.own_hi[jb], la = sd.own_lo[ja], lb = sd.own_lo[jb];
+    s_hi[lane] = make_float4(ha.x, hb.x, ha.y, hb.y);
+    s_lo[lane] = make_float4(la.x, lb.x, la.y, lb.y);
+    s_q[lane] = make_float2(va ? __ldg(q + ja) : 0.f, vb ? __ldg(q + jb) : 0.f);
+    const int packed = sd.own_base[item.x];
+    const int c1 = base1(packed) / cg.cell, c2 = base2(packed) / cg.cell;
+    const float h = np.hcell, eps = sqrtf(np.eps2);
+    // the sources' box in the item's frame (offsets from the item cell's corner)
+    const float lx = warp_min(fminf(ha.x, hb.x)), hx = warp_max(fmaxf(ha.x, hb.x));
+    const float ly = warp_min(fminf(ha.y, hb.y)), hy = warp_max(fmaxf(ha.y, hb.y));
+    const float margin = 1e-4f * eps + 1e-5f;
+    const float reach = eps + margin, reach2 = reach * reach;
+    const float close_reach = sqrtf(np.close2) + margin, close_reach2 = close_reach * close_reach;
+    const unsigned below = (1u << lane) - 1u;
+    const float rcoef = np.rcoef;
+    __syncwarp();
+    int nf = 0, nc = 0;
+    for (int e1 = max(c1 - 1, 0); e1 <= min(c1 + 1, cg.n_c - 1); ++e1) {
+        const float ox = (float)(e1 - c1) * h;        // cell step into the item's frame
+        const float gxc = fmaxf(0.f, fmaxf(ox - hx, lx - (ox + h)));
+        for (int e2 = max(c2 - 1, 0); e2 <= min(c2 + 1, cg.n_c - 1); ++e2) {
+            const float oy = (float)(e2 - c2) * h;
+            const float gyc = fmaxf(0.f, fmaxf(oy - hy, ly - (oy + h)));
+            if (gxc * gxc + gyc * gyc > reach2)
+                continue;                             // the whole cell is beyond reach (warp-uniform)
+            const int kbase = cg.key(e1, e2) * kSub;
+            const int j0 = sd.oth_start[kbase], j1 = sd.oth_start[kbase + kSub];
+            for (int jb0 = j0; jb0 < j1; jb0 += 32) {
+                const int j = jb0 + lane;
+                const bool in = j < j1;
+                float2 th = make_float2(0.f, 0.f);
+                if (in)
+                    th = __ldg(sd.oth_hi + j);
+                const float tx = th.x + ox, ty = th.y + oy;
+                const float dxb = fmaxf(0.f, fmaxf(tx - hx, lx - tx));
+                const float dyb = fmaxf(0.f, fmaxf(ty - hy, ly - ty));
+                const float g2 = dxb * dxb + dyb * dyb;
+                const bool keep = in && g2 <= reach2;
+                const bool close = keep && g2 <= close_reach2;
+                const unsigned mf = __ballot_sync(0xffffffffu, keep && !close);
+                const unsigned mc = __ballot_sync(0xffffffffu, close);
+                if (keep && !close)
+                    far[nf + __popc(mf & below)] = make_float4(tx, ty, __int_as_float(j), 0.f);
+                if (close) {
+                    const int at = nc + __popc(mc & below);
+                    const float2 tl = __ldg(sd.oth_lo + j);
+                    ca[at] = make_float4(th.x, th.y, tl.x, tl.y);
+                    cb[at] = make_float4(ox, oy, __int_as_float(j), 0.f);
+                }
+                nf += __popc(mf);
+                nc += __popc(mc);
+                if (nf > kSrcMajorCap - 32) {
+                    __syncwarp();
+                    near_src_eval<P, false>(s_hi, s_lo, s_q, far, nullptr, nf, lane, np, rcoef, phi_s, grad_s, coinc);
+                    nf = 0;
+                    __syncwarp();
+                }
+                if (nc > kSrcMajorCap - 32) {
+                    __syncwarp();
+                    near_src_eval<P, true>(s_hi, s_lo, s_q, ca, cb, nc, lane, np, rcoef, phi_s, grad_s, coinc);
+                    nc = 0;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __syncwarp();
+    near_src_eval<P, false>(s_hi, s_lo, s_q, far, nullptr, nf, lane, np, rcoef, phi_s, grad_s, coinc);
+    near_src_eval<P, true>(s_hi, s_lo, s_q, ca, cb, nc, lane, np, rcoef, phi_s, grad_s, coinc);
+}
+
 // Calls f(std::integral_constant<int, P>) for the expansion degree p in 1..16.
 template <class F> cudaError_t with_degree(int p, F &&f)
 {

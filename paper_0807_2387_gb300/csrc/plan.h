@@ -75,8 +75,9 @@ struct fs_plan {
     std::vector<int2> near_items_h;   // host copies (merged into batch work lists)
     std::vector<int64_t> near_work_h; // estimated pair work per near item
     std::vector<fs::SpreadItem> items_h;
-    int2 *src_near_items = nullptr;   // FP32 adjoint near field: (first source, count <= 64) per warp
+    int2 *src_near_items = nullptr;   // FP32 adjoint and source-major near field: (first source, count <= 64)
     int64_t n_src_near_items = 0;
+    bool src_major = false;           // FP32 forward near field over source items (many more sources than targets)
     void *mul = nullptr, *tw = nullptr;
     void *grid = nullptr, *spec = nullptr;
     void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
