@@ -5,13 +5,17 @@
 // kernel here is the 2D one with a third coordinate:
 //   spreading    g_k = sum_j q_j psi(k1 - u_j1) psi(k2 - u_j2) psi(k3 - u_j3) over the
 //                (2m)^3 grid lines around each source; one warp per source, lanes 0..6m-1
-//                hold the window values of the three coordinates, every lane owns
-//                (2m)^3 / 32 taps and adds them to the grid with atomics (the grid of the
-//                active window stays in L2 for the sizes this path serves);
+//                hold the window values of the three coordinates and every lane owns
+//                (2m)^3 / 32 taps.  FP32: warp-private shared tiles of the source cell with a
+//                TwoSum compensation plane, flushed once per item (k_spread3_tile); FP64 (or
+//                tiles too large for shared memory): global atomics (k_spread3);
 //   interpolation phi and grad phi from the same taps, the window and its slope;
 //   near field   q (1/(4 pi r) - T_I(r)) and its gradient for 0 < r < eps_I over the 27
-//                cells around the target's (cells at least eps_I wide), -q T_I(0) for
-//                coincident points;
+//                cells around, -q T_I(0) for coincident points.  FP32: warp items over the
+//                targets with candidate lists (k_near3_warp) or, when sources outnumber
+//                targets three to one, over the sources (k_near3_src); pairs closer than
+//                eps_I / 8 take their difference from the FP64 positions.  FP64: thread per
+//                target (k_near3_f64);
 //   output       phi = s phi~, H = -s^2 grad~ phi~ (1/r is homogeneous of degree -1).
 // Grid layout: g[z][y][x], x fastest, edge n_a (the active window); a point's base grid
 // line per coordinate is packed into 10 bits each.
