@@ -562,9 +562,21 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         pl->release(cnt);
     }
 
+    // FP32 target-major plans overlap the near field with spreading and the transform
+    if (sizeof(real) == 4 && !pl->src_major && N > 0) {
+        FS_CUDA(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
+        FS_CUDA(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming));
+        FS_CUDA(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming));
+        pl->overlap = true;
+    }
     if (pl->flags & FS_FLAG_TIMING) {
         for (int i = 0; i <= kStages; ++i)
             FS_CUDA(cudaEventCreate(&pl->ev[i]));
+        if (pl->overlap) {
+            FS_CUDA(cudaEventCreate(&pl->ev_n0));
+            FS_CUDA(cudaEventCreate(&pl->ev_n1));
+            FS_CUDA(cudaEventCreate(&pl->ev_j));
+        }
         FS_CUDA(cudaEventCreate(&pl->ev_q0));
         FS_CUDA(cudaEventCreate(&pl->ev_q1));
         pl->events = true;
@@ -603,6 +615,13 @@ void plan_destroy(fs_plan *pl)
         cudaEventDestroy(pl->ev_q0);
     if (pl->ev_q1)
         cudaEventDestroy(pl->ev_q1);
+    for (cudaEvent_t e : {pl->ev_fork, pl->ev_join, pl->ev_n0, pl->ev_n1, pl->ev_j})
+        if (e)
+            cudaEventDestroy(e);
+    if (pl->aux) {
+        cudaStreamSynchronize(pl->aux);
+        cudaStreamDestroy(pl->aux);
+    }
     delete pl;
 }
 
@@ -653,9 +672,25 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
         const real *q = (const real *)pl->q_sorted + (int64_t)r * pl->M;
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[0], st));
+        if (pl->overlap)
+            FS_CUDA(cudaEventRecord(pl->ev_fork, st));   // the charges are in
         FS_CUDA(cudaMemsetAsync(pl->grid, 0, (size_t)pl->n_a * pl->pitch * sizeof(real), st));
         FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w, pl->wpoly,
                                     (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
+        if (pl->overlap) {
+            // the near field (stored, not added) on the second stream, submitted after the
+            // spreading so that the spreading's blocks are scheduled first
+            FS_CUDA(cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0));
+            if (rec)
+                FS_CUDA(cudaEventRecord(pl->ev_n0, pl->aux));
+            FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
+                                  pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q,
+                                  make_near<float>(pl), (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc,
+                                  true, pl->aux));
+            if (rec)
+                FS_CUDA(cudaEventRecord(pl->ev_n1, pl->aux));
+            FS_CUDA(cudaEventRecord(pl->ev_join, pl->aux));
+        }
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[1], st));
         FS_CUDA(launch_fft_rows_fwd<real>((const real *)pl->grid, pl->pitch, pl->n_a, pl->n_os, pl->n / 2,
@@ -670,12 +705,19 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
                                           (real *)pl->grid, pl->pitch, (const C *)pl->tw, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[4], st));
+        if (pl->overlap) {
+            FS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
+            if (rec)
+                FS_CUDA(cudaEventRecord(pl->ev_j, st));
+        }
         FS_CUDA(launch_interp<real>(pl->N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly, (const real *)pl->grid, pl->pitch,
-                                    (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, st));
+                                    (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, pl->overlap, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[5], st));
         if constexpr (sizeof(real) == 4) {
-            if (pl->src_major) {
+            if (pl->overlap) {
+                // the near field ran on the second stream
+            } else if (pl->src_major) {
                 FS_CUDA(cudaMemsetAsync(pl->coinc, 0, sizeof(float) * (size_t)std::max<int64_t>(pl->N, 1), st));
                 FS_CUDA(launch_near_src32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
                                           pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
@@ -684,7 +726,7 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
             } else {
                 FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
                                       pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q, np,
-                                      (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc, st));
+                                      (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc, false, st));
             }
         } else
             FS_CUDA(launch_near64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
@@ -824,7 +866,7 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
                                             pl->pitch, pl->n_a, pl->kahan, st));
             FS_TRY(spectral_pipeline<real>(pl));
             FS_CUDA(launch_interp<real>(M, pl->m, pl->src_base, pl->src_frac, w, pl->wpoly, (const real *)pl->grid,
-                                        pl->pitch, (real)pl->n_os, (real *)pl->adj_a, (real *)pl->adj_ga, st));
+                                        pl->pitch, (real)pl->n_os, (real *)pl->adj_a, (real *)pl->adj_ga, false, st));
             if constexpr (sizeof(real) == 4)
                 FS_CUDA(launch_near_adj32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
                                           pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
@@ -1155,6 +1197,13 @@ fs_status fs_stage_times(fs_plan *plan, double *ms, int count)
     for (int i = 1; i < kStages; ++i) {
         FS_CUDA(cudaEventElapsedTime(&t, plan->ev[i - 1], plan->ev[i]));
         ms[i] = t;
+    }
+    if (plan->overlap) {
+        // interpolation from the join; the near field on its own stream (overlapping stages 1-4)
+        FS_CUDA(cudaEventElapsedTime(&t, plan->ev_j, plan->ev[5]));
+        ms[5] = t;
+        FS_CUDA(cudaEventElapsedTime(&t, plan->ev_n0, plan->ev_n1));
+        ms[6] = t;
     }
     return FS_OK;
 }

@@ -236,9 +236,10 @@ cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int
                           const void *frac, const real *q, Window<real> w, const WindowPoly &wp, real *grid,
                           int pitch, int n_a, bool kahan, cudaStream_t st);
 template <typename real>
+// acc: add to phi_s / grad_s (the near field already stored there) instead of writing them
 cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w,
                           const WindowPoly &wp, const real *grid, int pitch, real n_os, real *phi_s, real *grad_s,
-                          cudaStream_t st);
+                          bool acc, cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_spread_dip(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
@@ -271,10 +272,12 @@ cudaError_t launch_near64(int64_t N, const int *tgt_base, const double2 *tgt_pos
                           const int *src_start, CellGrid cg, const double *q, NearParams<double> np, double *phi_s,
                           double *grad_s, double *coinc, cudaStream_t st);
 // items: (first target, count <= 64) per warp, never spanning two cells
+// (assign: store phi_s and grad_s instead of adding to them, for the near field that runs on a
+// second stream beside spreading and the transform)
 cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
                           const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                           CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,
-                          cudaStream_t st);
+                          bool assign, cudaStream_t st);
 // source-major variant for plans with many more sources than targets: items (first source,
 // count <= 64) per warp; phi_s, grad_s and coinc (zeroed by the caller) receive atomic adds
 cudaError_t launch_near_src32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,

@@ -132,6 +132,7 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
     float *__restrict__ coinc;
     int64_t q_stride, n_stride;
     float rcoef;
+    bool assign;   // store phi_s / grad_s instead of adding (the far field is added later)
     float qj[R];
     float2 phi[R], gx[R], gy[R], qc[R];
     float2 rphi[kRows ? R : 1], rgx[kRows ? R : 1], rgy[kRows ? R : 1];
@@ -206,9 +207,15 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int64_t kk = k + r * n_stride;
-            phi_s[kk] += comp(phi[r], t);
-            grad_s[2 * kk] += rcoef * comp(gx[r], t);
-            grad_s[2 * kk + 1] += rcoef * comp(gy[r], t);
+            if (assign) {
+                phi_s[kk] = comp(phi[r], t);
+                grad_s[2 * kk] = rcoef * comp(gx[r], t);
+                grad_s[2 * kk + 1] = rcoef * comp(gy[r], t);
+            } else {
+                phi_s[kk] += comp(phi[r], t);
+                grad_s[2 * kk] += rcoef * comp(gx[r], t);
+                grad_s[2 * kk + 1] += rcoef * comp(gy[r], t);
+            }
             coinc[kk] = comp(qc[r], t);
         }
     }
@@ -276,6 +283,7 @@ __global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_
     op.q_stride = b.M;
     op.n_stride = b.N;
     op.rcoef = np.rcoef;
+    op.assign = false;
     __shared__ NearLists<R> L;
     const int w = threadIdx.x >> 5;
     near_traverse_list(make_int2(it.x, it.y), lane, sd, cg, np, op, L.xy[w], L.q[w], L.cxy[w], L.cl[w], L.cq[w]);
@@ -355,7 +363,7 @@ cudaError_t launch_near64(int64_t N, const int *tgt_base, const double2 *tgt_pos
 cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
                           const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                           CellGrid cg, const float *q, NearParams<float> np, float *phi_s, float *grad_s, float *coinc,
-                          cudaStream_t st)
+                          bool assign, cudaStream_t st)
 {
     const NearSides sd{tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start};
     return with_degree(np.p, [&](auto pc) {
@@ -367,6 +375,7 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
         op.q_stride = 0;
         op.n_stride = 0;
         op.rcoef = np.rcoef;
+        op.assign = assign;
         return launch_near_list(n_items, items, sd, cg, np, op, st);
     });
 }

@@ -184,7 +184,8 @@ template <typename real, int M2>
 __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ base,
                                              const real2_t<real> *__restrict__ frac, const Window<real> &w,
                                              const WindowPoly &wp, const real *__restrict__ grid, int pitch, real n_os,
-                                             real *__restrict__ phi_s, real *__restrict__ grad_s)
+                                             real *__restrict__ phi_s, real *__restrict__ grad_s,
+                                             bool acc = false)
 {
     constexpr int m = M2 / 2;
     constexpr bool kRef = sizeof(real) == 4 && m >= 5;
@@ -233,20 +234,21 @@ __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ 
 #pragma unroll
     for (int a = 0; a < M2; ++a)
         g1 += d1[a] * (kRef ? rsv[a] - rsv[m - 1] : rsv[a]);
-    phi_s[k] = phi;
-    grad_s[2 * k] = n_os * g1;
-    grad_s[2 * k + 1] = n_os * g2;
+    // acc: the near field was stored first (overlapped with spreading and the transform)
+    phi_s[k] = acc ? phi_s[k] + phi : phi;
+    grad_s[2 * k] = acc ? grad_s[2 * k] + n_os * g1 : n_os * g1;
+    grad_s[2 * k + 1] = acc ? grad_s[2 * k + 1] + n_os * g2 : n_os * g2;
 }
 
 template <typename real, int M2>
 __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict__ base,
                                                 const real2_t<real> *__restrict__ frac, Window<real> w, WindowPoly wp,
                                                 const real *__restrict__ grid, int pitch, real n_os,
-                                                real *__restrict__ phi_s, real *__restrict__ grad_s)
+                                                real *__restrict__ phi_s, real *__restrict__ grad_s, bool acc)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < N)
-        interp_point<real, M2>(k, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s);
+        interp_point<real, M2>(k, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc);
 }
 
 // Batched interpolation: block -> (instance, block of its targets), blockIdx.y = right-hand side.
@@ -486,11 +488,11 @@ cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const in
 
 template <typename real, int M2>
 cudaError_t interp_m(int64_t N, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
-                     const real *grid, int pitch, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+                     const real *grid, int pitch, real n_os, real *phi_s, real *grad_s, bool acc, cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((N + 255) / 256);
     k_interp<real, M2><<<blocks, 256, 0, st>>>(N, base, (const real2_t<real> *)frac, w, wp, grid, pitch, n_os, phi_s,
-                                                grad_s);
+                                                grad_s, acc);
     return cudaGetLastError();
 }
 
@@ -615,18 +617,19 @@ cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int
 
 template <typename real>
 cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
-                          const real *grid, int pitch, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+                          const real *grid, int pitch, real n_os, real *phi_s, real *grad_s, bool acc,
+                          cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
     switch (m) {
-    case 2: return interp_m<real, 4>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
-    case 3: return interp_m<real, 6>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
-    case 4: return interp_m<real, 8>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
-    case 5: return interp_m<real, 10>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
-    case 6: return interp_m<real, 12>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
-    case 7: return interp_m<real, 14>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
-    case 8: return interp_m<real, 16>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, st);
+    case 2: return interp_m<real, 4>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
+    case 3: return interp_m<real, 6>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
+    case 4: return interp_m<real, 8>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
+    case 5: return interp_m<real, 10>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
+    case 6: return interp_m<real, 12>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
+    case 7: return interp_m<real, 14>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
+    case 8: return interp_m<real, 16>(N, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -638,9 +641,9 @@ template cudaError_t launch_spread<double>(const SpreadItem *, int, CellGrid, in
                                            const double *, Window<double>, const WindowPoly &, double *, int, int,
                                            bool, cudaStream_t);
 template cudaError_t launch_interp<float>(int64_t, int, const int *, const void *, Window<float>, const WindowPoly &,
-                                          const float *, int, float, float *, float *, cudaStream_t);
+                                          const float *, int, float, float *, float *, bool, cudaStream_t);
 template cudaError_t launch_interp<double>(int64_t, int, const int *, const void *, Window<double>,
-                                           const WindowPoly &, const double *, int, double, double *, double *,
+                                           const WindowPoly &, const double *, int, double, double *, double *, bool,
                                            cudaStream_t);
 
 namespace {
