@@ -62,6 +62,9 @@ typedef enum { FS_F32 = 32, FS_F64 = 64 } fs_dtype;
 #define FS_FLAG_TIMING 2u     /* record per-stage CUDA events (see fs_stage_times) */
 #define FS_FLAG_AUTOTUNE 4u   /* fs_batch_create: choose cell and tile_cells per instance class
                                  by timing candidate plans */
+#define FS_FLAG_SERIAL 8u     /* FP32 plans: run the near field on the plan's stream after the
+                                 interpolation instead of on a second stream beside spreading
+                                 and the transform (slower; stage times then do not overlap) */
 
 /* Plan options.  A zeroed struct (or NULL) selects every default. */
 typedef struct {

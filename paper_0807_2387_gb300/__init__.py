@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import ctypes
 
-from ._native import (FS_F32, FS_F64, FS_FLAG_AUTOTUNE, FS_FLAG_NO_KAHAN, FS_FLAG_TIMING,  # noqa: F401
+from ._native import (FS_F32, FS_F64, FS_FLAG_AUTOTUNE, FS_FLAG_NO_KAHAN, FS_FLAG_SERIAL, FS_FLAG_TIMING,  # noqa: F401
                       FastSumError, FsBatchFacts, FsInfo, FsInstance, FsOpts, NativeLibraryMissing, check, load)
 
 __all__ = [
@@ -31,7 +31,7 @@ __all__ = [
     "FS_FLAG_TIMING", "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization",
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path", "FastSumFn",
-    "FS_FLAG_AUTOTUNE", "FastSumBatch", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status",
+    "FS_FLAG_AUTOTUNE", "FS_FLAG_SERIAL", "FastSumBatch", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status",
     "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest", "FastSum3", "fs3_plan_create",
     "fs3_set_charges", "fs3_eval_field", "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
     "fs3_plan_create_fem", "fs3_set_magnetization", "fs3_fem_charges", "fs3_fem_sources",

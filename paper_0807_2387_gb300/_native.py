@@ -12,7 +12,7 @@ FS_OK, FS_EINVAL, FS_EDOMAIN, FS_ENOMEM, FS_ECUDA, FS_ETIMEOUT, FS_EUNSUPPORTED 
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_EDOMAIN", 3: "FS_ENOMEM", 4: "FS_ECUDA",
                 5: "FS_ETIMEOUT", 6: "FS_EUNSUPPORTED"}
 FS_F32, FS_F64 = 32, 64
-FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FS_FLAG_AUTOTUNE = 1, 2, 4
+FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FS_FLAG_AUTOTUNE, FS_FLAG_SERIAL = 1, 2, 4, 8
 
 EXPORTED = (
     "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization", "fs_set_magnetization_static",

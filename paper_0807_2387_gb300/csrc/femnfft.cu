@@ -563,7 +563,7 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     }
 
     // FP32 target-major plans overlap the near field with spreading and the transform
-    if (sizeof(real) == 4 && !pl->src_major && N > 0) {
+    if (sizeof(real) == 4 && !pl->src_major && N > 0 && !(pl->flags & FS_FLAG_SERIAL)) {
         FS_CUDA(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
         FS_CUDA(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming));
         FS_CUDA(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming));
