@@ -161,8 +161,9 @@ def algorithmic_bytes(info, n_points):
 # the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
 # reports null until it is re-captured).
 NEAR_TRAFFIC = {
-    # profiles/k_near_list_mixture_2p19.md: 27.77 MB per launch at 2^19 points, scaled by the point count
-    "b329bc8abd3974da49bc4d2051818f73b45954ca6d3c846ff6dbf50c1314b203": 2 * (27765504 + 1024),
+    # profiles/k_near_list_mixture_2p19.md: 21.46 MB per launch at 2^19 points (the spreading, now
+    # launched just before it, leaves part of the point data in L2), scaled by the point count
+    "2784a642e434f3e53400edcc751f5a32aaff08cce0ec712d366fd034ea193681": 2 * 21456640,
 }
 
 
