@@ -453,3 +453,25 @@ def test_dense_pile_overflows_candidate_lists(pkg, precision, tol):
     phi, H, _ = gpu_field(pkg, case, precision)
     phi_o, H_o = oracle_field(case)
     assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))
+
+
+def test_overlapped_near_field_matches_serial(pkg):
+    """The near field on a second stream (stored first, far field added by the interpolation) gives the
+    results of the serial order (far field first) up to the rounding of the spreading's atomic tile
+    flushes; a missing dependency would lose or double the whole near field instead."""
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(41, 20000, 15000, n=128, m=5, eps_I=5 / 128, coincident=True)
+    dev = torch.device("cuda", 0)
+    src = torch.tensor(case["src"], device=dev)
+    tgt = torch.tensor(case["tgt"], device=dev)
+    q = torch.tensor(np.stack([case["q"], -2.0 * case["q"] + 0.5]), device=dev)
+    out = []
+    for flags in (0, pkg.FS_FLAG_SERIAL):
+        fs = pkg.FastSum(src, tgt, case["n"], case["sigma"], case["m"], case["eps_I"], precision=32, flags=flags)
+        fs.set_charges(q)
+        phi, H = fs.field()
+        fs.sync()
+        out.append((phi.cpu().numpy(), H.cpu().numpy()))
+        fs.close()
+    assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6, \
+        (rel(out[0][0], out[1][0]), rel(out[0][1], out[1][1]))
