@@ -95,9 +95,11 @@ constexpr int kSpread3ItemMax = 1024;
 size_t spread3_tile_smem(int cell, int m);
 cudaError_t launch_spread3_tile(const int2 *items, int n_items, int m, int cell, const int *base, const float *frac,
                                 const float *q, const WindowPoly &wp, float *grid, int n_a, cudaStream_t st);
+// acc: add to phi_s / grad_s (the near field stored there first) instead of writing them
 template <typename real>
 cudaError_t launch_interp3(int64_t N, int m, const int *base, const real *frac, Window<real> w, const WindowPoly &wp,
-                           const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, cudaStream_t st);
+                           const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, bool acc,
+                           cudaStream_t st);
 // FP64 near field, thread per target over the 27 cells around its own
 cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_pos, const double *src_pos,
                              const int *src_start, CellGrid3 cg, const double *q, NearParams<double> np,
@@ -105,10 +107,11 @@ cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_p
 // FP32 near field over warp items {first target, count <= 64} of one cell each (sorted order);
 // coincident pairs (equal positions) are listed per target in coinc_start / coinc_src
 // (pairs closer than eps_I / 8 refine their difference from the FP64 positions tgt_pos, src_pos)
+// (assign: store phi_s / grad_s instead of adding, for the near field run beside the far field)
 cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_base, const float4 *tgt_p32,
                               const float4 *src_p32, const double *tgt_pos, const double *src_pos, const float *q,
                               const int *src_start, CellGrid3 cg, const Near3Params &np, const int *coinc_start,
-                              const int *coinc_src, float *phi_s, float *grad_s, cudaStream_t st);
+                              const int *coinc_src, float *phi_s, float *grad_s, bool assign, cudaStream_t st);
 // Source-major FP32 near field (many more sources than targets): items of at most 64 sources of
 // one cell; phi and grad phi are added to the targets with atomics, then the coincident pairs'
 // -q T_I(0) when any_coincident

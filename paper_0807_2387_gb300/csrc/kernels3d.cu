@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(kSpread3Warps * 32) k_spread3_tile(const int2 
 template <typename real, int M2>
 __global__ void __launch_bounds__(256) k_interp3(int64_t N, const int *__restrict__ base, const real *__restrict__ frac,
                                                  Window<real> w, WindowPoly wp, const real *__restrict__ grid, int n_a,
-                                                 real n_os, real *__restrict__ phi_s, real *__restrict__ grad_s)
+                                                 real n_os, real *__restrict__ phi_s, real *__restrict__ grad_s,
+                                                 bool acc)
 {
     constexpr int m = M2 / 2;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -346,10 +347,11 @@ __global__ void __launch_bounds__(256) k_interp3(int64_t N, const int *__restric
         gy += wt[2][c] * ty;
         gz += dt[2][c] * t;
     }
-    phi_s[k] = phi;
-    grad_s[3 * k] = n_os * gx;
-    grad_s[3 * k + 1] = n_os * gy;
-    grad_s[3 * k + 2] = n_os * gz;
+    // acc: the near field was stored first (it ran beside spreading and the transform)
+    phi_s[k] = acc ? phi_s[k] + phi : phi;
+    grad_s[3 * k] = acc ? grad_s[3 * k] + n_os * gx : n_os * gx;
+    grad_s[3 * k + 1] = acc ? grad_s[3 * k + 1] + n_os * gy : n_os * gy;
+    grad_s[3 * k + 2] = acc ? grad_s[3 * k + 2] + n_os * gz : n_os * gz;
 }
 
 // FP64 near-field correction at target k (thread per target) over the 27 cells around its cell.
@@ -544,7 +546,8 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
                                                                  const int *__restrict__ src_start, CellGrid3 cg,
                                                                  Near3Params np, const int *__restrict__ coinc_start,
                                                                  const int *__restrict__ coinc_src,
-                                                                 float *__restrict__ phi_s, float *__restrict__ grad_s)
+                                                                 float *__restrict__ phi_s, float *__restrict__ grad_s,
+                                                                 bool assign)
 {
     __shared__ float4 lists[kNear3Warps][kNear3Cap][2];
     __shared__ float4 clists[kNear3Warps][kNear3CloseCap][2];
@@ -647,10 +650,11 @@ __global__ void __launch_bounds__(kNear3Warps * 32) k_near3_warp(const int2 *__r
         float self = 0.f;
         for (int c = coinc_start[k]; c < coinc_start[k + 1]; ++c)
             self += q[coinc_src[c]];
-        phi_s[k] += ph[t] - np.beta0 * self;
-        grad_s[3 * k] -= np.inv_eps * ggx[t];
-        grad_s[3 * k + 1] -= np.inv_eps * ggy[t];
-        grad_s[3 * k + 2] -= np.inv_eps * ggz[t];
+        const float p0 = assign ? 0.f : phi_s[k];
+        phi_s[k] = p0 + (ph[t] - np.beta0 * self);
+        grad_s[3 * k] = (assign ? 0.f : grad_s[3 * k]) - np.inv_eps * ggx[t];
+        grad_s[3 * k + 1] = (assign ? 0.f : grad_s[3 * k + 1]) - np.inv_eps * ggy[t];
+        grad_s[3 * k + 2] = (assign ? 0.f : grad_s[3 * k + 2]) - np.inv_eps * ggz[t];
     }
 }
 
@@ -976,13 +980,14 @@ cudaError_t launch_spread3_tile(const int2 *items, int n_items, int m, int cell,
 
 template <typename real>
 cudaError_t launch_interp3(int64_t N, int m, const int *base, const real *frac, Window<real> w, const WindowPoly &wp,
-                           const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, cudaStream_t st)
+                           const real *grid, int n_a, real n_os, real *phi_s, real *grad_s, bool acc,
+                           cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
     return with_width3(m, [&](auto mc) {
         constexpr int M2 = decltype(mc)::value;
-        k_interp3<real, M2><<<nblk(N, 256), 256, 0, st>>>(N, base, frac, w, wp, grid, n_a, n_os, phi_s, grad_s);
+        k_interp3<real, M2><<<nblk(N, 256), 256, 0, st>>>(N, base, frac, w, wp, grid, n_a, n_os, phi_s, grad_s, acc);
         return cudaGetLastError();
     });
 }
@@ -1000,7 +1005,7 @@ cudaError_t launch_near3_f64(int64_t N, const int *tgt_base, const double *tgt_p
 cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_base, const float4 *tgt_p32,
                               const float4 *src_p32, const double *tgt_pos, const double *src_pos, const float *q,
                               const int *src_start, CellGrid3 cg, const Near3Params &np, const int *coinc_start,
-                              const int *coinc_src, float *phi_s, float *grad_s, cudaStream_t st)
+                              const int *coinc_src, float *phi_s, float *grad_s, bool assign, cudaStream_t st)
 {
     if (n_items <= 0)
         return cudaSuccess;
@@ -1009,7 +1014,7 @@ cudaError_t launch_near3_warp(const int2 *items, int n_items, const int *tgt_bas
         constexpr int P = decltype(pc)::value;
         k_near3_warp<P><<<blocks, kNear3Warps * 32, 0, st>>>(items, n_items, tgt_base, tgt_p32, src_p32, tgt_pos,
                                                               src_pos, q, src_start, cg, np, coinc_start, coinc_src,
-                                                              phi_s, grad_s);
+                                                              phi_s, grad_s, assign);
         return cudaGetLastError();
     });
 }
@@ -1066,7 +1071,7 @@ cudaError_t launch_unpermute3(int64_t N, const real *phi_s, const real *grad_s, 
     template cudaError_t launch_spread3<real>(int64_t, int, const int *, const real *, const real *, Window<real>, \
                                               const WindowPoly &, real *, int, cudaStream_t);                     \
     template cudaError_t launch_interp3<real>(int64_t, int, const int *, const real *, Window<real>,               \
-                                              const WindowPoly &, const real *, int, real, real *, real *,        \
+                                              const WindowPoly &, const real *, int, real, real *, real *, bool,  \
                                               cudaStream_t);                                                      \
     template cudaError_t launch_unpermute3<real>(int64_t, const real *, const real *, const int *, double, void *, \
                                                  void *, int, cudaStream_t);

@@ -51,6 +51,9 @@ struct fs3_plan {
     int2 *src_items = nullptr;
     int n_src_items = 0;
     int n_coinc = 0;
+    // FP32: the near field on a second stream beside spreading and the transform
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int *coinc_start = nullptr, *coinc_src = nullptr;
     // tetrahedral FEM plans: sources are the quadrature points, targets the nodes
     bool is_fem = false;
@@ -382,6 +385,11 @@ fs_status near_setup3(fs3_plan *pl)
                                     cudaMemcpyHostToDevice, st));
     }
     pl->src_major = pl->N > 0 && pl->M >= 3 * pl->N;
+    if (pl->N > 0) {
+        FS_CUDA(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
+        FS_CUDA(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming));
+        FS_CUDA(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming));
+    }
     if (pl->src_major)
         FS_TRY(make_items(pl->src_start, &pl->src_items, &pl->n_src_items));
     else
@@ -524,8 +532,13 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
     const Near3Params np32 = sizeof(real) == 4 ? make_near3_f32(pl) : Near3Params{};
     const size_t osz = dtype == FS_F64 ? 8 : 4;
     const size_t cube = (size_t)pl->n_a * pl->n_a * pl->n_a;
+    // FP32 plans run the near field on a second stream beside spreading and the transform: it
+    // stores phi_s and grad_s (or adds atomically into zeroed ones) and the interpolation adds
+    const bool overlap = sizeof(real) == 4 && pl->aux != nullptr;
     for (int r = 0; r < pl->nrhs; ++r) {
         const real *q = (const real *)pl->q_sorted + (int64_t)r * pl->M;
+        if (overlap)
+            FS_CUDA(cudaEventRecord(pl->ev_fork, st));   // the charges are in
         FS_CUDA(cudaMemsetAsync(pl->grid, 0, cube * sizeof(real), st));
         if (sizeof(real) == 4 && pl->spread_tiles)
             FS_CUDA(launch_spread3_tile(pl->spread_items, pl->n_spread_items, pl->m, pl->cg.cell, pl->src_base,
@@ -534,24 +547,34 @@ template <typename real> fs_status eval3_t(fs3_plan *pl, void *phi, void *H, fs_
         else
             FS_CUDA(launch_spread3<real>(pl->M, pl->m, pl->src_base, (const real *)pl->src_frac, q, w, pl->wpoly,
                                          (real *)pl->grid, pl->n_a, st));
+        if constexpr (sizeof(real) == 4) {
+            if (overlap) {
+                cudaStream_t sa = pl->aux;
+                FS_CUDA(cudaStreamWaitEvent(sa, pl->ev_fork, 0));
+                if (pl->src_major) {
+                    FS_CUDA(cudaMemsetAsync(pl->phi_s, 0, sizeof(float) * (size_t)pl->N, sa));
+                    FS_CUDA(cudaMemsetAsync(pl->grad_s, 0, sizeof(float) * 3 * (size_t)pl->N, sa));
+                    FS_CUDA(launch_near3_src(pl->src_items, pl->n_src_items, pl->src_base, pl->src_p32, pl->tgt_p32,
+                                             pl->tgt_pos, pl->src_pos, (const float *)q, pl->tgt_start, pl->cg, np32,
+                                             pl->N, pl->coinc_start, pl->coinc_src, pl->n_coinc > 0,
+                                             (float *)pl->phi_s, (float *)pl->grad_s, sa));
+                } else {
+                    FS_CUDA(launch_near3_warp(pl->near_items, pl->n_near_items, pl->tgt_base, pl->tgt_p32,
+                                              pl->src_p32, pl->tgt_pos, pl->src_pos, (const float *)q, pl->src_start,
+                                              pl->cg, np32, pl->coinc_start, pl->coinc_src, (float *)pl->phi_s,
+                                              (float *)pl->grad_s, true, sa));
+                }
+                FS_CUDA(cudaEventRecord(pl->ev_join, sa));
+            }
+        }
         FS_CUDA(launch_fft3<real>((real *)pl->grid, pl->n_a, pl->n_os, pl->n, (C *)pl->spec1, (C *)pl->spec2,
                                   (const real *)pl->mul, (const C *)pl->tw, st));
+        if (overlap)
+            FS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
         FS_CUDA(launch_interp3<real>(pl->N, pl->m, pl->tgt_base, (const real *)pl->tgt_frac, w, pl->wpoly,
                                      (const real *)pl->grid, pl->n_a, (real)pl->n_os, (real *)pl->phi_s,
-                                     (real *)pl->grad_s, st));
-        if constexpr (sizeof(real) == 4) {
-            if (pl->src_major)
-                FS_CUDA(launch_near3_src(pl->src_items, pl->n_src_items, pl->src_base, pl->src_p32, pl->tgt_p32,
-                                         pl->tgt_pos, pl->src_pos, (const float *)q, pl->tgt_start, pl->cg, np32,
-                                         pl->N, pl->coinc_start, pl->coinc_src, pl->n_coinc > 0, (float *)pl->phi_s,
-                                         (float *)pl->grad_s, st));
-            else
-                FS_CUDA(launch_near3_warp(pl->near_items, pl->n_near_items, pl->tgt_base, pl->tgt_p32, pl->src_p32,
-                                          pl->tgt_pos, pl->src_pos, (const float *)q, pl->src_start, pl->cg, np32,
-                                          pl->coinc_start, pl->coinc_src, (float *)pl->phi_s, (float *)pl->grad_s,
-                                          st));
-        }
-        else
+                                     (real *)pl->grad_s, overlap, st));
+        if constexpr (sizeof(real) == 8)
             FS_CUDA(launch_near3_f64(pl->N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg,
                                      (const double *)q, np, (double *)pl->phi_s, (double *)pl->grad_s, st));
         void *po = phi ? (unsigned char *)phi + (size_t)r * pl->N * osz : nullptr;
@@ -568,6 +591,13 @@ void plan3_free(fs3_plan *pl)
         return;
     if (pl->stream)
         cudaStreamSynchronize(pl->stream);
+    if (pl->aux) {
+        cudaStreamSynchronize(pl->aux);
+        cudaStreamDestroy(pl->aux);
+    }
+    for (cudaEvent_t e : {pl->ev_fork, pl->ev_join})
+        if (e)
+            cudaEventDestroy(e);
     for (void *ptr : pl->allocs)
         cudaFree(ptr);
     delete pl;

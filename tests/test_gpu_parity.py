@@ -473,5 +473,5 @@ def test_overlapped_near_field_matches_serial(pkg):
         fs.sync()
         out.append((phi.cpu().numpy(), H.cpu().numpy()))
         fs.close()
-    assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6, \
+    assert rel(out[0][0], out[1][0]) <= 1e-5 and rel(out[0][1], out[1][1]) <= 1e-5, \
         (rel(out[0][0], out[1][0]), rel(out[0][1], out[1][1]))
