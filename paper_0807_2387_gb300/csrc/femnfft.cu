@@ -562,8 +562,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
         pl->release(cnt);
     }
 
-    // FP32 target-major plans overlap the near field with spreading and the transform
-    if (sizeof(real) == 4 && !pl->src_major && N > 0 && !(pl->flags & FS_FLAG_SERIAL)) {
+    // FP32 plans overlap the near field with spreading and the transform
+    if (sizeof(real) == 4 && N > 0 && !(pl->flags & FS_FLAG_SERIAL)) {
         FS_CUDA(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
         FS_CUDA(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming));
         FS_CUDA(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming));
@@ -683,10 +683,22 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
             FS_CUDA(cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0));
             if (rec)
                 FS_CUDA(cudaEventRecord(pl->ev_n0, pl->aux));
-            FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
-                                  pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q,
-                                  make_near<float>(pl), (float *)pl->phi_s, (float *)pl->grad_s, (float *)pl->coinc,
-                                  true, pl->aux));
+            if (pl->src_major) {
+                // source items add with atomics: zero the near-field sums first
+                const size_t nb = sizeof(float) * (size_t)pl->N;
+                FS_CUDA(cudaMemsetAsync(pl->phi_s, 0, nb, pl->aux));
+                FS_CUDA(cudaMemsetAsync(pl->grad_s, 0, 2 * nb, pl->aux));
+                FS_CUDA(cudaMemsetAsync(pl->coinc, 0, nb, pl->aux));
+                FS_CUDA(launch_near_src32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
+                                          pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
+                                          (const float *)q, make_near<float>(pl), (float *)pl->phi_s,
+                                          (float *)pl->grad_s, (float *)pl->coinc, pl->aux));
+            } else {
+                FS_CUDA(launch_near32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32, pl->tgt_lo32,
+                                      pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, (const float *)q,
+                                      make_near<float>(pl), (float *)pl->phi_s, (float *)pl->grad_s,
+                                      (float *)pl->coinc, true, pl->aux));
+            }
             if (rec)
                 FS_CUDA(cudaEventRecord(pl->ev_n1, pl->aux));
             FS_CUDA(cudaEventRecord(pl->ev_join, pl->aux));

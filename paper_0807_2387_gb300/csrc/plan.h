@@ -100,8 +100,8 @@ struct fs_plan {
     cudaEvent_t ev[fs::kStages + 1] = {};
     cudaEvent_t ev_q0 = nullptr, ev_q1 = nullptr;
     bool events = false;
-    // FP32 target-major plans: the near field runs on a second stream beside spreading and the
-    // transform (fork after the charges, join before the interpolation adds the far field)
+    // FP32 plans: the near field runs on a second stream beside spreading and the transform
+    // (fork after the charges, join before the interpolation adds the far field)
     bool overlap = false;
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
