@@ -852,39 +852,71 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
         const real *q = (const real *)pl->q_sorted + (int64_t)r * M;
         const void *gp = g_phi ? (const unsigned char *)g_phi + (size_t)r * N * isz : nullptr;
         const void *gh = g_H ? (const unsigned char *)g_H + (size_t)r * N * 2 * isz : nullptr;
+        // FP32 plans with a second stream run each near part beside the spreading and transform
+        // it does not depend on (stored first; the interpolation adds the far part)
+        const bool ovl = sizeof(real) == 4 && pl->aux != nullptr;
         if (dtgt) {
             // forward field and its Hessian at the targets (the grid is recomputed, not stored)
+            if constexpr (sizeof(real) == 4) {
+                if (ovl) {
+                    FS_CUDA(cudaEventRecord(pl->ev_fork, st));
+                    FS_CUDA(cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0));
+                    FS_CUDA(launch_near_hess32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32,
+                                               pl->tgt_lo32, pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, q, np,
+                                               (float *)pl->grad_s, (float *)pl->adj_hess, true, pl->aux));
+                    FS_CUDA(cudaEventRecord(pl->ev_join, pl->aux));
+                }
+            }
             FS_CUDA(cudaMemsetAsync(pl->grid, 0, grid_bytes, st));
             FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w,
                                         pl->wpoly, (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
             FS_TRY(spectral_pipeline<real>(pl));
+            if (ovl)
+                FS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
             FS_CUDA(launch_interp_hess<real>(N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly, (const real *)pl->grid,
-                                             pl->pitch, (real)pl->n_os, (real *)pl->grad_s, (real *)pl->adj_hess, st));
-            if constexpr (sizeof(real) == 4)
-                FS_CUDA(launch_near_hess32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32,
-                                           pl->tgt_lo32, pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, q, np,
-                                           (float *)pl->grad_s, (float *)pl->adj_hess, st));
-            else
+                                             pl->pitch, (real)pl->n_os, (real *)pl->grad_s, (real *)pl->adj_hess, ovl,
+                                             st));
+            if constexpr (sizeof(real) == 4) {
+                if (!ovl)
+                    FS_CUDA(launch_near_hess32(pl->n_near_items, pl->near_items, pl->tgt_base, pl->tgt_pos32,
+                                               pl->tgt_lo32, pl->src_pos32, pl->src_lo32, pl->src_start, pl->cg, q, np,
+                                               (float *)pl->grad_s, (float *)pl->adj_hess, false, st));
+            } else {
                 FS_CUDA(launch_near_hess64(N, pl->tgt_base, pl->tgt_pos, pl->src_pos, pl->src_start, pl->cg, q, np,
                                            (double *)pl->grad_s, (double *)pl->adj_hess, st));
+            }
         }
         FS_CUDA(cudaMemsetAsync(pl->adj_gsum, 0, sizeof(double), st));
         FS_CUDA(launch_gather_adj<real>(N, pl->tgt_perm, gp, gh, in_dtype == FS_F64, pl->s, (double)pl->n_os,
                                         (real *)pl->adj_c, pl->adj_dn, pl->adj_df, pl->adj_gsum, st));
         if (dq || dsrc) {
+            if constexpr (sizeof(real) == 4) {
+                if (ovl) {
+                    FS_CUDA(cudaEventRecord(pl->ev_fork, st));   // the adjoint weights are in
+                    FS_CUDA(cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0));
+                    FS_CUDA(launch_near_adj32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
+                                              pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
+                                              (const float *)pl->adj_c, pl->adj_dn, np, (float *)pl->adj_a,
+                                              (float *)pl->adj_ga, (float *)pl->adj_cg, true, pl->aux));
+                    FS_CUDA(cudaEventRecord(pl->ev_join, pl->aux));
+                }
+            }
             FS_CUDA(cudaMemsetAsync(pl->grid, 0, grid_bytes, st));
             FS_CUDA(launch_spread_dip<real>(pl->tgt_items, pl->n_tgt_items, pl->cg, pl->m, pl->tgt_base, pl->tgt_frac,
                                             (const real *)pl->adj_c, pl->adj_df, w, pl->wpoly, (real *)pl->grid,
                                             pl->pitch, pl->n_a, pl->kahan, st));
             FS_TRY(spectral_pipeline<real>(pl));
+            if (ovl)
+                FS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
             FS_CUDA(launch_interp<real>(M, pl->m, pl->src_base, pl->src_frac, w, pl->wpoly, (const real *)pl->grid,
-                                        pl->pitch, (real)pl->n_os, (real *)pl->adj_a, (real *)pl->adj_ga, false, st));
-            if constexpr (sizeof(real) == 4)
-                FS_CUDA(launch_near_adj32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
-                                          pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
-                                          (const float *)pl->adj_c, pl->adj_dn, np, (float *)pl->adj_a,
-                                          (float *)pl->adj_ga, (float *)pl->adj_cg, st));
-            else
+                                        pl->pitch, (real)pl->n_os, (real *)pl->adj_a, (real *)pl->adj_ga, ovl, st));
+            if constexpr (sizeof(real) == 4) {
+                if (!ovl)
+                    FS_CUDA(launch_near_adj32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
+                                              pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
+                                              (const float *)pl->adj_c, pl->adj_dn, np, (float *)pl->adj_a,
+                                              (float *)pl->adj_ga, (float *)pl->adj_cg, false, st));
+            } else
                 FS_CUDA(launch_near_adj64(M, pl->src_base, pl->src_pos, pl->tgt_pos, pl->tgt_start, pl->cg,
                                           (const double *)pl->adj_c, pl->adj_dn, np, (double *)pl->adj_a,
                                           (double *)pl->adj_ga, (double *)pl->adj_cg, st));

@@ -249,9 +249,10 @@ cudaError_t launch_spread_dip(const SpreadItem *items, int n_items, CellGrid cg,
                               const void *frac, const real *cq, const void *dq, Window<real> w, const WindowPoly &wp,
                               real *grid, int pitch, int n_a, bool kahan, cudaStream_t st);
 template <typename real>
+// (acc: add to grad_s / hess_s, where the near part was stored first)
 cudaError_t launch_interp_hess(int64_t N, int m, const int *base, const void *frac, Window<real> w,
                                const WindowPoly &wp, const real *grid, int pitch, real n_os, real *grad_s,
-                               real *hess_s, cudaStream_t st);
+                               real *hess_s, bool acc, cudaStream_t st);
 
 // ---- FFT and spectral multiply (kernels_fft.cu)
 template <typename real>
@@ -313,11 +314,12 @@ cudaError_t launch_near_hess64(int64_t N, const int *tgt_base, const double2 *tg
 cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,
                               const float2 *src_lo, const float2 *tgt_hi, const float2 *tgt_lo, const int *tgt_start,
                               CellGrid cg, const float *c, const void *dn, NearParams<float> np, float *a_s,
-                              float *ga_s, float *cg_s, cudaStream_t st);
+                              float *ga_s, float *cg_s, bool assign, cudaStream_t st);
+// (assign: store instead of adding, for the near parts run beside the spreading and transform)
 cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
                                const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                                CellGrid cg, const float *q, NearParams<float> np, float *grad_s, float *hess_s,
-                               cudaStream_t st);
+                               bool assign, cudaStream_t st);
 template <typename real>
 cudaError_t launch_adj_finish_src(int64_t M, const int *perm, const real *a_s, const real *ga_s, const real *cg_s,
                                   const real *q, double shift, const double *gsum, double s, void *dq, void *dy,

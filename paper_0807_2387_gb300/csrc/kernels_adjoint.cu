@@ -227,6 +227,7 @@ template <int P> struct NearHess32 {
     float *__restrict__ grad_s;
     float *__restrict__ hess_s;
     float rcoef, two_over_eps2, self_c;   // self_c = Hess T_I(0) / rc
+    bool assign;                           // store instead of adding (the far part is added later)
     float qj;
     float2 gx, gy, sI, sxx, sxy, syy;
 
@@ -259,12 +260,15 @@ template <int P> struct NearHess32 {
     __device__ __forceinline__ void row_end() {}
     __device__ __forceinline__ void store(int t, int64_t k)
     {
+        // (a select, not a product with 0: the stored-to buffers may hold anything, NaN included)
         const float i0 = comp(sI, t);
-        grad_s[2 * k] += rcoef * comp(gx, t);
-        grad_s[2 * k + 1] += rcoef * comp(gy, t);
-        hess_s[3 * k] += rcoef * fmaf(two_over_eps2, comp(sxx, t), i0);
-        hess_s[3 * k + 1] += rcoef * two_over_eps2 * comp(sxy, t);
-        hess_s[3 * k + 2] += rcoef * fmaf(two_over_eps2, comp(syy, t), i0);
+        const float v[5] = {rcoef * comp(gx, t), rcoef * comp(gy, t), rcoef * fmaf(two_over_eps2, comp(sxx, t), i0),
+                            rcoef * two_over_eps2 * comp(sxy, t), rcoef * fmaf(two_over_eps2, comp(syy, t), i0)};
+        grad_s[2 * k] = assign ? v[0] : grad_s[2 * k] + v[0];
+        grad_s[2 * k + 1] = assign ? v[1] : grad_s[2 * k + 1] + v[1];
+        hess_s[3 * k] = assign ? v[2] : hess_s[3 * k] + v[2];
+        hess_s[3 * k + 1] = assign ? v[3] : hess_s[3 * k + 1] + v[3];
+        hess_s[3 * k + 2] = assign ? v[4] : hess_s[3 * k + 2] + v[4];
     }
 };
 
@@ -281,6 +285,7 @@ template <int P> struct NearAdj32 {
     float *__restrict__ ga_s;
     float *__restrict__ cg_s;
     float rcoef, two_over_eps2, self_c;   // self_c = Hess T_I(0) / rc
+    bool assign;                           // store instead of adding (the far part is added later)
     float gp;
     float2 dn;
     float2 af, ac, gxc, gyc, gxk, gyk, gco;
@@ -334,9 +339,12 @@ template <int P> struct NearAdj32 {
     __device__ __forceinline__ void row_end() {}
     __device__ __forceinline__ void store(int t, int64_t k)
     {
-        a_s[k] += fmaf(-rcoef, comp(ac, t), comp(af, t));
-        ga_s[2 * k] += rcoef * fmaf(-two_over_eps2, comp(gxk, t), comp(gxc, t));
-        ga_s[2 * k + 1] += rcoef * fmaf(-two_over_eps2, comp(gyk, t), comp(gyc, t));
+        const float va = fmaf(-rcoef, comp(ac, t), comp(af, t));
+        const float vx = rcoef * fmaf(-two_over_eps2, comp(gxk, t), comp(gxc, t));
+        const float vy = rcoef * fmaf(-two_over_eps2, comp(gyk, t), comp(gyc, t));
+        a_s[k] = assign ? va : a_s[k] + va;
+        ga_s[2 * k] = assign ? vx : ga_s[2 * k] + vx;
+        ga_s[2 * k + 1] = assign ? vy : ga_s[2 * k + 1] + vy;
         cg_s[k] = comp(gco, t);
     }
 };
@@ -442,11 +450,12 @@ cudaError_t launch_near_hess64(int64_t N, const int *tgt_base, const double2 *tg
 cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src_base, const float2 *src_hi,
                               const float2 *src_lo, const float2 *tgt_hi, const float2 *tgt_lo, const int *tgt_start,
                               CellGrid cg, const float *c, const void *dn, NearParams<float> np, float *a_s,
-                              float *ga_s, float *cg_s, cudaStream_t st)
+                              float *ga_s, float *cg_s, bool assign, cudaStream_t st)
 {
     const NearSides sd{src_base, src_hi, src_lo, tgt_hi, tgt_lo, tgt_start};
     return with_degree(np.p, [&](auto pc) {
         NearAdj32<decltype(pc)::value> op{};
+        op.assign = assign;
         op.cw = c;
         op.dnw = (const float2 *)dn;
         op.a_s = a_s;
@@ -462,11 +471,12 @@ cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src
 cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tgt_base, const float2 *tgt_hi,
                                const float2 *tgt_lo, const float2 *src_hi, const float2 *src_lo, const int *src_start,
                                CellGrid cg, const float *q, NearParams<float> np, float *grad_s, float *hess_s,
-                               cudaStream_t st)
+                               bool assign, cudaStream_t st)
 {
     const NearSides sd{tgt_base, tgt_hi, tgt_lo, src_hi, src_lo, src_start};
     return with_degree(np.p, [&](auto pc) {
         NearHess32<decltype(pc)::value> op{};
+        op.assign = assign;
         op.q = q;
         op.grad_s = grad_s;
         op.hess_s = hess_s;

@@ -391,7 +391,8 @@ template <typename real, int M2>
 __global__ void __launch_bounds__(256) k_interp_hess(int64_t N, const int *__restrict__ base,
                                                      const real2_t<real> *__restrict__ frac, Window<real> w,
                                                      WindowPoly wp, const real *__restrict__ grid, int pitch,
-                                                     real n_os, real *__restrict__ grad_s, real *__restrict__ hess_s)
+                                                     real n_os, real *__restrict__ grad_s, real *__restrict__ hess_s,
+                                                     bool acc)
 {
     constexpr int m = M2 / 2;
     constexpr bool kRef = sizeof(real) == 4 && m >= 5;
@@ -452,12 +453,13 @@ __global__ void __launch_bounds__(256) k_interp_hess(int64_t N, const int *__res
         hxx += e1[a] * r0;
         hxy += d1[a] * r1;
     }
-    grad_s[2 * k] = n_os * gx;
-    grad_s[2 * k + 1] = n_os * gy;
+    // acc: the near part was stored first (it ran beside the spreading and the transform)
     const real n2 = n_os * n_os;
-    hess_s[3 * k] = n2 * hxx;
-    hess_s[3 * k + 1] = n2 * hxy;
-    hess_s[3 * k + 2] = n2 * hyy;
+    grad_s[2 * k] = acc ? grad_s[2 * k] + n_os * gx : n_os * gx;
+    grad_s[2 * k + 1] = acc ? grad_s[2 * k + 1] + n_os * gy : n_os * gy;
+    hess_s[3 * k] = acc ? hess_s[3 * k] + n2 * hxx : n2 * hxx;
+    hess_s[3 * k + 1] = acc ? hess_s[3 * k + 1] + n2 * hxy : n2 * hxy;
+    hess_s[3 * k + 2] = acc ? hess_s[3 * k + 2] + n2 * hyy : n2 * hyy;
 }
 
 template <typename real, int M2>
@@ -525,11 +527,12 @@ cudaError_t spread_dip_m(const SpreadItem *items, int n_items, CellGrid cg, cons
 
 template <typename real, int M2>
 cudaError_t interp_hess_m(int64_t N, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
-                          const real *grid, int pitch, real n_os, real *grad_s, real *hess_s, cudaStream_t st)
+                          const real *grid, int pitch, real n_os, real *grad_s, real *hess_s, bool acc,
+                          cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((N + 255) / 256);
     k_interp_hess<real, M2><<<blocks, 256, 0, st>>>(N, base, (const real2_t<real> *)frac, w, wp, grid, pitch, n_os,
-                                                     grad_s, hess_s);
+                                                     grad_s, hess_s, acc);
     return cudaGetLastError();
 }
 
@@ -562,14 +565,14 @@ cudaError_t launch_spread_dip(const SpreadItem *items, int n_items, CellGrid cg,
 template <typename real>
 cudaError_t launch_interp_hess(int64_t N, int m, const int *base, const void *frac, Window<real> w,
                                const WindowPoly &wp, const real *grid, int pitch, real n_os, real *grad_s,
-                               real *hess_s, cudaStream_t st)
+                               real *hess_s, bool acc, cudaStream_t st)
 {
     if (N <= 0)
         return cudaSuccess;
     switch (m) {
 #define FS_HESS_CASE(MM)                                                                                         \
     case MM:                                                                                                     \
-        return interp_hess_m<real, 2 * MM>(N, base, frac, w, wp, grid, pitch, n_os, grad_s, hess_s, st);
+        return interp_hess_m<real, 2 * MM>(N, base, frac, w, wp, grid, pitch, n_os, grad_s, hess_s, acc, st);
         FS_HESS_CASE(2)
         FS_HESS_CASE(3)
         FS_HESS_CASE(4)
@@ -589,11 +592,11 @@ template cudaError_t launch_spread_dip<double>(const SpreadItem *, int, CellGrid
                                                const double *, const void *, Window<double>, const WindowPoly &,
                                                double *, int, int, bool, cudaStream_t);
 template cudaError_t launch_interp_hess<float>(int64_t, int, const int *, const void *, Window<float>,
-                                               const WindowPoly &, const float *, int, float, float *, float *,
+                                               const WindowPoly &, const float *, int, float, float *, float *, bool,
                                                cudaStream_t);
 template cudaError_t launch_interp_hess<double>(int64_t, int, const int *, const void *, Window<double>,
                                                 const WindowPoly &, const double *, int, double, double *, double *,
-                                                cudaStream_t);
+                                                bool, cudaStream_t);
 
 template <typename real>
 cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base, const void *frac,
