@@ -23,7 +23,13 @@
  *  - The caller owns every buffer it passes; the plan owns its workspace
  *    (grids, sorted copies, coefficient tables) until fs_plan_destroy.
  *  - Compute calls are enqueued on the plan's stream (fs_opts.stream) and
- *    return before the work finishes, unless stated otherwise.
+ *    return before the work finishes, unless stated otherwise.  FP32 plans
+ *    (2D and 3D) also own a second, non-blocking stream: the near field of
+ *    fs_eval_field / fs_eval_potential / fs3_eval_field and of fs_adjoint runs
+ *    there beside the spreading and the transform, forked from and joined back
+ *    into the plan's stream with events, so every call still completes, as
+ *    seen from the plan's stream, in the order it was made (FS_FLAG_SERIAL
+ *    turns this off for 2D plans).
  *  - No call exits or aborts the process.  On failure a call returns a
  *    non-zero fs_status and fs_last_error() describes it; the plan stays
  *    valid for fs_plan_destroy.  Errors raised by kernels (points outside
