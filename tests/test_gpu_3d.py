@@ -139,3 +139,22 @@ def test_3d_dense_pile_overflows_candidate_lists(pkg, precision, tol):
         phi_o, H_o = phi, H
         phi, H, _ = gpu3(pkg, src, tgt, q, 32, 4, eps, 32)
     assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 5e-6)])
+def test_3d_source_major_with_coincident_points(pkg, precision, tol):
+    """Four sources per target (the FP32 plan sums the near field over source items) with targets on
+    sources: the coincident pairs' -q T_I(0) is applied per target after the atomic sums."""
+    from oracle import fastsum3 as F3
+    from oracle import kernel as K
+    rng = np.random.default_rng(24)
+    src = rng.uniform(-0.15, 0.15, (3200, 3))
+    tgt = np.concatenate([src[:500], rng.uniform(-0.15, 0.15, (300, 3))])
+    q = rng.standard_normal(len(src))
+    phi, H, _ = gpu3(pkg, src, tgt, q, 32, 4, 4 / 32, 64)
+    if precision == 64:
+        phi_o, H_o = F3.fast_sum3(src, tgt, q, K.make_params(32, 2.0, 4, 4 / 32), "nfft")
+    else:
+        phi_o, H_o = phi, H
+        phi, H, _ = gpu3(pkg, src, tgt, q, 32, 4, 4 / 32, 32)
+    assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))

@@ -475,3 +475,16 @@ def test_overlapped_near_field_matches_serial(pkg):
         fs.close()
     assert rel(out[0][0], out[1][0]) <= 1e-5 and rel(out[0][1], out[1][1]) <= 1e-5, \
         (rel(out[0][0], out[1][0]), rel(out[0][1], out[1][1]))
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 2e-5)])
+def test_source_major_near_field_with_coincident_points(pkg, precision, tol):
+    """Four sources per target (the FP32 plan then sums the near field over source items) and every
+    target on a source: the coincident charges reach the log shift through atomic adds."""
+    rng = np.random.default_rng(23)
+    src = rng.uniform(-0.2, 0.2, (4000, 2))
+    tgt = np.concatenate([src[:700], rng.uniform(-0.2, 0.2, (300, 2))])
+    case = dict(src=src, tgt=tgt, q=rng.standard_normal(4000), n=64, sigma=2.0, m=5, eps_I=5 / 64)
+    phi, H, _ = gpu_field(pkg, case, precision)
+    phi_o, H_o = oracle_field(case)
+    assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))
