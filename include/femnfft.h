@@ -423,7 +423,9 @@ fs_status fs3_sync_status(fs3_plan *plan);
 
 /* The plan's facts (fields of the 2D plan that have no 3D meaning are zero; for a
  * tetrahedral plan n_nodes, n_tris and n_bedges count nodes, tetrahedra and boundary
- * faces). */
+ * faces).  spread_items counts the FP32 spreading's shared-memory tile items: 0 when the
+ * plan spreads straight into the grid with atomics (its occupied cells hold fewer than
+ * about 300 sources on average, or the tiles do not fit in shared memory). */
 fs_status fs3_plan_info(const fs3_plan *plan, fs_info *info);
 
 /* Release the plan (synchronises its stream first). */

@@ -92,6 +92,11 @@ cudaError_t launch_spread3(int64_t M, int m, const int *base, const real *frac, 
 // FP32 spreading through warp-private shared tiles with compensation; items {first source,
 // count <= kSpread3ItemMax} of one cell each.  spread3_tile_smem is 0 when the tiles do not fit.
 constexpr int kSpread3ItemMax = 1024;
+// A tile costs its zeroing and its flush (2 (cell + 2m - 1)^3 words) per item, against one
+// global atomic per tap for direct spreading; FP32 plans take the tiles only where the cells
+// that hold sources hold at least this many on average (measured on GB300: direct spreading
+// wins up to ~190 sources per cell on tetrahedral meshes, tiles from ~440).
+constexpr int kSpread3TileMinPerCell = 300;
 size_t spread3_tile_smem(int cell, int m);
 cudaError_t launch_spread3_tile(const int2 *items, int n_items, int m, int cell, const int *base, const float *frac,
                                 const float *q, const WindowPoly &wp, float *grid, int n_a, cudaStream_t st);

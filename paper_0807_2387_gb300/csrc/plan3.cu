@@ -363,15 +363,20 @@ fs_status near_setup3(fs3_plan *pl)
             FS_CUDA(cudaMemcpyAsync(*out, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
         return FS_OK;
     };
-    // targets much sparser than sources (FEM meshes): items over the sources instead, whose boxes
-    // stay small where a cell's few targets would span the whole cell
-    // spreading items: the sources of each cell in pieces of at most kSpread3ItemMax
-    pl->spread_tiles = spread3_tile_smem(pl->cg.cell, pl->m) > 0;
-    if (pl->spread_tiles) {
-        std::vector<int> sstart((size_t)pl->cg.n_keys() + 1);
+    // spreading items: the sources of each cell in pieces of at most kSpread3ItemMax, where
+    // the tiles fit in shared memory and the occupied cells are dense enough to pay for them
+    std::vector<int> sstart;
+    if (spread3_tile_smem(pl->cg.cell, pl->m) > 0 && pl->M > 0) {
+        sstart.resize((size_t)pl->cg.n_keys() + 1);
         FS_CUDA(cudaMemcpyAsync(sstart.data(), pl->src_start, sizeof(int) * sstart.size(), cudaMemcpyDeviceToHost,
                                 st));
         FS_CUDA(cudaStreamSynchronize(st));
+        int64_t occupied = 0;
+        for (int c = 0; c < n_cells; ++c)
+            occupied += sstart[(size_t)(c + 1) * S3] > sstart[(size_t)c * S3];
+        pl->spread_tiles = pl->M >= (int64_t)kSpread3TileMinPerCell * occupied;
+    }
+    if (pl->spread_tiles) {
         std::vector<int2> sitems;
         for (int c = 0; c < n_cells; ++c) {
             const int a = sstart[(size_t)c * S3], b = sstart[(size_t)(c + 1) * S3];
@@ -384,6 +389,8 @@ fs_status near_setup3(fs3_plan *pl)
             FS_CUDA(cudaMemcpyAsync(pl->spread_items, sitems.data(), sizeof(int2) * sitems.size(),
                                     cudaMemcpyHostToDevice, st));
     }
+    // targets much sparser than sources (FEM meshes): near-field items over the sources
+    // instead, whose boxes stay small where a cell's few targets would span the whole cell
     pl->src_major = pl->N > 0 && pl->M >= 3 * pl->N;
     if (pl->N > 0) {
         FS_CUDA(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
@@ -802,6 +809,7 @@ fs_status fs3_plan_info(const fs3_plan *plan, fs_info *info)
     info->window_n = plan->n_a;
     info->cell = plan->cg.cell;
     info->cells_per_dim = plan->cg.n_c;
+    info->spread_items = plan->spread_tiles ? plan->n_spread_items : 0;
     info->workspace_bytes = plan->bytes;
     info->is_fem = plan->is_fem;
     info->n_nodes = plan->Nv;

@@ -79,6 +79,18 @@ def test_3d_fp32_matches_fp64(pkg, seed, ns, nt, n, m, eps, coinc):
     assert rel(H32, H64) <= 5e-6, rel(H32, H64)
 
 
+@pytest.mark.parametrize("ns,tiles", [(2000, False), (12000, True)])
+def test_3d_spreading_paths(pkg, ns, tiles):
+    """FP32 spreading straight into the grid with atomics (sparse cells) and through
+    shared-memory tiles (>= 300 sources per occupied cell) both match the FP64 path."""
+    src, tgt, q = case3(21, ns, 1500)
+    phi64, H64, _ = gpu3(pkg, src, tgt, q, 16, 4, 3 / 16, 64)
+    phi32, H32, info = gpu3(pkg, src, tgt, q, 16, 4, 3 / 16, 32)
+    assert (info["spread_items"] > 0) == tiles, info["spread_items"]
+    assert rel(phi32, phi64) <= 5e-6, rel(phi32, phi64)
+    assert rel(H32, H64) <= 5e-6, rel(H32, H64)
+
+
 def test_3d_approximation_error_against_direct_sum(pkg):
     from oracle import fastsum3 as F3
     src, tgt, q = case3(6, 4000, 3000)
