@@ -163,7 +163,10 @@ def algorithmic_bytes(info, n_points):
 NEAR_TRAFFIC = {
     # profiles/k_near_list_mixture_2p19.md: 21.46 MB per launch at 2^19 points (the spreading, now
     # launched just before it, leaves part of the point data in L2), scaled by the point count
-    "2784a642e434f3e53400edcc751f5a32aaff08cce0ec712d366fd034ea193681": 2 * 21456640,
+    "2784a642e434f3e53400edcc751f5a32aaff08cce0ec712d366fd034ea193681": (
+        2 * 21456640,
+        "captured on the same kernel source with the earlier target items (sub-cells of >= 32 "
+        "targets on their own); the items now split each cell evenly, not re-captured"),
 }
 
 
@@ -173,7 +176,8 @@ def near_traffic():
     for name in ("kernels_near.cu", "near_warp.cuh"):
         h.update(open(os.path.join(ROOT, "paper_0807_2387_gb300", "csrc", name), "rb").read())
     sha = h.hexdigest()
-    return NEAR_TRAFFIC.get(sha), sha
+    bytes_, note = NEAR_TRAFFIC.get(sha, (None, None))
+    return bytes_, note, sha
 
 
 def on_chip_bound_ms(info, stage, sm_mhz=2070.0):
@@ -625,11 +629,12 @@ def run_ours(args):
         achieved = info["near_pairs"] * fpp / (stage_ms["near"] / 1e3) / 1e12
         sm_max = 2070.0
         peak_alu = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-        traffic, sha = near_traffic()
+        traffic, traffic_note, sha = near_traffic()
         if args.traffic is not None:
-            traffic = args.traffic
+            traffic, traffic_note = args.traffic, "given with --traffic"
         roof = {"kernel": f"k_near_list<NearFwd<{info['p']},1,0>>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
+                "traffic_note": traffic_note,
                 "kernel_source_sha256": sha[:16],
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "work": f"{info['near_pairs']} pairs x {fpp} flop"}
