@@ -75,3 +75,45 @@ def test_product_path_does_not_import_the_oracle():
             glob.glob(os.path.join(pkg_dir, "csrc", "*")):
         text = open(path, errors="replace").read()
         assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), path
+
+
+def test_binding_layouts_and_constants_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the header's size and field offsets, and the
+    binding's status, dtype and flag constants have the header's values (compiled with gcc)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_0807_2387_gb300 import _native as N
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fs_opts": N.FsOpts, "fs_info": N.FsInfo, "fs_instance": N.FsInstance,
+               "fs_batch_facts": N.FsBatchFacts}
+    consts = ["FS_OK", "FS_EINVAL", "FS_EDOMAIN", "FS_ENOMEM", "FS_ECUDA", "FS_ETIMEOUT", "FS_EUNSUPPORTED",
+              "FS_F32", "FS_F64", "FS_FLAG_NO_KAHAN", "FS_FLAG_TIMING", "FS_FLAG_AUTOTUNE", "FS_FLAG_SERIAL"]
+    lines = ['#include <stdio.h>', '#include "femnfft.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("size {cname} %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("off {cname}.{field} %zu\\n", offsetof({cname}, {field}));')
+    for c in consts:
+        lines.append(f'printf("const {c} %lld\\n", (long long)({c}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            kind, name, value = line.split()
+            got[(kind, name)] = int(value)
+    for cname, cls in structs.items():
+        assert got[("size", cname)] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[("off", f"{cname}.{field}")] == getattr(cls, field).offset, (cname, field)
+    for c in consts:
+        assert got[("const", c)] == getattr(N, c), c
