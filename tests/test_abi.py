@@ -117,3 +117,51 @@ def test_binding_layouts_and_constants_match_the_header(tmp_path):
             assert got[("off", f"{cname}.{field}")] == getattr(cls, field).offset, (cname, field)
     for c in consts:
         assert got[("const", c)] == getattr(N, c), c
+
+
+def _header_params():
+    """Parameter kinds of every fs_/fs3_ entry point, read from the header's declarations."""
+    text = ""
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text += re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(fs3?_\w+)\s*\(([^()]*)\)\s*;", text):
+        params = [p.strip() for p in m.group(2).split(",")]
+        if params == ["void"]:
+            params = []
+        kinds = []
+        for p in params:
+            if "*" in p:
+                kinds.append("ptr")
+            elif re.search(r"\bint64_t\b", p):
+                kinds.append("i64")
+            elif re.search(r"\bdouble\b", p):
+                kinds.append("f64")
+            else:
+                kinds.append("i32")   # int, unsigned, fs_dtype (an enum)
+        out[m.group(1)] = kinds
+    return out
+
+
+def test_binding_argument_kinds_match_the_header(lib):
+    """The binding passes each entry point as many arguments as the header declares, each of
+    the declared kind (pointer, 64-bit integer, 32-bit integer or enum, double)."""
+    import ctypes
+    decl = _header_params()
+    assert decl, "no declarations parsed"
+    for name, kinds in decl.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None, name
+        got = []
+        for t in argtypes:
+            if t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "_type_") and issubclass(t, ctypes._Pointer):
+                got.append("ptr")
+            elif t is ctypes.c_int64:
+                got.append("i64")
+            elif t is ctypes.c_double:
+                got.append("f64")
+            elif t in (ctypes.c_int, ctypes.c_uint):
+                got.append("i32")
+            else:
+                got.append(repr(t))
+        assert got == kinds, (name, got, kinds)
