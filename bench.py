@@ -158,45 +158,73 @@ def algorithmic_bytes(info, n_points):
 
 
 # DRAM bytes per launch of the near-field kernel from an ncu capture, keyed by the SHA-256 of
-# the kernel sources it was taken on (kernels_near.cu + near_warp.cuh; a changed kernel
-# reports null until it is re-captured).
+# the code it was taken on: the kernel sources (kernels_near.cu, near_warp.cuh) and the
+# function that forms its work items (build_near_items in femnfft.cu).  A changed kernel or
+# item layout reports null until it is re-captured.
 NEAR_TRAFFIC = {
-    # profiles/k_near_list_mixture_2p19.md: 21.46 MB per launch at 2^19 points (the spreading, now
-    # launched just before it, leaves part of the point data in L2), scaled by the point count
-    "2784a642e434f3e53400edcc751f5a32aaff08cce0ec712d366fd034ea193681": (
-        2 * 21456640,
-        "captured on the same kernel source with the earlier target items (sub-cells of >= 32 "
-        "targets on their own); the items now split each cell evenly, not re-captured"),
+    # 21.48 MB per launch on the 2^19-point mixture (one-pass capture, -k regex:k_near_list -s 1 -c 1),
+    # scaled by the point count to the 2^20-point launch: the kernel reads per-point data once
+    "8be3b9f666b9503ab045cbff3e3a1e51f1dd16de3fa2435e939cb4183c6c3688": (
+        2 * 21484032, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 
-def near_traffic():
+def near_source_sha():
     import hashlib
+    csrc = os.path.join(ROOT, "paper_0807_2387_gb300", "csrc")
     h = hashlib.sha256()
     for name in ("kernels_near.cu", "near_warp.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_0807_2387_gb300", "csrc", name), "rb").read())
-    sha = h.hexdigest()
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    text = open(os.path.join(csrc, "femnfft.cu")).read()
+    start = text.index("fs_status build_near_items(")
+    h.update(text[start:text.index("\n}\n", start)].encode())
+    return h.hexdigest()
+
+
+def near_traffic():
+    sha = near_source_sha()
     bytes_, note = NEAR_TRAFFIC.get(sha, (None, None))
     return bytes_, note, sha
 
 
-def on_chip_bound_ms(info, stage, sm_mhz=2070.0):
+def on_chip_bound_ms(info, stage, sms, fp32_lane_ops_per_s, sm_mhz):
     """Lower bound of a grid stage that is not HBM-bound, from its on-chip work (None if not modelled).
 
     spread: per source, ceil((2m)^2 / 32) tap iterations of 4 shared-memory accesses (value and
     compensation, read and write) and 2 weight shuffles, at one warp-wide MIO operation per SM
-    and cycle.  interp: per target, (2m)^2 taps x (1 load + 3 FMA) + 4 (2m) window polynomials
-    of degree 12, at 128 FP32 lanes per SM and cycle.
+    and cycle (sms SMs at the SM clock sm_mhz sampled during the run).  interp: per target,
+    (2m)^2 taps x (1 load + 3 FMA) + 4 (2m) window polynomials of degree 12, at the measured
+    FP32 fma rate (lane operations per second over the whole GPU).
     """
     m2 = 2 * info["m"]
-    f = sm_mhz * 1e6
     if stage == "spread":
         per_src = -(-m2 * m2 // 32) * (4 + 2)
-        return 1e3 * info["n_src"] * per_src / (152 * f)
+        return 1e3 * info["n_src"] * per_src / (sms * sm_mhz * 1e6)
     if stage == "interp":
         per_tgt = m2 * m2 * 4 + 4 * m2 * 12
-        return 1e3 * info["n_tgt"] * per_tgt / (152 * 128 * f)
+        return 1e3 * info["n_tgt"] * per_tgt / fp32_lane_ops_per_s
     return None
+
+
+def measure_alu_peaks(pkg, dev):
+    """FP32 fma, packed fma and MUFU throughput of this GPU (fs_probe_throughput), with the SM clock
+    sampled while the probes run.  The FP32 peak is the larger of the scalar and packed rates."""
+    import torch
+    out = {}
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        for name, mode, iters in (("ffma", pkg.FS_PROBE_FFMA, 65536), ("ffma2", pkg.FS_PROBE_FFMA2, 65536),
+                                  ("mufu", pkg.FS_PROBE_MUFU, 16384)):
+            ops, ms = pkg.fs_probe_throughput(mode, iters, 5)
+            out[name] = {"ops_per_s": ops, "ms_per_launch": round(ms, 3)}
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(dev)
+    fp32 = max(out["ffma"]["ops_per_s"], out["ffma2"]["ops_per_s"])
+    return {"sms": props.multi_processor_count, "fp32_tflops": fp32 / 1e12,
+            "ffma_tflops": out["ffma"]["ops_per_s"] / 1e12, "ffma2_tflops": out["ffma2"]["ops_per_s"] / 1e12,
+            "mufu_tops": out["mufu"]["ops_per_s"] / 1e12, "sm_mhz": clocks["sm_mhz"],
+            "reasons": clocks["reasons"],
+            "method": "fs_probe_throughput: 4 blocks x 256 threads per SM, 8 independent chains per thread, "
+                      "5 launches timed by CUDA events after one warm-up"}
 
 
 def near_flops_per_pair(p):
@@ -611,6 +639,8 @@ def run_ours(args):
                "h2d_bytes_per_step": qh.numel() * 4, "d2h_bytes_per_step": (ph.numel() + Hh.numel()) * 4}
 
     hbm, peak_src = peaks()
+    alu = measure_alu_peaks(pkg, dev)
+    run_mhz = clk.summary()["sm_mhz"] or alu["sm_mhz"] or 2070.0
     abytes = algorithmic_bytes(info, n_pts)
     stages = {}
     for s in STAGES:
@@ -619,7 +649,7 @@ def run_ours(args):
         stages[s] = {"ms": round(t, 5), "algorithmic_bytes": abytes[s],
                      "GB_per_s": round(gbs, 1) if gbs else None,
                      "frac_hbm": round(gbs / hbm, 4) if gbs else None}
-        lb = on_chip_bound_ms(info, s)
+        lb = on_chip_bound_ms(info, s, alu["sms"], alu["fp32_tflops"] * 1e12 / 2, run_mhz)
         if lb is not None and t > 0:
             stages[s]["on_chip_bound_ms"] = round(lb, 5)
             stages[s]["frac_of_on_chip_bound"] = round(lb / t, 4)
@@ -627,16 +657,17 @@ def run_ours(args):
     if dominant == "near":
         fpp = near_flops_per_pair(info["p"])
         achieved = info["near_pairs"] * fpp / (stage_ms["near"] / 1e3) / 1e12
-        sm_max = 2070.0
-        peak_alu = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        peak_alu = alu["fp32_tflops"]
         traffic, traffic_note, sha = near_traffic()
         if args.traffic is not None:
             traffic, traffic_note = args.traffic, "given with --traffic"
-        roof = {"kernel": f"k_near_list<NearFwd<{info['p']},1,0>>", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
-                "traffic_note": traffic_note,
+        roof = {"kernel": f"k_near_list<NearFwd<{info['p']},1,0>>", "bound": "alu", "achieved": round(achieved, 3),
+                "peak": round(peak_alu, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4),
+                "traffic": traffic, "traffic_note": traffic_note,
                 "kernel_source_sha256": sha[:16],
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": (f"measured FP32 fma peak (fs_probe_throughput) on {alu['sms']} SMs: scalar "
+                                f"{alu['ffma_tflops']:.2f}, packed {alu['ffma2_tflops']:.2f} TFLOP/s; SM clock "
+                                f"median {alu['sm_mhz']} MHz during the probe, {run_mhz} MHz during the timed steps"),
                 "work": f"{info['near_pairs']} pairs x {fpp} flop"}
     else:
         t = stage_ms[dominant]
@@ -681,7 +712,7 @@ def run_ours(args):
             "accuracy": acc, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": KERNELS_PER_STEP * args.steps,
             "near_pairs": info["near_pairs"], "near_pairs_fp64": info["near_pairs_fp64"],
-            "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src},
+            "wall_s": round(wall, 3), "peaks": {"hbm_gbs": hbm, "source": peak_src, "alu": alu},
             "batch_c4": batch, "adjoint_c3": adj, "fem_time_loop_c1": femloop, "kernel_3d": ball3d,
             "fem3_time_loop": fem3,
             "fft_comparison": fftcmp,

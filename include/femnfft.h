@@ -184,6 +184,9 @@ fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs);
  *    vectors; otherwise FS_EINVAL (this call will not allocate it).
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is cached per device and per CUDA context: after
+ *    cudaDeviceReset (or under another context) the next call looks it up
+ *    again, so that call too should come before any stream capture.
  *  - All calls share the one array and each call overwrites every element it
  *    reads, so nothing needs clearing; but calls that overlap on the GPU (on
  *    other streams, or for other plans on the same device) race on it, so the
@@ -350,6 +353,26 @@ fs_status fs_batch_destroy(fs_batch *batch);
  * check the timeout path without a fault.
  */
 fs_status fs_wait_selftest(int spins);
+
+/*
+ * Arithmetic throughput of the current device, measured: the denominators of the roofline
+ * fractions of this library's ALU-bound kernels (near field, spreading, interpolation).
+ * The paper has no counterpart.  A grid of 4 blocks x 256 threads per SM runs `iters`
+ * steps of 8 independent chains per thread of one operation:
+ *   FS_PROBE_FFMA   scalar FP32 fma, counted as 2 flop per lane
+ *   FS_PROBE_FFMA2  packed two-wide FP32 fma, counted as 4 flop per lane
+ *   FS_PROBE_MUFU   MUFU reciprocal and base-2 logarithm (rcp.approx, lg2.approx on alternate
+ *                   chains, each followed by an add), counted as 1 op per lane
+ * One warm-up launch, then `reps` launches timed with CUDA events on a private stream.
+ *  ops_per_s      [host] out: flop/s (or MUFU op/s) over the timed launches
+ *  ms_per_launch  [host] out: mean launch duration
+ * Allocates and frees a small scratch buffer; synchronising.  FS_EINVAL for an unknown
+ * mode or iters, reps < 1.
+ */
+#define FS_PROBE_FFMA 0
+#define FS_PROBE_FFMA2 1
+#define FS_PROBE_MUFU 2
+fs_status fs_probe_throughput(int mode, int iters, int reps, double *ops_per_s, double *ms_per_launch);
 
 /*
  * The 3D kernel G(r) = 1/(4 pi r): the paper names it (with tetrahedral P1 elements) as

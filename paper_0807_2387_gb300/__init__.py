@@ -12,7 +12,7 @@ The functions ``fs_plan_create``, ``fs_plan_create_fem``, ``fs_set_charges``,
 ``fs_plan_info``, ``fs_stage_times``, ``fs_plan_destroy``, ``fs_adjoint`` and the
 batch calls ``fs_batch_create``, ``fs_batch_eval``, ``fs_batch_sync_status``,
 ``fs_batch_info``, ``fs_batch_plan``, ``fs_batch_destroy``,
-``fs_wait_selftest`` and the 3D calls ``fs3_plan_create``, ``fs3_set_charges``,
+``fs_wait_selftest``, ``fs_probe_throughput`` and the 3D calls ``fs3_plan_create``, ``fs3_set_charges``,
 ``fs3_eval_field``, ``fs3_sync_status``, ``fs3_plan_info`` and
 ``fs3_plan_destroy`` mirror the C entry points one to one, taking torch tensors
 (or numpy arrays for host buffers).  ``FastSum`` wraps a plan, ``FastSumBatch``
@@ -22,8 +22,10 @@ a batch and ``FastSum3`` a 3D plan with tensor-returning methods.
 from __future__ import annotations
 
 import ctypes
+import weakref
 
 from ._native import (FS_F32, FS_F64, FS_FLAG_AUTOTUNE, FS_FLAG_NO_KAHAN, FS_FLAG_SERIAL, FS_FLAG_TIMING,  # noqa: F401
+                      FS_PROBE_FFMA, FS_PROBE_FFMA2, FS_PROBE_MUFU,
                       FastSumError, FsBatchFacts, FsInfo, FsInstance, FsOpts, NativeLibraryMissing, check, load)
 
 __all__ = [
@@ -32,8 +34,8 @@ __all__ = [
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "library_path", "FastSumFn",
     "FS_FLAG_AUTOTUNE", "FS_FLAG_SERIAL", "FastSumBatch", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status",
-    "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest", "FastSum3", "fs3_plan_create",
-    "fs3_set_charges", "fs3_eval_field", "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
+    "fs_batch_info", "fs_batch_plan", "fs_batch_destroy", "fs_wait_selftest", "fs_probe_throughput", "FastSum3",
+    "fs3_plan_create", "fs3_set_charges", "fs3_eval_field", "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy",
     "fs3_plan_create_fem", "fs3_set_magnetization", "fs3_fem_charges", "fs3_fem_sources",
 ]
 
@@ -277,6 +279,15 @@ def fs_wait_selftest(spins):
     return int(load().fs_wait_selftest(int(spins)))
 
 
+def fs_probe_throughput(mode, iters, reps):
+    """Measured FP32 fma / packed fma / MUFU throughput of the current device -> (ops/s, ms per launch)."""
+    lib = load()
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib.fs_probe_throughput(int(mode), int(iters), int(reps), ctypes.byref(ops), ctypes.byref(ms)),
+          "fs_probe_throughput")
+    return ops.value, ms.value
+
+
 def fs3_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts):
     """src (M,3), tgt (N,3) float64 CUDA tensors -> 3D plan handle (kernel 1/(4 pi r))."""
     torch = _torch()
@@ -361,14 +372,60 @@ class FastSum:
                  _owned=True, **opts):
         torch = _torch()
         self._owned = _owned
+        self._params = None
         if _handle is None:
             self._h = fs_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
             self.device = src.device
+            self._params = (n_grid, sigma_os, m_window, eps_I, dict(opts))
+            self._remember_positions(src, tgt)
         else:
             self._h = _handle
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.info = fs_plan_info(self._h)
         self.nrhs = 0
+
+    def _remember_positions(self, src, tgt):
+        # a private copy of the positions the plan was binned on, and the caller's tensors with
+        # their version counters (an unchanged tensor is then recognised without a comparison)
+        self._src_copy = src.detach().clone()
+        self._tgt_copy = self._src_copy if tgt is src else tgt.detach().clone()
+        self._see(src, tgt)
+
+    def _see(self, src, tgt):
+        # weak references: the check must not keep the caller's tensors alive
+        self._seen = (weakref.ref(src), src._version, weakref.ref(tgt), tgt._version)
+
+    def positions_match(self, src, tgt) -> bool:
+        """True when src and tgt hold the positions this plan was built on (for a FEM plan: its
+        quadrature points and the mesh nodes).  Plans handed out by a batch own no copy of their
+        points and always match."""
+        torch = _torch()
+        if getattr(self, "_src_copy", None) is None:
+            return True
+        s0, v0, t0, w0 = self._seen
+        if src is s0() and tgt is t0() and src._version == v0 and tgt._version == w0:
+            return True
+        same = (tuple(src.shape) == tuple(self._src_copy.shape) and tuple(tgt.shape) == tuple(self._tgt_copy.shape)
+                and bool(torch.equal(src.detach(), self._src_copy)) and bool(torch.equal(tgt.detach(), self._tgt_copy)))
+        if same:
+            self._see(src, tgt)
+        return same
+
+    def rebuild(self, src, tgt):
+        """Re-create the plan (binning, cells, near-field items) on new positions with the same
+        grid, window, radius and options.  Charges must be set again afterwards."""
+        if self._params is None:
+            raise ValueError("only plans created from point sets can be rebuilt on new positions "
+                             "(FEM and batch plans take their points from the mesh or the batch)")
+        n_grid, sigma_os, m_window, eps_I, opts = self._params
+        h = fs_plan_create(src, tgt, n_grid, sigma_os, m_window, eps_I, **opts)
+        self.close()
+        self._h, self._owned = h, True
+        self.device = src.device
+        self.info = fs_plan_info(self._h)
+        self.nrhs = 0
+        self._remember_positions(src, tgt)
+        return self
 
     @classmethod
     def fem(cls, nodes, tris, n_grid, sigma_os=2.0, m_window=6, eps_I=None, **opts):
@@ -376,6 +433,9 @@ class FastSum:
         obj = cls(_handle=h)
         obj.device = nodes.device
         obj._nodes = nodes            # the plan reads the caller's node array
+        obj._src_copy = obj.sources()
+        obj._tgt_copy = nodes.detach().clone()
+        obj._seen = (lambda: None, -1, weakref.ref(nodes), nodes._version)
         return obj
 
     @property
@@ -591,13 +651,20 @@ def _make_autograd():
     class _FastSumFn(torch.autograd.Function):
         """(phi, H) = FastSumFn.apply(q, src, tgt, plan) with a backward through fs_adjoint.
 
-        ``plan`` must have been built on the same positions ``src``/``tgt``; their
-        gradients are returned (the plan is not rebuilt when positions change).  For
-        sources = targets pass the same tensor twice and autograd adds both parts.
+        The result is always that of the positions passed in: when ``src`` or ``tgt``
+        differ from the positions ``plan`` was built on (other values, or the same tensor
+        changed in place), the plan is rebuilt on them first, with the same grid, window,
+        radius and options (binning is a function of the positions).  A FEM plan cannot be
+        rebuilt this way and raises ValueError on a mismatch.  For sources = targets pass
+        the same tensor twice and autograd adds both parts.
         """
 
         @staticmethod
         def forward(ctx, q, src, tgt, plan):
+            if not plan.positions_match(src, tgt):
+                s_ = src.detach().contiguous()
+                plan.rebuild(s_, s_ if tgt is src else tgt.detach().contiguous())
+                plan._see(src, tgt)
             plan.set_charges(q.detach().contiguous())
             phi, H = plan.field(dtype=q.dtype)
             ctx.plan = plan

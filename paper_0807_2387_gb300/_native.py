@@ -13,13 +13,14 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_EDOMAIN", 3: "FS_ENOMEM", 4: 
                 5: "FS_ETIMEOUT", 6: "FS_EUNSUPPORTED"}
 FS_F32, FS_F64 = 32, 64
 FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FS_FLAG_AUTOTUNE, FS_FLAG_SERIAL = 1, 2, 4, 8
+FS_PROBE_FFMA, FS_PROBE_FFMA2, FS_PROBE_MUFU = 0, 1, 2
 
 EXPORTED = (
     "fs_plan_create", "fs_plan_create_fem", "fs_set_charges", "fs_set_magnetization", "fs_set_magnetization_static",
     "fs_fem_charges", "fs_fem_sources", "fs_eval_potential", "fs_eval_field", "fs_solve_host", "fs_adjoint",
     "fs_sync_status", "fs_plan_info", "fs_stage_times", "fs_plan_destroy", "fs_last_error",
     "fs_version", "fs_batch_create", "fs_batch_eval", "fs_batch_sync_status", "fs_batch_info", "fs_batch_plan",
-    "fs_batch_destroy", "fs_wait_selftest", "fs3_plan_create", "fs3_set_charges", "fs3_eval_field",
+    "fs_batch_destroy", "fs_wait_selftest", "fs_probe_throughput", "fs3_plan_create", "fs3_set_charges", "fs3_eval_field",
     "fs3_sync_status", "fs3_plan_info", "fs3_plan_destroy", "fs3_plan_create_fem", "fs3_set_magnetization",
     "fs3_fem_charges", "fs3_fem_sources",
 )
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
         "fs_batch_plan": [P, I32, PP],
         "fs_batch_destroy": [P],
         "fs_wait_selftest": [I32],
+        "fs_probe_throughput": [I32, I32, I32, ctypes.POINTER(D), ctypes.POINTER(D)],
         "fs3_plan_create": [P, I64, P, I64, I32, D, I32, D, ctypes.POINTER(FsOpts), PP],
         "fs3_set_charges": [P, P, I32, I32],
         "fs3_eval_field": [P, P, P, I32],
