@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/femnfft.h"
 #include "internal.h"
 #include "plan.h"
@@ -1284,8 +1286,11 @@ fs_status fs_plan_destroy(fs_plan *plan)
 //
 // The intermediate FEM charges live in this file-scope device array instead of memory the
 // plan allocates.  Host code cannot use the array's name as a device address (on the host it
-// is only a stand-in symbol), so the address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, and passed to the kernels.
+// is only a stand-in symbol), so the address is looked up with cudaGetSymbolAddress, with the
+// device current, and passed to the kernels.  The lookup is cached per device and keyed on the
+// unique id of the device's current CUDA context: after cudaDeviceReset, or under another
+// context, the module is loaded again at another address, and the id differs, so the address
+// is looked up again instead of reusing a stale one.
 
 namespace {
 
@@ -1294,8 +1299,37 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_fem_charge_scratch[kStaticFemCharges];
 
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double *addr;
+};
 std::mutex g_scratch_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
+ScratchEntry g_scratch[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context (false when none is current yet).  The
+// driver calls are reached through the runtime's entry-point table, so the library does not
+// link the driver library itself.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa{}, qb{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return false;
+        get_current = reinterpret_cast<GetCurrent>(a);
+        get_id = reinterpret_cast<GetId>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx)
+        return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 fs_status static_scratch_address(double **out)
 {
@@ -1304,15 +1338,20 @@ fs_status static_scratch_address(double **out)
     if (dev < 0 || dev >= kMaxDevices)
         return fail(FS_EUNSUPPORTED, "device index beyond the static scratch table");
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (!have_id || !g_scratch[dev].addr || g_scratch[dev].ctx_id != id) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_fem_charge_scratch);
         if (e != cudaSuccess || !ptr)
             return fail(FS_ECUDA, std::string("cudaGetSymbolAddress of the static charge scratch failed: ") +
                                       cudaGetErrorString(e));
-        g_scratch_addr[dev] = static_cast<double *>(ptr);
+        // the lookup made the device's primary context current if none was
+        if (!current_context_id(&id))
+            return fail(FS_ECUDA, "no current CUDA context after the static scratch lookup");
+        g_scratch[dev] = ScratchEntry{id, static_cast<double *>(ptr)};
     }
-    *out = g_scratch_addr[dev];
+    *out = g_scratch[dev].addr;
     return FS_OK;
 }
 

@@ -4,7 +4,8 @@ fs_set_magnetization_static serves callers that must not call cudaMalloc (an
 active stream capture, a fixed memory budget, a per-step time loop): its
 intermediate charges live in a static device array inside the library instead
 of memory the plan allocates.  Its results must equal those of
-fs_set_magnetization, and two calls in a row must not see each other's data.
+fs_set_magnetization, two calls in a row must not see each other's data, and a
+call must leave the device's free memory unchanged.
 """
 
 import numpy as np
@@ -72,4 +73,21 @@ def test_static_entry_rejects_oversize_and_unreserved(pkg):
     with pytest.raises(pkg.FastSumError) as ei:
         pkg.fs_set_magnetization_static(fs.handle, big, nrhs)
     assert ei.value.status == 1 and "524288" in str(ei.value)
+    fs.close()
+
+
+def test_static_entry_leaves_free_device_memory_unchanged(pkg):
+    """After one warm-up call, a call of the static entry point changes the device's free
+    memory by nothing: no allocation is made on its path (an allocation would take at least
+    one 2 MiB page from the device)."""
+    fs, mags = _mesh_plan(pkg, 64)
+    fs.set_magnetization(mags[0])             # reserves the plan's charge storage
+    pkg.fs_set_magnetization_static(fs.handle, mags[1])
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for m in mags:
+        pkg.fs_set_magnetization_static(fs.handle, m)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
     fs.close()
