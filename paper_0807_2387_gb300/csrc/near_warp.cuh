@@ -9,9 +9,9 @@
 // (ballot) and appends them to candidate lists in shared memory, which all 32 lanes then
 // evaluate with branch-free masked arithmetic against both of their points.  Positions are
 // FP32 offsets from the cell corner stored as hi + lo; candidates within eps_I / 8 of the box
-// go to a second list whose pairs closer than eps_I / 8 refine their difference with an exact
-// TwoSum of the hi parts plus the lo parts, so r keeps full FP32 relative accuracy for nearly
-// coincident points, and exactly coincident pairs are detected (G(0) := 0).
+// go to a second list that carries their position in the item's frame as hi + lo as well, so
+// the pair difference keeps full FP32 relative accuracy for nearly coincident points, and
+// exactly coincident pairs are detected (G(0) := 0).
 //
 // With w = r^2 / eps_I^2 and f = G - T_I (T_I the inner polynomial of the
 // regularised kernel, p-fold contact with G at r = eps_I):
@@ -172,7 +172,8 @@ struct NearSides {
 // warp's lists in shared memory: "far" candidates (beyond eps_I / 8 of the box: no pair can
 // need the refined difference) shifted into the item's cell frame and negated,
 // (-x, -x, -y, -y), with their Op::kR values (charges, or the adjoint's weights); "close"
-// candidates with their hi and lo parts and the cell step, for the refined path.  A list is
+// candidates the same way as hi + lo pairs (the TwoSum of the cell step and -y_hi, with -y_lo
+// added to the low part), for the refined path.  A list is
 // evaluated when it fills and at the end: one shared broadcast load per candidate and no
 // per-candidate test or vote in the far loop.  Partial sums are kept per list evaluation
 // (op.row_begin / row_end).  An Op provides kMinBlocks, kUnroll, kR, init(), fetch(j, v)
@@ -199,39 +200,34 @@ __device__ __forceinline__ void near_eval_far(const float4 *s_xy, const float *s
     op.row_end();
 }
 
+// Close candidates carry their negated position in the item's frame as hi + lo
+// (n = -(offset of the cell step) - y, TwoSum-exact at list time), so the difference
+// d = (x_hi + n_hi) + (x_lo + n_lo) keeps full FP32 relative accuracy however small it is:
+// when x_hi and -n_hi are close the first sum is exact (Sterbenz), and when they are not,
+// d is of their size and one rounding is harmless.  Exactly coincident points give d = 0
+// (G(0) := 0); they are handled on a warp-uniform branch.
 template <class Op>
-__device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float2 *s_cl, const float *s_cq, int n,
-                                                const float2 (&xh)[2], const float2 (&xl)[2],
+__device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float4 *s_cl, const float *s_cq, int n,
+                                                float2 X, float2 Y, float2 XL, float2 YL,
                                                 const NearParams<float> &np, Op &op)
 {
     op.row_begin();
     for (int e = 0; e < n; ++e) {
-        const float4 c = s_cxy[e];                // (yh.x, yh.y, offx, offy)
-        const float2 l = s_cl[e];                 // (yl.x, yl.y)
+        const float4 c = s_cxy[e];                // (n_hi.x, n_hi.x, n_hi.y, n_hi.y)
+        const float4 l = s_cl[e];                 // (n_lo.x, n_lo.x, n_lo.y, n_lo.y)
         op.set_q(s_cq + e * Op::kR);
-        float2 dx = make_float2(xh[0].x + c.z - c.x, xh[1].x + c.z - c.x);
-        float2 dy = make_float2(xh[0].y + c.w - c.y, xh[1].y + c.w - c.y);
+        const float2 dx = add2(add2(X, make_float2(c.x, c.y)), add2(XL, make_float2(l.x, l.y)));
+        const float2 dy = add2(add2(Y, make_float2(c.z, c.w)), add2(YL, make_float2(l.z, l.w)));
         float2 r2 = fma2(dy, dy, mul2(dx, dx));
-        const bool c0 = r2.x < np.close2, c1 = r2.y < np.close2;
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            if (t == 0 ? c0 : c1) {
-                const float ex = refine_diff(xh[t].x, c.x, c.z, xl[t].x, l.x);
-                const float ey = refine_diff(xh[t].y, c.y, c.w, xl[t].y, l.y);
-                float e2 = ex * ex + ey * ey;
-                if (ex == 0.f && ey == 0.f) {
-                    op.coincident(np, t);
-                    e2 = np.eps2;                 // masked out: w = 1
-                }
-                if (t == 0) {
-                    dx.x = ex;
-                    dy.x = ey;
-                    r2.x = e2;
-                } else {
-                    dx.y = ex;
-                    dy.y = ey;
-                    r2.y = e2;
-                }
+        const bool z0 = dx.x == 0.f && dy.x == 0.f, z1 = dx.y == 0.f && dy.y == 0.f;
+        if (__any_sync(0xffffffffu, z0 || z1)) {
+            if (z0) {
+                op.coincident(np, 0);
+                r2.x = np.eps2;                   // masked out: w = 1
+            }
+            if (z1) {
+                op.coincident(np, 1);
+                r2.y = np.eps2;
             }
         }
         op.pair2(np, r2, dx, dy);
@@ -242,7 +238,7 @@ __device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float
 template <class Op>
 __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const NearSides &sd, const CellGrid &cg,
                                                    const NearParams<float> &np, Op &op, float4 *s_xy, float *s_q,
-                                                   float4 *s_cxy, float2 *s_cl, float *s_cq)
+                                                   float4 *s_cxy, float4 *s_cl, float *s_cq)
 {
     constexpr int R = Op::kR;
     const float h = np.hcell, eps = sqrtf(np.eps2);
@@ -279,6 +275,7 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
         if (!valid[t])
             xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
     const float2 X = make_float2(xh[0].x, xh[1].x), Y = make_float2(xh[0].y, xh[1].y);
+    const float2 XL = make_float2(xl[0].x, xl[1].x), YL = make_float2(xl[0].y, xl[1].y);
     const float margin = 1e-4f * eps + 1e-5f;
     const float reach = eps + margin;
     const float reach2 = reach * reach;
@@ -332,8 +329,14 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                 }
                 if (close) {
                     const int at = nc + __popc(mc & below);
-                    s_cxy[at] = make_float4(yh.x, yh.y, offx, offy);
-                    s_cl[at] = __ldg(sd.oth_lo + j);
+                    const float2 yl = __ldg(sd.oth_lo + j);
+                    // -(source in the item's frame) = off - y_hi - y_lo as hi + lo (TwoSum of off and -y_hi)
+                    const float hx = offx - yh.x, bx = hx - offx;
+                    const float lx = ((offx - (hx - bx)) + (-yh.x - bx)) - yl.x;
+                    const float hy = offy - yh.y, by = hy - offy;
+                    const float ly = ((offy - (hy - by)) + (-yh.y - by)) - yl.y;
+                    s_cxy[at] = make_float4(hx, hx, hy, hy);
+                    s_cl[at] = make_float4(lx, lx, ly, ly);
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         s_cq[at * R + r] = qv[r];
@@ -348,7 +351,7 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                 }
                 if (nc > kCloseCap - 32) {
                     __syncwarp();
-                    near_eval_close(s_cxy, s_cl, s_cq, nc, xh, xl, np, op);
+                    near_eval_close(s_cxy, s_cl, s_cq, nc, X, Y, XL, YL, np, op);
                     nc = 0;
                     __syncwarp();
                 }
@@ -357,7 +360,7 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
     }
     __syncwarp();
     near_eval_far(s_xy, s_q, nf, X, Y, np, op);
-    near_eval_close(s_cxy, s_cl, s_cq, nc, xh, xl, np, op);
+    near_eval_close(s_cxy, s_cl, s_cq, nc, X, Y, XL, YL, np, op);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
         if (valid[t])
@@ -369,7 +372,7 @@ template <int R> struct NearLists {
     float4 xy[4][kListCap];
     float q[4][kListCap * R];
     float4 cxy[4][kCloseCap];
-    float2 cl[4][kCloseCap];
+    float4 cl[4][kCloseCap];
     float cq[4][kCloseCap * R];
 };
 
