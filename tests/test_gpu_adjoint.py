@@ -6,9 +6,12 @@
   Richardson-extrapolated from h = 2e-6 and 1e-6 so close pairs' third derivatives
   do not swamp the check; points at the largest radius held fixed so the torus
   scale does not change);
+* the oracle's transposed fast summation O3^T (oracle/adjoint.py: the same algorithm in FP64
+  numpy), element by element: dq, dy and dx each within 1e-12 in relative L2 and in
+  max|gpu - oracle| / max|oracle| (only the rounding order differs);
 * the oracle's direct-sum gradient, within a small multiple of the forward's own
   approximation error against the direct sum;
-* FP32 against FP64.
+* FP32 against FP64 (the 2^18-point adjoint workload within 1e-5, element-wise bound included).
 """
 
 import numpy as np
@@ -30,8 +33,18 @@ def pkg():
 
 
 def rel(a, b):
+    """Relative L2 error (approximation-level comparisons with the direct sum)."""
     a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rel_elem(a, b):
+    """The larger of the relative L2 error and max|a - b| / max|b| (parity gates): one wrong
+    element cannot hide under a norm taken over many correct ones."""
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    nb, mb = np.linalg.norm(b), np.max(np.abs(b), initial=0.0)
+    return max(float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)),
+               float(np.max(np.abs(a - b), initial=0.0) / (mb if mb > 0 else 1.0)))
 
 
 def _case(seed, ns, nt, coincident=False, n=64, m=6, eps_I=4 / 64):
@@ -190,4 +203,132 @@ def test_autograd_function_energy_and_field_loss(pkg):
     dq_o, dy_o, dx_o = D.direct_adjoint(pts, pts, qn, 0.5 * qn, 2 * wn[:, None] * H_d)
     assert rel(gq, 0.5 * phi_d + dq_o) < 5e-5
     assert rel(gP, dy_o + dx_o) < 5e-5
+    fs.close()
+
+
+def _gpu_adjoint(pkg, fs, gphi, gH):
+    dev = torch.device("cuda", 0)
+    dq, dy, dx = fs.adjoint(torch.tensor(gphi, device=dev), torch.tensor(gH, device=dev), want_src=True,
+                            want_tgt=True, dtype=torch.float64)
+    fs.sync()
+    return dq.cpu().numpy(), dy.cpu().numpy(), dx.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed,ns,nt,n,m,eps,coincident", [
+    (211, 1, 1, 16, 3, 2 / 16, False),          # one source, one target
+    (212, 37, 53, 16, 4, 2 / 16, False),        # tiny, ragged
+    (213, 1500, 1300, 64, 6, 4 / 64, False),
+    (214, 1400, 1400, 128, 8, 8 / 128, True),   # sources = targets: coincident pairs
+    (215, 4000, 3100, 256, 5, 6 / 256, False),  # many cells and spreading tiles, ragged tail
+])
+def test_fp64_adjoint_matches_oracle_transpose(pkg, seed, ns, nt, n, m, eps, coincident):
+    from oracle import adjoint as A
+    from oracle import kernel as K
+    c = _case(seed, ns, nt, coincident=coincident, n=n, m=m, eps_I=eps)
+    rng = np.random.default_rng(seed)
+    nt = len(c["tgt"])
+    gphi, gH = rng.standard_normal(nt), rng.standard_normal((nt, 2))
+    fs, _, _ = _forward(pkg, c["src"], c["tgt"], c["q"], c, 64)
+    got = _gpu_adjoint(pkg, fs, gphi, gH)
+    fs.close()
+    par = K.make_params(c["n"], c["sigma"], c["m"], c["eps_I"])
+    want = A.fast_sum_adjoint(c["src"], c["tgt"], c["q"], gphi, gH, par)
+    for name, g, w in zip(("dq", "dy", "dx"), got, want):
+        assert rel_elem(g, w) <= 1e-12, (name, rel_elem(g, w))
+
+
+def test_fp64_fem_adjoint_matches_oracle_transpose(pkg):
+    """FEM plan: gradients with respect to the quadrature charges, the quadrature points and
+    the mesh nodes, against O3^T on the oracle's own quadrature points and charges."""
+    from oracle import adjoint as A
+    from oracle import fem
+    from oracle import kernel as K
+    from paper_0807_2387_gb300 import workloads as W
+    rng = np.random.default_rng(216)
+    nodes, tris = W.ring_mesh(rng, 24)
+    mag = W.vortex_magnetisation(nodes) + 0.3 * W.uniform_magnetisation(nodes)
+    dev = torch.device("cuda", 0)
+    fs = pkg.FastSum.fem(torch.tensor(nodes, device=dev), torch.tensor(tris, device=dev), 64, 2.0, 5, 4 / 64,
+                         precision=64)
+    fs.set_magnetization(torch.tensor(mag, device=dev))
+    gphi, gH = rng.standard_normal(len(nodes)), rng.standard_normal((len(nodes), 2))
+    got = _gpu_adjoint(pkg, fs, gphi, gH)
+    fs.close()
+    src = fem.quadrature_points(nodes, tris)
+    q = fem.assemble_charges(nodes, tris, mag)
+    want = A.fast_sum_adjoint(src, nodes, q, gphi, gH, K.make_params(64, 2.0, 5, 4 / 64))
+    for name, g, w in zip(("dq", "dy", "dx"), got, want):
+        assert rel_elem(g, w) <= 1e-12, (name, rel_elem(g, w))
+
+
+def test_fp32_adjoint_within_1e5_of_fp64_on_the_adjoint_workload(pkg):
+    """2^18 uniform points, sources = targets (n = 512, m = 5, eps_I = 6/512): the FP32 adjoint
+    against the FP64 adjoint, element-wise bound included."""
+    from paper_0807_2387_gb300 import workloads as W
+    c = W.uniform_c3()
+    rng = np.random.default_rng(217)
+    gphi, gH = 0.5 * c["q"], rng.standard_normal((len(c["tgt"]), 2))
+    out = {}
+    for precision in (32, 64):
+        fs, _, _ = _forward(pkg, c["src"], c["tgt"], c["q"], c, precision)
+        out[precision] = _gpu_adjoint(pkg, fs, gphi, gH)
+        fs.close()
+    for name, a, b in zip(("dq", "dy", "dx"), out[32], out[64]):
+        assert rel_elem(a, b) <= 1e-5, (name, rel_elem(a, b))
+
+
+def test_autograd_follows_moved_points(pkg):
+    """FastSumFn on moved points evaluates the moved points: the plan is rebuilt on them (same grid,
+    window and radius), for a new tensor and for the same tensor changed in place; the gradients
+    are those of a fresh plan on the new points."""
+    c = _case(218, 900, 800)
+    dev = torch.device("cuda", 0)
+    src = torch.tensor(c["src"], device=dev)
+    tgt = torch.tensor(c["tgt"], device=dev)
+    q = torch.tensor(c["q"], device=dev)
+    fs = pkg.FastSum(src, tgt, c["n"], c["sigma"], c["m"], c["eps_I"], precision=64)
+
+    def fresh(s_, t_):
+        f = pkg.FastSum(s_, t_, c["n"], c["sigma"], c["m"], c["eps_I"], precision=64)
+        f.set_charges(q)
+        p_, h_ = f.field(dtype=torch.float64)
+        f.sync()
+        return f, p_.cpu().numpy(), h_.cpu().numpy()
+
+    phi0, _ = pkg.FastSumFn.apply(q, src, tgt, fs)
+    src2 = (0.9 * src + 0.01).requires_grad_(True)
+    phi1, H1 = pkg.FastSumFn.apply(q, src2, tgt, fs)
+    ref, phi_r, H_r = fresh(src2.detach(), tgt)
+    assert rel_elem(phi1.detach().cpu().numpy(), phi_r) <= 1e-12
+    assert rel_elem(H1.detach().cpu().numpy(), H_r) <= 1e-12
+    assert rel(phi1.detach().cpu().numpy(), phi0.cpu().numpy()) > 1e-3     # the points did move
+    w = torch.tensor(np.random.default_rng(9).standard_normal(800), device=dev)
+    ((w * phi1).sum() + (H1 * H1).sum()).backward()
+    _, dy_r, _ = ref.adjoint(w, 2 * torch.tensor(H_r, device=dev), want_src=True, dtype=torch.float64)
+    ref.sync()
+    assert rel_elem(src2.grad.cpu().numpy(), dy_r.cpu().numpy()) <= 1e-12
+    ref.close()
+    # the same target tensor changed in place
+    with torch.no_grad():
+        tgt.mul_(0.95)
+    phi2, _ = pkg.FastSumFn.apply(q, src2.detach(), tgt, fs)
+    ref2, phi_r2, _ = fresh(src2.detach(), tgt)
+    assert rel_elem(phi2.cpu().numpy(), phi_r2) <= 1e-12
+    ref2.close()
+    fs.close()
+
+
+def test_autograd_rejects_moved_points_on_a_fem_plan(pkg):
+    from paper_0807_2387_gb300 import workloads as W
+    rng = np.random.default_rng(219)
+    nodes, tris = W.ring_mesh(rng, 16)
+    dev = torch.device("cuda", 0)
+    tn = torch.tensor(nodes, device=dev)
+    fs = pkg.FastSum.fem(tn, torch.tensor(tris, device=dev), 64, 2.0, 5, 4 / 64, precision=64)
+    src = fs.sources()
+    q = torch.ones(src.shape[0], dtype=torch.float64, device=dev)
+    phi, _ = pkg.FastSumFn.apply(q, src, tn, fs)                       # the plan's own points
+    assert torch.isfinite(phi).all()
+    with pytest.raises(ValueError):
+        pkg.FastSumFn.apply(q, src * 1.01, tn, fs)
     fs.close()
