@@ -21,6 +21,8 @@
 // FP64: one thread per point (the comparison path).  FP32: warp items over the
 // 8 x 8 sub-cells (near_warp.cuh), the Hessian over the forward's target items and
 // the adjoint potential over items of sources against the targets.
+#include <cmath>
+
 #include "internal.h"
 #include "near_warp.cuh"
 
@@ -216,7 +218,9 @@ __global__ void __launch_bounds__(256) k_near_hess64(int64_t N, const int *__res
 
 // Hessian at the targets (FP32 warp items, own = targets, other = sources, d = x - y):
 // grad += q c d, Hess += q (c I + (2 c' / eps_I^2) d d^T), with c = rc c^ and c' = rc c'^;
-// the sums over pairs are of the hatted forms and rc, 2 / eps_I^2 are applied at the store.
+// the sums over pairs are of the hatted forms with d in units of eps_I (as the traversal
+// hands it over, d = eps_I d'), so grad = rc eps_I sum q c^ d' and
+// Hess = rc sum q (c^ I + 2 c'^ d' d'^T): rc eps_I and rc are applied at the store.
 // For p >= 3 clamping w to 1 masks pairs beyond eps_I (c^ and c'^ vanish there); below, the
 // charge is masked.
 template <int P> struct NearHess32 {
@@ -226,7 +230,7 @@ template <int P> struct NearHess32 {
     const float *__restrict__ q;
     float *__restrict__ grad_s;
     float *__restrict__ hess_s;
-    float rcoef, two_over_eps2, self_c;   // self_c = Hess T_I(0) / rc
+    float rcoef, geps, self_c;             // rc, eps_I (gradient unit), self_c = Hess T_I(0) / rc
     bool assign;                           // store instead of adding (the far part is added later)
     float qj;
     float2 gx, gy, sI, sxx, sxy, syy;
@@ -239,7 +243,7 @@ template <int P> struct NearHess32 {
     __device__ __forceinline__ void coincident(const NearParams<float> &, int t) { add_comp(sI, t, -qj * self_c); }
     __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
-        float2 w = mul2(r2, f2(np.inv_eps2));
+        float2 w = r2;
         if constexpr (kClamp)
             w = min1(w);
         float2 c, cp;
@@ -261,9 +265,9 @@ template <int P> struct NearHess32 {
     __device__ __forceinline__ void store(int t, int64_t k)
     {
         // (a select, not a product with 0: the stored-to buffers may hold anything, NaN included)
-        const float i0 = comp(sI, t);
-        const float v[5] = {rcoef * comp(gx, t), rcoef * comp(gy, t), rcoef * fmaf(two_over_eps2, comp(sxx, t), i0),
-                            rcoef * two_over_eps2 * comp(sxy, t), rcoef * fmaf(two_over_eps2, comp(syy, t), i0)};
+        const float i0 = comp(sI, t), rg = rcoef * geps;
+        const float v[5] = {rg * comp(gx, t), rg * comp(gy, t), rcoef * fmaf(2.f, comp(sxx, t), i0),
+                            rcoef * 2.f * comp(sxy, t), rcoef * fmaf(2.f, comp(syy, t), i0)};
         grad_s[2 * k] = assign ? v[0] : grad_s[2 * k] + v[0];
         grad_s[2 * k + 1] = assign ? v[1] : grad_s[2 * k + 1] + v[1];
         hess_s[3 * k] = assign ? v[2] : hess_s[3 * k] + v[2];
@@ -274,7 +278,10 @@ template <int P> struct NearHess32 {
 
 // Adjoint potential at the sources (FP32 warp items, own = sources, other = targets,
 // d = y - x = -D):  A += gphi f - (dn . d) c,  grad_y A += c (gphi d - dn) - (2 c' / eps_I^2)(dn . d) d,
-// with the hatted c^, c'^ summed and rc, 2 / eps_I^2 applied at the store.
+// with the hatted c^, c'^ summed.  The traversal hands d over in units of eps_I (d = eps_I d')
+// and the dipoles are read as n' = dn / eps_I, so A = sum gphi f - rc eps_I^2 sum (n'.d') c^ and
+// grad_y A = rc eps_I sum (c^ (gphi d' - n') - 2 c'^ (n'.d') d'): the factors are applied at the
+// store.
 template <int P> struct NearAdj32 {
     static constexpr int kMinBlocks = 4;
     static constexpr int kUnroll = 2;
@@ -284,7 +291,7 @@ template <int P> struct NearAdj32 {
     float *__restrict__ a_s;
     float *__restrict__ ga_s;
     float *__restrict__ cg_s;
-    float rcoef, two_over_eps2, self_c;   // self_c = Hess T_I(0) / rc
+    float rcoef, geps, inv_eps, self_c;   // rc, eps_I, 1 / eps_I, self_c = Hess T_I(0) / rc
     bool assign;                           // store instead of adding (the far part is added later)
     float gp;
     float2 dn;
@@ -297,8 +304,8 @@ template <int P> struct NearAdj32 {
     {
         const float2 d = __ldg(dnw + i);
         v[0] = __ldg(cw + i);
-        v[1] = d.x;
-        v[2] = d.y;
+        v[1] = d.x * inv_eps;
+        v[2] = d.y * inv_eps;
     }
     __device__ __forceinline__ void set_q(const float *v)
     {
@@ -314,7 +321,7 @@ template <int P> struct NearAdj32 {
     }
     __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
-        float2 w = mul2(r2, f2(np.inv_eps2));
+        float2 w = r2;
         if constexpr (kClamp)
             w = min1(w);
         float2 c, cp;
@@ -339,9 +346,10 @@ template <int P> struct NearAdj32 {
     __device__ __forceinline__ void row_end() {}
     __device__ __forceinline__ void store(int t, int64_t k)
     {
-        const float va = fmaf(-rcoef, comp(ac, t), comp(af, t));
-        const float vx = rcoef * fmaf(-two_over_eps2, comp(gxk, t), comp(gxc, t));
-        const float vy = rcoef * fmaf(-two_over_eps2, comp(gyk, t), comp(gyc, t));
+        const float rg = rcoef * geps;
+        const float va = fmaf(-rg * geps, comp(ac, t), comp(af, t));
+        const float vx = rg * fmaf(-2.f, comp(gxk, t), comp(gxc, t));
+        const float vy = rg * fmaf(-2.f, comp(gyk, t), comp(gyc, t));
         a_s[k] = assign ? va : a_s[k] + va;
         ga_s[2 * k] = assign ? vx : ga_s[2 * k] + vx;
         ga_s[2 * k + 1] = assign ? vy : ga_s[2 * k + 1] + vy;
@@ -462,7 +470,8 @@ cudaError_t launch_near_adj32(int64_t n_items, const int2 *items, const int *src
         op.ga_s = ga_s;
         op.cg_s = cg_s;
         op.rcoef = np.rcoef;
-        op.two_over_eps2 = 2.f * np.inv_eps2;
+        op.geps = (float)std::sqrt((double)np.eps2);
+        op.inv_eps = (float)(1.0 / std::sqrt((double)np.eps2));
         op.self_c = self_hessian(np) / np.rcoef;
         return launch_near_list(n_items, items, sd, cg, np, op, st);
     });
@@ -481,7 +490,7 @@ cudaError_t launch_near_hess32(int64_t n_items, const int2 *items, const int *tg
         op.grad_s = grad_s;
         op.hess_s = hess_s;
         op.rcoef = np.rcoef;
-        op.two_over_eps2 = 2.f * np.inv_eps2;
+        op.geps = (float)std::sqrt((double)np.eps2);
         op.self_c = self_hessian(np) / np.rcoef;
         return launch_near_list(n_items, items, sd, cg, np, op, st);
     });

@@ -22,6 +22,8 @@
 // The output kernel adds the far and near fields and rescales:
 //     phi = phi~ + (log s / 2 pi) (sum_j q_j - coinc_i),   H = -s grad~ phi,
 // scattering back to the caller's target order.
+#include <cmath>
+
 #include "internal.h"
 #include "near_warp.cuh"
 
@@ -116,22 +118,24 @@ __global__ void __launch_bounds__(256) k_batch_near64(const BatchInst<double> *_
 
 // Forward correction at the targets for R right-hand sides at once (the pair geometry, the
 // log and the gradient coefficient are shared): phi += q f, grad += q c d, with the lane's
-// two targets as packed pairs and the factor rc of c applied once at the store.  With one
-// right-hand side the sums are split into partial sums per sub-cell row; with several the
-// registers go to the extra accumulators instead.  Right-hand side r reads q + r q_stride
-// and writes at r n_stride.
+// two targets as packed pairs and the factor rc eps_I of c applied once at the store (d
+// arrives in units of eps_I).  With one right-hand side the sums are split into partial sums
+// per list evaluation; with several the registers go to the extra accumulators instead.
+// Right-hand side r reads q + r q_stride and writes at r n_stride.
 template <int P, int R, bool BATCH = false> struct NearFwd {
-    // the batched kernel holds the instance's constants in registers (the single-plan one reads
-    // them from the constant bank), so it gets more registers and less unrolling
-    static constexpr int kMinBlocks = (R == 1 && !BATCH) ? 5 : 4;
-    static constexpr int kUnroll = (R == 1 && !BATCH) ? 4 : (R >= 4 ? 1 : 2);
+    // four blocks per SM (up to 128 registers); the single right-hand-side kernel unrolls its
+    // candidate loop eightfold (2.77 -> 2.66 ms at 2^20 points against fourfold at five blocks
+    // per SM); the batched kernel holds the instance's constants in registers (the single-plan
+    // one reads them from the constant bank) and unrolls less
+    static constexpr int kMinBlocks = 4;
+    static constexpr int kUnroll = (R == 1 && !BATCH) ? 8 : (R >= 4 ? 1 : 2);
     static constexpr bool kRows = R == 1;
     const float *__restrict__ q;
     float *__restrict__ phi_s;
     float *__restrict__ grad_s;
     float *__restrict__ coinc;
     int64_t q_stride, n_stride;
-    float rcoef;
+    float rcoef;   // rc eps_I: the pair differences arrive in units of eps_I
     bool assign;   // store phi_s / grad_s instead of adding (the far field is added later)
     float qj[R];
     float2 phi[R], gx[R], gy[R], qc[R];
@@ -171,7 +175,7 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
     }
     __device__ __forceinline__ void pair2(const NearParams<float> &np, float2 r2, float2 dx, float2 dy)
     {
-        float2 w = mul2(r2, f2(np.inv_eps2));
+        float2 w = r2;                                    // the traversal works in units of eps_I
         if constexpr (P >= 2)
             w = min1(w);                                  // f(1) = 0 and (w - 1)^(p-1) = 0: masked
         const float2 val = near_f2<P>(np, w);
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_
     op.coinc = b.coinc;
     op.q_stride = b.M;
     op.n_stride = b.N;
-    op.rcoef = np.rcoef;
+    op.rcoef = np.rcoef * sqrtf(np.eps2);
     op.assign = false;
     __shared__ NearLists<R> L;
     const int w = threadIdx.x >> 5;
@@ -374,7 +378,7 @@ cudaError_t launch_near32(int64_t n_items, const int2 *items, const int *tgt_bas
         op.coinc = coinc;
         op.q_stride = 0;
         op.n_stride = 0;
-        op.rcoef = np.rcoef;
+        op.rcoef = (float)((double)np.rcoef * std::sqrt((double)np.eps2));
         op.assign = assign;
         return launch_near_list(n_items, items, sd, cg, np, op, st);
     });

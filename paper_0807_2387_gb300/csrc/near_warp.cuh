@@ -179,7 +179,8 @@ struct NearSides {
 // (op.row_begin / row_end).  An Op provides kMinBlocks, kUnroll, kR, init(), fetch(j, v)
 // (the kR values of other point j), set_q(v) (those of the current candidate),
 // coincident(np, t) (slot t = 0, 1 coincides with it), pair2(np, r2, dx, dy) (both slots
-// packed; pairs with r2 >= eps_I^2 must contribute nothing), row_begin(), row_end() and
+// packed; dx, dy and r2 in units of eps_I, so w = r2, and np carries eps2 = inv_eps2 = 1 and
+// close2 = 1/64; pairs with r2 >= 1 must contribute nothing), row_begin(), row_end() and
 // store(t, k).
 constexpr int kListCap = 256;    // far candidates per warp
 constexpr int kCloseCap = 64;    // close candidates per warp
@@ -205,10 +206,11 @@ __device__ __forceinline__ void near_eval_far(const float4 *s_xy, const float *s
 // d = (x_hi + n_hi) + (x_lo + n_lo) keeps full FP32 relative accuracy however small it is:
 // when x_hi and -n_hi are close the first sum is exact (Sterbenz), and when they are not,
 // d is of their size and one rounding is harmless.  Exactly coincident points give d = 0
-// (G(0) := 0); they are handled on a warp-uniform branch.
+// (G(0) := 0); they are handled on a warp-uniform branch.  The exact difference is then scaled
+// by ie = 1 / eps_I, the unit of every difference handed to the Op.
 template <class Op>
 __device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float4 *s_cl, const float *s_cq, int n,
-                                                float2 X, float2 Y, float2 XL, float2 YL,
+                                                float2 X, float2 Y, float2 XL, float2 YL, float ie,
                                                 const NearParams<float> &np, Op &op)
 {
     op.row_begin();
@@ -216,10 +218,11 @@ __device__ __forceinline__ void near_eval_close(const float4 *s_cxy, const float
         const float4 c = s_cxy[e];                // (n_hi.x, n_hi.x, n_hi.y, n_hi.y)
         const float4 l = s_cl[e];                 // (n_lo.x, n_lo.x, n_lo.y, n_lo.y)
         op.set_q(s_cq + e * Op::kR);
-        const float2 dx = add2(add2(X, make_float2(c.x, c.y)), add2(XL, make_float2(l.x, l.y)));
-        const float2 dy = add2(add2(Y, make_float2(c.z, c.w)), add2(YL, make_float2(l.z, l.w)));
+        const float2 ex = add2(add2(X, make_float2(c.x, c.y)), add2(XL, make_float2(l.x, l.y)));
+        const float2 ey = add2(add2(Y, make_float2(c.z, c.w)), add2(YL, make_float2(l.z, l.w)));
+        const float2 dx = mul2(ex, f2(ie)), dy = mul2(ey, f2(ie));   // in units of eps_I
         float2 r2 = fma2(dy, dy, mul2(dx, dx));
-        const bool z0 = dx.x == 0.f && dy.x == 0.f, z1 = dx.y == 0.f && dy.y == 0.f;
+        const bool z0 = ex.x == 0.f && ey.x == 0.f, z1 = ex.y == 0.f && ey.y == 0.f;
         if (__any_sync(0xffffffffu, z0 || z1)) {
             if (z0) {
                 op.coincident(np, 0);
@@ -276,6 +279,14 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
             xh[t] = make_float2(1e6f, 1e6f);      // idle slots: every pair lands beyond eps_I
     const float2 X = make_float2(xh[0].x, xh[1].x), Y = make_float2(xh[0].y, xh[1].y);
     const float2 XL = make_float2(xl[0].x, xl[1].x), YL = make_float2(xl[0].y, xl[1].y);
+    // the Op sees differences in units of eps_I, so w = r^2 needs no scaling per pair: the far
+    // list holds sources in those units and the item's points are scaled once here
+    const float ie = sqrtf(np.inv_eps2);
+    const float2 XS = mul2(X, f2(ie)), YS = mul2(Y, f2(ie));
+    NearParams<float> nps = np;
+    nps.eps2 = 1.f;
+    nps.inv_eps2 = 1.f;
+    nps.close2 = 1.f / 64.f;
     const float margin = 1e-4f * eps + 1e-5f;
     const float reach = eps + margin;
     const float reach2 = reach * reach;
@@ -321,7 +332,8 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                 const unsigned mc = __ballot_sync(0xffffffffu, close);
                 if (keep && !close) {
                     const int at = nf + __popc(mf & below);
-                    const float nx = offx - yh.x, ny = offy - yh.y;   // -(source in the item's frame)
+                    // -(source in the item's frame), in units of eps_I
+                    const float nx = (offx - yh.x) * ie, ny = (offy - yh.y) * ie;
                     s_xy[at] = make_float4(nx, nx, ny, ny);
 #pragma unroll
                     for (int r = 0; r < R; ++r)
@@ -345,13 +357,13 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
                 nc += __popc(mc);
                 if (nf > kListCap - 32) {
                     __syncwarp();
-                    near_eval_far(s_xy, s_q, nf, X, Y, np, op);
+                    near_eval_far(s_xy, s_q, nf, XS, YS, nps, op);
                     nf = 0;
                     __syncwarp();
                 }
                 if (nc > kCloseCap - 32) {
                     __syncwarp();
-                    near_eval_close(s_cxy, s_cl, s_cq, nc, X, Y, XL, YL, np, op);
+                    near_eval_close(s_cxy, s_cl, s_cq, nc, X, Y, XL, YL, ie, nps, op);
                     nc = 0;
                     __syncwarp();
                 }
@@ -359,8 +371,8 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
         }
     }
     __syncwarp();
-    near_eval_far(s_xy, s_q, nf, X, Y, np, op);
-    near_eval_close(s_cxy, s_cl, s_cq, nc, X, Y, XL, YL, np, op);
+    near_eval_far(s_xy, s_q, nf, XS, YS, nps, op);
+    near_eval_close(s_cxy, s_cl, s_cq, nc, X, Y, XL, YL, ie, nps, op);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
         if (valid[t])
