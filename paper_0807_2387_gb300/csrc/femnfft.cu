@@ -1031,10 +1031,16 @@ fs_status fs_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tri
         FS_CUDA(cudaStreamSynchronize(st));
         pl->precision = o.precision == 64 ? 64 : 32;
         if (pl->precision == 64)
-            return plan_init<double>(pl, (const double *)pl->fem_src, Ms, nodes, Nv, n_grid, sigma_os, m_window,
-                                     eps_I, o);
-        return plan_init<float>(pl, (const double *)pl->fem_src, Ms, nodes, Nv, n_grid, sigma_os, m_window, eps_I,
-                                o);
+            FS_TRY(plan_init<double>(pl, (const double *)pl->fem_src, Ms, nodes, Nv, n_grid, sigma_os, m_window,
+                                     eps_I, o));
+        else
+            FS_TRY(plan_init<float>(pl, (const double *)pl->fem_src, Ms, nodes, Nv, n_grid, sigma_os, m_window,
+                                    eps_I, o));
+        // source index -> sorted index: the assembly writes each element's charges into cell order
+        FS_TRY(pl->alloc(&pl->src_inv_perm, Ms));
+        FS_CUDA(launch_invert_perm(pl->src_perm, Ms, pl->src_inv_perm, pl->stream));
+        FS_CUDA(cudaStreamSynchronize(pl->stream));
+        return FS_OK;
     };
     fs_status st = body();
     if (st != FS_OK) {
@@ -1086,7 +1092,7 @@ fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs)
         return fail(FS_EINVAL, "bad magnetisation arguments");
     if ((reinterpret_cast<uintptr_t>(mag) & 15u) != 0)
         return fail(FS_EINVAL, "magnetisation must be 16-byte aligned (read as (Mx, My) pairs)");
-    // assembly fused with the gather: the charges go straight into cell order
+    // assembly fused with the gather: each element's charges go straight into cell order
     cudaStream_t st = plan->stream;
     if (plan->precision == 64)
         FS_TRY(reserve_charges<double>(plan, nrhs));
@@ -1097,13 +1103,13 @@ fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs)
         FS_CUDA(cudaEventRecord(plan->ev_q0, st));
     FS_CUDA(cudaMemsetAsync(plan->q_sum, 0, sizeof(double) * nrhs, st));
     if (plan->precision == 64)
-        FS_CUDA(launch_fem_charges_sorted<double>(plan->nodes, plan->tris, plan->Nt, plan->bedges, (const double2 *)mag,
-                                                  plan->Nv, nrhs, plan->src_perm, plan->M, (double *)plan->q_sorted,
-                                                  plan->q_sum, st));
+        FS_CUDA(launch_fem_charges_scatter<double>(plan->nodes, plan->tris, plan->Nt, plan->bedges, plan->Ne,
+                                                   (const double2 *)mag, plan->Nv, nrhs, plan->src_inv_perm, plan->M,
+                                                   (double *)plan->q_sorted, plan->q_sum, st));
     else
-        FS_CUDA(launch_fem_charges_sorted<float>(plan->nodes, plan->tris, plan->Nt, plan->bedges, (const double2 *)mag,
-                                                 plan->Nv, nrhs, plan->src_perm, plan->M, (float *)plan->q_sorted,
-                                                 plan->q_sum, st));
+        FS_CUDA(launch_fem_charges_scatter<float>(plan->nodes, plan->tris, plan->Nt, plan->bedges, plan->Ne,
+                                                  (const double2 *)mag, plan->Nv, nrhs, plan->src_inv_perm, plan->M,
+                                                  (float *)plan->q_sorted, plan->q_sum, st));
     if (plan->events)
         FS_CUDA(cudaEventRecord(plan->ev_q1, st));
     return FS_OK;

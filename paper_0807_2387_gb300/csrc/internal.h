@@ -339,19 +339,22 @@ cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt
 cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
                                int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, double *q,
                                int64_t M, cudaStream_t st);
-// charges of perm's sources in cell order (q_sorted, stride M per rhs) and their sums (q_sum, zeroed)
+// charges straight into cell order (q_sorted, stride M per rhs; inv_perm: source -> sorted index)
+// and their sums (q_sum, zeroed), one thread per triangle or boundary edge
 template <typename real>
-cudaError_t launch_fem_charges_sorted(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
-                                      const double2 *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
-                                      real *q_sorted, double *q_sum, cudaStream_t st);
+cudaError_t launch_fem_charges_scatter(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
+                                       int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, const int *inv_perm,
+                                       int64_t M, real *q_sorted, double *q_sum, cudaStream_t st);
+// inv[perm[k]] = k
+cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t st);
 // tetrahedra: nodes (Nv, 3), tets (Nt, 4), faces (Nf, 4) = (i0 < i1 < i2, fourth node), mag (nrhs, Nv, 3)
 cudaError_t launch_fem3_sources(const double *nodes, const int *tets, int64_t Nt, const int *faces, int64_t Nf,
                                 double *src, cudaStream_t st);
 cudaError_t launch_fem3_charges(const double *nodes, const int *tets, int64_t Nt, const int *faces,
                                 const double *mag, int64_t Nv, int nrhs, double *q, int64_t M, cudaStream_t st);
 template <typename real>
-cudaError_t launch_fem3_charges_sorted(const double *nodes, const int *tets, int64_t Nt, const int *faces,
-                                       const double *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
-                                       real *q_sorted, double *q_sum, cudaStream_t st);
+cudaError_t launch_fem3_charges_scatter(const double *nodes, const int *tets, int64_t Nt, const int *faces,
+                                        int64_t Nf, const double *mag, int64_t Nv, int nrhs, const int *inv_perm,
+                                        int64_t M, real *q_sorted, double *q_sum, cudaStream_t st);
 
 }  // namespace fs

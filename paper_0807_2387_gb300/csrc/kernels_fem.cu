@@ -12,7 +12,8 @@
 //
 // Source order: 3 per triangle (triangle-major), then 2 per boundary edge.  For a time loop
 // (one plan, many M(t)) the assembly is fused with the gather into cell order
-// (k_fem_charges_sorted), so a magnetisation becomes sorted charges in one pass.
+// (k_fem_charges_scatter: each element's charges computed once and written to their sorted
+// slots), so a magnetisation becomes sorted charges in one pass.
 #include "internal.h"
 
 namespace fs {
@@ -41,7 +42,9 @@ __global__ void k_fem_sources(const double2 *__restrict__ nodes, const int *__re
     }
 }
 
-// Charge of one triangle point: rho_T |T| / 3 (the same for its three points).
+// Charge of one triangle point: rho_T |T| / 3 (the same for its three points).  With
+// S = sum_k M_k . (rotated opposite edge) = -rho_T 2A (A the signed area),
+// rho_T |T| / 3 = -(S / 2A) |2A| / 6 = -S sign(2A) / 6: no division.
 __device__ __forceinline__ double triangle_charge(const double2 *__restrict__ nodes, const int *__restrict__ tris,
                                                   int64_t t, const double2 *__restrict__ mg)
 {
@@ -49,28 +52,28 @@ __device__ __forceinline__ double triangle_charge(const double2 *__restrict__ no
     const double2 pa = nodes[ia], pb = nodes[ib], pc = nodes[ic];
     const double two_a = (pb.x - pa.x) * (pc.y - pa.y) - (pb.y - pa.y) * (pc.x - pa.x);
     const double2 ma = mg[ia], mb = mg[ib], mc = mg[ic];
-    // sum_k M_k . (rotated opposite edge), divided by 2A
-    const double div = (ma.x * (pb.y - pc.y) + ma.y * (pc.x - pb.x) + mb.x * (pc.y - pa.y) + mb.y * (pa.x - pc.x) +
-                        mc.x * (pa.y - pb.y) + mc.y * (pb.x - pa.x)) / two_a;
-    return -div * fabs(two_a) / 6.0;
+    const double S = ma.x * (pb.y - pc.y) + ma.y * (pc.x - pb.x) + mb.x * (pc.y - pa.y) + mb.y * (pa.x - pc.x) +
+                     mc.x * (pa.y - pb.y) + mc.y * (pb.x - pa.x);
+    return two_a > 0.0 ? S * (-1.0 / 6.0) : S * (1.0 / 6.0);
 }
 
-// Charge of Gauss point g (0: t = 1/2 - 1/(2 sqrt 3), 1: t = 1/2 + 1/(2 sqrt 3)) of boundary edge e.
+// Charge of Gauss point g (0: t = 1/2 - 1/(2 sqrt 3), 1: t = 1/2 + 1/(2 sqrt 3)) of boundary edge e:
+// (M(t) . n_e) |e| / 2 with n_e |e| = +-(t_y, -t_x) for the edge vector t (outward sign): no
+// square root or division.
 __device__ __forceinline__ double edge_charge(const double2 *__restrict__ nodes, const int *__restrict__ bedges,
                                               int64_t e, int g, const double2 *__restrict__ mg)
 {
     const int i0 = bedges[3 * e], i1 = bedges[3 * e + 1], i3 = bedges[3 * e + 2];
     const double2 p0 = nodes[i0], p1 = nodes[i1], p3 = nodes[i3];
     const double tx = p1.x - p0.x, ty = p1.y - p0.y;
-    const double len = sqrt(tx * tx + ty * ty);
-    double nx = ty / len, ny = -tx / len;
+    double nx = ty, ny = -tx;                      // normal scaled by |e|
     if (nx * (p3.x - p0.x) + ny * (p3.y - p0.y) > 0.0) {
         nx = -nx;
         ny = -ny;
     }
     const double2 m0 = mg[i0], m1 = mg[i1];
     const double t = g == 0 ? kGaussLo : kGaussHi;
-    return (((1.0 - t) * m0.x + t * m1.x) * nx + ((1.0 - t) * m0.y + t * m1.y) * ny) * len * 0.5;
+    return (((1.0 - t) * m0.x + t * m1.x) * nx + ((1.0 - t) * m0.y + t * m1.y) * ny) * 0.5;
 }
 
 __global__ void k_fem_charges(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
@@ -95,23 +98,32 @@ __global__ void k_fem_charges(const double2 *__restrict__ nodes, const int *__re
 }
 
 // Charges straight into cell order (the assembly fused with the gather of fs_set_charges):
-// sorted source k is canonical source perm[k], whose charge is computed from the nodal M in
-// FP64 and stored in the plan's precision; the block sums go to q_sum.
+// one thread per triangle (or boundary edge) computes its charge once, in FP64, and writes it
+// to the sorted slots of its quadrature points (inv_perm: source index -> sorted index, built
+// with the plan), in the plan's precision; the block sums go to q_sum.
 template <typename real>
-__global__ void k_fem_charges_sorted(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
-                                     const int *__restrict__ bedges, const double2 *__restrict__ mag, int64_t Nv,
-                                     const int *__restrict__ perm, int64_t M, real *__restrict__ q_sorted,
-                                     double *__restrict__ q_sum)
+__global__ void k_fem_charges_scatter(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
+                                      const int *__restrict__ bedges, int64_t Ne, const double2 *__restrict__ mag,
+                                      int64_t Nv, const int *__restrict__ inv_perm, int64_t M,
+                                      real *__restrict__ q_sorted, double *__restrict__ q_sum)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     const double2 *mg = mag + (int64_t)r * Nv;
+    real *qs = q_sorted + (int64_t)r * M;
     double v = 0.0;
-    if (k < M) {
-        const int64_t i = perm[k];
-        v = i < 3 * Nt ? triangle_charge(nodes, tris, i / 3, mg)
-                       : edge_charge(nodes, bedges, (i - 3 * Nt) / 2, (int)((i - 3 * Nt) % 2), mg);
-        q_sorted[(int64_t)r * M + k] = (real)v;
+    if (i < Nt) {
+        const double qt = triangle_charge(nodes, tris, i, mg);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+            qs[inv_perm[3 * i + p]] = (real)qt;
+        v = 3.0 * qt;
+    } else if (i < Nt + Ne) {
+        const int64_t e = i - Nt, o = 3 * Nt + 2 * e;
+        const double q0 = edge_charge(nodes, bedges, e, 0, mg), q1 = edge_charge(nodes, bedges, e, 1, mg);
+        qs[inv_perm[o]] = (real)q0;
+        qs[inv_perm[o + 1]] = (real)q1;
+        v = q0 + q1;
     }
     for (int o = 16; o > 0; o >>= 1)
         v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -126,6 +138,13 @@ __global__ void k_fem_charges_sorted(const double2 *__restrict__ nodes, const in
         if (threadIdx.x == 0)
             atomicAdd(&q_sum[r], v);
     }
+}
+
+__global__ void k_invert_perm(const int *__restrict__ perm, int64_t n, int *__restrict__ inv)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n)
+        inv[perm[k]] = (int)k;
 }
 
 // ---------------------------------------------------------------- tetrahedra (d = 3)
@@ -202,7 +221,7 @@ __device__ __forceinline__ double tet_charge(const double *__restrict__ nodes, c
     // div M * det = sum_k (M_k - M_0) . (row k of adj J); q = -div M |det| / 24
     const double num = dot3(sub3(ld3(mg, i1), m0), vw) + dot3(sub3(ld3(mg, i2), m0), wu) +
                        dot3(sub3(ld3(mg, i3), m0), uv);
-    return det > 0.0 ? -num / 24.0 : num / 24.0;
+    return det > 0.0 ? num * (-1.0 / 24.0) : num * (1.0 / 24.0);
 }
 
 // Charge of point k (the 2/3 weight on node k) of boundary face f: (M . n_F) |F| / 3.
@@ -241,19 +260,42 @@ __global__ void k_fem3_charges(const double *__restrict__ nodes, const int *__re
         q[(int64_t)r * M + i] = fem3_point_charge(nodes, tets, Nt, faces, i, mag + (int64_t)r * 3 * Nv);
 }
 
-// 3D assembly fused with the gather into cell order (as k_fem_charges_sorted).
+// 3D assembly straight into cell order (as k_fem_charges_scatter): one thread per tetrahedron
+// (its four points share one charge) or boundary face (one normal for its three points).
 template <typename real>
-__global__ void k_fem3_charges_sorted(const double *__restrict__ nodes, const int *__restrict__ tets, int64_t Nt,
-                                      const int *__restrict__ faces, const double *__restrict__ mag, int64_t Nv,
-                                      const int *__restrict__ perm, int64_t M, real *__restrict__ q_sorted,
-                                      double *__restrict__ q_sum)
+__global__ void k_fem3_charges_scatter(const double *__restrict__ nodes, const int *__restrict__ tets, int64_t Nt,
+                                       const int *__restrict__ faces, int64_t Nf, const double *__restrict__ mag,
+                                       int64_t Nv, const int *__restrict__ inv_perm, int64_t M,
+                                       real *__restrict__ q_sorted, double *__restrict__ q_sum)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
+    const double *mg = mag + (int64_t)r * 3 * Nv;
+    real *qs = q_sorted + (int64_t)r * M;
     double v = 0.0;
-    if (k < M) {
-        v = fem3_point_charge(nodes, tets, Nt, faces, perm[k], mag + (int64_t)r * 3 * Nv);
-        q_sorted[(int64_t)r * M + k] = (real)v;
+    if (i < Nt) {
+        const double qt = tet_charge(nodes, tets, i, mg);
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            qs[inv_perm[4 * i + p]] = (real)qt;
+        v = 4.0 * qt;
+    } else if (i < Nt + Nf) {
+        const int64_t f = i - Nt;
+        const int i0 = faces[4 * f], i1 = faces[4 * f + 1], i2 = faces[4 * f + 2], io = faces[4 * f + 3];
+        const V3 p0 = ld3(nodes, i0);
+        const V3 c = cross3(sub3(ld3(nodes, i1), p0), sub3(ld3(nodes, i2), p0));   // |c| = 2 |F|
+        const double sgn = dot3(c, sub3(ld3(nodes, io), p0)) > 0.0 ? -1.0 : 1.0;   // outward
+        const V3 ma = ld3(mg, i0), mb = ld3(mg, i1), mc = ld3(mg, i2);
+        const double mean6 = dot3(V3{ma.x + mb.x + mc.x, ma.y + mb.y + mc.y, ma.z + mb.z + mc.z}, c) * (1.0 / 6.0);
+        const int64_t o = 4 * Nt + 3 * f;
+        const V3 mk[3] = {ma, mb, mc};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // (M . n_F) |F| / 3 with M = (Ma + Mb + Mc)/6 + Mk/2 at the point: M . c / 6
+            const double qk = sgn * (mean6 + 0.5 * dot3(mk[k], c)) * (1.0 / 6.0);
+            qs[inv_perm[o + k]] = (real)qk;
+            v += qk;
+        }
     }
     for (int o = 16; o > 0; o >>= 1)
         v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -293,23 +335,25 @@ cudaError_t launch_fem3_charges(const double *nodes, const int *tets, int64_t Nt
 }
 
 template <typename real>
-cudaError_t launch_fem3_charges_sorted(const double *nodes, const int *tets, int64_t Nt, const int *faces,
-                                       const double *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
-                                       real *q_sorted, double *q_sum, cudaStream_t st)
+cudaError_t launch_fem3_charges_scatter(const double *nodes, const int *tets, int64_t Nt, const int *faces,
+                                        int64_t Nf, const double *mag, int64_t Nv, int nrhs, const int *inv_perm,
+                                        int64_t M, real *q_sorted, double *q_sum, cudaStream_t st)
 {
-    if (M <= 0 || nrhs <= 0)
+    const int64_t n = Nt + Nf;
+    if (n <= 0 || nrhs <= 0)
         return cudaSuccess;
-    dim3 grid((unsigned)((M + 255) / 256), nrhs);
-    k_fem3_charges_sorted<real><<<grid, 256, 0, st>>>(nodes, tets, Nt, faces, mag, Nv, perm, M, q_sorted, q_sum);
+    dim3 grid((unsigned)((n + 255) / 256), nrhs);
+    k_fem3_charges_scatter<real><<<grid, 256, 0, st>>>(nodes, tets, Nt, faces, Nf, mag, Nv, inv_perm, M, q_sorted,
+                                                        q_sum);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fem3_charges_sorted<float>(const double *, const int *, int64_t, const int *,
-                                                       const double *, int64_t, int, const int *, int64_t, float *,
-                                                       double *, cudaStream_t);
-template cudaError_t launch_fem3_charges_sorted<double>(const double *, const int *, int64_t, const int *,
-                                                        const double *, int64_t, int, const int *, int64_t,
-                                                        double *, double *, cudaStream_t);
+template cudaError_t launch_fem3_charges_scatter<float>(const double *, const int *, int64_t, const int *, int64_t,
+                                                        const double *, int64_t, int, const int *, int64_t, float *,
+                                                        double *, cudaStream_t);
+template cudaError_t launch_fem3_charges_scatter<double>(const double *, const int *, int64_t, const int *, int64_t,
+                                                         const double *, int64_t, int, const int *, int64_t,
+                                                         double *, double *, cudaStream_t);
 
 cudaError_t launch_fem_sources(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges, int64_t Ne,
                                double2 *src, cudaStream_t st)
@@ -333,22 +377,32 @@ cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt
 }
 
 template <typename real>
-cudaError_t launch_fem_charges_sorted(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
-                                      const double2 *mag, int64_t Nv, int nrhs, const int *perm, int64_t M,
-                                      real *q_sorted, double *q_sum, cudaStream_t st)
+cudaError_t launch_fem_charges_scatter(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
+                                       int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, const int *inv_perm,
+                                       int64_t M, real *q_sorted, double *q_sum, cudaStream_t st)
 {
-    if (M <= 0 || nrhs <= 0)
+    const int64_t n = Nt + Ne;
+    if (n <= 0 || nrhs <= 0)
         return cudaSuccess;
-    dim3 grid((unsigned)((M + 255) / 256), nrhs);
-    k_fem_charges_sorted<real><<<grid, 256, 0, st>>>(nodes, tris, Nt, bedges, mag, Nv, perm, M, q_sorted, q_sum);
+    dim3 grid((unsigned)((n + 255) / 256), nrhs);
+    k_fem_charges_scatter<real><<<grid, 256, 0, st>>>(nodes, tris, Nt, bedges, Ne, mag, Nv, inv_perm, M, q_sorted,
+                                                       q_sum);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fem_charges_sorted<float>(const double2 *, const int *, int64_t, const int *,
-                                                      const double2 *, int64_t, int, const int *, int64_t, float *,
-                                                      double *, cudaStream_t);
-template cudaError_t launch_fem_charges_sorted<double>(const double2 *, const int *, int64_t, const int *,
-                                                       const double2 *, int64_t, int, const int *, int64_t, double *,
+template cudaError_t launch_fem_charges_scatter<float>(const double2 *, const int *, int64_t, const int *, int64_t,
+                                                       const double2 *, int64_t, int, const int *, int64_t, float *,
                                                        double *, cudaStream_t);
+template cudaError_t launch_fem_charges_scatter<double>(const double2 *, const int *, int64_t, const int *, int64_t,
+                                                        const double2 *, int64_t, int, const int *, int64_t, double *,
+                                                        double *, cudaStream_t);
+
+cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k_invert_perm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, n, inv);
+    return cudaGetLastError();
+}
 
 }  // namespace fs

@@ -91,6 +91,7 @@ struct fs_plan {
     const double2 *nodes = nullptr;   // caller's (valid while the plan is used)
     int *tris = nullptr, *bedges = nullptr;
     double2 *fem_src = nullptr;
+    int *src_inv_perm = nullptr;      // source index -> sorted index (charges assembled into cell order)
     // host staging for fs_solve_host
     void *d_q_stage = nullptr, *d_phi_stage = nullptr, *d_H_stage = nullptr;
     size_t q_stage_bytes = 0, phi_stage_bytes = 0, H_stage_bytes = 0;

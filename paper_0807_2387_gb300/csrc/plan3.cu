@@ -58,6 +58,7 @@ struct fs3_plan {
     // tetrahedral FEM plans: sources are the quadrature points, targets the nodes
     bool is_fem = false;
     int64_t Nv = 0, Nt = 0, Nf = 0;
+    int *src_inv_perm = nullptr;      // source index -> sorted index (charges assembled into cell order)
     const double *nodes = nullptr;
     int *tets = nullptr, *faces = nullptr;
     double *fem_src = nullptr;
@@ -515,8 +516,8 @@ template <typename real> fs_status set_magnetization3_t(fs3_plan *pl, const doub
     FS_TRY(reserve_charges3<real>(pl, nrhs));
     pl->nrhs = nrhs;
     FS_CUDA(cudaMemsetAsync(pl->q_sum, 0, sizeof(double) * nrhs, pl->stream));
-    FS_CUDA(launch_fem3_charges_sorted<real>(pl->nodes, pl->tets, pl->Nt, pl->faces, mag, pl->Nv, nrhs, pl->src_perm,
-                                             pl->M, (real *)pl->q_sorted, pl->q_sum, pl->stream));
+    FS_CUDA(launch_fem3_charges_scatter<real>(pl->nodes, pl->tets, pl->Nt, pl->faces, pl->Nf, mag, pl->Nv, nrhs,
+                                              pl->src_inv_perm, pl->M, (real *)pl->q_sorted, pl->q_sum, pl->stream));
     return FS_OK;
 }
 
@@ -709,8 +710,13 @@ fs_status fs3_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *te
         FS_CUDA(cudaStreamSynchronize(st));
         pl->M = Ms;
         pl->N = Nv;
-        return pl->precision == 64 ? plan3_init<double>(pl, pl->fem_src, Ms, nodes, Nv)
-                                   : plan3_init<float>(pl, pl->fem_src, Ms, nodes, Nv);
+        FS_TRY(pl->precision == 64 ? plan3_init<double>(pl, pl->fem_src, Ms, nodes, Nv)
+                                   : plan3_init<float>(pl, pl->fem_src, Ms, nodes, Nv));
+        // source index -> sorted index: the assembly writes each element's charges into cell order
+        FS_TRY(pl->alloc(&pl->src_inv_perm, (size_t)Ms));
+        FS_CUDA(launch_invert_perm(pl->src_perm, Ms, pl->src_inv_perm, pl->stream));
+        FS_CUDA(cudaStreamSynchronize(pl->stream));
+        return FS_OK;
     };
     const fs_status s = body();
     if (s != FS_OK) {
