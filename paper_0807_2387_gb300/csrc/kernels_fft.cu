@@ -15,9 +15,10 @@
 // Only the active window of n_a rows/columns that hold points is read or
 // written; the rest of the L x L grid is known to be zero and is never stored.
 //
-// Each 1D transform is a Stockham autosort FFT in shared memory: radix-4
-// passes (radix 2 for the last when log2 L is odd), ping-pong buffers, one
-// __syncthreads per pass, twiddles from a table of exp(-2 pi i t / L).
+// Each 1D transform is a Stockham autosort FFT in shared memory: radix-8
+// butterflies held in registers (a final radix-4 or radix-2 pass for the rest of
+// log2 L), ping-pong buffers, one __syncthreads per pass, twiddles from a table
+// of exp(-2 pi i t / L) that the 2D kernels first copy into shared memory.
 #include "internal.h"
 
 namespace fs {
@@ -29,50 +30,119 @@ template <typename real> using cplx = typename Cplx<real>::type;
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
-// In-place (via ping-pong) FFT of one line of length L held in shared memory.
+// Multiply by -i (forward) or +i (inverse).
+template <bool INV, typename C> __device__ __forceinline__ C rot_i(C a)
+{
+    C r;
+    if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+
+// In-register radix-4 DFT of (v0, v1, v2, v3) (forward e^-, inverse e^+), outputs in order.
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C &v0, C &v1, C &v2, C &v3)
+{
+    const C a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = rot_i<INV>(csub(v1, v3));
+    v0 = cadd(a0, a2);
+    v1 = cadd(a1, a3);
+    v2 = csub(a0, a2);
+    v3 = csub(a1, a3);
+}
+
+// In-register radix-8 DFT: two radix-4 DFTs of the sums and the twiddled differences
+// v_k +- v_{k+4}, the differences rotated by e^-+(2 pi i k / 8); X_{2m} from the sums,
+// X_{2m+1} from the differences.
+template <bool INV, typename real, typename C> __device__ __forceinline__ void dft8(C (&v)[8])
+{
+    const real h = real(0.70710678118654752440084436210484903928);   // 1 / sqrt 2
+    C a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = cadd(v[k], v[k + 4]);
+        b[k] = csub(v[k], v[k + 4]);
+    }
+    // b1 *= e^-+(i pi/4), b2 *= -+i, b3 *= e^-+(3 i pi/4)
+    C t;
+    if (INV) { t.x = h * (b[1].x - b[1].y); t.y = h * (b[1].x + b[1].y); }
+    else { t.x = h * (b[1].x + b[1].y); t.y = h * (b[1].y - b[1].x); }
+    b[1] = t;
+    b[2] = rot_i<INV>(b[2]);
+    if (INV) { t.x = -h * (b[3].x + b[3].y); t.y = h * (b[3].x - b[3].y); }
+    else { t.x = h * (b[3].y - b[3].x); t.y = -h * (b[3].x + b[3].y); }
+    b[3] = t;
+    dft4<INV>(a[0], a[1], a[2], a[3]);
+    dft4<INV>(b[0], b[1], b[2], b[3]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        v[2 * m] = a[m];
+        v[2 * m + 1] = b[m];
+    }
+}
+
+// One Stockham pass of radix R over the line: butterfly j reads src[j + r L/R], twiddles by
+// tw[r k L/(Ns R)] (k = j mod Ns), transforms in registers and writes dst[(j - k) R + k + r Ns].
+template <typename real, bool INV, int R>
+__device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> *dst, int L, int Ns,
+                                              const cplx<real> *__restrict__ tw)
+{
+    using C = cplx<real>;
+    const int nb = L / R;
+    const int tstep = L / (Ns * R);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int k = j & (Ns - 1);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            v[r] = src[j + r * nb];
+        if (k) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C t = tw[r * k * tstep];
+                if (INV)
+                    t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
+        }
+        if constexpr (R == 8) {
+            dft8<INV, real>(v);
+        } else if constexpr (R == 4) {
+            dft4<INV>(v[0], v[1], v[2], v[3]);
+        } else {
+            const C t = v[1];
+            v[1] = csub(v[0], t);
+            v[0] = cadd(v[0], t);
+        }
+        const int idx = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            dst[idx + r * Ns] = v[r];
+    }
+}
+
+// In-place (via ping-pong) FFT of one line of length L (a power of two) held in shared memory:
+// radix-8 passes, then one radix-4 or radix-2 pass for the remaining factor, one __syncthreads
+// per pass (2048 points: 4 passes).  tw[t] = exp(-2 pi i t / L), in shared or global memory.
 // Returns the buffer holding the result (a or b).  All threads of the block take part.
 template <typename real, bool INV>
 __device__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<real> *__restrict__ tw)
 {
     cplx<real> *src = a, *dst = b;
     for (int Ns = 1; Ns < L;) {
-        const int R = ((L / Ns) % 4 == 0) ? 4 : 2;
-        const int nb = L / R;
-        const int tstep = L / (Ns * R);
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-            const int k = j & (Ns - 1);
-            const int idx = (j - k) * R + k;
-            if (R == 4) {
-                cplx<real> v0 = src[j], v1 = src[j + nb], v2 = src[j + 2 * nb], v3 = src[j + 3 * nb];
-                if (k) {
-                    cplx<real> t1 = tw[k * tstep], t2 = tw[2 * k * tstep], t3 = tw[3 * k * tstep];
-                    if (INV) { t1.y = -t1.y; t2.y = -t2.y; t3.y = -t3.y; }
-                    v1 = cmul(v1, t1);
-                    v2 = cmul(v2, t2);
-                    v3 = cmul(v3, t3);
-                }
-                const cplx<real> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3);
-                cplx<real> a3 = csub(v1, v3);
-                // forward multiplies (v1 - v3) by -i, inverse by +i
-                cplx<real> r3;
-                if (INV) { r3.x = -a3.y; r3.y = a3.x; } else { r3.x = a3.y; r3.y = -a3.x; }
-                dst[idx] = cadd(a0, a2);
-                dst[idx + Ns] = cadd(a1, r3);
-                dst[idx + 2 * Ns] = csub(a0, a2);
-                dst[idx + 3 * Ns] = csub(a1, r3);
-            } else {
-                cplx<real> v0 = src[j], v1 = src[j + nb];
-                if (k) {
-                    cplx<real> t1 = tw[k * tstep];
-                    if (INV) t1.y = -t1.y;
-                    v1 = cmul(v1, t1);
-                }
-                dst[idx] = cadd(v0, v1);
-                dst[idx + Ns] = csub(v0, v1);
-            }
+        const int rest = L / Ns;
+        int R;
+        if (rest % 8 == 0) {
+            stockham_pass<real, INV, 8>(src, dst, L, Ns, tw);
+            R = 8;
+        } else if (rest == 4) {
+            stockham_pass<real, INV, 4>(src, dst, L, Ns, tw);
+            R = 4;
+        } else {
+            stockham_pass<real, INV, 2>(src, dst, L, Ns, tw);
+            R = 2;
         }
         __syncthreads();
-        cplx<real> *t = src; src = dst; dst = t;
+        cplx<real> *t = src;
+        src = dst;
+        dst = t;
         Ns *= R;
     }
     return src;
@@ -202,13 +272,25 @@ __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restri
     }
 }
 
+// Copy the twiddle table into shared memory (the caller's next __syncthreads publishes it):
+// every pass reads it at scattered indices, which from global memory stalled each pass on
+// the load latency.
+template <typename real>
+__device__ __forceinline__ cplx<real> *stage_twiddles(cplx<real> *dst, const cplx<real> *__restrict__ tw, int L)
+{
+    for (int t = threadIdx.x; t < L; t += blockDim.x)
+        dst[t] = tw[t];
+    return dst;
+}
+
 template <typename real>
 __global__ void k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a, int L, int n_half,
                                cplx<real> *__restrict__ spec, int ld, const cplx<real> *__restrict__ tw)
 {
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    rows_fwd_unit<real>(blockIdx.x, grid, pitch, n_a, L, n_half, spec, ld, tw, a, a + L);
+    cplx<real> *s_tw = stage_twiddles<real>(a + 2 * L, tw, L);   // published by the unit's first barrier
+    rows_fwd_unit<real>(blockIdx.x, grid, pitch, n_a, L, n_half, spec, ld, s_tw, a, a + L);
 }
 
 template <typename real>
@@ -217,7 +299,8 @@ __global__ void k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L
 {
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cols_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n, mul, tw, a, a + L);
+    cplx<real> *s_tw = stage_twiddles<real>(a + 2 * L, tw, L);
+    cols_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n, mul, s_tw, a, a + L);
 }
 
 template <typename real>
@@ -226,7 +309,8 @@ __global__ void k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int 
 {
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    rows_inv_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n_half, grid, pitch, tw, a, a + L);
+    cplx<real> *s_tw = stage_twiddles<real>(a + 2 * L, tw, L);
+    rows_inv_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n_half, grid, pitch, s_tw, a, a + L);
 }
 
 // Thread 0 waits until *ctr >= target; the wait ends early (failed) when the error word is
@@ -605,7 +689,7 @@ template <typename real>
 cudaError_t launch_fft_rows_fwd(const real *grid, int pitch, int n_a, int L, int n_half, cplx<real> *spec, int ld,
                                 const cplx<real> *tw, cudaStream_t st)
 {
-    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    const size_t smem = 3 * (size_t)L * sizeof(cplx<real>);   // two line buffers and the twiddles
     cudaError_t e = set_smem(k_fft_rows_fwd<real>, smem);
     if (e != cudaSuccess)
         return e;
@@ -618,7 +702,7 @@ template <typename real>
 cudaError_t launch_fft_cols(cplx<real> *spec, int ld, int n_a, int L, int n, const real *mul, const cplx<real> *tw,
                             cudaStream_t st)
 {
-    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    const size_t smem = 3 * (size_t)L * sizeof(cplx<real>);   // two line buffers and the twiddles
     cudaError_t e = set_smem(k_fft_cols<real>, smem);
     if (e != cudaSuccess)
         return e;
@@ -630,7 +714,7 @@ template <typename real>
 cudaError_t launch_fft_rows_inv(const cplx<real> *spec, int ld, int n_a, int L, int n_half, real *grid, int pitch,
                                 const cplx<real> *tw, cudaStream_t st)
 {
-    const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
+    const size_t smem = 3 * (size_t)L * sizeof(cplx<real>);   // two line buffers and the twiddles
     cudaError_t e = set_smem(k_fft_rows_inv<real>, smem);
     if (e != cudaSuccess)
         return e;
