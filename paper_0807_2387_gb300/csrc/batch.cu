@@ -177,9 +177,10 @@ fs_status tune_instance(const fs_instance &in, double sigma, int m, const fs_opt
             // a batch sizes the spreading kernel's shared memory for its largest tile, so tiles
             // that would leave fewer than four CTAs per SM are not candidates
             const int P = t * c + 2 * m - 1;
-            const size_t rsz = probe.precision == 64 ? 8 : 4;
-            const int planes = (probe.precision != 64 && !(probe.flags & FS_FLAG_NO_KAHAN)) ? 2 : 1;
-            if ((size_t)kSpreadWarps * P * spread_pitch(P, 2 * m) * rsz * planes > kMaxTileSmem)
+            const bool comp = probe.precision != 64 && !(probe.flags & FS_FLAG_NO_KAHAN);
+            const size_t bytes = probe.precision == 64 ? spread_smem_bytes<double>(P, 2 * m, false)
+                                                       : spread_smem_bytes<float>(P, 2 * m, comp);
+            if (bytes > kMaxTileSmem)
                 continue;
             fs_opts o = probe;
             o.cell = c;

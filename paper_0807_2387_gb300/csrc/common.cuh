@@ -178,6 +178,7 @@ template <int DEG> __device__ __forceinline__ float poly_eval(const float *c, fl
     return acc;
 }
 
+
 // Spreading tiles in shared memory: a warp's tile holds `rows` x `rows` grid lines at a row
 // pitch q >= rows.  The M2 x M2 taps of one source sit at offsets a q + b (a, b < M2) from the
 // source's corner; tap (a, b) lies on bank (a q + b) mod 32 relative to the corner.  Dealing the
@@ -211,6 +212,43 @@ __device__ __forceinline__ int spread_pitch_warp(int rows, int M2, int lane)
     const int per = (M2 * M2 + 31) / 32;
     for (int q = rows; q < rows + 32; ++q)
         if (__reduce_max_sync(0xffffffffu, spread_taps_on_bank(lane, q, M2)) <= per)
+            return q;
+    return rows;   // not reached
+}
+
+// Row groups of the spreading's tap lanes (k_spread, k_batch_spread): G groups of M2 lanes, G the
+// largest divisor of M2 with G M2 <= 32; lane (g, b) owns column b of the source's M2 x M2 taps
+// and the M2 / G consecutive rows g M2/G .. (g + 1) M2/G - 1.  At every row step the lanes touch
+// G runs of M2 consecutive columns, G M2/G rows apart: spread_group_pitch picks the smallest row
+// pitch q >= rows at which those runs lie on distinct banks (each step is the first one shifted
+// by i q, so checking the first suffices; a pitch within 8 of rows exists for M2 = 4..16).
+__host__ __device__ constexpr int spread_groups(int M2)
+{
+    int G = 1;
+    for (int d = 1; d <= M2; ++d)
+        if (M2 % d == 0 && d * M2 <= 32)
+            G = d;
+    return G;
+}
+
+__host__ __device__ inline bool spread_group_banks_ok(int q, int M2)
+{
+    const int G = spread_groups(M2), RPL = M2 / G;
+    unsigned used = 0u;
+    for (int g = 0; g < G; ++g)
+        for (int b = 0; b < M2; ++b) {
+            const int bank = (g * RPL * q + b) % 32;
+            if ((used >> bank) & 1u)
+                return false;
+            used |= 1u << bank;
+        }
+    return true;
+}
+
+__host__ __device__ inline int spread_group_pitch(int rows, int M2)
+{
+    for (int q = rows; q < rows + 32; ++q)
+        if (spread_group_banks_ok(q, M2))
             return q;
     return rows;   // not reached
 }

@@ -448,11 +448,12 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     pl->cg.cell = cell;
     pl->cg.n_c = (n_a + cell - 1) / cell;
     int T = o.tile_cells > 0 ? o.tile_cells : std::max(1, (int)std::lround(16.0 / cell));
-    auto smem_for = [&](int t) {
+    auto smem_for = [&](int t) {   // the larger of the value spreading's and the adjoint's dipole spreading's
         const int P = t * cell + 2 * m - 1;
-        return (size_t)kSpreadWarps * P * spread_pitch(P, 2 * m) * sizeof(real) *
-                   ((pl->kahan && sizeof(real) == 4) ? 2 : 1) +
-               sizeof(float) * 2 * m * (kPolyD + 1);
+        const bool comp = pl->kahan && sizeof(real) == 4;
+        const size_t dip = (size_t)kSpreadWarps * P * spread_pitch(P, 2 * m) * sizeof(real) * (comp ? 2 : 1) +
+                           sizeof(float) * 2 * m * (2 * kPolyD + 1);
+        return std::max(dip, spread_smem_bytes<real>(P, 2 * m, comp));
     };
     while (T > 1 && smem_for(T) > 160 * 1024)
         --T;

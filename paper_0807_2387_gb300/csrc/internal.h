@@ -11,6 +11,26 @@ namespace fs {
 // Warps per spreading CTA; each holds a private padded tile in shared memory.
 constexpr int kSpreadWarps = 4;
 
+// Shared memory of the spreading kernels: the warp tiles (PLANES planes of P rows at pitch Q),
+// padded to 16 bytes, then each warp's window weights (a group's row weights vector-aligned,
+// then the column weights), then the FP32 window polynomials.
+template <typename real> __host__ __device__ constexpr int spread_weight_stride(int M2)
+{
+    const int G = spread_groups(M2), RPL = M2 / G, VW = 16 / (int)sizeof(real);
+    return G * ((RPL + VW - 1) / VW * VW) + (M2 + VW - 1) / VW * VW;
+}
+
+template <typename real> __host__ __device__ inline size_t spread_tiles_bytes(int P, int Q, int planes)
+{
+    return ((size_t)kSpreadWarps * P * Q * planes * sizeof(real) + 15) / 16 * 16;
+}
+
+template <typename real> inline size_t spread_smem_bytes(int P, int M2, bool comp)   // k_spread, k_batch_spread
+{
+    return spread_tiles_bytes<real>(P, spread_group_pitch(P, M2), comp ? 2 : 1) +
+           (size_t)kSpreadWarps * spread_weight_stride<real>(M2) * sizeof(real) + sizeof(float) * M2 * (kPolyD + 1);
+}
+
 // One spreading work unit: sources [start, start+count) of tile `tile` (cell-sorted order).
 struct SpreadItem {
     int tile;

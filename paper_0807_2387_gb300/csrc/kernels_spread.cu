@@ -29,6 +29,33 @@ namespace {
 
 template <typename real> using real2_t = typename Cplx<real>::type;
 
+// Loads a group's RPL row weights from 16-byte aligned shared memory in vectors.
+template <typename real, int RPL> __device__ __forceinline__ void load_row_weights(const real *src, real (&w)[RPL])
+{
+    constexpr int VW = 16 / (int)sizeof(real);
+#pragma unroll
+    for (int v = 0; v < (RPL + VW - 1) / VW; ++v) {
+        if constexpr (sizeof(real) == 4) {
+            const float4 t = reinterpret_cast<const float4 *>(src)[v];
+            const float e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (4 * v + k < RPL)
+                    w[4 * v + k] = e[k];
+        } else {
+            const double2 t = reinterpret_cast<const double2 *>(src)[v];
+            w[2 * v] = t.x;
+            if (2 * v + 1 < RPL)
+                w[2 * v + 1] = t.y;
+        }
+    }
+}
+
+__device__ __forceinline__ float2 sub2f(float2 a, float2 b)   // a - b, one rounding
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 template <typename real, int M2, bool KAHAN>
 __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid &cg, const int *__restrict__ base,
                                             const real2_t<real> *__restrict__ frac, const real *__restrict__ q,
@@ -36,19 +63,23 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
                                             int pitch, int n_a)
 {
     constexpr int m = M2 / 2;
-    constexpr int TAPS = M2 * M2;
-    constexpr int PER = (TAPS + 31) / 32;
+    constexpr int G = spread_groups(M2);
+    constexpr int RPL = M2 / G;                               // rows per tap lane
+    constexpr int VW = 16 / (int)sizeof(real);
+    constexpr int RPAD = (RPL + VW - 1) / VW * VW;            // a group's row weights, vector-aligned
+    constexpr int WSTRIDE = spread_weight_stride<real>(M2);
     constexpr int PLANES = KAHAN ? 2 : 1;
     constexpr bool kPoly = sizeof(real) == 4;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Q = spread_pitch_warp(P, M2, lane);   // row pitch: bank-conflict-free taps
-    const int PP = P * Q;                             // one plane of a warp tile
+    const int Q = spread_group_pitch(P, M2);                 // row pitch: conflict-free tap rows
+    const int PP = P * Q;                                     // one plane of a warp tile
     real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
-    // FP32 window polynomials, one row per tap, after the warp tiles (taps differ across lanes)
-    float *poly = reinterpret_cast<float *>(reinterpret_cast<real *>(smem_raw) + (size_t)kSpreadWarps * PP * PLANES);
+    unsigned char *after_tiles = smem_raw + spread_tiles_bytes<real>(P, Q, PLANES);
+    real *wb = reinterpret_cast<real *>(after_tiles) + warp * WSTRIDE;
+    float *poly = reinterpret_cast<float *>(after_tiles + (size_t)kSpreadWarps * WSTRIDE * sizeof(real));
     if (kPoly) {
         for (int i = threadIdx.x; i < M2 * (kPolyD + 1); i += blockDim.x)
             poly[i] = wp.c[i / (kPolyD + 1)][i % (kPolyD + 1)];
@@ -58,20 +89,23 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
     for (int i = lane; i < PP * PLANES; i += 32)
         acc[i] = real(0);
     __syncthreads();
-    // this lane's taps: those on its shared-memory bank (spread_lane_taps)
-    int toff[PER], ta[PER], tb[PER];
-    unsigned valid;
-    spread_lane_taps<M2, PER>(lane, Q, ta, tb, toff, valid);
+    // weight lanes: lane a < M2 evaluates the first coordinate's weight of row a, lane M2 + b the
+    // second coordinate's weight of column b (times q); they go to the warp's weight slots
     const bool first = lane < M2;
     const int jw = first ? lane : lane - M2;
-    // the lane's window polynomial (FP32 path), held in registers for the whole item
-    float pc[kPolyD + 1];
+    const int wslot = first ? (jw / RPL) * RPAD + (jw % RPL) : G * RPAD + jw;
+    float pc[kPolyD + 1];   // the lane's window polynomial (FP32 path), in registers for the item
     {
         const float *prow = poly + (lane < 2 * M2 ? jw : 0) * (kPolyD + 1);
 #pragma unroll
         for (int k = 0; k <= kPolyD; ++k)
             pc[k] = kPoly ? prow[k] : 0.f;
     }
+    // tap lanes: lane (g, b) owns column b and rows g RPL .. g RPL + RPL - 1 of every source
+    const bool tap_lane = lane < G * M2;
+    const int g = lane / M2, b = lane - (lane / M2) * M2;
+    const real *wrow = wb + (tap_lane ? g : 0) * RPAD;
+    const real *wcol = wb + G * RPAD + (tap_lane ? b : 0);
     const int end = it.start + it.count;
     int j = it.start + warp;
     // software pipeline: the next source's record is in flight while this one is spread
@@ -92,41 +126,62 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
             nf = frac[j + kSpreadWarps];
             nq = q[j + kSpreadWarps];
         }
-        real wv = real(0);
         if (lane < 2 * M2) {
             const real fr = first ? f.x : f.y;
+            real wv;
             if constexpr (kPoly)
                 wv = poly_eval<kPolyD>(pc, (float)fr - 0.5f);
             else
                 wv = kb_value<real>(w, fr, m - 1 - jw);
-            if (!first)
-                wv *= qj;
+            wb[wslot] = first ? wv : wv * qj;
         }
-        real *corner = acc + (base1(packed) - m + 1 - o1) * Q + (base2(packed) - m + 1 - o2);
-        // A lane's taps of one source are distinct cells (and distinct from the other lanes'),
-        // so every read of this source is issued before any write: one shared-memory latency
-        // per source instead of one per tap.
-        real v[PER], old[PER], cmp[PER];
+        __syncwarp();
+        if (tap_lane) {
+            real w1[RPL];
+            load_row_weights<real, RPL>(wrow, w1);
+            const real w2 = *wcol;
+            // the taps of a lane are distinct cells, and distinct from the other lanes': every read
+            // of this source is issued before any write
+            real *cell = acc + (base1(packed) - m + 1 - o1 + g * RPL) * Q + (base2(packed) - m + 1 - o2 + b);
+            real v[RPL], old[RPL], cmp[RPL];
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const real w1 = __shfl_sync(0xffffffffu, wv, ta[i]);
-            const real w2 = __shfl_sync(0xffffffffu, wv, M2 + tb[i]);
-            v[i] = w1 * w2;
-            if ((valid >> i) & 1u) {
-                old[i] = corner[toff[i]];
+            for (int i = 0; i < RPL; ++i) {
+                v[i] = w1[i] * w2;
+                old[i] = cell[i * Q];
                 if (KAHAN)
-                    cmp[i] = corner[toff[i] + PP];
+                    cmp[i] = cell[i * Q + PP];
             }
-        }
+            if constexpr (KAHAN && sizeof(real) == 4) {
+                // TwoSum of (old, v) for two taps per packed instruction; the error goes to the
+                // compensation plane
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            if ((valid >> i) & 1u) {
-                real *cell = corner + toff[i];
-                const real s = old[i] + v[i];
-                *cell = s;
-                if (KAHAN) {
-                    const real bb = s - old[i];
-                    cell[PP] = cmp[i] + ((old[i] - (s - bb)) + (v[i] - bb));
+                for (int i = 0; i + 1 < RPL; i += 2) {
+                    const float2 o = make_float2(old[i], old[i + 1]), vv = make_float2(v[i], v[i + 1]);
+                    const float2 sm = __fadd2_rn(o, vv);
+                    const float2 bb = sub2f(sm, o);
+                    const float2 e = __fadd2_rn(sub2f(o, sub2f(sm, bb)), sub2f(vv, bb));
+                    const float2 c = __fadd2_rn(make_float2(cmp[i], cmp[i + 1]), e);
+                    cell[i * Q] = sm.x;
+                    cell[(i + 1) * Q] = sm.y;
+                    cell[i * Q + PP] = c.x;
+                    cell[(i + 1) * Q + PP] = c.y;
+                }
+                if constexpr (RPL % 2 == 1) {
+                    constexpr int i = RPL - 1;
+                    const real sm = old[i] + v[i];
+                    const real bb = sm - old[i];
+                    cell[i * Q] = sm;
+                    cell[i * Q + PP] = cmp[i] + ((old[i] - (sm - bb)) + (v[i] - bb));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) {
+                    const real sm = old[i] + v[i];
+                    cell[i * Q] = sm;
+                    if (KAHAN) {
+                        const real bb = sm - old[i];
+                        cell[i * Q + PP] = cmp[i] + ((old[i] - (sm - bb)) + (v[i] - bb));
+                    }
                 }
             }
         }
@@ -469,8 +524,7 @@ cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const in
 {
     const int TG = cg.T * cg.cell;
     const int P = TG + M2 - 1;
-    const size_t smem = (size_t)kSpreadWarps * P * spread_pitch(P, M2) * sizeof(real) * (kahan ? 2 : 1) +
-                        sizeof(float) * M2 * (kPolyD + 1);
+    const size_t smem = spread_smem_bytes<real>(P, M2, kahan);
     const real2_t<real> *fr = (const real2_t<real> *)frac;
     if (kahan) {
         auto kern = k_spread<real, M2, true>;
@@ -666,15 +720,15 @@ template <class F> cudaError_t with_width(int m, F &&f)
     }
 }
 
-// Instances have tiles of up to max_tile grid lines; a tile of r <= P rows takes r x
-// spread_pitch(r) words per plane, which is below P^2 <= P x spread_pitch(P) unless r > P - 32.
+// Instances have tiles of up to max_tile grid lines; a tile of r <= P rows takes at most
+// r (r + 31) words per plane, which is below P^2 <= P x pitch(P) unless r > P - 32.
 template <typename real> size_t batch_spread_smem(int M2, int max_tile, bool comp)
 {
     const int P = max_tile + M2 - 1;
-    size_t words = 0;
+    size_t bytes = 0;
     for (int r = P > 32 ? P - 32 : 1; r <= P; ++r)
-        words = std::max(words, (size_t)r * spread_pitch(r, M2));
-    return (size_t)kSpreadWarps * words * sizeof(real) * (comp ? 2 : 1) + sizeof(float) * M2 * (kPolyD + 1);
+        bytes = std::max(bytes, spread_smem_bytes<real>(r, M2, comp));
+    return bytes;
 }
 
 }  // namespace
