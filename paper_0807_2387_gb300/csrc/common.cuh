@@ -178,6 +178,20 @@ template <int DEG> __device__ __forceinline__ float poly_eval(const float *c, fl
     return acc;
 }
 
+// Even and odd parts of sum_i c[i] t^i as polynomials in s = t^2: e = sum_j c[2j] s^j,
+// o = sum_j c[2j+1] s^j, so that the polynomial at +-t is e +- t o.
+template <int DEG> __device__ __forceinline__ void poly_even_odd(const float *c, float s, float &e, float &o)
+{
+    constexpr int NE = DEG / 2, NO = (DEG - 1) / 2;   // highest even / odd half-index
+    e = c[2 * NE];
+#pragma unroll
+    for (int j = NE - 1; j >= 0; --j)
+        e = fmaf(e, s, c[2 * j]);
+    o = c[2 * NO + 1];
+#pragma unroll
+    for (int j = NO - 1; j >= 0; --j)
+        o = fmaf(o, s, c[2 * j + 1]);
+}
 
 // Spreading tiles in shared memory: a warp's tile holds `rows` x `rows` grid lines at a row
 // pitch q >= rows.  The M2 x M2 taps of one source sit at offsets a q + b (a, b < M2) from the

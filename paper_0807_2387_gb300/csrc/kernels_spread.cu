@@ -248,14 +248,27 @@ __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ 
     const real2_t<real> f = frac[k];
     real w1[M2], d1[M2], w2[M2], d2[M2];
     if constexpr (sizeof(real) == 4) {
-        // FP32: per-tap window polynomials (coefficients are warp-uniform kernel parameters)
+        // FP32: per-tap window polynomials in t = frac - 1/2 (coefficients are warp-uniform kernel
+        // parameters).  The window is even, so tap M2-1-a at t is tap a at -t: each pair takes
+        // the even and odd parts of tap a's polynomials in t^2 once (value p(+-t) = E +- t O,
+        // slope of the mirrored tap -p'(-t) = t O' - E'), about half the FMAs of 2 evaluations.
         const float t1 = (float)f.x - 0.5f, t2 = (float)f.y - 0.5f;
+        const float s1 = t1 * t1, s2 = t2 * t2;
 #pragma unroll
-        for (int a = 0; a < M2; ++a) {
-            w1[a] = poly_eval<kPolyD>(wp.c[a], t1);
-            d1[a] = poly_eval<kPolyD - 1>(wp.d[a], t1);
-            w2[a] = poly_eval<kPolyD>(wp.c[a], t2);
-            d2[a] = poly_eval<kPolyD - 1>(wp.d[a], t2);
+        for (int a = 0; a < m; ++a) {
+            float e, o;
+            poly_even_odd<kPolyD>(wp.c[a], s1, e, o);
+            w1[a] = fmaf(t1, o, e);
+            w1[M2 - 1 - a] = fmaf(-t1, o, e);
+            poly_even_odd<kPolyD>(wp.c[a], s2, e, o);
+            w2[a] = fmaf(t2, o, e);
+            w2[M2 - 1 - a] = fmaf(-t2, o, e);
+            poly_even_odd<kPolyD - 1>(wp.d[a], s1, e, o);
+            d1[a] = fmaf(t1, o, e);
+            d1[M2 - 1 - a] = fmaf(t1, o, -e);
+            poly_even_odd<kPolyD - 1>(wp.d[a], s2, e, o);
+            d2[a] = fmaf(t2, o, e);
+            d2[M2 - 1 - a] = fmaf(t2, o, -e);
         }
     } else {
 #pragma unroll
