@@ -71,6 +71,13 @@ typedef enum { FS_F32 = 32, FS_F64 = 64 } fs_dtype;
 #define FS_FLAG_SERIAL 8u     /* FP32 plans: run the near field on the plan's stream after the
                                  interpolation instead of on a second stream beside spreading
                                  and the transform (slower; stage times then do not overlap) */
+#define FS_FLAG_SPREAD_DIRECT 16u  /* 2D plans: spread every tap straight into the grid with global
+                                      atomics (FP32: with a compensation plane) instead of through
+                                      shared-memory tiles */
+#define FS_FLAG_SPREAD_TILES 32u   /* 2D plans: use the shared-memory tiles (the default: on
+                                      GB300 they were faster at every density measured, 1.4 to
+                                      over 700 sources per occupied tile; fs_info.spread_direct
+                                      reports the mode a plan uses) */
 
 /* Plan options.  A zeroed struct (or NULL) selects every default. */
 typedef struct {
@@ -103,6 +110,8 @@ typedef struct {
     int64_t workspace_bytes;
     int is_fem;               /* plan built by fs_plan_create_fem */
     int64_t n_nodes, n_tris, n_bedges;
+    int spread_direct;        /* 1: the plan spreads with global atomics (FS_FLAG_SPREAD_DIRECT or
+                                 too few sources per tile), 0: shared-memory tiles */
 } fs_info;
 
 /*

@@ -25,7 +25,7 @@ import ctypes
 import weakref
 
 from ._native import (FS_F32, FS_F64, FS_FLAG_AUTOTUNE, FS_FLAG_NO_KAHAN, FS_FLAG_SERIAL, FS_FLAG_TIMING,  # noqa: F401
-                      FS_PROBE_FFMA, FS_PROBE_FFMA2, FS_PROBE_MUFU,
+                      FS_FLAG_SPREAD_DIRECT, FS_FLAG_SPREAD_TILES, FS_PROBE_FFMA, FS_PROBE_FFMA2, FS_PROBE_MUFU,
                       FastSumError, FsBatchFacts, FsInfo, FsInstance, FsOpts, NativeLibraryMissing, check, load)
 
 __all__ = [

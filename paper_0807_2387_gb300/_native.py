@@ -13,6 +13,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_EDOMAIN", 3: "FS_ENOMEM", 4: 
                 5: "FS_ETIMEOUT", 6: "FS_EUNSUPPORTED"}
 FS_F32, FS_F64 = 32, 64
 FS_FLAG_NO_KAHAN, FS_FLAG_TIMING, FS_FLAG_AUTOTUNE, FS_FLAG_SERIAL = 1, 2, 4, 8
+FS_FLAG_SPREAD_DIRECT, FS_FLAG_SPREAD_TILES = 16, 32
 FS_PROBE_FFMA, FS_PROBE_FFMA2, FS_PROBE_MUFU = 0, 1, 2
 
 EXPORTED = (
@@ -42,7 +43,8 @@ class FsInfo(ctypes.Structure):
                 ("tile_cells", ctypes.c_int), ("spread_items", ctypes.c_int),
                 ("near_pairs", ctypes.c_int64), ("near_pairs_fp64", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("is_fem", ctypes.c_int),
-                ("n_nodes", ctypes.c_int64), ("n_tris", ctypes.c_int64), ("n_bedges", ctypes.c_int64)]
+                ("n_nodes", ctypes.c_int64), ("n_tris", ctypes.c_int64), ("n_bedges", ctypes.c_int64),
+                ("spread_direct", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

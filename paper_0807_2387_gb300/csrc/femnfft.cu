@@ -534,6 +534,24 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
             FS_CUDA(cudaMemcpy(*dst, items.data(), items.size() * sizeof(SpreadItem), cudaMemcpyHostToDevice));
     }
 
+    // spreading mode: shared-memory tiles, or global atomics when the occupied tiles hold so few
+    // sources that zeroing and flushing a tile costs more than the atomics it saves
+    {
+        int occupied = 0, prev = -1;
+        for (const SpreadItem &it : pl->items_h)
+            if (it.tile != prev) {
+                ++occupied;
+                prev = it.tile;
+            }
+        const double per_tile = occupied > 0 ? (double)M / occupied : 0.0;
+        if (o.flags & FS_FLAG_SPREAD_DIRECT)
+            pl->spread_direct = true;
+        else if (o.flags & FS_FLAG_SPREAD_TILES)
+            pl->spread_direct = false;
+        else
+            pl->spread_direct = M > 0 && per_tile < kDirectSpreadBelow;
+    }
+
     if (pl->precision == 32) {
         FS_TRY(build_near_items(pl, pl->tgt_start, pl->src_start, true, &pl->near_items, &pl->n_near_items,
                                 &pl->near_items_h, &pl->near_work_h));
@@ -552,6 +570,8 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
 
     // grids and per-target intermediates
     FS_TRY(pl->alloc_bytes(&pl->grid, (size_t)n_a * pl->pitch * sizeof(real)));
+    if (pl->spread_direct && pl->kahan && sizeof(real) == 4)
+        FS_TRY(pl->alloc_bytes(&pl->grid_comp, (size_t)n_a * pl->pitch * sizeof(real)));
     FS_TRY(pl->alloc_bytes(&pl->spec, (size_t)(pl->n / 2 + 1) * pl->ld * 2 * sizeof(real)));
     FS_TRY(pl->alloc_bytes(&pl->phi_s, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
     FS_TRY(pl->alloc_bytes(&pl->grad_s, (size_t)std::max<int64_t>(N, 1) * 2 * sizeof(real)));
@@ -678,6 +698,24 @@ template <typename real> fs_status set_charges_t(fs_plan *pl, const void *q, fs_
     return FS_OK;
 }
 
+// Step (c): the grid is zeroed and the charges spread into it, through shared-memory tiles or
+// (sparse plans, FS_FLAG_SPREAD_DIRECT) with global atomics and a compensation plane.
+template <typename real> fs_status spread_forward(fs_plan *pl, const real *q, const Window<real> &w, cudaStream_t st)
+{
+    const size_t grid_bytes = (size_t)pl->n_a * pl->pitch * sizeof(real);
+    FS_CUDA(cudaMemsetAsync(pl->grid, 0, grid_bytes, st));
+    if (!pl->spread_direct) {
+        FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w, pl->wpoly,
+                                    (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
+        return FS_OK;
+    }
+    if (pl->grid_comp)
+        FS_CUDA(cudaMemsetAsync(pl->grid_comp, 0, grid_bytes, st));
+    FS_CUDA(launch_spread_direct<real>(pl->M, pl->m, pl->src_base, pl->src_frac, q, w, pl->wpoly, (real *)pl->grid,
+                                       (real *)pl->grid_comp, pl->pitch, pl->n_a, pl->kahan, st));
+    return FS_OK;
+}
+
 template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dtype dtype)
 {
     cudaStream_t st = pl->stream;
@@ -693,9 +731,7 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
             FS_CUDA(cudaEventRecord(pl->ev[0], st));
         if (pl->overlap)
             FS_CUDA(cudaEventRecord(pl->ev_fork, st));   // the charges are in
-        FS_CUDA(cudaMemsetAsync(pl->grid, 0, (size_t)pl->n_a * pl->pitch * sizeof(real), st));
-        FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w, pl->wpoly,
-                                    (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
+        FS_TRY(spread_forward<real>(pl, q, w, st));
         if (pl->overlap) {
             // the near field (stored, not added) on the second stream, submitted after the
             // spreading so that the spreading's blocks are scheduled first
@@ -887,9 +923,7 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
                     FS_CUDA(cudaEventRecord(pl->ev_join, pl->aux));
                 }
             }
-            FS_CUDA(cudaMemsetAsync(pl->grid, 0, grid_bytes, st));
-            FS_CUDA(launch_spread<real>(pl->items, pl->n_items, pl->cg, pl->m, pl->src_base, pl->src_frac, q, w,
-                                        pl->wpoly, (real *)pl->grid, pl->pitch, pl->n_a, pl->kahan, st));
+            FS_TRY(spread_forward<real>(pl, q, w, st));
             FS_TRY(spectral_pipeline<real>(pl));
             if (ovl)
                 FS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
@@ -1250,6 +1284,7 @@ fs_status fs_plan_info(const fs_plan *plan, fs_info *info)
     info->n_nodes = plan->Nv;
     info->n_tris = plan->Nt;
     info->n_bedges = plan->Ne;
+    info->spread_direct = plan->spread_direct ? 1 : 0;
     return FS_OK;
 }
 

@@ -263,6 +263,12 @@ template <typename real>
 cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
                           const void *frac, const real *q, Window<real> w, const WindowPoly &wp, real *grid,
                           int pitch, int n_a, bool kahan, cudaStream_t st);
+// direct spreading (global atomics, no tiles); comp: compensation plane of the grid's size
+// (FP32 with compensation; folded into the grid at the end), may be null otherwise
+template <typename real>
+cudaError_t launch_spread_direct(int64_t M, int m, const int *base, const void *frac, const real *q, Window<real> w,
+                                 const WindowPoly &wp, real *grid, real *comp, int pitch, int n_a, bool kahan,
+                                 cudaStream_t st);
 template <typename real>
 // acc: add to phi_s / grad_s (the near field already stored there) instead of writing them
 cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, Window<real> w,

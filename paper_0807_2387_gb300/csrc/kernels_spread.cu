@@ -205,6 +205,80 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
     }
 }
 
+// Direct spreading, the alternative to the shared-memory tiles for sparse plans: a warp per
+// source (grid-stride), the same row-group lanes, every tap added straight to the grid with a
+// global atomic.  FP32 plans with compensation take the old value the atomic returns, recover
+// the addition's rounding error exactly (TwoSum of the old and the added value: the atomic
+// rounds to nearest like the add it replaces) and add it to a compensation plane, which
+// k_fold_comp folds into the grid before the transform.  The window weights reach the tap
+// lanes by shuffles.
+template <typename real, int M2, bool KAHAN>
+__global__ void __launch_bounds__(256) k_spread_direct(int64_t M, const int *__restrict__ base,
+                                                       const real2_t<real> *__restrict__ frac,
+                                                       const real *__restrict__ q, Window<real> w, WindowPoly wp,
+                                                       real *__restrict__ grid, real *__restrict__ comp, int pitch)
+{
+    constexpr int m = M2 / 2;
+    constexpr int G = spread_groups(M2);
+    constexpr int RPL = M2 / G;
+    constexpr bool kPoly = sizeof(real) == 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool first = lane < M2;
+    const int jw = first ? lane : lane - M2;
+    float pc[kPolyD + 1];
+#pragma unroll
+    for (int k = 0; k <= kPolyD; ++k)
+        pc[k] = (kPoly && lane < 2 * M2) ? wp.c[jw][k] : 0.f;
+    const bool tap_lane = lane < G * M2;
+    const int g = lane / M2, b = lane - (lane / M2) * M2;
+    for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < M; j += warps) {
+        const int packed = base[j];
+        const real2_t<real> f = frac[j];
+        const real qj = q[j];
+        real wv = real(0);
+        if (lane < 2 * M2) {
+            const real fr = first ? f.x : f.y;
+            if constexpr (kPoly)
+                wv = poly_eval<kPolyD>(pc, (float)fr - 0.5f);
+            else
+                wv = kb_value<real>(w, fr, m - 1 - jw);
+            if (!first)
+                wv *= qj;
+        }
+        const real w2 = __shfl_sync(0xffffffffu, wv, M2 + (tap_lane ? b : 0));
+        real w1[RPL];
+#pragma unroll
+        for (int i = 0; i < RPL; ++i)
+            w1[i] = __shfl_sync(0xffffffffu, wv, (tap_lane ? g : 0) * RPL + i);
+        if (tap_lane) {
+            const int64_t at = (int64_t)(base1(packed) - m + 1 + g * RPL) * pitch + (base2(packed) - m + 1 + b);
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) {
+                const real v = w1[i] * w2;
+                const int64_t k = at + (int64_t)i * pitch;
+                if constexpr (KAHAN) {
+                    const real old = atomicAdd(grid + k, v);
+                    const real sm = old + v, bb = sm - old;
+                    const real e = (old - (sm - bb)) + (v - bb);
+                    if (e != real(0))
+                        atomicAdd(comp + k, e);
+                } else {
+                    atomicAdd(grid + k, v);
+                }
+            }
+        }
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_fold_comp(int64_t n, real *__restrict__ grid, const real *__restrict__ comp)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n)
+        grid[k] += comp[k];
+}
+
 template <typename real, int M2, bool KAHAN>
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
                                                               const int *__restrict__ base,
@@ -665,6 +739,21 @@ template cudaError_t launch_interp_hess<double>(int64_t, int, const int *, const
                                                 const WindowPoly &, const double *, int, double, double *, double *,
                                                 bool, cudaStream_t);
 
+// Calls f(std::integral_constant<int, 2m>) for the window half-width m in 2..8.
+template <class F> cudaError_t with_width_spread(int m, F &&f)
+{
+    switch (m) {
+    case 2: return f(std::integral_constant<int, 4>{});
+    case 3: return f(std::integral_constant<int, 6>{});
+    case 4: return f(std::integral_constant<int, 8>{});
+    case 5: return f(std::integral_constant<int, 10>{});
+    case 6: return f(std::integral_constant<int, 12>{});
+    case 7: return f(std::integral_constant<int, 14>{});
+    case 8: return f(std::integral_constant<int, 16>{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename real>
 cudaError_t launch_spread(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base, const void *frac,
                           const real *q, Window<real> w, const WindowPoly &wp, real *grid, int pitch, int n_a,
@@ -710,6 +799,44 @@ template cudaError_t launch_spread<float>(const SpreadItem *, int, CellGrid, int
 template cudaError_t launch_spread<double>(const SpreadItem *, int, CellGrid, int, const int *, const void *,
                                            const double *, Window<double>, const WindowPoly &, double *, int, int,
                                            bool, cudaStream_t);
+template <typename real>
+cudaError_t launch_spread_direct(int64_t M, int m, const int *base, const void *frac, const real *q, Window<real> w,
+                                 const WindowPoly &wp, real *grid, real *comp, int pitch, int n_a, bool kahan,
+                                 cudaStream_t st)
+{
+    if (M <= 0)
+        return cudaSuccess;
+    const bool comp_on = kahan && sizeof(real) == 4 && comp;
+    const real2_t<real> *fr = (const real2_t<real> *)frac;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t want = (M + 7) / 8;   // 8 warps (sources in flight) per block of 256
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    e = with_width_spread(m, [&](auto mc) {
+        constexpr int M2 = decltype(mc)::value;
+        if (comp_on)
+            k_spread_direct<real, M2, true><<<blocks, 256, 0, st>>>(M, base, fr, q, w, wp, grid, comp, pitch);
+        else
+            k_spread_direct<real, M2, false><<<blocks, 256, 0, st>>>(M, base, fr, q, w, wp, grid, comp, pitch);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess || !comp_on)
+        return e;
+    const int64_t n = (int64_t)n_a * pitch;
+    k_fold_comp<real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, grid, comp);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_spread_direct<float>(int64_t, int, const int *, const void *, const float *, Window<float>,
+                                                 const WindowPoly &, float *, float *, int, int, bool, cudaStream_t);
+template cudaError_t launch_spread_direct<double>(int64_t, int, const int *, const void *, const double *,
+                                                  Window<double>, const WindowPoly &, double *, double *, int, int,
+                                                  bool, cudaStream_t);
+
 template cudaError_t launch_interp<float>(int64_t, int, const int *, const void *, Window<float>, const WindowPoly &,
                                           const float *, int, float, float *, float *, bool, cudaStream_t);
 template cudaError_t launch_interp<double>(int64_t, int, const int *, const void *, Window<double>,

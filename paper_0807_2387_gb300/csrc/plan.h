@@ -18,6 +18,12 @@ fs_status fail(fs_status st, const std::string &msg);
 
 constexpr int kStages = 8;
 constexpr int kSpreadChunk = 512;   // sources per spreading work item
+// 2D plans whose occupied spreading tiles hold fewer sources than this on average spread with
+// global atomics (the plan's choice in plan_init).  Zero: on GB300 the tiles won at every
+// density measured, from 1.4 to over 700 sources per occupied tile (uniform discs of 2^10 to
+// 2^20 points on n = 128 and 512 grids, m = 5: 12.9 vs 19.9 us at the sparse end, 170 vs
+// 545 us at the dense end), so direct spreading is used only when FS_FLAG_SPREAD_DIRECT asks.
+constexpr double kDirectSpreadBelow = 0.0;
 
 }  // namespace fs
 
@@ -80,6 +86,8 @@ struct fs_plan {
     bool src_major = false;           // FP32 forward near field over source items (many more sources than targets)
     void *mul = nullptr, *tw = nullptr;
     void *grid = nullptr, *spec = nullptr;
+    void *grid_comp = nullptr;        // direct spreading (FP32): compensation plane of the grid
+    bool spread_direct = false;       // spread with global atomics instead of shared-memory tiles
     void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
     // charges
     void *q_sorted = nullptr;

@@ -93,7 +93,7 @@ def test_binding_layouts_and_constants_match_the_header(tmp_path):
                "fs_batch_facts": N.FsBatchFacts}
     consts = ["FS_OK", "FS_EINVAL", "FS_EDOMAIN", "FS_ENOMEM", "FS_ECUDA", "FS_ETIMEOUT", "FS_EUNSUPPORTED",
               "FS_F32", "FS_F64", "FS_FLAG_NO_KAHAN", "FS_FLAG_TIMING", "FS_FLAG_AUTOTUNE", "FS_FLAG_SERIAL",
-              "FS_PROBE_FFMA", "FS_PROBE_FFMA2", "FS_PROBE_MUFU"]
+              "FS_PROBE_FFMA", "FS_PROBE_FFMA2", "FS_PROBE_MUFU", "FS_FLAG_SPREAD_DIRECT", "FS_FLAG_SPREAD_TILES"]
     lines = ['#include <stdio.h>', '#include "femnfft.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("size {cname} %zu\\n", sizeof({cname}));')

@@ -528,3 +528,36 @@ def test_source_major_near_field_with_coincident_points(pkg, precision, tol):
     phi, H, _ = gpu_field(pkg, case, precision)
     phi_o, H_o = oracle_field(case)
     assert rel(phi, phi_o) <= tol and rel(H, H_o) <= tol, (rel(phi, phi_o), rel(H, H_o))
+
+
+@pytest.mark.parametrize("seed,ns,nt,n,m,eps", [(151, 1, 40, 32, 4, 2 / 32), (152, 37, 53, 16, 3, 2 / 16),
+                                                (153, 2500, 2200, 64, 6, 4 / 64)])
+def test_direct_spreading_matches_oracle(pkg, seed, ns, nt, n, m, eps):
+    """FS_FLAG_SPREAD_DIRECT (every tap added to the grid with global atomics): FP64 vs O3 at 1e-12,
+    FP32 (with its compensation plane) vs FP64 within 2e-5."""
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(seed, ns, nt, n=n, m=m, eps_I=eps)
+    phi_o, H_o = oracle_field(case)
+    phi, H, info = gpu_field(pkg, case, 64, flags=pkg.FS_FLAG_SPREAD_DIRECT)
+    assert info["spread_direct"] == 1
+    assert rel(phi, phi_o) <= 1e-12 and rel(H, H_o) <= 1e-12, (rel(phi, phi_o), rel(H, H_o))
+    phi32, H32, info32 = gpu_field(pkg, case, 32, flags=pkg.FS_FLAG_SPREAD_DIRECT)
+    assert info32["spread_direct"] == 1
+    assert rel(phi32, phi) <= 2e-5 and rel(H32, H) <= 2e-5, (rel(phi32, phi), rel(H32, H))
+
+
+def test_spread_mode_choice(pkg):
+    """The tiles are the default at every density (they won every measured case on GB300), the
+    flags force either mode, and both modes agree on a sparse and a dense plan."""
+    from paper_0807_2387_gb300 import workloads as W
+    sparse = W.small_case(154, 300, 300, n=256, m=5, eps_I=4 / 256)
+    phi_a, H_a, auto = gpu_field(pkg, sparse, 32)
+    _, _, tiles = gpu_field(pkg, sparse, 32, flags=pkg.FS_FLAG_SPREAD_TILES)
+    phi_s, H_s, direct = gpu_field(pkg, sparse, 32, flags=pkg.FS_FLAG_SPREAD_DIRECT)
+    assert auto["spread_direct"] == 0 and tiles["spread_direct"] == 0 and direct["spread_direct"] == 1
+    assert rel(phi_s, phi_a) <= 1e-6 and rel(H_s, H_a) <= 1e-6, (rel(phi_s, phi_a), rel(H_s, H_a))
+    dense = W.small_case(155, 20000, 2000, n=64, m=4, eps_I=2 / 64)
+    phi_t, H_t, info = gpu_field(pkg, dense, 32)
+    assert info["spread_direct"] == 0
+    phi_d, H_d, _ = gpu_field(pkg, dense, 32, flags=pkg.FS_FLAG_SPREAD_DIRECT)
+    assert rel(phi_d, phi_t) <= 1e-6 and rel(H_d, H_t) <= 1e-6, (rel(phi_d, phi_t), rel(H_d, H_t))
