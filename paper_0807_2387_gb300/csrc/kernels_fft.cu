@@ -349,7 +349,7 @@ __device__ bool block_wait_geq(const int *ctr, int target, int *err, int spins)
 // units a block waits for were taken earlier by blocks that are running and never wait on
 // later units, so the waits end; each is bounded all the same (error word on timeout).
 template <typename real>
-__global__ void __launch_bounds__(256) k_batch_fft(const BatchInst<real> *__restrict__ inst,
+__global__ void __launch_bounds__(256, 5) k_batch_fft(const BatchInst<real> *__restrict__ inst,
                                                    const FftUnit *__restrict__ units, int n_units, int n_inst,
                                                    int nrhs, int L_max, int *counters, int *err, int spins)
 {
