@@ -167,11 +167,31 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
 {
     const int r = 2 * rp;
     const bool has2 = r + 1 < n_a;
-    for (int c = threadIdx.x; c < L; c += blockDim.x) {
-        cplx<real> z;
-        z.x = c < n_a ? grid[(int64_t)r * pitch + c] : real(0);
-        z.y = (c < n_a && has2) ? grid[(int64_t)(r + 1) * pitch + c] : real(0);
-        a[c] = z;
+    if constexpr (sizeof(real) == 4) {
+        // 16-byte loads of four values of each row (n_a and the pitch are multiples of 4),
+        // several in flight per thread
+        const float4 *r0 = reinterpret_cast<const float4 *>(grid + (int64_t)r * pitch);
+        const float4 *r1 = reinterpret_cast<const float4 *>(grid + (int64_t)(has2 ? r + 1 : r) * pitch);
+        const int nv = n_a / 4;
+#pragma unroll 4
+        for (int v = threadIdx.x; v < L / 4; v += blockDim.x) {
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+            if (v < nv) {
+                x = r0[v];
+                if (has2)
+                    y = r1[v];
+            }
+            float4 *dst = reinterpret_cast<float4 *>(a + 4 * v);
+            dst[0] = make_float4(x.x, y.x, x.y, y.y);
+            dst[1] = make_float4(x.z, y.z, x.w, y.w);
+        }
+    } else {
+        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+            cplx<real> z;
+            z.x = c < n_a ? grid[(int64_t)r * pitch + c] : real(0);
+            z.y = (c < n_a && has2) ? grid[(int64_t)(r + 1) * pitch + c] : real(0);
+            a[c] = z;
+        }
     }
     __syncthreads();
     const cplx<real> *Z = fft_line<real, false>(a, b, L, tw);
@@ -184,9 +204,17 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
         X.y = real(0.5) * (zk.y - zc.y);
         Y.x = real(0.5) * (zk.y + zc.y);
         Y.y = real(-0.5) * (zk.x - zc.x);
-        spec[(int64_t)k * ld + r] = X;
-        if (has2)
-            spec[(int64_t)k * ld + r + 1] = Y;
+        if constexpr (sizeof(real) == 4) {
+            // the two rows' bins are adjacent (ld and r even): one 16-byte store
+            if (has2)
+                *reinterpret_cast<float4 *>(spec + (int64_t)k * ld + r) = make_float4(X.x, X.y, Y.x, Y.y);
+            else
+                spec[(int64_t)k * ld + r] = X;
+        } else {
+            spec[(int64_t)k * ld + r] = X;
+            if (has2)
+                spec[(int64_t)k * ld + r + 1] = Y;
+        }
     }
 }
 
@@ -197,15 +225,23 @@ __device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec,
                                           cplx<real> *a, cplx<real> *b)
 {
     cplx<real> *col = spec + (int64_t)l1 * ld;
-    for (int r = threadIdx.x; r < L; r += blockDim.x) {
-        cplx<real> v;
-        if (r < n_a) {
-            v = load<CG>(col + r);
-        } else {
-            v.x = real(0);
-            v.y = real(0);
+    if constexpr (sizeof(real) == 4) {
+        // two complex values per 16-byte load (ld and n_a are multiples of 4)
+        const float4 *c4 = reinterpret_cast<const float4 *>(col);
+#pragma unroll 4
+        for (int v = threadIdx.x; v < L / 2; v += blockDim.x)
+            reinterpret_cast<float4 *>(a)[v] = 2 * v < n_a ? load<CG>(c4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int r = threadIdx.x; r < L; r += blockDim.x) {
+            cplx<real> v;
+            if (r < n_a) {
+                v = load<CG>(col + r);
+            } else {
+                v.x = real(0);
+                v.y = real(0);
+            }
+            a[r] = v;
         }
-        a[r] = v;
     }
     __syncthreads();
     cplx<real> *F = fft_line<real, false>(a, b, L, tw);
@@ -227,8 +263,13 @@ __device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec,
     }
     __syncthreads();
     const cplx<real> *G = fft_line<real, true>(F, other, L, tw);
-    for (int r = threadIdx.x; r < n_a; r += blockDim.x)
-        col[r] = G[r];
+    if constexpr (sizeof(real) == 4) {
+        for (int v = threadIdx.x; v < n_a / 2; v += blockDim.x)
+            reinterpret_cast<float4 *>(col)[v] = reinterpret_cast<const float4 *>(G)[v];
+    } else {
+        for (int r = threadIdx.x; r < n_a; r += blockDim.x)
+            col[r] = G[r];
+    }
 }
 
 // Hermitian-extended inverse of two rows (2 rp, 2 rp + 1): real outputs on the window columns.
@@ -239,36 +280,77 @@ __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restri
 {
     const int r = 2 * rp;
     const bool has2 = r + 1 < n_a;
-    for (int c = threadIdx.x; c < L; c += blockDim.x) {
-        cplx<real> X, Y;
-        X.x = X.y = Y.x = Y.y = real(0);
-        if (c <= n_half) {
-            X = load<CG>(spec + (int64_t)c * ld + r);
-            if (has2)
-                Y = load<CG>(spec + (int64_t)c * ld + r + 1);
-            if (c == 0) {
-                X.y = real(0);
-                Y.y = real(0);
+    if constexpr (sizeof(real) == 4) {
+        // the two rows' bins are adjacent: one 16-byte load per column, several in flight
+#pragma unroll 4
+        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool lower = c <= n_half, upper = c >= L - n_half;
+            if (lower || upper) {
+                const cplx<real> *at = spec + (int64_t)(lower ? c : L - c) * ld + r;
+                if (has2) {
+                    t = load<CG>(reinterpret_cast<const float4 *>(at));
+                } else {
+                    const float2 x = load<CG>(at);
+                    t = make_float4(x.x, x.y, 0.f, 0.f);
+                }
+                if (!lower) {            // the Hermitian half: conjugates
+                    t.y = -t.y;
+                    t.w = -t.w;
+                } else if (c == 0) {
+                    t.y = 0.f;
+                    t.w = 0.f;
+                }
             }
-        } else if (c >= L - n_half) {
-            X = load<CG>(spec + (int64_t)(L - c) * ld + r);
-            X.y = -X.y;
-            if (has2) {
-                Y = load<CG>(spec + (int64_t)(L - c) * ld + r + 1);
-                Y.y = -Y.y;
-            }
+            cplx<real> z;   // X + i Y with X = (t.x, t.y), Y = (t.z, t.w)
+            z.x = t.x - t.w;
+            z.y = t.y + t.z;
+            a[c] = z;
         }
-        cplx<real> z;   // X + i Y
-        z.x = X.x - Y.y;
-        z.y = X.y + Y.x;
-        a[c] = z;
-    }
-    __syncthreads();
-    const cplx<real> *Z = fft_line<real, true>(a, b, L, tw);
-    for (int c = threadIdx.x; c < n_a; c += blockDim.x) {
-        grid[(int64_t)r * pitch + c] = Z[c].x;
-        if (has2)
-            grid[(int64_t)(r + 1) * pitch + c] = Z[c].y;
+        __syncthreads();
+        const cplx<real> *Z = fft_line<real, true>(a, b, L, tw);
+        // four columns of both rows per step: 16-byte stores (n_a and the pitch are multiples of 4)
+        float4 *r0 = reinterpret_cast<float4 *>(grid + (int64_t)r * pitch);
+        float4 *r1 = reinterpret_cast<float4 *>(grid + (int64_t)(r + 1) * pitch);
+        for (int v = threadIdx.x; v < n_a / 4; v += blockDim.x) {
+            const float4 p = reinterpret_cast<const float4 *>(Z)[2 * v];       // Z[4v], Z[4v + 1]
+            const float4 q = reinterpret_cast<const float4 *>(Z)[2 * v + 1];   // Z[4v + 2], Z[4v + 3]
+            r0[v] = make_float4(p.x, p.z, q.x, q.z);
+            if (has2)
+                r1[v] = make_float4(p.y, p.w, q.y, q.w);
+        }
+    } else {
+        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+            cplx<real> X, Y;
+            X.x = X.y = Y.x = Y.y = real(0);
+            if (c <= n_half) {
+                X = load<CG>(spec + (int64_t)c * ld + r);
+                if (has2)
+                    Y = load<CG>(spec + (int64_t)c * ld + r + 1);
+                if (c == 0) {
+                    X.y = real(0);
+                    Y.y = real(0);
+                }
+            } else if (c >= L - n_half) {
+                X = load<CG>(spec + (int64_t)(L - c) * ld + r);
+                X.y = -X.y;
+                if (has2) {
+                    Y = load<CG>(spec + (int64_t)(L - c) * ld + r + 1);
+                    Y.y = -Y.y;
+                }
+            }
+            cplx<real> z;   // X + i Y
+            z.x = X.x - Y.y;
+            z.y = X.y + Y.x;
+            a[c] = z;
+        }
+        __syncthreads();
+        const cplx<real> *Z = fft_line<real, true>(a, b, L, tw);
+        for (int c = threadIdx.x; c < n_a; c += blockDim.x) {
+            grid[(int64_t)r * pitch + c] = Z[c].x;
+            if (has2)
+                grid[(int64_t)(r + 1) * pitch + c] = Z[c].y;
+        }
     }
 }
 
