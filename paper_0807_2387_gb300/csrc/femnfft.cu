@@ -317,11 +317,7 @@ fs_status build_near_items(fs_plan *pl, const int *own_start_d, const int *oth_s
 template <typename real> fs_status twiddles(fs_plan *pl, int L, void **out)
 {
     std::vector<real> h(2 * (size_t)L);
-    for (int t = 0; t < L; ++t) {
-        const double ang = 2.0 * kPi * (double)t / (double)L;
-        h[2 * t] = (real)std::cos(ang);
-        h[2 * t + 1] = (real)(-std::sin(ang));
-    }
+    fft_twiddle_table<real>(L, h.data());
     FS_TRY(pl->alloc_bytes(out, h.size() * sizeof(real)));
     FS_CUDA(cudaMemcpyAsync(*out, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, pl->stream));
     FS_CUDA(cudaStreamSynchronize(pl->stream));

@@ -286,6 +286,13 @@ cudaError_t launch_interp_hess(int64_t N, int m, const int *base, const void *fr
                                real *hess_s, bool acc, cudaStream_t st);
 
 // ---- FFT and spectral multiply (kernels_fft.cu)
+// Radix of the Stockham pass that follows the first L / rest points: 8 while 8 divides the
+// rest, then one pass of 4 or 2.
+__host__ __device__ constexpr int fft_pass_radix(int rest) { return rest % 8 == 0 ? 8 : (rest == 4 ? 4 : 2); }
+// Twiddles of a length-L transform (L a power of two, 2 L values re, im): for each pass
+// (Ns points already combined, radix R) the entries Ns - 1 + (r - 1) Ns + k, r = 1..R-1,
+// k = 0..Ns-1, hold exp(-2 pi i r k / (Ns R)); entry L - 1 is 1.  Computed in FP64.
+template <typename real> void fft_twiddle_table(int L, real *re_im);
 template <typename real>
 cudaError_t launch_fft_rows_fwd(const real *grid, int pitch, int n_a, int L, int n_half,
                                 typename Cplx<real>::type *spec, int ld, const typename Cplx<real>::type *tw,

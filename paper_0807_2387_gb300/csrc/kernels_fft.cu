@@ -17,8 +17,13 @@
 //
 // Each 1D transform is a Stockham autosort FFT in shared memory: radix-8
 // butterflies held in registers (a final radix-4 or radix-2 pass for the rest of
-// log2 L), ping-pong buffers, one __syncthreads per pass, twiddles from a table
-// of exp(-2 pi i t / L) that the 2D kernels first copy into shared memory.
+// log2 L), ping-pong buffers, one __syncthreads per pass.  The twiddles of each
+// pass sit together in a table ordered by pass, multiple and butterfly (see
+// fft_twiddle_table), which the 2D kernels first copy into shared memory; the
+// buffers between two passes are stored with an XOR swizzle of the index so that
+// the strided writes of the early passes hit distinct banks.
+#include <cmath>
+
 #include "internal.h"
 
 namespace fs {
@@ -78,25 +83,34 @@ template <bool INV, typename real, typename C> __device__ __forceinline__ void d
     }
 }
 
-// One Stockham pass of radix R over the line: butterfly j reads src[j + r L/R], twiddles by
-// tw[r k L/(Ns R)] (k = j mod Ns), transforms in registers and writes dst[(j - k) R + k + r Ns].
+// Shared-memory position of element i of a buffer between two passes: the low four bits
+// XORed with the next four (a permutation within each aligned run of 16 elements).  Every
+// warp-wide access of a pass then touches 16 distinct 8-byte bank pairs per half-warp, where
+// the first pass's writes, 8 elements apart, would otherwise fall on two.  m = 15 turns the
+// swizzle on, m = 0 leaves the natural order (the line's input and result).
+__device__ __forceinline__ int swz(int i, int m) { return i ^ ((i >> 4) & m); }
+
+// One Stockham pass of radix R over the line: butterfly j reads src[j + r L/R], multiplies
+// element r by w^(r k) with w = exp(-+2 pi i / (Ns R)) (k = j mod Ns), transforms in
+// registers and writes dst[(j - k) R + k + r Ns].  The pass's twiddles are tw[Ns - 1 +
+// (r - 1) Ns + k], consecutive in k, so that a warp reads them without bank conflicts.
 template <typename real, bool INV, int R>
 __device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> *dst, int L, int Ns,
-                                              const cplx<real> *__restrict__ tw)
+                                              const cplx<real> *__restrict__ tw, int m_in, int m_out)
 {
     using C = cplx<real>;
     const int nb = L / R;
-    const int tstep = L / (Ns * R);
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         const int k = j & (Ns - 1);
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            v[r] = src[j + r * nb];
+            v[r] = src[swz(j + r * nb, m_in)];
         if (k) {
+            const C *twk = tw + (Ns - 1) + k;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C t = tw[r * k * tstep];
+                C t = twk[(r - 1) * Ns];
                 if (INV)
                     t.y = -t.y;
                 v[r] = cmul(v[r], t);
@@ -114,31 +128,29 @@ __device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> 
         const int idx = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            dst[idx + r * Ns] = v[r];
+            dst[swz(idx + r * Ns, m_out)] = v[r];
     }
 }
 
 // In-place (via ping-pong) FFT of one line of length L (a power of two) held in shared memory:
-// radix-8 passes, then one radix-4 or radix-2 pass for the remaining factor, one __syncthreads
-// per pass (2048 points: 4 passes).  tw[t] = exp(-2 pi i t / L), in shared or global memory.
-// Returns the buffer holding the result (a or b).  All threads of the block take part.
+// radix-8 passes, then one radix-4 or radix-2 pass for the remaining factor (fft_pass_radix),
+// one __syncthreads per pass (2048 points: 4 passes).  Input and result are in natural order,
+// the buffers in between swizzled.  tw: the per-pass table of fft_twiddle_table, in shared or
+// global memory.  Returns the buffer holding the result (a or b).  All threads of the block
+// take part.
 template <typename real, bool INV>
 __device__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<real> *__restrict__ tw)
 {
     cplx<real> *src = a, *dst = b;
     for (int Ns = 1; Ns < L;) {
-        const int rest = L / Ns;
-        int R;
-        if (rest % 8 == 0) {
-            stockham_pass<real, INV, 8>(src, dst, L, Ns, tw);
-            R = 8;
-        } else if (rest == 4) {
-            stockham_pass<real, INV, 4>(src, dst, L, Ns, tw);
-            R = 4;
-        } else {
-            stockham_pass<real, INV, 2>(src, dst, L, Ns, tw);
-            R = 2;
-        }
+        const int R = fft_pass_radix(L / Ns);
+        const int m_in = Ns > 1 ? 15 : 0, m_out = Ns * R < L ? 15 : 0;
+        if (R == 8)
+            stockham_pass<real, INV, 8>(src, dst, L, Ns, tw, m_in, m_out);
+        else if (R == 4)
+            stockham_pass<real, INV, 4>(src, dst, L, Ns, tw, m_in, m_out);
+        else
+            stockham_pass<real, INV, 2>(src, dst, L, Ns, tw, m_in, m_out);
         __syncthreads();
         cplx<real> *t = src;
         src = dst;
@@ -431,7 +443,7 @@ __device__ bool block_wait_geq(const int *ctr, int target, int *err, int spins)
 // units a block waits for were taken earlier by blocks that are running and never wait on
 // later units, so the waits end; each is bounded all the same (error word on timeout).
 template <typename real>
-__global__ void __launch_bounds__(256, 5) k_batch_fft(const BatchInst<real> *__restrict__ inst,
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 5 : 3) k_batch_fft(const BatchInst<real> *__restrict__ inst,
                                                    const FftUnit *__restrict__ units, int n_units, int n_inst,
                                                    int nrhs, int L_max, int *counters, int *err, int spins)
 {
@@ -915,6 +927,25 @@ cudaError_t launch_build_mul(const double2 *bhat, int n, const double *c_tab, re
     k_build_mul<real><<<grid, 128, 0, st>>>(bhat, n, c_tab, mul);
     return cudaGetLastError();
 }
+
+template <typename real> void fft_twiddle_table(int L, real *re_im)
+{
+    re_im[2 * (L - 1)] = real(1);
+    re_im[2 * (L - 1) + 1] = real(0);
+    for (int Ns = 1; Ns < L;) {
+        const int R = fft_pass_radix(L / Ns);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                const double ang = 2.0 * kPi * (double)(r * k) / (double)(Ns * R);
+                const int t = Ns - 1 + (r - 1) * Ns + k;
+                re_im[2 * t] = (real)std::cos(ang);
+                re_im[2 * t + 1] = (real)(-std::sin(ang));
+            }
+        Ns *= R;
+    }
+}
+template void fft_twiddle_table<float>(int, float *);
+template void fft_twiddle_table<double>(int, double *);
 
 template cudaError_t launch_fft_rows_fwd<float>(const float *, int, int, int, int, float2 *, int, const float2 *,
                                                 cudaStream_t);

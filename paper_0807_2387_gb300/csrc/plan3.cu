@@ -144,11 +144,7 @@ bool near_coefficients3(double eps, int p, double *beta)
 template <typename real> fs_status twiddles3(fs3_plan *pl, int L, void **out)
 {
     std::vector<real> h(2 * (size_t)L);
-    for (int t = 0; t < L; ++t) {
-        const double ang = 2.0 * kPi * (double)t / (double)L;
-        h[2 * t] = (real)std::cos(ang);
-        h[2 * t + 1] = (real)(-std::sin(ang));
-    }
+    fft_twiddle_table<real>(L, h.data());
     real *d = nullptr;
     FS_TRY(pl->alloc(&d, h.size()));
     FS_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice));
