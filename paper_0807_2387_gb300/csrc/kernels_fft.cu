@@ -23,6 +23,7 @@
 // buffers between two passes are stored with an XOR swizzle of the index so that
 // the strided writes of the early passes hit distinct banks.
 #include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -94,19 +95,25 @@ __device__ __forceinline__ int swz(int i, int m) { return i ^ ((i >> 4) & m); }
 // element r by w^(r k) with w = exp(-+2 pi i / (Ns R)) (k = j mod Ns), transforms in
 // registers and writes dst[(j - k) R + k + r Ns].  The pass's twiddles are tw[Ns - 1 +
 // (r - 1) Ns + k], consecutive in k, so that a warp reads them without bank conflicts.
-template <typename real, bool INV, int R>
-__device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> *dst, int L, int Ns,
-                                              const cplx<real> *__restrict__ tw, int m_in, int m_out)
+// LC, NsC and NT, when nonzero, fix L, Ns and the thread count at compile time (the index
+// arithmetic then folds to constants); zero takes the run-time L, Ns and blockDim.x.
+template <typename real, bool INV, int R, int LC = 0, int NsC = 0, int NT = 0>
+__device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> *dst, int L_rt, int Ns_rt,
+                                              const cplx<real> *__restrict__ tw)
 {
     using C = cplx<real>;
+    const int L = LC ? LC : L_rt;
+    const int Ns = NsC ? NsC : Ns_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
+    const int m_in = Ns > 1 ? 15 : 0, m_out = Ns * R < L ? 15 : 0;
     const int nb = L / R;
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    for (int j = threadIdx.x; j < nb; j += nt) {
         const int k = j & (Ns - 1);
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r)
             v[r] = src[swz(j + r * nb, m_in)];
-        if (k) {
+        if (Ns > 1 && k) {
             const C *twk = tw + (Ns - 1) + k;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -132,32 +139,49 @@ __device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> 
     }
 }
 
+// The passes of a line of compile-time length L from Ns points combined on.
+template <typename real, bool INV, int L, int NT, int Ns>
+__device__ __forceinline__ cplx<real> *fft_passes(cplx<real> *src, cplx<real> *dst, const cplx<real> *__restrict__ tw)
+{
+    if constexpr (Ns >= L) {
+        return src;
+    } else {
+        constexpr int R = fft_pass_radix(L / Ns);
+        stockham_pass<real, INV, R, L, Ns, NT>(src, dst, L, Ns, tw);
+        __syncthreads();
+        return fft_passes<real, INV, L, NT, Ns * R>(dst, src, tw);
+    }
+}
+
 // In-place (via ping-pong) FFT of one line of length L (a power of two) held in shared memory:
 // radix-8 passes, then one radix-4 or radix-2 pass for the remaining factor (fft_pass_radix),
 // one __syncthreads per pass (2048 points: 4 passes).  Input and result are in natural order,
 // the buffers in between swizzled.  tw: the per-pass table of fft_twiddle_table, in shared or
 // global memory.  Returns the buffer holding the result (a or b).  All threads of the block
-// take part.
-template <typename real, bool INV>
-__device__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<real> *__restrict__ tw)
+// take part.  LC > 0: L = LC known at compile time, with NT threads (0: blockDim.x).
+template <typename real, bool INV, int LC = 0, int NT = 0>
+__device__ __forceinline__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<real> *__restrict__ tw)
 {
-    cplx<real> *src = a, *dst = b;
-    for (int Ns = 1; Ns < L;) {
-        const int R = fft_pass_radix(L / Ns);
-        const int m_in = Ns > 1 ? 15 : 0, m_out = Ns * R < L ? 15 : 0;
-        if (R == 8)
-            stockham_pass<real, INV, 8>(src, dst, L, Ns, tw, m_in, m_out);
-        else if (R == 4)
-            stockham_pass<real, INV, 4>(src, dst, L, Ns, tw, m_in, m_out);
-        else
-            stockham_pass<real, INV, 2>(src, dst, L, Ns, tw, m_in, m_out);
-        __syncthreads();
-        cplx<real> *t = src;
-        src = dst;
-        dst = t;
-        Ns *= R;
+    if constexpr (LC > 0) {
+        return fft_passes<real, INV, LC, NT, 1>(a, b, tw);
+    } else {
+        cplx<real> *src = a, *dst = b;
+        for (int Ns = 1; Ns < L;) {
+            const int R = fft_pass_radix(L / Ns);
+            if (R == 8)
+                stockham_pass<real, INV, 8>(src, dst, L, Ns, tw);
+            else if (R == 4)
+                stockham_pass<real, INV, 4>(src, dst, L, Ns, tw);
+            else
+                stockham_pass<real, INV, 2>(src, dst, L, Ns, tw);
+            __syncthreads();
+            cplx<real> *t = src;
+            src = dst;
+            dst = t;
+            Ns *= R;
+        }
+        return src;
     }
-    return src;
 }
 
 // Loads of data that other blocks of the same launch wrote (the batched transform) go
@@ -172,11 +196,13 @@ template <bool CG, typename T> __device__ __forceinline__ T load(const T *p)
 
 // Two real rows (2 rp, 2 rp + 1) of the window -> half spectra, bins 0..n_half, written to
 // spec[l1 * ld + r].  a, b: 2 L complex values of shared memory.
-template <typename real>
-__device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ grid, int pitch, int n_a, int L,
+template <typename real, int LC = 0, int NT = 0>
+__device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ grid, int pitch, int n_a, int L_rt,
                                               int n_half, cplx<real> *__restrict__ spec, int ld,
                                               const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
 {
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
     const int r = 2 * rp;
     const bool has2 = r + 1 < n_a;
     if constexpr (sizeof(real) == 4) {
@@ -186,7 +212,7 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
         const float4 *r1 = reinterpret_cast<const float4 *>(grid + (int64_t)(has2 ? r + 1 : r) * pitch);
         const int nv = n_a / 4;
 #pragma unroll 4
-        for (int v = threadIdx.x; v < L / 4; v += blockDim.x) {
+        for (int v = threadIdx.x; v < L / 4; v += nt) {
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
             if (v < nv) {
                 x = r0[v];
@@ -198,7 +224,7 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
             dst[1] = make_float4(x.z, y.z, x.w, y.w);
         }
     } else {
-        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        for (int c = threadIdx.x; c < L; c += nt) {
             cplx<real> z;
             z.x = c < n_a ? grid[(int64_t)r * pitch + c] : real(0);
             z.y = (c < n_a && has2) ? grid[(int64_t)(r + 1) * pitch + c] : real(0);
@@ -206,8 +232,8 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
         }
     }
     __syncthreads();
-    const cplx<real> *Z = fft_line<real, false>(a, b, L, tw);
-    for (int k = threadIdx.x; k <= n_half; k += blockDim.x) {
+    const cplx<real> *Z = fft_line<real, false, LC, NT>(a, b, L, tw);
+    for (int k = threadIdx.x; k <= n_half; k += nt) {
         const cplx<real> zk = Z[k];
         const cplx<real> zc = Z[(L - k) & (L - 1)];
         cplx<real> X, Y;
@@ -231,20 +257,22 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
 }
 
 // Column l1: forward FFT over rows, multiply, inverse FFT, keep the window rows.
-template <typename real, bool CG>
-__device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
+template <typename real, bool CG, int LC = 0, int NT = 0>
+__device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec, int ld, int n_a, int L_rt, int n,
                                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw,
                                           cplx<real> *a, cplx<real> *b)
 {
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
     cplx<real> *col = spec + (int64_t)l1 * ld;
     if constexpr (sizeof(real) == 4) {
         // two complex values per 16-byte load (ld and n_a are multiples of 4)
         const float4 *c4 = reinterpret_cast<const float4 *>(col);
 #pragma unroll 4
-        for (int v = threadIdx.x; v < L / 2; v += blockDim.x)
+        for (int v = threadIdx.x; v < L / 2; v += nt)
             reinterpret_cast<float4 *>(a)[v] = 2 * v < n_a ? load<CG>(c4 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
     } else {
-        for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        for (int r = threadIdx.x; r < L; r += nt) {
             cplx<real> v;
             if (r < n_a) {
                 v = load<CG>(col + r);
@@ -256,11 +284,11 @@ __device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec,
         }
     }
     __syncthreads();
-    cplx<real> *F = fft_line<real, false>(a, b, L, tw);
+    cplx<real> *F = fft_line<real, false, LC, NT>(a, b, L, tw);
     cplx<real> *other = (F == a) ? b : a;
     const real *mrow = mul + (int64_t)l1 * (n + 1);
     const int h = n / 2;
-    for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x) {
+    for (int k2 = threadIdx.x; k2 < L; k2 += nt) {
         const int l2 = k2 < L / 2 ? k2 : k2 - L;
         cplx<real> v = F[k2];
         if (l2 >= -h && l2 <= h) {
@@ -274,28 +302,30 @@ __device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec,
         F[k2] = v;
     }
     __syncthreads();
-    const cplx<real> *G = fft_line<real, true>(F, other, L, tw);
+    const cplx<real> *G = fft_line<real, true, LC, NT>(F, other, L, tw);
     if constexpr (sizeof(real) == 4) {
-        for (int v = threadIdx.x; v < n_a / 2; v += blockDim.x)
+        for (int v = threadIdx.x; v < n_a / 2; v += nt)
             reinterpret_cast<float4 *>(col)[v] = reinterpret_cast<const float4 *>(G)[v];
     } else {
-        for (int r = threadIdx.x; r < n_a; r += blockDim.x)
+        for (int r = threadIdx.x; r < n_a; r += nt)
             col[r] = G[r];
     }
 }
 
 // Hermitian-extended inverse of two rows (2 rp, 2 rp + 1): real outputs on the window columns.
-template <typename real, bool CG>
-__device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restrict__ spec, int ld, int n_a, int L,
+template <typename real, bool CG, int LC = 0, int NT = 0>
+__device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restrict__ spec, int ld, int n_a, int L_rt,
                                               int n_half, real *__restrict__ grid, int pitch,
                                               const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
 {
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
     const int r = 2 * rp;
     const bool has2 = r + 1 < n_a;
     if constexpr (sizeof(real) == 4) {
         // the two rows' bins are adjacent: one 16-byte load per column, several in flight
 #pragma unroll 4
-        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        for (int c = threadIdx.x; c < L; c += nt) {
             float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
             const bool lower = c <= n_half, upper = c >= L - n_half;
             if (lower || upper) {
@@ -320,11 +350,11 @@ __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restri
             a[c] = z;
         }
         __syncthreads();
-        const cplx<real> *Z = fft_line<real, true>(a, b, L, tw);
+        const cplx<real> *Z = fft_line<real, true, LC, NT>(a, b, L, tw);
         // four columns of both rows per step: 16-byte stores (n_a and the pitch are multiples of 4)
         float4 *r0 = reinterpret_cast<float4 *>(grid + (int64_t)r * pitch);
         float4 *r1 = reinterpret_cast<float4 *>(grid + (int64_t)(r + 1) * pitch);
-        for (int v = threadIdx.x; v < n_a / 4; v += blockDim.x) {
+        for (int v = threadIdx.x; v < n_a / 4; v += nt) {
             const float4 p = reinterpret_cast<const float4 *>(Z)[2 * v];       // Z[4v], Z[4v + 1]
             const float4 q = reinterpret_cast<const float4 *>(Z)[2 * v + 1];   // Z[4v + 2], Z[4v + 3]
             r0[v] = make_float4(p.x, p.z, q.x, q.z);
@@ -332,7 +362,7 @@ __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restri
                 r1[v] = make_float4(p.y, p.w, q.y, q.w);
         }
     } else {
-        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        for (int c = threadIdx.x; c < L; c += nt) {
             cplx<real> X, Y;
             X.x = X.y = Y.x = Y.y = real(0);
             if (c <= n_half) {
@@ -357,8 +387,8 @@ __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restri
             a[c] = z;
         }
         __syncthreads();
-        const cplx<real> *Z = fft_line<real, true>(a, b, L, tw);
-        for (int c = threadIdx.x; c < n_a; c += blockDim.x) {
+        const cplx<real> *Z = fft_line<real, true, LC, NT>(a, b, L, tw);
+        for (int c = threadIdx.x; c < n_a; c += nt) {
             grid[(int64_t)r * pitch + c] = Z[c].x;
             if (has2)
                 grid[(int64_t)(r + 1) * pitch + c] = Z[c].y;
@@ -369,42 +399,55 @@ __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restri
 // Copy the twiddle table into shared memory (the caller's next __syncthreads publishes it):
 // every pass reads it at scattered indices, which from global memory stalled each pass on
 // the load latency.
-template <typename real>
-__device__ __forceinline__ cplx<real> *stage_twiddles(cplx<real> *dst, const cplx<real> *__restrict__ tw, int L)
+template <typename real, int LC = 0, int NT = 0>
+__device__ __forceinline__ cplx<real> *stage_twiddles(cplx<real> *dst, const cplx<real> *__restrict__ tw, int L_rt)
 {
-    for (int t = threadIdx.x; t < L; t += blockDim.x)
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
+#pragma unroll 8
+    for (int t = threadIdx.x; t < L; t += nt)
         dst[t] = tw[t];
     return dst;
 }
 
-template <typename real>
-__global__ void k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a, int L, int n_half,
-                               cplx<real> *__restrict__ spec, int ld, const cplx<real> *__restrict__ tw)
+// Threads of the 2D transform kernels for a line of L points: a quarter of L, 32 to 256.
+__host__ __device__ constexpr int fft_threads(int L) { return L / 4 > 256 ? 256 : (L / 4 < 32 ? 32 : L / 4); }
+
+// The three 2D kernels.  LC > 0 fixes the line length at compile time (one instance per
+// length the plans use, 256 .. 4096 points), LC = 0 takes it at run time.
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft_rows_fwd(const real *__restrict__ grid, int pitch, int n_a, int L,
+                                                      int n_half, cplx<real> *__restrict__ spec, int ld,
+                                                      const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cplx<real> *s_tw = stage_twiddles<real>(a + 2 * L, tw, L);   // published by the unit's first barrier
-    rows_fwd_unit<real>(blockIdx.x, grid, pitch, n_a, L, n_half, spec, ld, s_tw, a, a + L);
+    cplx<real> *s_tw = stage_twiddles<real, LC, NT>(a + 2 * L, tw, L);   // published by the unit's first barrier
+    rows_fwd_unit<real, LC, NT>(blockIdx.x, grid, pitch, n_a, L, n_half, spec, ld, s_tw, a, a + L);
 }
 
-template <typename real>
-__global__ void k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
-                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw)
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft_cols(cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n,
+                                                  const real *__restrict__ mul, const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cplx<real> *s_tw = stage_twiddles<real>(a + 2 * L, tw, L);
-    cols_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n, mul, s_tw, a, a + L);
+    cplx<real> *s_tw = stage_twiddles<real, LC, NT>(a + 2 * L, tw, L);
+    cols_unit<real, false, LC, NT>(blockIdx.x, spec, ld, n_a, L, n, mul, s_tw, a, a + L);
 }
 
-template <typename real>
-__global__ void k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int n_a, int L, int n_half,
-                               real *__restrict__ grid, int pitch, const cplx<real> *__restrict__ tw)
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft_rows_inv(const cplx<real> *__restrict__ spec, int ld, int n_a, int L,
+                                                      int n_half, real *__restrict__ grid, int pitch,
+                                                      const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
-    cplx<real> *s_tw = stage_twiddles<real>(a + 2 * L, tw, L);
-    rows_inv_unit<real, false>(blockIdx.x, spec, ld, n_a, L, n_half, grid, pitch, s_tw, a, a + L);
+    cplx<real> *s_tw = stage_twiddles<real, LC, NT>(a + 2 * L, tw, L);
+    rows_inv_unit<real, false, LC, NT>(blockIdx.x, spec, ld, n_a, L, n_half, grid, pitch, s_tw, a, a + L);
 }
 
 // Thread 0 waits until *ctr >= target; the wait ends early (failed) when the error word is
@@ -434,6 +477,20 @@ __device__ bool block_wait_geq(const int *ctr, int target, int *err, int spins)
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// One unit of the batched transform (256 threads) on a line of LC points (0: bi.L at run time).
+template <typename real, int LC>
+__device__ __forceinline__ void batch_unit(const FftUnit &fu, const BatchInst<real> &bi, cplx<real> *spec, real *grid,
+                                           cplx<real> *a, cplx<real> *b)
+{
+    const int L = bi.L, n_a = bi.n_a, n = bi.n;
+    if (fu.kind == 0)
+        rows_fwd_unit<real, LC, 256>(fu.index, grid, bi.pitch, n_a, L, n / 2, spec, bi.ld, bi.tw, a, b);
+    else if (fu.kind == 1)
+        cols_unit<real, true, LC, 256>(fu.index, spec, bi.ld, n_a, L, n, bi.mul, bi.tw, a, b);
+    else
+        rows_inv_unit<real, true, LC, 256>(fu.index, spec, bi.ld, n_a, L, n / 2, grid, bi.pitch, bi.tw, a, b);
 }
 
 // Batched transform of all instances and right-hand sides in one persistent launch.  Blocks
@@ -473,12 +530,13 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 5 : 3) k_batch_fft(co
         else if (fu.kind == 2)
             ok = block_wait_geq(cols_done, n / 2 + 1, err, spins);
         if (ok) {
-            if (fu.kind == 0)
-                rows_fwd_unit<real>(fu.index, grid, bi.pitch, n_a, L, n / 2, spec, bi.ld, bi.tw, a, b);
-            else if (fu.kind == 1)
-                cols_unit<real, true>(fu.index, spec, bi.ld, n_a, L, n, bi.mul, bi.tw, a, b);
-            else
-                rows_inv_unit<real, true>(fu.index, spec, bi.ld, n_a, L, n / 2, grid, bi.pitch, bi.tw, a, b);
+            switch (L) {   // the line lengths of the instances' plans, as compile-time constants
+            case 256: batch_unit<real, 256>(fu, bi, spec, grid, a, b); break;
+            case 512: batch_unit<real, 512>(fu, bi, spec, grid, a, b); break;
+            case 1024: batch_unit<real, 1024>(fu, bi, spec, grid, a, b); break;
+            case 2048: batch_unit<real, 2048>(fu, bi, spec, grid, a, b); break;
+            default: batch_unit<real, 0>(fu, bi, spec, grid, a, b); break;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0 && fu.kind < 2) {
@@ -764,13 +822,6 @@ __global__ void k_build_mul(const double2 *__restrict__ bhat, int n, const doubl
     mul[(int64_t)l1 * (n + 1) + i2] = (real)(wgt * b / (c1 * c1 * c2 * c2));
 }
 
-template <typename real> inline int fft_threads(int L)
-{
-    int t = L / 4;
-    if (t > 256) t = 256;
-    if (t < 32) t = 32;
-    return t;
-}
 
 template <typename K> cudaError_t set_smem(K kern, size_t bytes)
 {
@@ -779,17 +830,33 @@ template <typename K> cudaError_t set_smem(K kern, size_t bytes)
 
 }  // namespace
 
+// Calls f with the compile-time line length of L (0 for lengths without an instance of their own).
+template <typename F> cudaError_t with_line_length(int L, F &&f)
+{
+    switch (L) {
+    case 256: return f(std::integral_constant<int, 256>{});
+    case 512: return f(std::integral_constant<int, 512>{});
+    case 1024: return f(std::integral_constant<int, 1024>{});
+    case 2048: return f(std::integral_constant<int, 2048>{});
+    case 4096: return f(std::integral_constant<int, 4096>{});
+    default: return f(std::integral_constant<int, 0>{});
+    }
+}
+
 template <typename real>
 cudaError_t launch_fft_rows_fwd(const real *grid, int pitch, int n_a, int L, int n_half, cplx<real> *spec, int ld,
                                 const cplx<real> *tw, cudaStream_t st)
 {
     const size_t smem = 3 * (size_t)L * sizeof(cplx<real>);   // two line buffers and the twiddles
-    cudaError_t e = set_smem(k_fft_rows_fwd<real>, smem);
-    if (e != cudaSuccess)
-        return e;
-    k_fft_rows_fwd<real><<<(n_a + 1) / 2, fft_threads<real>(L), smem, st>>>(grid, pitch, n_a, L, n_half, spec, ld,
-                                                                            tw);
-    return cudaGetLastError();
+    return with_line_length(L, [&](auto lc) {
+        constexpr int LC = decltype(lc)::value;
+        cudaError_t e = set_smem(k_fft_rows_fwd<real, LC>, smem);
+        if (e != cudaSuccess)
+            return e;
+        k_fft_rows_fwd<real, LC><<<(n_a + 1) / 2, fft_threads(L), smem, st>>>(grid, pitch, n_a, L, n_half, spec, ld,
+                                                                              tw);
+        return cudaGetLastError();
+    });
 }
 
 template <typename real>
@@ -797,11 +864,14 @@ cudaError_t launch_fft_cols(cplx<real> *spec, int ld, int n_a, int L, int n, con
                             cudaStream_t st)
 {
     const size_t smem = 3 * (size_t)L * sizeof(cplx<real>);   // two line buffers and the twiddles
-    cudaError_t e = set_smem(k_fft_cols<real>, smem);
-    if (e != cudaSuccess)
-        return e;
-    k_fft_cols<real><<<n / 2 + 1, fft_threads<real>(L), smem, st>>>(spec, ld, n_a, L, n, mul, tw);
-    return cudaGetLastError();
+    return with_line_length(L, [&](auto lc) {
+        constexpr int LC = decltype(lc)::value;
+        cudaError_t e = set_smem(k_fft_cols<real, LC>, smem);
+        if (e != cudaSuccess)
+            return e;
+        k_fft_cols<real, LC><<<n / 2 + 1, fft_threads(L), smem, st>>>(spec, ld, n_a, L, n, mul, tw);
+        return cudaGetLastError();
+    });
 }
 
 template <typename real>
@@ -809,12 +879,15 @@ cudaError_t launch_fft_rows_inv(const cplx<real> *spec, int ld, int n_a, int L, 
                                 const cplx<real> *tw, cudaStream_t st)
 {
     const size_t smem = 3 * (size_t)L * sizeof(cplx<real>);   // two line buffers and the twiddles
-    cudaError_t e = set_smem(k_fft_rows_inv<real>, smem);
-    if (e != cudaSuccess)
-        return e;
-    k_fft_rows_inv<real><<<(n_a + 1) / 2, fft_threads<real>(L), smem, st>>>(spec, ld, n_a, L, n_half, grid, pitch,
-                                                                            tw);
-    return cudaGetLastError();
+    return with_line_length(L, [&](auto lc) {
+        constexpr int LC = decltype(lc)::value;
+        cudaError_t e = set_smem(k_fft_rows_inv<real, LC>, smem);
+        if (e != cudaSuccess)
+            return e;
+        k_fft_rows_inv<real, LC><<<(n_a + 1) / 2, fft_threads(L), smem, st>>>(spec, ld, n_a, L, n_half, grid, pitch,
+                                                                              tw);
+        return cudaGetLastError();
+    });
 }
 
 template <typename real> cudaError_t batch_fft_blocks(int L_max, int *blocks)
@@ -862,7 +935,7 @@ cudaError_t launch_fft3(real *grid, int n_a, int L, int n, cplx<real> *spec1, cp
         (e = set_smem(k_fft3_z<real>, smem)) != cudaSuccess || (e = set_smem(k_fft3_y_inv<real>, smem)) != cudaSuccess ||
         (e = set_smem(k_fft3_x_inv<real>, smem)) != cudaSuccess)
         return e;
-    const int h = n / 2, thr = fft_threads<real>(L);
+    const int h = n / 2, thr = fft_threads(L);
     k_fft3_x_fwd<real><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(grid, n_a, L, h, spec1, tw);
     k_fft3_y_fwd<real><<<dim3(h + 1, n_a), thr, smem, st>>>(spec1, n_a, L, n, spec2, tw);
     k_fft3_z<real><<<dim3(n + 1, h + 1), thr, smem, st>>>(spec2, n_a, L, n, mul3, tw);
@@ -909,7 +982,7 @@ cudaError_t launch_fft_lines_c64(double2 *data, int lines, int L, const double2 
     cudaError_t e = set_smem(k_fft_lines_c64, smem);
     if (e != cudaSuccess)
         return e;
-    k_fft_lines_c64<<<lines, fft_threads<double>(L), smem, st>>>(data, L, tw);
+    k_fft_lines_c64<<<lines, fft_threads(L), smem, st>>>(data, L, tw);
     return cudaGetLastError();
 }
 
