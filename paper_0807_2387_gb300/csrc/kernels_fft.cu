@@ -139,17 +139,73 @@ __device__ __forceinline__ void stockham_pass(const cplx<real> *src, cplx<real> 
     }
 }
 
-// The passes of a line of compile-time length L from Ns points combined on.
-template <typename real, bool INV, int L, int NT, int Ns>
-__device__ __forceinline__ cplx<real> *fft_passes(cplx<real> *src, cplx<real> *dst, const cplx<real> *__restrict__ tw)
+// A pass of compile-time shape (radix R, length L, Ns points combined, NT threads) whose
+// operands come from ld(e, it, r) (element e, the thread's butterfly it and operand r) and go
+// to st(i, v) (element i): the first pass of a line can read global memory and the last one
+// write it, with no shared-memory sweep before or after the transform.
+template <typename real, bool INV, int R, int L, int Ns, int NT, class Ld, class St>
+__device__ __forceinline__ void pass_io(const cplx<real> *__restrict__ tw, Ld &&ld, St &&st)
 {
-    if constexpr (Ns >= L) {
+    using C = cplx<real>;
+    constexpr int nb = L / R;
+    constexpr int IT = (nb + NT - 1) / NT;   // butterflies per thread
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = threadIdx.x + it * NT;
+        if (IT * NT > nb && j >= nb)
+            break;
+        const int k = j & (Ns - 1);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            v[r] = ld(j + r * nb, it, r);
+        if (Ns > 1 && k) {
+            const C *twk = tw + (Ns - 1) + k;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C t = twk[(r - 1) * Ns];
+                if (INV)
+                    t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
+        }
+        if constexpr (R == 8) {
+            dft8<INV, real>(v);
+        } else if constexpr (R == 4) {
+            dft4<INV>(v[0], v[1], v[2], v[3]);
+        } else {
+            const C t = v[1];
+            v[1] = csub(v[0], t);
+            v[0] = cadd(v[0], t);
+        }
+        const int idx = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            st(idx + r * Ns, v[r]);
+    }
+}
+
+// Ns of the last pass of a length-L line.
+__host__ __device__ constexpr int fft_last_ns(int L)
+{
+    int Ns = 1;
+    while (Ns * fft_pass_radix(L / Ns) < L)
+        Ns *= fft_pass_radix(L / Ns);
+    return Ns;
+}
+
+// The shared-memory passes of a line of compile-time length L from Ns points combined up to
+// NsEnd (L: to the end); returns the buffer holding the result.
+template <typename real, bool INV, int L, int NT, int Ns, int NsEnd>
+__device__ __forceinline__ cplx<real> *fft_mid(cplx<real> *src, cplx<real> *dst, const cplx<real> *__restrict__ tw)
+{
+    if constexpr (Ns >= NsEnd) {
         return src;
     } else {
         constexpr int R = fft_pass_radix(L / Ns);
         stockham_pass<real, INV, R, L, Ns, NT>(src, dst, L, Ns, tw);
         __syncthreads();
-        return fft_passes<real, INV, L, NT, Ns * R>(dst, src, tw);
+        return fft_mid<real, INV, L, NT, Ns * R, NsEnd>(dst, src, tw);
     }
 }
 
@@ -163,7 +219,7 @@ template <typename real, bool INV, int LC = 0, int NT = 0>
 __device__ __forceinline__ cplx<real> *fft_line(cplx<real> *a, cplx<real> *b, int L, const cplx<real> *__restrict__ tw)
 {
     if constexpr (LC > 0) {
-        return fft_passes<real, INV, LC, NT, 1>(a, b, tw);
+        return fft_mid<real, INV, LC, NT, 1, LC>(a, b, tw);
     } else {
         cplx<real> *src = a, *dst = b;
         for (int Ns = 1; Ns < L;) {
@@ -194,13 +250,189 @@ template <bool CG, typename T> __device__ __forceinline__ T load(const T *p)
         return *p;
 }
 
+// ---- Units with the line length L known at compile time (NT threads): the first pass of a
+// transform reads its operands from global memory and the last pass of an inverse writes its
+// results there, and the spectral multiply rides on the first inverse pass; against the
+// run-time units below each line skips one to two shared-memory sweeps and barriers per
+// transform.  The twiddles staged by the caller are first read in the second pass, after the
+// barrier that ends the first.
+
+template <typename real, int L, int NT>
+__device__ __forceinline__ void rows_fwd_fused(int rp, const real *__restrict__ grid, int pitch, int n_a, int n_half,
+                                               cplx<real> *__restrict__ spec, int ld,
+                                               const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
+{
+    using C = cplx<real>;
+    constexpr int R0 = fft_pass_radix(L);
+    const int r = 2 * rp;
+    const bool has2 = r + 1 < n_a;
+    const real *x0 = grid + (int64_t)r * pitch;
+    const real *x1 = grid + (int64_t)(has2 ? r + 1 : r) * pitch;
+    pass_io<real, false, R0, L, 1, NT>(
+        tw,
+        [&](int c, int, int) {
+            C z;
+            z.x = c < n_a ? x0[c] : real(0);
+            z.y = (c < n_a && has2) ? x1[c] : real(0);
+            return z;
+        },
+        [&](int i, const C &v) { b[swz(i, 15)] = v; });
+    __syncthreads();
+    const C *Z = fft_mid<real, false, L, NT, R0, L>(b, a, tw);
+    for (int k = threadIdx.x; k <= n_half; k += NT) {
+        const C zk = Z[k];
+        const C zc = Z[(L - k) & (L - 1)];
+        C X, Y;
+        // X = (Z_k + conj Z_{-k}) / 2,  Y = (Z_k - conj Z_{-k}) / (2i)
+        X.x = real(0.5) * (zk.x + zc.x);
+        X.y = real(0.5) * (zk.y - zc.y);
+        Y.x = real(0.5) * (zk.y + zc.y);
+        Y.y = real(-0.5) * (zk.x - zc.x);
+        if constexpr (sizeof(real) == 4) {
+            // the two rows' bins are adjacent (ld and r even): one 16-byte store
+            if (has2)
+                *reinterpret_cast<float4 *>(spec + (int64_t)k * ld + r) = make_float4(X.x, X.y, Y.x, Y.y);
+            else
+                spec[(int64_t)k * ld + r] = X;
+        } else {
+            spec[(int64_t)k * ld + r] = X;
+            if (has2)
+                spec[(int64_t)k * ld + r + 1] = Y;
+        }
+    }
+}
+
+template <typename real, bool CG, int L, int NT>
+__device__ __forceinline__ void cols_fused(int l1, cplx<real> *__restrict__ spec, int ld, int n_a, int n,
+                                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw,
+                                           cplx<real> *a, cplx<real> *b)
+{
+    using C = cplx<real>;
+    constexpr int R0 = fft_pass_radix(L), NB0 = L / R0, IT0 = (NB0 + NT - 1) / NT;
+    constexpr int NSL = fft_last_ns(L), RL = L / NSL;
+    cplx<real> *col = spec + (int64_t)l1 * ld;
+    // the multipliers of the operands of this thread's first inverse pass, fetched now so that
+    // their latency hides behind the forward transform
+    const real *mrow = mul + (int64_t)l1 * (n + 1);
+    const int h = n / 2;
+    real mp[IT0][R0];
+#pragma unroll
+    for (int it = 0; it < IT0; ++it) {
+        const int j = threadIdx.x + it * NT;
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            const int e = j + q * NB0;
+            const int l2 = e < L / 2 ? e : e - L;
+            mp[it][q] = (j < NB0 && l2 >= -h && l2 <= h) ? mrow[l2 + h] : real(0);
+        }
+    }
+    pass_io<real, false, R0, L, 1, NT>(
+        tw,
+        [&](int c, int, int) {
+            C z;
+            if (c < n_a) {
+                z = load<CG>(col + c);
+            } else {
+                z.x = real(0);
+                z.y = real(0);
+            }
+            return z;
+        },
+        [&](int i, const C &v) { b[swz(i, 15)] = v; });
+    __syncthreads();
+    C *F = fft_mid<real, false, L, NT, R0, L>(b, a, tw);
+    C *other = (F == a) ? b : a;
+    pass_io<real, true, R0, L, 1, NT>(
+        tw,
+        [&](int e, int it, int q) {
+            C z = F[e];
+            z.x *= mp[it][q];
+            z.y *= mp[it][q];
+            return z;
+        },
+        [&](int i, const C &v) { other[swz(i, 15)] = v; });
+    __syncthreads();
+    const C *Y = fft_mid<real, true, L, NT, R0, NSL>(other, F, tw);
+    pass_io<real, true, RL, L, NSL, NT>(
+        tw, [&](int e, int, int) { return Y[swz(e, 15)]; },
+        [&](int i, const C &v) {
+            if (i < n_a)
+                col[i] = v;
+        });
+}
+
+template <typename real, bool CG, int L, int NT>
+__device__ __forceinline__ void rows_inv_fused(int rp, const cplx<real> *__restrict__ spec, int ld, int n_a,
+                                               int n_half, real *__restrict__ grid, int pitch,
+                                               const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
+{
+    using C = cplx<real>;
+    constexpr int R0 = fft_pass_radix(L);
+    constexpr int NSL = fft_last_ns(L), RL = L / NSL;
+    const int r = 2 * rp;
+    const bool has2 = r + 1 < n_a;
+    pass_io<real, true, R0, L, 1, NT>(
+        tw,
+        [&](int c, int, int) {
+            // X + i Y from the half spectra of the two rows (Hermitian extension above n_half)
+            C X, Y;
+            X.x = X.y = Y.x = Y.y = real(0);
+            const bool lower = c <= n_half, upper = c >= L - n_half;
+            if (lower || upper) {
+                const C *at = spec + (int64_t)(lower ? c : L - c) * ld + r;
+                if constexpr (sizeof(real) == 4) {
+                    if (has2) {
+                        const float4 t = load<CG>(reinterpret_cast<const float4 *>(at));
+                        X = make_float2(t.x, t.y);
+                        Y = make_float2(t.z, t.w);
+                    } else {
+                        X = load<CG>(at);
+                    }
+                } else {
+                    X = load<CG>(at);
+                    if (has2)
+                        Y = load<CG>(at + 1);
+                }
+                if (!lower) {
+                    X.y = -X.y;
+                    Y.y = -Y.y;
+                } else if (c == 0) {
+                    X.y = real(0);
+                    Y.y = real(0);
+                }
+            }
+            C z;
+            z.x = X.x - Y.y;
+            z.y = X.y + Y.x;
+            return z;
+        },
+        [&](int i, const C &v) { b[swz(i, 15)] = v; });
+    __syncthreads();
+    const C *Y = fft_mid<real, true, L, NT, R0, NSL>(b, a, tw);
+    real *g0 = grid + (int64_t)r * pitch;
+    real *g1 = grid + (int64_t)(r + 1) * pitch;
+    pass_io<real, true, RL, L, NSL, NT>(
+        tw, [&](int e, int, int) { return Y[swz(e, 15)]; },
+        [&](int i, const C &v) {
+            if (i < n_a) {
+                g0[i] = v.x;
+                if (has2)
+                    g1[i] = v.y;
+            }
+        });
+}
+
 // Two real rows (2 rp, 2 rp + 1) of the window -> half spectra, bins 0..n_half, written to
 // spec[l1 * ld + r].  a, b: 2 L complex values of shared memory.
-template <typename real, int LC = 0, int NT = 0>
+template <typename real, int LC = 0, int NT = 0, bool FUSED = true>
 __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ grid, int pitch, int n_a, int L_rt,
                                               int n_half, cplx<real> *__restrict__ spec, int ld,
                                               const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
 {
+    if constexpr (LC > 0 && FUSED) {
+        rows_fwd_fused<real, LC, NT>(rp, grid, pitch, n_a, n_half, spec, ld, tw, a, b);
+        return;
+    }
     const int L = LC ? LC : L_rt;
     const int nt = NT ? NT : (int)blockDim.x;
     const int r = 2 * rp;
@@ -257,11 +489,15 @@ __device__ __forceinline__ void rows_fwd_unit(int rp, const real *__restrict__ g
 }
 
 // Column l1: forward FFT over rows, multiply, inverse FFT, keep the window rows.
-template <typename real, bool CG, int LC = 0, int NT = 0>
+template <typename real, bool CG, int LC = 0, int NT = 0, bool FUSED = true>
 __device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec, int ld, int n_a, int L_rt, int n,
                                           const real *__restrict__ mul, const cplx<real> *__restrict__ tw,
                                           cplx<real> *a, cplx<real> *b)
 {
+    if constexpr (LC > 0 && FUSED) {
+        cols_fused<real, CG, LC, NT>(l1, spec, ld, n_a, n, mul, tw, a, b);
+        return;
+    }
     const int L = LC ? LC : L_rt;
     const int nt = NT ? NT : (int)blockDim.x;
     cplx<real> *col = spec + (int64_t)l1 * ld;
@@ -313,11 +549,15 @@ __device__ __forceinline__ void cols_unit(int l1, cplx<real> *__restrict__ spec,
 }
 
 // Hermitian-extended inverse of two rows (2 rp, 2 rp + 1): real outputs on the window columns.
-template <typename real, bool CG, int LC = 0, int NT = 0>
+template <typename real, bool CG, int LC = 0, int NT = 0, bool FUSED = true>
 __device__ __forceinline__ void rows_inv_unit(int rp, const cplx<real> *__restrict__ spec, int ld, int n_a, int L_rt,
                                               int n_half, real *__restrict__ grid, int pitch,
                                               const cplx<real> *__restrict__ tw, cplx<real> *a, cplx<real> *b)
 {
+    if constexpr (LC > 0 && FUSED) {
+        rows_inv_fused<real, CG, LC, NT>(rp, spec, ld, n_a, n_half, grid, pitch, tw, a, b);
+        return;
+    }
     const int L = LC ? LC : L_rt;
     const int nt = NT ? NT : (int)blockDim.x;
     const int r = 2 * rp;
@@ -480,17 +720,19 @@ __device__ bool block_wait_geq(const int *ctr, int target, int *err, int spins)
 }
 
 // One unit of the batched transform (256 threads) on a line of LC points (0: bi.L at run time).
+// The shared-memory sweeps stay (FUSED = false): the fused units' extra registers made this
+// kernel, which holds every line length, spill at five blocks per SM, for no measured gain.
 template <typename real, int LC>
 __device__ __forceinline__ void batch_unit(const FftUnit &fu, const BatchInst<real> &bi, cplx<real> *spec, real *grid,
                                            cplx<real> *a, cplx<real> *b)
 {
     const int L = bi.L, n_a = bi.n_a, n = bi.n;
     if (fu.kind == 0)
-        rows_fwd_unit<real, LC, 256>(fu.index, grid, bi.pitch, n_a, L, n / 2, spec, bi.ld, bi.tw, a, b);
+        rows_fwd_unit<real, LC, 256, false>(fu.index, grid, bi.pitch, n_a, L, n / 2, spec, bi.ld, bi.tw, a, b);
     else if (fu.kind == 1)
-        cols_unit<real, true, LC, 256>(fu.index, spec, bi.ld, n_a, L, n, bi.mul, bi.tw, a, b);
+        cols_unit<real, true, LC, 256, false>(fu.index, spec, bi.ld, n_a, L, n, bi.mul, bi.tw, a, b);
     else
-        rows_inv_unit<real, true, LC, 256>(fu.index, spec, bi.ld, n_a, L, n / 2, grid, bi.pitch, bi.tw, a, b);
+        rows_inv_unit<real, true, LC, 256, false>(fu.index, spec, bi.ld, n_a, L, n / 2, grid, bi.pitch, bi.tw, a, b);
 }
 
 // Batched transform of all instances and right-hand sides in one persistent launch.  Blocks
