@@ -166,6 +166,9 @@ NEAR_TRAFFIC = {
     # scaled by the point count to the 2^20-point launch: the kernel reads per-point data once
     "8be3b9f666b9503ab045cbff3e3a1e51f1dd16de3fa2435e939cb4183c6c3688": (
         2 * 21484032, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), differences in units of eps_I
+    "84ff42b81a248c29efae16affc7c55ecd8690f5eb8264ed13e62181d2b5db201": (
+        2 * 21455616, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 
@@ -190,15 +193,18 @@ def near_traffic():
 def on_chip_bound_ms(info, stage, sms, fp32_lane_ops_per_s, sm_mhz):
     """Lower bound of a grid stage that is not HBM-bound, from its on-chip work (None if not modelled).
 
-    spread: per source, ceil((2m)^2 / 32) tap iterations of 4 shared-memory accesses (value and
-    compensation, read and write) and 2 weight shuffles, at one warp-wide MIO operation per SM
-    and cycle (sms SMs at the SM clock sm_mhz sampled during the run).  interp: per target,
+    spread: per source, the shared-memory wavefronts of the row-group lanes (G groups of 2m lanes,
+    G the largest divisor of 2m with 2m G <= 32; each lane reads and writes the value and the
+    compensation of 2m/G taps, ceil(G 2m 4 / 128) wavefronts per warp-wide access) plus 3 for the
+    window weights (one store, the row and column reads), at one wavefront per SM and cycle (sms
+    SMs at the SM clock sm_mhz sampled during the run).  interp: per target,
     (2m)^2 taps x (1 load + 3 FMA) + 4 (2m) window polynomials of degree 12, at the measured
     FP32 fma rate (lane operations per second over the whole GPU).
     """
     m2 = 2 * info["m"]
     if stage == "spread":
-        per_src = -(-m2 * m2 // 32) * (4 + 2)
+        groups = max(d for d in range(1, m2 + 1) if m2 % d == 0 and d * m2 <= 32)
+        per_src = 4 * (m2 // groups) * -(-groups * m2 * 4 // 128) + 3
         return 1e3 * info["n_src"] * per_src / (sms * sm_mhz * 1e6)
     if stage == "interp":
         per_tgt = m2 * m2 * 4 + 4 * m2 * 12
