@@ -198,8 +198,9 @@ def on_chip_bound_ms(info, stage, sms, fp32_lane_ops_per_s, sm_mhz):
     compensation of 2m/G taps, ceil(G 2m 4 / 128) wavefronts per warp-wide access) plus 3 for the
     window weights (one store, the row and column reads), at one wavefront per SM and cycle (sms
     SMs at the SM clock sm_mhz sampled during the run).  interp: per target,
-    (2m)^2 taps x (1 load + 3 FMA) + 4 (2m) window polynomials of degree 12, at the measured
-    FP32 fma rate (lane operations per second over the whole GPU).
+    (2m)^2 taps x (1 load + 3 FMA) + the window polynomials of degree 12, value and slope, per
+    symmetric pair of taps as even and odd parts in t^2 (2 dimensions x m pairs x 26 FMA), at
+    the measured FP32 fma rate (lane operations per second over the whole GPU).
     """
     m2 = 2 * info["m"]
     if stage == "spread":
@@ -207,7 +208,7 @@ def on_chip_bound_ms(info, stage, sms, fp32_lane_ops_per_s, sm_mhz):
         per_src = 4 * (m2 // groups) * -(-groups * m2 * 4 // 128) + 3
         return 1e3 * info["n_src"] * per_src / (sms * sm_mhz * 1e6)
     if stage == "interp":
-        per_tgt = m2 * m2 * 4 + 4 * m2 * 12
+        per_tgt = m2 * m2 * 4 + 2 * (m2 // 2) * 26
         return 1e3 * info["n_tgt"] * per_tgt / fp32_lane_ops_per_s
     return None
 

@@ -88,6 +88,13 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---- packed pairs of FP32 values (x: the lane's first point, y: its second)
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -97,6 +104,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 min1(float2 w) { return make_float2(fminf(w.x, 1.f), fminf(w.y, 1.f)); }
 __device__ __forceinline__ float2 lg2_2(float2 w) { return make_float2(lg2_approx(w.x), lg2_approx(w.y)); }
 __device__ __forceinline__ float2 rcp_2(float2 w) { return make_float2(rcp_approx(w.x), rcp_approx(w.y)); }
+__device__ __forceinline__ float2 ex2_2(float2 w) { return make_float2(ex2_approx(w.x), ex2_approx(w.y)); }
 __device__ __forceinline__ float2 select2(float2 r2, float eps2, float2 v)
 {
     return make_float2(r2.x < eps2 ? v.x : 0.f, r2.y < eps2 ? v.y : 0.f);
@@ -431,9 +439,16 @@ __device__ __forceinline__ void near_src_pair(const NearParams<float> &np, float
     if constexpr (P >= 2)
         w = min1(w);                                      // f(1) = 0 and (w - 1)^(p-1) = 0: masked
     const float2 val = near_f2<P>(np, w);
-    float2 coef = rcp_2(w);
-    if constexpr (P >= 2)
-        coef = mul2(ipow2<P - 1>(add2(w, f2(-1.f))), coef);
+    float2 coef;
+    if constexpr (P >= 2) {
+        // |w - 1|^(p-1) / w = 2^((p-1) log2(1 - w) - log2 w) (log2 w shared with val; the sign
+        // (-1)^(p-1) is applied at the store; w = 1 gives 2^-inf = 0)
+        const float2 lw = lg2_2(w);
+        const float2 lo = lg2_2(add2(f2(1.f), make_float2(-w.x, -w.y)));
+        coef = ex2_2(fma2(f2((float)(P - 1)), lo, make_float2(-lw.x, -lw.y)));
+    } else {
+        coef = rcp_2(w);
+    }
     if constexpr (P == 1)
         q2 = select2(r2, np.eps2, q2);
     phi = fma2(q2, val, phi);
@@ -497,9 +512,10 @@ __device__ __forceinline__ void near_src_eval(const float4 *s_hi, const float4 *
             near_src_pair<P>(np, r2, dx, dy, q2, phi, gx, gy);
         }
         if (valid) {
+            const float rc = (P >= 2 && (P - 1) % 2 == 1) ? -rcoef : rcoef;   // near_src_pair's coef is |w - 1|^(p-1) / w
             atomicAdd(phi_s + k, phi.x + phi.y);
-            atomicAdd(grad_s + 2 * (int64_t)k, rcoef * (gx.x + gx.y));
-            atomicAdd(grad_s + 2 * (int64_t)k + 1, rcoef * (gy.x + gy.y));
+            atomicAdd(grad_s + 2 * (int64_t)k, rc * (gx.x + gx.y));
+            atomicAdd(grad_s + 2 * (int64_t)k + 1, rc * (gy.x + gy.y));
             if (CLOSE && cq != 0.f)
                 atomicAdd(coinc + k, cq);
         }
