@@ -169,6 +169,9 @@ NEAR_TRAFFIC = {
     # 21.46 MB per launch on the 2^19-point mixture (same capture), differences in units of eps_I
     "84ff42b81a248c29efae16affc7c55ecd8690f5eb8264ed13e62181d2b5db201": (
         2 * 21455616, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), exp2 form of the coefficient
+    "e656075e0636d17def29386190236016d48a29c2ca46fe0723d94bd36c4ba764": (
+        2 * 21455104, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 

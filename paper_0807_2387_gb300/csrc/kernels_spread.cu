@@ -309,6 +309,33 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_batch_spread(const Spread
 // size n_os |s| that would otherwise dominate the FP32 gradient error.  For
 // m <= 4 the periodisation is flat only to ~1e-7, no better than FP32 rounding,
 // so those widths (and the FP64 path) sum directly.
+// One row of a target's taps: the row sum rs with the column weights w2 and the derivative
+// sum rd with d2 (against the reference column m - 1 when kRef), added to phi and grad with the
+// row's weights wr, dr.  The first coordinate's derivative sum is taken against the row sum of
+// row m - 1, which the caller visits first (rs_ref).
+template <typename real, int M2, bool kRef>
+__device__ __forceinline__ void interp_row(const real *__restrict__ rowp, const real (&w2)[M2], const real (&d2)[M2],
+                                           real wr, real dr, bool ref_row, real &rs_ref, real &phi, real &g1,
+                                           real &g2)
+{
+    constexpr int m = M2 / 2;
+    real gv[M2];
+#pragma unroll
+    for (int b = 0; b < M2; ++b)
+        gv[b] = __ldg(rowp + b);
+    real rs = 0, rd = 0;
+#pragma unroll
+    for (int b = 0; b < M2; ++b) {
+        rs += w2[b] * gv[b];
+        rd += d2[b] * (kRef ? gv[b] - gv[m - 1] : gv[b]);
+    }
+    if (ref_row)
+        rs_ref = rs;
+    phi += wr * rs;
+    g2 += wr * rd;
+    g1 += dr * (kRef ? rs - rs_ref : rs);
+}
+
 template <typename real, int M2>
 __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ base,
                                              const real2_t<real> *__restrict__ frac, const Window<real> &w,
@@ -320,62 +347,53 @@ __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ 
     constexpr bool kRef = sizeof(real) == 4 && m >= 5;
     const int packed = base[k];
     const real2_t<real> f = frac[k];
-    real w1[M2], d1[M2], w2[M2], d2[M2];
+    const int row0 = base1(packed) - m + 1;
+    const int col0 = base2(packed) - m + 1;
+    real phi = 0, g1 = 0, g2 = 0, rs_ref = 0;
+    real w2[M2], d2[M2];
     if constexpr (sizeof(real) == 4) {
         // FP32: per-tap window polynomials in t = frac - 1/2 (coefficients are warp-uniform kernel
         // parameters).  The window is even, so tap M2-1-a at t is tap a at -t: each pair takes
         // the even and odd parts of tap a's polynomials in t^2 once (value p(+-t) = E +- t O,
         // slope of the mirrored tap -p'(-t) = t O' - E'), about half the FMAs of 2 evaluations.
+        // The column weights are held for all rows; the row weights of each symmetric pair of
+        // rows are evaluated just before those two rows (middle pair first, so that row m - 1,
+        // the reference, comes first), which keeps 2 M2 fewer values live across the loop.
         const float t1 = (float)f.x - 0.5f, t2 = (float)f.y - 0.5f;
         const float s1 = t1 * t1, s2 = t2 * t2;
 #pragma unroll
         for (int a = 0; a < m; ++a) {
             float e, o;
-            poly_even_odd<kPolyD>(wp.c[a], s1, e, o);
-            w1[a] = fmaf(t1, o, e);
-            w1[M2 - 1 - a] = fmaf(-t1, o, e);
             poly_even_odd<kPolyD>(wp.c[a], s2, e, o);
             w2[a] = fmaf(t2, o, e);
             w2[M2 - 1 - a] = fmaf(-t2, o, e);
-            poly_even_odd<kPolyD - 1>(wp.d[a], s1, e, o);
-            d1[a] = fmaf(t1, o, e);
-            d1[M2 - 1 - a] = fmaf(t1, o, -e);
             poly_even_odd<kPolyD - 1>(wp.d[a], s2, e, o);
             d2[a] = fmaf(t2, o, e);
             d2[M2 - 1 - a] = fmaf(t2, o, -e);
         }
+#pragma unroll
+        for (int q = 0; q < m; ++q) {
+            const int a = m - 1 - q, a2 = M2 - 1 - a;
+            float e, o, de, dd;
+            poly_even_odd<kPolyD>(wp.c[a], s1, e, o);
+            poly_even_odd<kPolyD - 1>(wp.d[a], s1, de, dd);
+            interp_row<real, M2, kRef>(grid + (int64_t)(row0 + a) * pitch + col0, w2, d2, fmaf(t1, o, e),
+                                       fmaf(t1, dd, de), q == 0, rs_ref, phi, g1, g2);
+            interp_row<real, M2, kRef>(grid + (int64_t)(row0 + a2) * pitch + col0, w2, d2, fmaf(-t1, o, e),
+                                       fmaf(t1, dd, -de), false, rs_ref, phi, g1, g2);
+        }
     } else {
+        real w1[M2], d1[M2];
 #pragma unroll
         for (int a = 0; a < M2; ++a) {
             kb_value_slope<real>(w, f.x, m - 1 - a, w1[a], d1[a]);
             kb_value_slope<real>(w, f.y, m - 1 - a, w2[a], d2[a]);
         }
+#pragma unroll
+        for (int a = 0; a < M2; ++a)
+            interp_row<real, M2, kRef>(grid + (int64_t)(row0 + a) * pitch + col0, w2, d2, w1[a], d1[a], false,
+                                       rs_ref, phi, g1, g2);
     }
-    const int row0 = base1(packed) - m + 1;
-    const int col0 = base2(packed) - m + 1;
-    real rsv[M2];
-    real phi = 0, g2 = 0;
-#pragma unroll
-    for (int a = 0; a < M2; ++a) {
-        const real *rowp = grid + (int64_t)(row0 + a) * pitch + col0;
-        real gv[M2];
-#pragma unroll
-        for (int b = 0; b < M2; ++b)
-            gv[b] = __ldg(rowp + b);
-        real rs = 0, rd = 0;
-#pragma unroll
-        for (int b = 0; b < M2; ++b) {
-            rs += w2[b] * gv[b];
-            rd += d2[b] * (kRef ? gv[b] - gv[m - 1] : gv[b]);
-        }
-        rsv[a] = rs;
-        phi += w1[a] * rs;
-        g2 += w1[a] * rd;
-    }
-    real g1 = 0;
-#pragma unroll
-    for (int a = 0; a < M2; ++a)
-        g1 += d1[a] * (kRef ? rsv[a] - rsv[m - 1] : rsv[a]);
     // acc: the near field was stored first (overlapped with spreading and the transform)
     phi_s[k] = acc ? phi_s[k] + phi : phi;
     grad_s[2 * k] = acc ? grad_s[2 * k] + n_os * g1 : n_os * g1;
