@@ -190,7 +190,8 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
             // instead of a reciprocal and five multiplications; log2 w is shared with val, and
             // the sign (-1)^(p-1) is applied at the store.  w = 1 (masked) gives 2^-inf = 0.
             const float2 lw = lg2_2(w);
-            const float2 lo = lg2_2(add2(f2(1.f), make_float2(-w.x, -w.y)));
+            const float2 om = add2(w, f2(-1.f));   // the value's w - 1: 1 - w = -om, no add of its own
+            const float2 lo = lg2_2(make_float2(-om.x, -om.y));
             coef = ex2_2(fma2(f2((float)(P - 1)), lo, make_float2(-lw.x, -lw.y)));
         } else {
             coef = rcp_2(w);

@@ -444,7 +444,8 @@ __device__ __forceinline__ void near_src_pair(const NearParams<float> &np, float
         // |w - 1|^(p-1) / w = 2^((p-1) log2(1 - w) - log2 w) (log2 w shared with val; the sign
         // (-1)^(p-1) is applied at the store; w = 1 gives 2^-inf = 0)
         const float2 lw = lg2_2(w);
-        const float2 lo = lg2_2(add2(f2(1.f), make_float2(-w.x, -w.y)));
+        const float2 om = add2(w, f2(-1.f));   // the value's w - 1: 1 - w = -om, no add of its own
+        const float2 lo = lg2_2(make_float2(-om.x, -om.y));
         coef = ex2_2(fma2(f2((float)(P - 1)), lo, make_float2(-lw.x, -lw.y)));
     } else {
         coef = rcp_2(w);
