@@ -561,3 +561,21 @@ def test_spread_mode_choice(pkg):
     assert info["spread_direct"] == 0
     phi_d, H_d, _ = gpu_field(pkg, dense, 32, flags=pkg.FS_FLAG_SPREAD_DIRECT)
     assert rel(phi_d, phi_t) <= 1e-6 and rel(H_d, H_t) <= 1e-6, (rel(phi_d, phi_t), rel(H_d, H_t))
+
+
+def test_4096_point_lines_against_direct_sum(pkg):
+    """n = 2048 (oversampled 4096^2) runs the transform's compiled 4096-point lines, which no case
+    the oracle's FP64 NFFT can afford reaches: the FP64 path against the direct sum O1 at the
+    approximation level (an indexing error in a pass would be of order one), and the FP32 path
+    against the FP64 path at the metric's bar."""
+    from oracle import direct as D
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(161, 3000, 2500, n=2048, m=6, eps_I=8 / 2048)
+    phi64, H64, info = gpu_field(pkg, case, 64)
+    assert info["n_os"] == 4096
+    phi_d, H_d = D.direct_sum(case["tgt"], case["src"], case["q"])
+    assert rel_l2(phi64, phi_d) <= 1e-6, rel_l2(phi64, phi_d)
+    assert rel_l2(H64, H_d) <= 1e-4, rel_l2(H64, H_d)
+    phi32, H32, _ = gpu_field(pkg, case, 32)
+    assert rel(phi32, phi64) <= 1e-5, rel(phi32, phi64)
+    assert rel(H32, H64) <= 1e-5, rel(H32, H64)
