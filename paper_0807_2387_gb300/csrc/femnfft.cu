@@ -768,19 +768,32 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
                                           (real *)pl->grid, pl->pitch, (const C *)pl->tw, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[4], st));
+        void *po = phi ? (unsigned char *)phi + (size_t)r * pl->N * osz : nullptr;
+        void *ho = H ? (unsigned char *)H + (size_t)r * pl->N * 2 * osz : nullptr;
         if (pl->overlap) {
             FS_CUDA(cudaStreamWaitEvent(st, pl->ev_join, 0));
             if (rec)
                 FS_CUDA(cudaEventRecord(pl->ev_j, st));
+            // steps (f) and (h) in one pass: the far field added to the near field's sums and
+            // written to the caller's buffers (the output stage's time is in the interpolation's)
+            FS_CUDA(launch_interp_out<real>(pl->N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly,
+                                            (const real *)pl->grid, pl->pitch, (real)pl->n_os,
+                                            (const real *)pl->phi_s, (const real *)pl->grad_s,
+                                            (const real *)pl->coinc, pl->tgt_perm, shift, pl->q_sum + r, pl->s, po, ho,
+                                            dtype == FS_F64, st));
+            if (rec) {
+                FS_CUDA(cudaEventRecord(pl->ev[5], st));
+                FS_CUDA(cudaEventRecord(pl->ev[6], st));
+                FS_CUDA(cudaEventRecord(pl->ev[7], st));
+            }
+            continue;
         }
         FS_CUDA(launch_interp<real>(pl->N, pl->m, pl->tgt_base, pl->tgt_frac, w, pl->wpoly, (const real *)pl->grid, pl->pitch,
-                                    (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, pl->overlap, st));
+                                    (real)pl->n_os, (real *)pl->phi_s, (real *)pl->grad_s, false, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[5], st));
         if constexpr (sizeof(real) == 4) {
-            if (pl->overlap) {
-                // the near field ran on the second stream
-            } else if (pl->src_major) {
+            if (pl->src_major) {
                 FS_CUDA(cudaMemsetAsync(pl->coinc, 0, sizeof(float) * (size_t)std::max<int64_t>(pl->N, 1), st));
                 FS_CUDA(launch_near_src32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
                                           pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
@@ -797,8 +810,6 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
                                   (double *)pl->coinc, st));
         if (rec)
             FS_CUDA(cudaEventRecord(pl->ev[6], st));
-        void *po = phi ? (unsigned char *)phi + (size_t)r * pl->N * osz : nullptr;
-        void *ho = H ? (unsigned char *)H + (size_t)r * pl->N * 2 * osz : nullptr;
         FS_CUDA(launch_unpermute<real>(pl->N, (const real *)pl->phi_s, (const real *)pl->grad_s,
                                        (const real *)pl->coinc, pl->tgt_perm, shift, pl->q_sum + r, pl->s, po, ho,
                                        dtype == FS_F64, st));

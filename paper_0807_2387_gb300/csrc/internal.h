@@ -275,6 +275,15 @@ cudaError_t launch_interp(int64_t N, int m, const int *base, const void *frac, W
                           const WindowPoly &wp, const real *grid, int pitch, real n_os, real *phi_s, real *grad_s,
                           bool acc, cudaStream_t st);
 
+// Interpolation and output in one pass (plans whose near field stored phi_s / grad_s / coinc
+// first): the caller's phi and H at perm[k], as launch_interp with acc followed by launch_unpermute.
+template <typename real>
+cudaError_t launch_interp_out(int64_t N, int m, const int *base, const void *frac, Window<real> w,
+                              const WindowPoly &wp, const real *grid, int pitch, real n_os, const real *phi_s,
+                              const real *grad_s, const real *coinc, const int *perm, double shift,
+                              const double *q_sum, double s, void *phi_out, void *H_out, int out_is_f64,
+                              cudaStream_t st);
+
 template <typename real>
 cudaError_t launch_spread_dip(const SpreadItem *items, int n_items, CellGrid cg, int m, const int *base,
                               const void *frac, const real *cq, const void *dq, Window<real> w, const WindowPoly &wp,

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "output.cuh"
 #include "near_warp.cuh"
 
 namespace fs {
@@ -316,25 +317,8 @@ __device__ __forceinline__ void unpermute_point(int64_t k, const real *__restric
                                                 const int *__restrict__ perm, double shift, double q_sum, double s,
                                                 void *__restrict__ phi_out, void *__restrict__ H_out, int out_is_f64)
 {
-    const int64_t i = perm[k];
-    const double phi = (double)phi_s[k] + shift * (q_sum - (double)coinc[k]);
-    const double hx = -s * (double)grad_s[2 * k];
-    const double hy = -s * (double)grad_s[2 * k + 1];
-    if (out_is_f64) {
-        if (phi_out)
-            ((double *)phi_out)[i] = phi;
-        if (H_out) {
-            ((double *)H_out)[2 * i] = hx;
-            ((double *)H_out)[2 * i + 1] = hy;
-        }
-    } else {
-        if (phi_out)
-            ((float *)phi_out)[i] = (float)phi;
-        if (H_out) {
-            ((float *)H_out)[2 * i] = (float)hx;
-            ((float *)H_out)[2 * i + 1] = (float)hy;
-        }
-    }
+    output_point<real>(k, phi_s[k], grad_s[2 * k], grad_s[2 * k + 1], coinc[k], perm, shift, q_sum, s, phi_out, H_out,
+                       out_is_f64);
 }
 
 template <typename real>

@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "output.cuh"
 
 namespace fs {
 
@@ -336,12 +337,13 @@ __device__ __forceinline__ void interp_row(const real *__restrict__ rowp, const 
     g1 += dr * (kRef ? rs - rs_ref : rs);
 }
 
+// The far-field sums of target k: phi and the two derivative sums in grid units (times n_os for
+// the gradient).
 template <typename real, int M2>
-__device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ base,
-                                             const real2_t<real> *__restrict__ frac, const Window<real> &w,
-                                             const WindowPoly &wp, const real *__restrict__ grid, int pitch, real n_os,
-                                             real *__restrict__ phi_s, real *__restrict__ grad_s,
-                                             bool acc = false)
+__device__ __forceinline__ void interp_sums(int64_t k, const int *__restrict__ base,
+                                            const real2_t<real> *__restrict__ frac, const Window<real> &w,
+                                            const WindowPoly &wp, const real *__restrict__ grid, int pitch, real &phi,
+                                            real &g1, real &g2)
 {
     constexpr int m = M2 / 2;
     constexpr bool kRef = sizeof(real) == 4 && m >= 5;
@@ -349,7 +351,8 @@ __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ 
     const real2_t<real> f = frac[k];
     const int row0 = base1(packed) - m + 1;
     const int col0 = base2(packed) - m + 1;
-    real phi = 0, g1 = 0, g2 = 0, rs_ref = 0;
+    real rs_ref = 0;
+    phi = g1 = g2 = 0;
     real w2[M2], d2[M2];
     if constexpr (sizeof(real) == 4) {
         // FP32: per-tap window polynomials in t = frac - 1/2 (coefficients are warp-uniform kernel
@@ -394,6 +397,17 @@ __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ 
             interp_row<real, M2, kRef>(grid + (int64_t)(row0 + a) * pitch + col0, w2, d2, w1[a], d1[a], false,
                                        rs_ref, phi, g1, g2);
     }
+}
+
+template <typename real, int M2>
+__device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ base,
+                                             const real2_t<real> *__restrict__ frac, const Window<real> &w,
+                                             const WindowPoly &wp, const real *__restrict__ grid, int pitch, real n_os,
+                                             real *__restrict__ phi_s, real *__restrict__ grad_s,
+                                             bool acc = false)
+{
+    real phi, g1, g2;
+    interp_sums<real, M2>(k, base, frac, w, wp, grid, pitch, phi, g1, g2);
     // acc: the near field was stored first (overlapped with spreading and the transform)
     phi_s[k] = acc ? phi_s[k] + phi : phi;
     grad_s[2 * k] = acc ? grad_s[2 * k] + n_os * g1 : n_os * g1;
@@ -409,6 +423,30 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < N)
         interp_point<real, M2>(k, base, frac, w, wp, grid, pitch, n_os, phi_s, grad_s, acc);
+}
+
+// Interpolation and output in one pass, for plans whose near field was stored first: the far
+// field is added to the near field's sums in the working precision exactly as k_interp does,
+// and the result goes straight to the caller's buffers (k_unpermute's step), so the sums are not
+// written back and read again.
+template <typename real, int M2>
+__global__ void __launch_bounds__(256) k_interp_out(int64_t N, const int *__restrict__ base,
+                                                    const real2_t<real> *__restrict__ frac, Window<real> w,
+                                                    WindowPoly wp, const real *__restrict__ grid, int pitch, real n_os,
+                                                    const real *__restrict__ phi_s, const real *__restrict__ grad_s,
+                                                    const real *__restrict__ coinc, const int *__restrict__ perm,
+                                                    double shift, const double *__restrict__ q_sum, double s,
+                                                    void *__restrict__ phi_out, void *__restrict__ H_out, int out_is_f64)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= N)
+        return;
+    real phi, g1, g2;
+    interp_sums<real, M2>(k, base, frac, w, wp, grid, pitch, phi, g1, g2);
+    const real pt = phi_s[k] + phi;
+    const real gx = grad_s[2 * k] + n_os * g1;
+    const real gy = grad_s[2 * k + 1] + n_os * g2;
+    output_point<real>(k, pt, gx, gy, coinc[k], perm, shift, q_sum[0], s, phi_out, H_out, out_is_f64);
 }
 
 // Batched interpolation: block -> (instance, block of its targets), blockIdx.y = right-hand side.
@@ -890,6 +928,31 @@ template <typename real> size_t batch_spread_smem(int M2, int max_tile, bool com
 }
 
 }  // namespace
+
+template <typename real>
+cudaError_t launch_interp_out(int64_t N, int m, const int *base, const void *frac, Window<real> w, const WindowPoly &wp,
+                              const real *grid, int pitch, real n_os, const real *phi_s, const real *grad_s,
+                              const real *coinc, const int *perm, double shift, const double *q_sum, double s,
+                              void *phi_out, void *H_out, int out_is_f64, cudaStream_t st)
+{
+    if (N <= 0)
+        return cudaSuccess;
+    return with_width(m, [&](auto mc) {
+        constexpr int M2 = decltype(mc)::value;
+        k_interp_out<real, M2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
+            N, base, (const real2_t<real> *)frac, w, wp, grid, pitch, n_os, phi_s, grad_s, coinc, perm, shift, q_sum, s,
+            phi_out, H_out, out_is_f64);
+        return cudaGetLastError();
+    });
+}
+template cudaError_t launch_interp_out<float>(int64_t, int, const int *, const void *, Window<float>,
+                                              const WindowPoly &, const float *, int, float, const float *,
+                                              const float *, const float *, const int *, double, const double *,
+                                              double, void *, void *, int, cudaStream_t);
+template cudaError_t launch_interp_out<double>(int64_t, int, const int *, const void *, Window<double>,
+                                               const WindowPoly &, const double *, int, double, const double *,
+                                               const double *, const double *, const int *, double, const double *,
+                                               double, void *, void *, int, cudaStream_t);
 
 // Raises the dynamic shared memory limit of the batched spreading kernel (outside graph capture).
 template <typename real> cudaError_t prepare_batch_spread(int m, int max_tile, bool kahan)
