@@ -415,16 +415,23 @@ template <typename real> fs_status batch_enqueue(fs_batch *b, int q_f64, int out
     FS_CUDA(cudaMemsetAsync(b->grids, 0, b->grid_bytes, st));
     FS_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(int) * (2 * (size_t)K * R + 1), st));
     FS_CUDA(launch_batch_gather_charges<real>(inst, b->io, src_map, b->src_blocks, R, q_f64, st));
+    if constexpr (sizeof(real) == 4) {
+        // the near field first, storing its sums (every target lies in one item); the grids are
+        // then still in L2 when one pass adds the far field and writes the caller's buffers
+        FS_CUDA(launch_batch_near32(b->n_near_items, b->near_items, (const BatchInst<float> *)b->inst, b->p, R, true,
+                                    st));
+    }
     FS_CUDA(launch_batch_spread<real>(b->spread_items, b->n_spread_items, R, inst, b->m, b->max_tile, w, p0->wpoly,
                                       b->kahan, st));
     FS_CUDA(launch_batch_fft<real>(inst, b->fft_units, b->n_fft_units, K, R, b->L_max, b->fft_blocks, b->counters,
                                    b->err, kWaitSpins, st));
-    FS_CUDA(launch_batch_interp<real>(inst, tgt_map, b->tgt_blocks, R, b->m, w, p0->wpoly, st));
-    if constexpr (sizeof(real) == 4)
-        FS_CUDA(launch_batch_near32(b->n_near_items, b->near_items, (const BatchInst<float> *)b->inst, b->p, R, st));
-    else
+    if constexpr (sizeof(real) == 4) {
+        FS_CUDA(launch_batch_interp_out<real>(inst, b->io, tgt_map, b->tgt_blocks, R, b->m, w, p0->wpoly, out_f64, st));
+    } else {
+        FS_CUDA(launch_batch_interp<real>(inst, tgt_map, b->tgt_blocks, R, b->m, w, p0->wpoly, st));
         FS_CUDA(launch_batch_near64((const BatchInst<double> *)b->inst, tgt_map, b->tgt_blocks, R, st));
-    FS_CUDA(launch_batch_unpermute<real>(inst, b->io, tgt_map, b->tgt_blocks, R, out_f64, st));
+        FS_CUDA(launch_batch_unpermute<real>(inst, b->io, tgt_map, b->tgt_blocks, R, out_f64, st));
+    }
     return FS_OK;
 }
 

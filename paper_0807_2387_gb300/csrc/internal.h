@@ -225,6 +225,10 @@ cudaError_t prepare_batch_spread(int m, int max_tile, bool kahan);
 template <typename real>
 cudaError_t launch_batch_interp(const BatchInst<real> *inst, BlockMap bm, int blocks, int nrhs, int m,
                                 Window<real> w, const WindowPoly &wp, cudaStream_t st);
+// FP32 batches: interpolation and output in one pass, after the near field stored its sums
+template <typename real>
+cudaError_t launch_batch_interp_out(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks, int nrhs,
+                                    int m, Window<real> w, const WindowPoly &wp, int out_is_f64, cudaStream_t st);
 // counters: 2 * n_inst * nrhs ints (rows done, columns done) plus the queue head, zeroed
 // before each launch; err: set to 1 when a wait ran out of spins
 template <typename real>
@@ -235,7 +239,7 @@ template <typename real> cudaError_t batch_fft_blocks(int L_max, int *blocks);
 cudaError_t launch_wait_selftest(int *counter, int *err, int spins, cudaStream_t st);
 // items: (first target, count <= 64, instance, 0) per warp
 cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchInst<float> *inst, int p, int nrhs,
-                                cudaStream_t st);
+                                bool assign, cudaStream_t st);
 cudaError_t launch_batch_near64(const BatchInst<double> *inst, BlockMap bm, int blocks, int nrhs, cudaStream_t st);
 template <typename real>
 cudaError_t launch_batch_unpermute(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks, int nrhs,

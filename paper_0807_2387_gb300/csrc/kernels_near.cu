@@ -286,7 +286,8 @@ struct NearCount {
 template <int P, int R>
 __global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_near32(int64_t n_items,
                                                                                const int4 *__restrict__ items,
-                                                                               const BatchInst<float> *__restrict__ inst)
+                                                                               const BatchInst<float> *__restrict__ inst,
+                                                                               bool assign)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_
     op.q_stride = b.M;
     op.n_stride = b.N;
     op.rcoef = np.rcoef * sqrtf(np.eps2);
-    op.assign = false;
+    op.assign = assign;
     __shared__ NearLists<R> L;
     const int w = threadIdx.x >> 5;
     near_traverse_list(make_int2(it.x, it.y), lane, sd, cg, np, op, L.xy[w], L.q[w], L.cxy[w], L.cl[w], L.cq[w]);
@@ -429,7 +430,7 @@ cudaError_t launch_near_count32(int64_t n_items, const int2 *items, const int *t
 }
 
 cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchInst<float> *inst, int p, int nrhs,
-                                cudaStream_t st)
+                                bool assign, cudaStream_t st)
 {
     if (n_items <= 0 || nrhs <= 0)
         return cudaSuccess;
@@ -437,10 +438,10 @@ cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchI
     return with_degree(p, [&](auto pc) {
         constexpr int P = decltype(pc)::value;
         switch (nrhs) {
-        case 1: k_batch_near32<P, 1><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
-        case 2: k_batch_near32<P, 2><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
-        case 3: k_batch_near32<P, 3><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
-        case 4: k_batch_near32<P, 4><<<blocks, 128, 0, st>>>(n_items, items, inst); break;
+        case 1: k_batch_near32<P, 1><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
+        case 2: k_batch_near32<P, 2><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
+        case 3: k_batch_near32<P, 3><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
+        case 4: k_batch_near32<P, 4><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

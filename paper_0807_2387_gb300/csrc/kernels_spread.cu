@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) k_interp(int64_t N, const int *__restrict
 // and the result goes straight to the caller's buffers (k_unpermute's step), so the sums are not
 // written back and read again.
 template <typename real, int M2>
-__global__ void __launch_bounds__(256) k_interp_out(int64_t N, const int *__restrict__ base,
+__global__ void __launch_bounds__(256, 3) k_interp_out(int64_t N, const int *__restrict__ base,
                                                     const real2_t<real> *__restrict__ frac, Window<real> w,
                                                     WindowPoly wp, const real *__restrict__ grid, int pitch, real n_os,
                                                     const real *__restrict__ phi_s, const real *__restrict__ grad_s,
@@ -464,6 +464,33 @@ __global__ void __launch_bounds__(256) k_batch_interp(const BatchInst<real> *__r
     interp_point<real, M2>(k, b.tgt_base, (const real2_t<real> *)b.tgt_frac, w, wp,
                            b.grid + (int64_t)r * b.grid_stride, b.pitch, (real)b.L, b.phi_s + (int64_t)r * N,
                            b.grad_s + 2 * (int64_t)r * N);
+}
+
+// Batched interpolation and output in one pass (FP32 batches, whose near field stored the sums
+// first): block -> (instance, block of its targets), blockIdx.y = right-hand side; writes the
+// caller's (nrhs, N) and (nrhs, N, 2) buffers of each instance.
+template <typename real, int M2>
+__global__ void __launch_bounds__(256, 3) k_batch_interp_out(const BatchInst<real> *__restrict__ inst,
+                                                          const BatchIO *__restrict__ io, BlockMap bm, Window<real> w,
+                                                          WindowPoly wp, int out_is_f64)
+{
+    const int i = bm.inst[blockIdx.x];
+    const BatchInst<real> &b = inst[i];
+    const int64_t k = (int64_t)(blockIdx.x - bm.first[i]) * blockDim.x + threadIdx.x;
+    const int64_t N = b.N;
+    if (k >= N)
+        return;
+    const int r = blockIdx.y;
+    real phi, g1, g2;
+    interp_sums<real, M2>(k, b.tgt_base, (const real2_t<real> *)b.tgt_frac, w, wp, b.grid + (int64_t)r * b.grid_stride,
+                          b.pitch, phi, g1, g2);
+    const real n_os = (real)b.L;
+    const real *ps = b.phi_s + (int64_t)r * N, *gs = b.grad_s + 2 * (int64_t)r * N;
+    const size_t osz = out_is_f64 ? 8 : 4;
+    void *po = io[i].phi ? (unsigned char *)io[i].phi + (size_t)r * N * osz : nullptr;
+    void *ho = io[i].H ? (unsigned char *)io[i].H + (size_t)r * N * 2 * osz : nullptr;
+    output_point<real>(k, ps[k] + phi, gs[2 * k] + n_os * g1, gs[2 * k + 1] + n_os * g2, b.coinc[(int64_t)r * N + k],
+                       b.tgt_perm, b.shift, b.q_sum[r], b.s, po, ho, out_is_f64);
 }
 
 // Adjoint spreading at the targets: each point carries a monopole c and a dipole d (2-vector)
@@ -1000,12 +1027,29 @@ cudaError_t launch_batch_interp(const BatchInst<real> *inst, BlockMap bm, int bl
     });
 }
 
+template <typename real>
+cudaError_t launch_batch_interp_out(const BatchInst<real> *inst, const BatchIO *io, BlockMap bm, int blocks, int nrhs,
+                                    int m, Window<real> w, const WindowPoly &wp, int out_is_f64, cudaStream_t st)
+{
+    if (blocks <= 0 || nrhs <= 0)
+        return cudaSuccess;
+    return with_width(m, [&](auto mc) {
+        constexpr int M2 = decltype(mc)::value;
+        k_batch_interp_out<real, M2><<<dim3((unsigned)blocks, (unsigned)nrhs), 256, 0, st>>>(inst, io, bm, w, wp,
+                                                                                           out_is_f64);
+        return cudaGetLastError();
+    });
+}
+
 #define FS_INST(real)                                                                                          \
     template cudaError_t prepare_batch_spread<real>(int, int, bool);                                           \
     template cudaError_t launch_batch_spread<real>(const SpreadItem *, int, int, const BatchInst<real> *, int, \
                                                    int, Window<real>, const WindowPoly &, bool, cudaStream_t); \
     template cudaError_t launch_batch_interp<real>(const BatchInst<real> *, BlockMap, int, int, int,           \
-                                                   Window<real>, const WindowPoly &, cudaStream_t);
+                                                   Window<real>, const WindowPoly &, cudaStream_t);           \
+    template cudaError_t launch_batch_interp_out<real>(const BatchInst<real> *, const BatchIO *, BlockMap, int, \
+                                                       int, int, Window<real>, const WindowPoly &, int,        \
+                                                       cudaStream_t);
 FS_INST(float)
 FS_INST(double)
 #undef FS_INST
