@@ -175,6 +175,9 @@ NEAR_TRAFFIC = {
     # 21.46 MB per launch on the 2^19-point mixture (same capture), log2(1 - w) from the value's w - 1
     "43c5cc089aecb07f88b53eec773067e57d90b1e8aa98549d206e96811265ad37": (
         2 * 21456128, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), batched near field storing its sums
+    "f4aa79e81d4265ac184bfce8785142663845de7ff5a3c01b4dda5e37af254e87": (
+        2 * 21455104, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 
