@@ -178,6 +178,9 @@ NEAR_TRAFFIC = {
     # 21.46 MB per launch on the 2^19-point mixture (same capture), batched near field storing its sums
     "f4aa79e81d4265ac184bfce8785142663845de7ff5a3c01b4dda5e37af254e87": (
         2 * 21455104, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), the coefficient's forms alternating
+    "6d78ca882bd0b1789f672b79907034e7cc0b8f3e469fde9f7a5af4bc86826020": (
+        2 * 21457664, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 

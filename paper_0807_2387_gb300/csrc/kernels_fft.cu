@@ -804,27 +804,32 @@ __device__ double kr_sample(double r, const KernelParams &kp);
 //   E  Hermitian-extended inverse of x rows per plane (rows_inv_unit)
 // The multiplier carries the weights that make the real part of the sum over I_n^3 exact.
 
-template <typename real>
-__global__ void k_fft3_x_fwd(const real *__restrict__ grid, int n_a, int L, int n_half, cplx<real> *__restrict__ spec1,
-                             const cplx<real> *__restrict__ tw)
+// LC > 0: the line length L = LC compiled as a constant (NT threads), as in the 2D kernels.
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft3_x_fwd(const real *__restrict__ grid, int n_a, int L, int n_half,
+                                                    cplx<real> *__restrict__ spec1, const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
     const int64_t z = blockIdx.y;
-    rows_fwd_unit<real>(blockIdx.x, grid + z * n_a * n_a, n_a, n_a, L, n_half,
-                        spec1 + z * (int64_t)(n_half + 1) * n_a, n_a, tw, a, a + L);
+    rows_fwd_unit<real, LC, NT>(blockIdx.x, grid + z * n_a * n_a, n_a, n_a, L, n_half,
+                                spec1 + z * (int64_t)(n_half + 1) * n_a, n_a, tw, a, a + L);
 }
 
-template <typename real>
-__global__ void k_fft3_y_fwd(const cplx<real> *__restrict__ spec1, int n_a, int L, int n,
-                             cplx<real> *__restrict__ spec2, const cplx<real> *__restrict__ tw)
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft3_y_fwd(const cplx<real> *__restrict__ spec1, int n_a, int L_rt, int n,
+                                                    cplx<real> *__restrict__ spec2, const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
     const int h = n / 2;
     const int64_t line = (int64_t)blockIdx.y * (h + 1) + blockIdx.x;   // (z, l1)
     const cplx<real> *in = spec1 + line * n_a;
-    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+    for (int r = threadIdx.x; r < L; r += nt) {
         cplx<real> v;
         v.x = v.y = real(0);
         if (r < n_a)
@@ -832,16 +837,19 @@ __global__ void k_fft3_y_fwd(const cplx<real> *__restrict__ spec1, int n_a, int 
         a[r] = v;
     }
     __syncthreads();
-    const cplx<real> *F = fft_line<real, false>(a, a + L, L, tw);
+    const cplx<real> *F = fft_line<real, false, LC, NT>(a, a + L, L, tw);
     cplx<real> *out = spec2 + line * (n + 1);
-    for (int k = threadIdx.x; k <= n; k += blockDim.x)
+    for (int k = threadIdx.x; k <= n; k += nt)
         out[k] = F[(k - h + L) & (L - 1)];
 }
 
-template <typename real>
-__global__ void k_fft3_z(cplx<real> *__restrict__ spec2, int n_a, int L, int n, const real *__restrict__ mul3,
-                         const cplx<real> *__restrict__ tw)
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft3_z(cplx<real> *__restrict__ spec2, int n_a, int L_rt, int n,
+                                                const real *__restrict__ mul3, const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
     cplx<real> *b = a + L;
@@ -849,7 +857,7 @@ __global__ void k_fft3_z(cplx<real> *__restrict__ spec2, int n_a, int L, int n, 
     const int k2 = blockIdx.x, l1 = blockIdx.y;
     const int64_t stride = (int64_t)(h + 1) * (n + 1);
     cplx<real> *col = spec2 + (int64_t)l1 * (n + 1) + k2;
-    for (int z = threadIdx.x; z < L; z += blockDim.x) {
+    for (int z = threadIdx.x; z < L; z += nt) {
         cplx<real> v;
         v.x = v.y = real(0);
         if (z < n_a)
@@ -857,10 +865,10 @@ __global__ void k_fft3_z(cplx<real> *__restrict__ spec2, int n_a, int L, int n, 
         a[z] = v;
     }
     __syncthreads();
-    cplx<real> *F = fft_line<real, false>(a, b, L, tw);
+    cplx<real> *F = fft_line<real, false, LC, NT>(a, b, L, tw);
     cplx<real> *other = (F == a) ? b : a;
     const real *mrow = mul3 + ((int64_t)l1 * (n + 1) + k2) * (n + 1);
-    for (int k3 = threadIdx.x; k3 < L; k3 += blockDim.x) {
+    for (int k3 = threadIdx.x; k3 < L; k3 += nt) {
         const int l3 = k3 < L / 2 ? k3 : k3 - L;
         cplx<real> v = F[k3];
         const real f = (l3 >= -h && l3 <= h) ? mrow[l3 + h] : real(0);
@@ -869,44 +877,48 @@ __global__ void k_fft3_z(cplx<real> *__restrict__ spec2, int n_a, int L, int n, 
         F[k3] = v;
     }
     __syncthreads();
-    const cplx<real> *G = fft_line<real, true>(F, other, L, tw);
-    for (int z = threadIdx.x; z < n_a; z += blockDim.x)
+    const cplx<real> *G = fft_line<real, true, LC, NT>(F, other, L, tw);
+    for (int z = threadIdx.x; z < n_a; z += nt)
         col[z * stride] = G[z];
 }
 
-template <typename real>
-__global__ void k_fft3_y_inv(const cplx<real> *__restrict__ spec2, int n_a, int L, int n,
-                             cplx<real> *__restrict__ spec1, const cplx<real> *__restrict__ tw)
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft3_y_inv(const cplx<real> *__restrict__ spec2, int n_a, int L_rt, int n,
+                                                    cplx<real> *__restrict__ spec1, const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
+    const int L = LC ? LC : L_rt;
+    const int nt = NT ? NT : (int)blockDim.x;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
     const int h = n / 2;
     const int64_t line = (int64_t)blockIdx.y * (h + 1) + blockIdx.x;   // (z, l1)
-    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+    for (int r = threadIdx.x; r < L; r += nt) {
         cplx<real> v;
         v.x = v.y = real(0);
         a[r] = v;
     }
     __syncthreads();
     const cplx<real> *in = spec2 + line * (n + 1);
-    for (int k = threadIdx.x; k <= n; k += blockDim.x)
+    for (int k = threadIdx.x; k <= n; k += nt)
         a[(k - h + L) & (L - 1)] = in[k];
     __syncthreads();
-    const cplx<real> *G = fft_line<real, true>(a, a + L, L, tw);
+    const cplx<real> *G = fft_line<real, true, LC, NT>(a, a + L, L, tw);
     cplx<real> *out = spec1 + line * n_a;
-    for (int y = threadIdx.x; y < n_a; y += blockDim.x)
+    for (int y = threadIdx.x; y < n_a; y += nt)
         out[y] = G[y];
 }
 
-template <typename real>
-__global__ void k_fft3_x_inv(const cplx<real> *__restrict__ spec1, int n_a, int L, int n_half, real *__restrict__ grid,
-                             const cplx<real> *__restrict__ tw)
+template <typename real, int LC>
+__global__ void __launch_bounds__(256) k_fft3_x_inv(const cplx<real> *__restrict__ spec1, int n_a, int L, int n_half,
+                                                    real *__restrict__ grid, const cplx<real> *__restrict__ tw)
 {
+    constexpr int NT = LC ? fft_threads(LC) : 0;
     extern __shared__ unsigned char smem_raw[];
     cplx<real> *a = reinterpret_cast<cplx<real> *>(smem_raw);
     const int64_t z = blockIdx.y;
-    rows_inv_unit<real, false>(blockIdx.x, spec1 + z * (int64_t)(n_half + 1) * n_a, n_a, n_a, L, n_half,
-                               grid + z * n_a * n_a, n_a, tw, a, a + L);
+    rows_inv_unit<real, false, LC, NT>(blockIdx.x, spec1 + z * (int64_t)(n_half + 1) * n_a, n_a, n_a, L, n_half,
+                                       grid + z * n_a * n_a, n_a, tw, a, a + L);
 }
 
 // out[(i3 n + i1) n + i2] = in[(i1 n + i2) n + i3]: the middle axis becomes the fastest.
@@ -1172,18 +1184,23 @@ cudaError_t launch_fft3(real *grid, int n_a, int L, int n, cplx<real> *spec1, cp
                         const cplx<real> *tw, cudaStream_t st)
 {
     const size_t smem = 2 * (size_t)L * sizeof(cplx<real>);
-    cudaError_t e;
-    if ((e = set_smem(k_fft3_x_fwd<real>, smem)) != cudaSuccess || (e = set_smem(k_fft3_y_fwd<real>, smem)) != cudaSuccess ||
-        (e = set_smem(k_fft3_z<real>, smem)) != cudaSuccess || (e = set_smem(k_fft3_y_inv<real>, smem)) != cudaSuccess ||
-        (e = set_smem(k_fft3_x_inv<real>, smem)) != cudaSuccess)
-        return e;
-    const int h = n / 2, thr = fft_threads(L);
-    k_fft3_x_fwd<real><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(grid, n_a, L, h, spec1, tw);
-    k_fft3_y_fwd<real><<<dim3(h + 1, n_a), thr, smem, st>>>(spec1, n_a, L, n, spec2, tw);
-    k_fft3_z<real><<<dim3(n + 1, h + 1), thr, smem, st>>>(spec2, n_a, L, n, mul3, tw);
-    k_fft3_y_inv<real><<<dim3(h + 1, n_a), thr, smem, st>>>(spec2, n_a, L, n, spec1, tw);
-    k_fft3_x_inv<real><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(spec1, n_a, L, h, grid, tw);
-    return cudaGetLastError();
+    return with_line_length(L, [&](auto lc) {
+        constexpr int LC = decltype(lc)::value;
+        cudaError_t e;
+        if ((e = set_smem(k_fft3_x_fwd<real, LC>, smem)) != cudaSuccess ||
+            (e = set_smem(k_fft3_y_fwd<real, LC>, smem)) != cudaSuccess ||
+            (e = set_smem(k_fft3_z<real, LC>, smem)) != cudaSuccess ||
+            (e = set_smem(k_fft3_y_inv<real, LC>, smem)) != cudaSuccess ||
+            (e = set_smem(k_fft3_x_inv<real, LC>, smem)) != cudaSuccess)
+            return e;
+        const int h = n / 2, thr = fft_threads(L);
+        k_fft3_x_fwd<real, LC><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(grid, n_a, L, h, spec1, tw);
+        k_fft3_y_fwd<real, LC><<<dim3(h + 1, n_a), thr, smem, st>>>(spec1, n_a, L, n, spec2, tw);
+        k_fft3_z<real, LC><<<dim3(n + 1, h + 1), thr, smem, st>>>(spec2, n_a, L, n, mul3, tw);
+        k_fft3_y_inv<real, LC><<<dim3(h + 1, n_a), thr, smem, st>>>(spec2, n_a, L, n, spec1, tw);
+        k_fft3_x_inv<real, LC><<<dim3((n_a + 1) / 2, n_a), thr, smem, st>>>(spec1, n_a, L, h, grid, tw);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_coeffs3(double2 *samp, double2 *tmp, int n, KernelParams kp, const double2 *tw64,

@@ -193,18 +193,52 @@ struct NearSides {
 constexpr int kListCap = 256;    // far candidates per warp
 constexpr int kCloseCap = 64;    // close candidates per warp
 
+// Ops with kAlt = true alternate two forms of the pair arithmetic between consecutive far
+// candidates (pair2, pair2_alt) whose pipe mixes differ, so that the FMA and MUFU pipes share
+// the load; the others evaluate every candidate with pair2.
+template <class Op, class = void> struct AltForms : std::false_type {};
+template <class Op> struct AltForms<Op, std::void_t<decltype(Op::kAlt)>> : std::bool_constant<Op::kAlt> {};
+
 template <class Op>
 __device__ __forceinline__ void near_eval_far(const float4 *s_xy, const float *s_q, int n, float2 X, float2 Y,
                                               const NearParams<float> &np, Op &op)
 {
     op.row_begin();
+    if constexpr (AltForms<Op>::value) {
+        int e = 0;
+#pragma unroll(Op::kUnroll / 2)
+        for (; e + 1 < n; e += 2) {
+            {
+                const float4 a = s_xy[e];
+                op.set_q(s_q + e * Op::kR);
+                const float2 dx = add2(X, make_float2(a.x, a.y));
+                const float2 dy = add2(Y, make_float2(a.z, a.w));
+                op.pair2(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
+            }
+            {
+                const float4 a = s_xy[e + 1];
+                op.set_q(s_q + (e + 1) * Op::kR);
+                const float2 dx = add2(X, make_float2(a.x, a.y));
+                const float2 dy = add2(Y, make_float2(a.z, a.w));
+                op.pair2_alt(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
+            }
+        }
+        if (e < n) {
+            const float4 a = s_xy[e];
+            op.set_q(s_q + e * Op::kR);
+            const float2 dx = add2(X, make_float2(a.x, a.y));
+            const float2 dy = add2(Y, make_float2(a.z, a.w));
+            op.pair2(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
+        }
+    } else {
 #pragma unroll(Op::kUnroll)
-    for (int e = 0; e < n; ++e) {
-        const float4 a = s_xy[e];
-        op.set_q(s_q + e * Op::kR);
-        const float2 dx = add2(X, make_float2(a.x, a.y));
-        const float2 dy = add2(Y, make_float2(a.z, a.w));
-        op.pair2(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
+        for (int e = 0; e < n; ++e) {
+            const float4 a = s_xy[e];
+            op.set_q(s_q + e * Op::kR);
+            const float2 dx = add2(X, make_float2(a.x, a.y));
+            const float2 dy = add2(Y, make_float2(a.z, a.w));
+            op.pair2(np, fma2(dy, dy, mul2(dx, dx)), dx, dy);
+        }
     }
     op.row_end();
 }
