@@ -465,7 +465,7 @@ template <class Op> cudaError_t launch_near_list(int64_t n_items, const int2 *it
 // the hi and lo parts exactly as in the target-major traversal.
 constexpr int kSrcMajorCap = 128;   // listed targets per warp and list
 
-template <int P>
+template <int P, bool ALT = false>
 __device__ __forceinline__ void near_src_pair(const NearParams<float> &np, float2 r2, float2 dx, float2 dy,
                                               float2 q2, float2 &phi, float2 &gx, float2 &gy)
 {
@@ -474,7 +474,12 @@ __device__ __forceinline__ void near_src_pair(const NearParams<float> &np, float
         w = min1(w);                                      // f(1) = 0 and (w - 1)^(p-1) = 0: masked
     const float2 val = near_f2<P>(np, w);
     float2 coef;
-    if constexpr (P >= 2) {
+    if constexpr (P >= 2 && ALT) {
+        // the power form with the same sign, (1 - w)^(p-1) / w: the caller alternates the two
+        // forms between consecutive sources so that the FMA and MUFU pipes share the load
+        const float2 om = add2(w, f2(-1.f));
+        coef = mul2(ipow2<P - 1>(make_float2(-om.x, -om.y)), rcp_2(w));
+    } else if constexpr (P >= 2) {
         // |w - 1|^(p-1) / w = 2^((p-1) log2(1 - w) - log2 w) (log2 w shared with val; the sign
         // (-1)^(p-1) is applied at the store; w = 1 gives 2^-inf = 0)
         const float2 lw = lg2_2(w);
@@ -544,7 +549,10 @@ __device__ __forceinline__ void near_src_eval(const float4 *s_hi, const float4 *
                     }
                 }
             }
-            near_src_pair<P>(np, r2, dx, dy, q2, phi, gx, gy);
+            if (i & 1)
+                near_src_pair<P, true>(np, r2, dx, dy, q2, phi, gx, gy);
+            else
+                near_src_pair<P, false>(np, r2, dx, dy, q2, phi, gx, gy);
         }
         if (valid) {
             const float rc = (P >= 2 && (P - 1) % 2 == 1) ? -rcoef : rcoef;   // near_src_pair's coef is |w - 1|^(p-1) / w
