@@ -181,6 +181,9 @@ NEAR_TRAFFIC = {
     # 21.46 MB per launch on the 2^19-point mixture (same capture), the coefficient's forms alternating
     "6d78ca882bd0b1789f672b79907034e7cc0b8f3e469fde9f7a5af4bc86826020": (
         2 * 21457664, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), source-major kernel alternating too
+    "a33d24b40980e496e92b5144481c9df4a034abfa1b8aa6cf4fd355dca9d51a0f": (
+        2 * 21456128, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 
