@@ -264,7 +264,10 @@ fs_status fs_plan_info(const fs_plan *plan, fs_info *info);
  * With FS_FLAG_TIMING: milliseconds of each stage of the last evaluation,
  * measured with CUDA events on the plan's stream.  Stage order: 0 charges,
  * 1 spread, 2 fft rows fwd, 3 fft cols + multiply, 4 fft rows inv,
- * 5 interpolate, 6 near field, 7 unpermute.  Synchronises the stream.
+ * 5 interpolate, 6 near field, 7 unpermute.  FP32 plans without FS_FLAG_SERIAL
+ * run the near field on a second stream beside stages 1-4 (stage 6 is its own
+ * duration there) and write the output in the interpolation kernel (stage 5
+ * includes it; stage 7 is empty).  Synchronises the stream.
  * count = number of doubles available in ms (8 or more).
  */
 fs_status fs_stage_times(fs_plan *plan, double *ms, int count);
