@@ -662,6 +662,8 @@ void plan_destroy(fs_plan *pl)
         cudaStreamSynchronize(pl->aux);
         cudaStreamDestroy(pl->aux);
     }
+    if (pl->status_host)
+        cudaFreeHost(pl->status_host);
     delete pl;
 }
 
@@ -1004,6 +1006,18 @@ fs_status adjoint_t(fs_plan *pl, const void *g_phi, const void *g_H, fs_dtype in
 
 }  // namespace
 
+// The device status word (read back after a synchronisation) as the API's status; a
+// non-zero word is reset so that the next call starts clean.
+static fs_status status_from_code(fs_plan *plan, int code)
+{
+    if (code == 0)
+        return FS_OK;
+    FS_CUDA(cudaMemset(plan->status, 0, sizeof(int)));
+    if (code == kDevTimeout)
+        return fail(FS_ETIMEOUT, "a bounded device wait gave up");
+    return fail(FS_EDOMAIN, "a point fell outside the admissible region");
+}
+
 extern "C" {
 
 const char *fs_last_error(void) { return g_last_error.c_str(); }
@@ -1233,8 +1247,12 @@ fs_status fs_solve_host(fs_plan *plan, const void *q, fs_dtype q_dtype, int nrhs
         FS_CUDA(cudaMemcpyAsync(phi, plan->d_phi_stage, ob, cudaMemcpyDeviceToHost, st));
     if (ob)
         FS_CUDA(cudaMemcpyAsync(H, plan->d_H_stage, 2 * ob, cudaMemcpyDeviceToHost, st));
+    // the device status word comes back with the outputs: one synchronisation per call
+    if (!plan->status_host)
+        FS_CUDA(cudaMallocHost(&plan->status_host, sizeof(int)));
+    FS_CUDA(cudaMemcpyAsync(plan->status_host, plan->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     FS_CUDA(cudaStreamSynchronize(st));
-    return fs_sync_status(plan);
+    return status_from_code(plan, *plan->status_host);
 }
 
 fs_status fs_adjoint(fs_plan *plan, const void *g_phi, const void *g_H, fs_dtype in_dtype, void *dq, void *dsrc,
@@ -1259,12 +1277,7 @@ fs_status fs_sync_status(fs_plan *plan)
     FS_CUDA(cudaStreamSynchronize(plan->stream));
     int code = 0;
     FS_CUDA(cudaMemcpy(&code, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (code == 0)
-        return FS_OK;
-    FS_CUDA(cudaMemset(plan->status, 0, sizeof(int)));
-    if (code == kDevTimeout)
-        return fail(FS_ETIMEOUT, "a bounded device wait gave up");
-    return fail(FS_EDOMAIN, "a point fell outside the admissible region");
+    return status_from_code(plan, code);
 }
 
 fs_status fs_plan_info(const fs_plan *plan, fs_info *info)

@@ -61,6 +61,7 @@ struct fs_plan {
     std::vector<void *> allocs;
     int64_t bytes = 0;
     int *status = nullptr;
+    int *status_host = nullptr;           // page-locked copy of *status (fs_solve_host)
     int *src_perm = nullptr, *tgt_perm = nullptr;
     int *src_base = nullptr, *tgt_base = nullptr;
     void *src_frac = nullptr, *tgt_frac = nullptr;
