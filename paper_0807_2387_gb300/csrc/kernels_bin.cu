@@ -203,6 +203,7 @@ __global__ void k_gather_charges(const void *__restrict__ q, int q_is_f64, const
 {
     const int r = blockIdx.y;
     double acc = 0.0;
+#pragma unroll 4
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t src = (int64_t)r * M + perm[k];
         const double v = q_is_f64 ? ((const double *)q)[src] : (double)((const float *)q)[src];
@@ -345,9 +346,24 @@ cudaError_t launch_gather_charges(const void *q, int q_is_f64, const int *perm, 
 {
     if (M <= 0 || nrhs <= 0)
         return cudaSuccess;
+    // four blocks per SM, each thread with several gathers in flight: fewer blocks also mean
+    // fewer FP64 atomics on the charge sum (2^20 charges: 19.9 -> 16.3 us against 2048 blocks)
+    static int sms_of[64] = {0};   // per device ordinal (SM counts can differ between GPUs)
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 64 && sms_of[dev] > 0) {
+        sms = sms_of[dev];
+    } else {
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        if (dev < 64)
+            sms_of[dev] = sms;
+    }
     unsigned bx = blocks_for(M, 256);
-    if (bx > 2048)
-        bx = 2048;
+    if (bx > 4u * (unsigned)sms)
+        bx = 4u * (unsigned)sms;
     k_gather_charges<real><<<dim3(bx, nrhs), 256, 0, st>>>(q, q_is_f64, perm, M, q_sorted, q_sum);
     return cudaGetLastError();
 }
