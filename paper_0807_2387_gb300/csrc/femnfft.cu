@@ -1089,6 +1089,8 @@ fs_status fs_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *tri
         const int64_t Ms = 3 * Nt + 2 * pl->Ne;
         FS_TRY(pl->alloc(&pl->fem_src, Ms));
         FS_CUDA(launch_fem_sources((const double2 *)nodes, pl->tris, Nt, pl->bedges, pl->Ne, pl->fem_src, st));
+        FS_TRY(pl->alloc(&pl->fem_tri_coef, std::max<int64_t>(3 * Nt, 1)));
+        FS_CUDA(launch_fem_tri_coef((const double2 *)nodes, pl->tris, Nt, pl->fem_tri_coef, st));
         FS_CUDA(cudaStreamSynchronize(st));
         pl->precision = o.precision == 64 ? 64 : 32;
         if (pl->precision == 64)
@@ -1164,11 +1166,13 @@ fs_status fs_set_magnetization(fs_plan *plan, const double *mag, int nrhs)
         FS_CUDA(cudaEventRecord(plan->ev_q0, st));
     FS_CUDA(cudaMemsetAsync(plan->q_sum, 0, sizeof(double) * nrhs, st));
     if (plan->precision == 64)
-        FS_CUDA(launch_fem_charges_scatter<double>(plan->nodes, plan->tris, plan->Nt, plan->bedges, plan->Ne,
+        FS_CUDA(launch_fem_charges_scatter<double>(plan->nodes, plan->tris, plan->Nt, plan->fem_tri_coef, plan->bedges,
+                                                   plan->Ne,
                                                    (const double2 *)mag, plan->Nv, nrhs, plan->src_inv_perm, plan->M,
                                                    (double *)plan->q_sorted, plan->q_sum, st));
     else
-        FS_CUDA(launch_fem_charges_scatter<float>(plan->nodes, plan->tris, plan->Nt, plan->bedges, plan->Ne,
+        FS_CUDA(launch_fem_charges_scatter<float>(plan->nodes, plan->tris, plan->Nt, plan->fem_tri_coef, plan->bedges,
+                                                  plan->Ne,
                                                   (const double2 *)mag, plan->Nv, nrhs, plan->src_inv_perm, plan->M,
                                                   (float *)plan->q_sorted, plan->q_sum, st));
     if (plan->events)

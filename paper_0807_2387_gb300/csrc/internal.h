@@ -388,9 +388,11 @@ cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt
 // charges straight into cell order (q_sorted, stride M per rhs; inv_perm: source -> sorted index)
 // and their sums (q_sum, zeroed), one thread per triangle or boundary edge
 template <typename real>
-cudaError_t launch_fem_charges_scatter(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
-                                       int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, const int *inv_perm,
-                                       int64_t M, real *q_sorted, double *q_sum, cudaStream_t st);
+cudaError_t launch_fem_charges_scatter(const double2 *nodes, const int *tris, int64_t Nt, const double2 *tri_coef,
+                                       const int *bedges, int64_t Ne, const double2 *mag, int64_t Nv, int nrhs,
+                                       const int *inv_perm, int64_t M, real *q_sorted, double *q_sum, cudaStream_t st);
+// per triangle, the coefficients c_k of its charge sum_k M_k . c_k (3 per triangle)
+cudaError_t launch_fem_tri_coef(const double2 *nodes, const int *tris, int64_t Nt, double2 *coef, cudaStream_t st);
 // inv[perm[k]] = k
 cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t st);
 // tetrahedra: nodes (Nv, 3), tets (Nt, 4), faces (Nf, 4) = (i0 < i1 < i2, fourth node), mag (nrhs, Nv, 3)

@@ -57,6 +57,23 @@ __device__ __forceinline__ double triangle_charge(const double2 *__restrict__ no
     return two_a > 0.0 ? S * (-1.0 / 6.0) : S * (1.0 / 6.0);
 }
 
+// The triangle's charge as a linear form in its nodal magnetisations: rho_T |T| / 3 =
+// sum_k M_k . c_k with c_k the rotated opposite edge times -sign(2A) / 6 (the geometry part of
+// triangle_charge, computed once with the plan; a time step then takes 6 FP64 FMAs per triangle).
+__global__ void k_fem_tri_coef(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
+                               double2 *__restrict__ coef)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= Nt)
+        return;
+    const double2 pa = nodes[tris[3 * t]], pb = nodes[tris[3 * t + 1]], pc = nodes[tris[3 * t + 2]];
+    const double two_a = (pb.x - pa.x) * (pc.y - pa.y) - (pb.y - pa.y) * (pc.x - pa.x);
+    const double s = two_a > 0.0 ? -1.0 / 6.0 : 1.0 / 6.0;
+    coef[3 * t] = make_double2(s * (pb.y - pc.y), s * (pc.x - pb.x));
+    coef[3 * t + 1] = make_double2(s * (pc.y - pa.y), s * (pa.x - pc.x));
+    coef[3 * t + 2] = make_double2(s * (pa.y - pb.y), s * (pb.x - pa.x));
+}
+
 // Charge of Gauss point g (0: t = 1/2 - 1/(2 sqrt 3), 1: t = 1/2 + 1/(2 sqrt 3)) of boundary edge e:
 // (M(t) . n_e) |e| / 2 with n_e |e| = +-(t_y, -t_x) for the edge vector t (outward sign): no
 // square root or division.
@@ -103,9 +120,10 @@ __global__ void k_fem_charges(const double2 *__restrict__ nodes, const int *__re
 // with the plan), in the plan's precision; the block sums go to q_sum.
 template <typename real>
 __global__ void k_fem_charges_scatter(const double2 *__restrict__ nodes, const int *__restrict__ tris, int64_t Nt,
-                                      const int *__restrict__ bedges, int64_t Ne, const double2 *__restrict__ mag,
-                                      int64_t Nv, const int *__restrict__ inv_perm, int64_t M,
-                                      real *__restrict__ q_sorted, double *__restrict__ q_sum)
+                                      const double2 *__restrict__ tri_coef, const int *__restrict__ bedges,
+                                      int64_t Ne, const double2 *__restrict__ mag, int64_t Nv,
+                                      const int *__restrict__ inv_perm, int64_t M, real *__restrict__ q_sorted,
+                                      double *__restrict__ q_sum)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
@@ -113,7 +131,14 @@ __global__ void k_fem_charges_scatter(const double2 *__restrict__ nodes, const i
     real *qs = q_sorted + (int64_t)r * M;
     double v = 0.0;
     if (i < Nt) {
-        const double qt = triangle_charge(nodes, tris, i, mg);
+        double qt;
+        if (tri_coef) {
+            const double2 ma = mg[tris[3 * i]], mb = mg[tris[3 * i + 1]], mc = mg[tris[3 * i + 2]];
+            const double2 ca = tri_coef[3 * i], cb = tri_coef[3 * i + 1], cc = tri_coef[3 * i + 2];
+            qt = ma.x * ca.x + ma.y * ca.y + mb.x * cb.x + mb.y * cb.y + mc.x * cc.x + mc.y * cc.y;
+        } else {
+            qt = triangle_charge(nodes, tris, i, mg);
+        }
 #pragma unroll
         for (int p = 0; p < 3; ++p)
             qs[inv_perm[3 * i + p]] = (real)qt;
@@ -377,25 +402,33 @@ cudaError_t launch_fem_charges(const double2 *nodes, const int *tris, int64_t Nt
 }
 
 template <typename real>
-cudaError_t launch_fem_charges_scatter(const double2 *nodes, const int *tris, int64_t Nt, const int *bedges,
-                                       int64_t Ne, const double2 *mag, int64_t Nv, int nrhs, const int *inv_perm,
-                                       int64_t M, real *q_sorted, double *q_sum, cudaStream_t st)
+cudaError_t launch_fem_charges_scatter(const double2 *nodes, const int *tris, int64_t Nt, const double2 *tri_coef,
+                                       const int *bedges, int64_t Ne, const double2 *mag, int64_t Nv, int nrhs,
+                                       const int *inv_perm, int64_t M, real *q_sorted, double *q_sum, cudaStream_t st)
 {
     const int64_t n = Nt + Ne;
     if (n <= 0 || nrhs <= 0)
         return cudaSuccess;
     dim3 grid((unsigned)((n + 255) / 256), nrhs);
-    k_fem_charges_scatter<real><<<grid, 256, 0, st>>>(nodes, tris, Nt, bedges, Ne, mag, Nv, inv_perm, M, q_sorted,
-                                                       q_sum);
+    k_fem_charges_scatter<real><<<grid, 256, 0, st>>>(nodes, tris, Nt, tri_coef, bedges, Ne, mag, Nv, inv_perm, M,
+                                                       q_sorted, q_sum);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fem_charges_scatter<float>(const double2 *, const int *, int64_t, const int *, int64_t,
-                                                       const double2 *, int64_t, int, const int *, int64_t, float *,
-                                                       double *, cudaStream_t);
-template cudaError_t launch_fem_charges_scatter<double>(const double2 *, const int *, int64_t, const int *, int64_t,
-                                                        const double2 *, int64_t, int, const int *, int64_t, double *,
-                                                        double *, cudaStream_t);
+template cudaError_t launch_fem_charges_scatter<float>(const double2 *, const int *, int64_t, const double2 *,
+                                                       const int *, int64_t, const double2 *, int64_t, int,
+                                                       const int *, int64_t, float *, double *, cudaStream_t);
+template cudaError_t launch_fem_charges_scatter<double>(const double2 *, const int *, int64_t, const double2 *,
+                                                        const int *, int64_t, const double2 *, int64_t, int,
+                                                        const int *, int64_t, double *, double *, cudaStream_t);
+
+cudaError_t launch_fem_tri_coef(const double2 *nodes, const int *tris, int64_t Nt, double2 *coef, cudaStream_t st)
+{
+    if (Nt <= 0)
+        return cudaSuccess;
+    k_fem_tri_coef<<<(unsigned)((Nt + 255) / 256), 256, 0, st>>>(nodes, tris, Nt, coef);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_invert_perm(const int *perm, int64_t n, int *inv, cudaStream_t st)
 {

@@ -99,6 +99,7 @@ struct fs_plan {
     int64_t Nv = 0, Nt = 0, Ne = 0;
     const double2 *nodes = nullptr;   // caller's (valid while the plan is used)
     int *tris = nullptr, *bedges = nullptr;
+    double2 *fem_tri_coef = nullptr;      // per triangle: its charge = sum_k M_k . coef_k (k_fem_tri_coef)
     double2 *fem_src = nullptr;
     int *src_inv_perm = nullptr;      // source index -> sorted index (charges assembled into cell order)
     // host staging for fs_solve_host
