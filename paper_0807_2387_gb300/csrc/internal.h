@@ -401,8 +401,11 @@ cudaError_t launch_fem3_sources(const double *nodes, const int *tets, int64_t Nt
 cudaError_t launch_fem3_charges(const double *nodes, const int *tets, int64_t Nt, const int *faces,
                                 const double *mag, int64_t Nv, int nrhs, double *q, int64_t M, cudaStream_t st);
 template <typename real>
-cudaError_t launch_fem3_charges_scatter(const double *nodes, const int *tets, int64_t Nt, const int *faces,
-                                        int64_t Nf, const double *mag, int64_t Nv, int nrhs, const int *inv_perm,
-                                        int64_t M, real *q_sorted, double *q_sum, cudaStream_t st);
+cudaError_t launch_fem3_charges_scatter(const double *nodes, const int *tets, int64_t Nt, const double *tet_coef,
+                                        const int *faces, int64_t Nf, const double *mag, int64_t Nv, int nrhs,
+                                        const int *inv_perm, int64_t M, real *q_sorted, double *q_sum,
+                                        cudaStream_t st);
+// per tetrahedron, the 9 coefficients g_1..g_3 of its charge sum_k (M_k - M_0) . g_k
+cudaError_t launch_fem3_tet_coef(const double *nodes, const int *tets, int64_t Nt, double *coef, cudaStream_t st);
 
 }  // namespace fs

@@ -61,6 +61,7 @@ struct fs3_plan {
     int *src_inv_perm = nullptr;      // source index -> sorted index (charges assembled into cell order)
     const double *nodes = nullptr;
     int *tets = nullptr, *faces = nullptr;
+    double *fem_tet_coef = nullptr;       // per tetrahedron: 9 charge coefficients (k_fem3_tet_coef)
     double *fem_src = nullptr;
 
     template <typename T> fs_status alloc(T **out, size_t count)
@@ -512,7 +513,8 @@ template <typename real> fs_status set_magnetization3_t(fs3_plan *pl, const doub
     FS_TRY(reserve_charges3<real>(pl, nrhs));
     pl->nrhs = nrhs;
     FS_CUDA(cudaMemsetAsync(pl->q_sum, 0, sizeof(double) * nrhs, pl->stream));
-    FS_CUDA(launch_fem3_charges_scatter<real>(pl->nodes, pl->tets, pl->Nt, pl->faces, pl->Nf, mag, pl->Nv, nrhs,
+    FS_CUDA(launch_fem3_charges_scatter<real>(pl->nodes, pl->tets, pl->Nt, pl->fem_tet_coef, pl->faces, pl->Nf, mag,
+                                              pl->Nv, nrhs,
                                               pl->src_inv_perm, pl->M, (real *)pl->q_sorted, pl->q_sum, pl->stream));
     return FS_OK;
 }
@@ -703,6 +705,8 @@ fs_status fs3_plan_create_fem(const double *nodes, int64_t Nv, const int32_t *te
         const int64_t Ms = 4 * Nt + 3 * pl->Nf;
         FS_TRY(pl->alloc(&pl->fem_src, 3 * (size_t)Ms));
         FS_CUDA(launch_fem3_sources(nodes, pl->tets, Nt, pl->faces, pl->Nf, pl->fem_src, st));
+        FS_TRY(pl->alloc(&pl->fem_tet_coef, 9 * (size_t)Nt));
+        FS_CUDA(launch_fem3_tet_coef(nodes, pl->tets, Nt, pl->fem_tet_coef, st));
         FS_CUDA(cudaStreamSynchronize(st));
         pl->M = Ms;
         pl->N = Nv;
