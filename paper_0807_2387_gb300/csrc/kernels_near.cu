@@ -199,15 +199,28 @@ template <int P, int R, bool BATCH = false> struct NearFwd {
             if constexpr (P >= 2)
                 coef = mul2(ipow2<P - 1>(add2(w, f2(-1.f))), coef);
         }
+        if constexpr (R >= 3 && P >= 2) {
+            // three or more right-hand sides: the pair's gradient vector once, then one FMA per
+            // component and right-hand side (batched replay 8.01 -> 7.77 ms at three)
+            const float2 cdx = mul2(coef, dx), cdy = mul2(coef, dy);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 qq = f2(qj[r]);
-            if constexpr (P == 1)
-                qq = select2(r2, np.eps2, qq);
-            acc_phi(r) = fma2(qq, val, acc_phi(r));
-            const float2 tq = mul2(qq, coef);
-            acc_gx(r) = fma2(tq, dx, acc_gx(r));
-            acc_gy(r) = fma2(tq, dy, acc_gy(r));
+            for (int r = 0; r < R; ++r) {
+                const float2 qq = f2(qj[r]);
+                acc_phi(r) = fma2(qq, val, acc_phi(r));
+                acc_gx(r) = fma2(qq, cdx, acc_gx(r));
+                acc_gy(r) = fma2(qq, cdy, acc_gy(r));
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 qq = f2(qj[r]);
+                if constexpr (P == 1)
+                    qq = select2(r2, np.eps2, qq);
+                acc_phi(r) = fma2(qq, val, acc_phi(r));
+                const float2 tq = mul2(qq, coef);
+                acc_gx(r) = fma2(tq, dx, acc_gx(r));
+                acc_gy(r) = fma2(tq, dy, acc_gy(r));
+            }
         }
     }
     // every other far candidate takes the power form, (1 - w)^(p-1) / w (the exp2 form's sign):
