@@ -184,6 +184,9 @@ NEAR_TRAFFIC = {
     # 21.46 MB per launch on the 2^19-point mixture (same capture), source-major kernel alternating too
     "a33d24b40980e496e92b5144481c9df4a034abfa1b8aa6cf4fd355dca9d51a0f": (
         2 * 21456128, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), batched kernel's shared gradient vector
+    "b12c2c7150071a579c8f043241c69b6a9284e77f8901863be1001ae973bf37bd": (
+        2 * 21456896, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 
