@@ -316,7 +316,7 @@ struct NearCount {
 // Batched FP32 near field: one warp per item (first target, count, instance); all R
 // right-hand sides in one candidate-list traversal.
 template <int P, int R>
-__global__ void __launch_bounds__(128, NearFwd<P, R, true>::kMinBlocks) k_batch_near32(int64_t n_items,
+__global__ void __launch_bounds__(32 * kNearWarps, NearFwd<P, R, true>::kMinBlocks * 4 / kNearWarps) k_batch_near32(int64_t n_items,
                                                                                const int4 *__restrict__ items,
                                                                                const BatchInst<float> *__restrict__ inst,
                                                                                bool assign)
@@ -466,14 +466,15 @@ cudaError_t launch_batch_near32(int64_t n_items, const int4 *items, const BatchI
 {
     if (n_items <= 0 || nrhs <= 0)
         return cudaSuccess;
-    const unsigned blocks = (unsigned)((n_items + 3) / 4);
+    const unsigned blocks = (unsigned)((n_items + kNearWarps - 1) / kNearWarps);
+    constexpr int T = 32 * kNearWarps;
     return with_degree(p, [&](auto pc) {
         constexpr int P = decltype(pc)::value;
         switch (nrhs) {
-        case 1: k_batch_near32<P, 1><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
-        case 2: k_batch_near32<P, 2><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
-        case 3: k_batch_near32<P, 3><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
-        case 4: k_batch_near32<P, 4><<<blocks, 128, 0, st>>>(n_items, items, inst, assign); break;
+        case 1: k_batch_near32<P, 1><<<blocks, T, 0, st>>>(n_items, items, inst, assign); break;
+        case 2: k_batch_near32<P, 2><<<blocks, T, 0, st>>>(n_items, items, inst, assign); break;
+        case 3: k_batch_near32<P, 3><<<blocks, T, 0, st>>>(n_items, items, inst, assign); break;
+        case 4: k_batch_near32<P, 4><<<blocks, T, 0, st>>>(n_items, items, inst, assign); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();

@@ -421,17 +421,19 @@ __device__ __forceinline__ void near_traverse_list(int2 item, int lane, const Ne
             op.store(t, kt[t]);
 }
 
-// Per-warp lists of a 4-warp block (R charges per candidate).
+// Warps per block of the candidate-list kernels (a warp per item), and their per-warp lists
+// (R charges per candidate).  An Op's kMinBlocks counts blocks of four warps.
+constexpr int kNearWarps = 4;
 template <int R> struct NearLists {
-    float4 xy[4][kListCap];
-    float q[4][kListCap * R];
-    float4 cxy[4][kCloseCap];
-    float4 cl[4][kCloseCap];
-    float cq[4][kCloseCap * R];
+    float4 xy[kNearWarps][kListCap];
+    float q[kNearWarps][kListCap * R];
+    float4 cxy[kNearWarps][kCloseCap];
+    float4 cl[kNearWarps][kCloseCap];
+    float cq[kNearWarps][kCloseCap * R];
 };
 
 template <class Op>
-__global__ void __launch_bounds__(128, Op::kMinBlocks) k_near_list(int64_t n_items, const int2 *__restrict__ items,
+__global__ void __launch_bounds__(32 * kNearWarps, Op::kMinBlocks * 4 / kNearWarps) k_near_list(int64_t n_items, const int2 *__restrict__ items,
                                                                    NearSides sd, CellGrid cg, NearParams<float> np,
                                                                    Op op)
 {
@@ -448,8 +450,8 @@ template <class Op> cudaError_t launch_near_list(int64_t n_items, const int2 *it
 {
     if (n_items <= 0)
         return cudaSuccess;
-    const unsigned blocks = (unsigned)((n_items + 3) / 4);
-    k_near_list<Op><<<blocks, 128, 0, st>>>(n_items, items, sd, cg, np, op);
+    const unsigned blocks = (unsigned)((n_items + kNearWarps - 1) / kNearWarps);
+    k_near_list<Op><<<blocks, 32 * kNearWarps, 0, st>>>(n_items, items, sd, cg, np, op);
     return cudaGetLastError();
 }
 
