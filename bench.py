@@ -187,6 +187,9 @@ NEAR_TRAFFIC = {
     # 21.46 MB per launch on the 2^19-point mixture (same capture), batched kernel's shared gradient vector
     "b12c2c7150071a579c8f043241c69b6a9284e77f8901863be1001ae973bf37bd": (
         2 * 21456896, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
+    # 21.46 MB per launch on the 2^19-point mixture (same capture), warps per block as a constant
+    "288ddfa52cfeaf9f265d07a52b5ca7a93974a7b356843dfe00170e01047d7a1d": (
+        2 * 21459712, "captured at 2^19 points on this source and item layout, scaled x2 to 2^20"),
 }
 
 

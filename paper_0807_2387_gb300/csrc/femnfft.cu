@@ -574,9 +574,12 @@ fs_status plan_init(fs_plan *pl, const double *src, int64_t M, const double *tgt
     if (pl->spread_direct && pl->kahan && sizeof(real) == 4)
         FS_TRY(pl->alloc_bytes(&pl->grid_comp, (size_t)n_a * pl->pitch * sizeof(real)));
     FS_TRY(pl->alloc_bytes(&pl->spec, (size_t)(pl->n / 2 + 1) * pl->ld * 2 * sizeof(real)));
-    FS_TRY(pl->alloc_bytes(&pl->phi_s, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
-    FS_TRY(pl->alloc_bytes(&pl->grad_s, (size_t)std::max<int64_t>(N, 1) * 2 * sizeof(real)));
-    FS_TRY(pl->alloc_bytes(&pl->coinc, (size_t)std::max<int64_t>(N, 1) * sizeof(real)));
+    // the near field's sums in one block (phi_s, grad_s, coinc; each part 16-byte aligned), so
+    // that the source-major near field zeroes them with one memset
+    pl->sums_n = (std::max<int64_t>(N, 1) + 3) / 4 * 4;
+    FS_TRY(pl->alloc_bytes(&pl->phi_s, (size_t)pl->sums_n * 4 * sizeof(real)));
+    pl->grad_s = (unsigned char *)pl->phi_s + (size_t)pl->sums_n * sizeof(real);
+    pl->coinc = (unsigned char *)pl->phi_s + (size_t)pl->sums_n * 3 * sizeof(real);
 
     // near-field pair statistics: the FP32 path counts with its own traversal (the pairs its
     // near-field kernel evaluates), the FP64 path with FP64 distances
@@ -742,11 +745,8 @@ template <typename real> fs_status eval_t(fs_plan *pl, void *phi, void *H, fs_dt
             if (rec)
                 FS_CUDA(cudaEventRecord(pl->ev_n0, pl->aux));
             if (pl->src_major) {
-                // source items add with atomics: zero the near-field sums first
-                const size_t nb = sizeof(float) * (size_t)pl->N;
-                FS_CUDA(cudaMemsetAsync(pl->phi_s, 0, nb, pl->aux));
-                FS_CUDA(cudaMemsetAsync(pl->grad_s, 0, 2 * nb, pl->aux));
-                FS_CUDA(cudaMemsetAsync(pl->coinc, 0, nb, pl->aux));
+                // source items add with atomics: zero the near-field sums first (one block)
+                FS_CUDA(cudaMemsetAsync(pl->phi_s, 0, sizeof(float) * 4 * (size_t)pl->sums_n, pl->aux));
                 FS_CUDA(launch_near_src32(pl->n_src_near_items, pl->src_near_items, pl->src_base, pl->src_pos32,
                                           pl->src_lo32, pl->tgt_pos32, pl->tgt_lo32, pl->tgt_start, pl->cg,
                                           (const float *)q, make_near<float>(pl), (float *)pl->phi_s,

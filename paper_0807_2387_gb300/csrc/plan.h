@@ -89,7 +89,8 @@ struct fs_plan {
     void *grid = nullptr, *spec = nullptr;
     void *grid_comp = nullptr;        // direct spreading (FP32): compensation plane of the grid
     bool spread_direct = false;       // spread with global atomics instead of shared-memory tiles
-    void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;
+    void *phi_s = nullptr, *grad_s = nullptr, *coinc = nullptr;   // one allocation, at 0, sums_n and 3 sums_n
+    int64_t sums_n = 0;
     // charges
     void *q_sorted = nullptr;
     double *q_sum = nullptr;
