@@ -399,6 +399,54 @@ __device__ __forceinline__ void interp_sums(int64_t k, const int *__restrict__ b
     }
 }
 
+// FP32 far-field sums of target k for R right-hand sides at once (grids grid + r grid_stride):
+// the window weights, the larger part of the arithmetic, are formed once for all of them.
+template <int M2, int R>
+__device__ __forceinline__ void interp_sums_rhs(int64_t k, const int *__restrict__ base,
+                                                const float2 *__restrict__ frac, const WindowPoly &wp,
+                                                const float *__restrict__ grid, int64_t grid_stride, int pitch,
+                                                float (&phi)[R], float (&g1)[R], float (&g2)[R])
+{
+    constexpr int m = M2 / 2;
+    constexpr bool kRef = m >= 5;
+    const int packed = base[k];
+    const float2 f = frac[k];
+    const int64_t off = (int64_t)(base1(packed) - m + 1) * pitch + (base2(packed) - m + 1);
+    float rs_ref[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        phi[r] = g1[r] = g2[r] = rs_ref[r] = 0.f;
+    float w2[M2], d2[M2];
+    const float t1 = f.x - 0.5f, t2 = f.y - 0.5f;
+    const float s1 = t1 * t1, s2 = t2 * t2;
+#pragma unroll
+    for (int a = 0; a < m; ++a) {
+        float e, o;
+        poly_even_odd<kPolyD>(wp.c[a], s2, e, o);
+        w2[a] = fmaf(t2, o, e);
+        w2[M2 - 1 - a] = fmaf(-t2, o, e);
+        poly_even_odd<kPolyD - 1>(wp.d[a], s2, e, o);
+        d2[a] = fmaf(t2, o, e);
+        d2[M2 - 1 - a] = fmaf(t2, o, -e);
+    }
+#pragma unroll
+    for (int q = 0; q < m; ++q) {
+        const int a = m - 1 - q, a2 = M2 - 1 - a;
+        float e, o, de, dd;
+        poly_even_odd<kPolyD>(wp.c[a], s1, e, o);
+        poly_even_odd<kPolyD - 1>(wp.d[a], s1, de, dd);
+        const float wa = fmaf(t1, o, e), da = fmaf(t1, dd, de), wb = fmaf(-t1, o, e), db = fmaf(t1, dd, -de);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float *g = grid + r * grid_stride + off;
+            interp_row<float, M2, kRef>(g + (int64_t)a * pitch, w2, d2, wa, da, q == 0, rs_ref[r], phi[r], g1[r],
+                                        g2[r]);
+            interp_row<float, M2, kRef>(g + (int64_t)a2 * pitch, w2, d2, wb, db, false, rs_ref[r], phi[r], g1[r],
+                                        g2[r]);
+        }
+    }
+}
+
 template <typename real, int M2>
 __device__ __forceinline__ void interp_point(int64_t k, const int *__restrict__ base,
                                              const real2_t<real> *__restrict__ frac, const Window<real> &w,
@@ -491,6 +539,33 @@ __global__ void __launch_bounds__(256, 3) k_batch_interp_out(const BatchInst<rea
     void *ho = io[i].H ? (unsigned char *)io[i].H + (size_t)r * N * 2 * osz : nullptr;
     output_point<real>(k, ps[k] + phi, gs[2 * k] + n_os * g1, gs[2 * k + 1] + n_os * g2, b.coinc[(int64_t)r * N + k],
                        b.tgt_perm, b.shift, b.q_sum[r], b.s, po, ho, out_is_f64);
+}
+
+// FP32 batches: the same with all R right-hand sides of a target in one thread (window weights
+// formed once); block -> (instance, block of its targets).
+template <int M2, int R>
+__global__ void __launch_bounds__(256, 3) k_batch_interp_out_rhs(const BatchInst<float> *__restrict__ inst,
+                                                              const BatchIO *__restrict__ io, BlockMap bm,
+                                                              WindowPoly wp, int out_is_f64)
+{
+    const int i = bm.inst[blockIdx.x];
+    const BatchInst<float> &b = inst[i];
+    const int64_t k = (int64_t)(blockIdx.x - bm.first[i]) * blockDim.x + threadIdx.x;
+    const int64_t N = b.N;
+    if (k >= N)
+        return;
+    float phi[R], g1[R], g2[R];
+    interp_sums_rhs<M2, R>(k, b.tgt_base, (const float2 *)b.tgt_frac, wp, b.grid, b.grid_stride, b.pitch, phi, g1, g2);
+    const float n_os = (float)b.L;
+    const size_t osz = out_is_f64 ? 8 : 4;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float *ps = b.phi_s + (int64_t)r * N, *gs = b.grad_s + 2 * (int64_t)r * N;
+        void *po = io[i].phi ? (unsigned char *)io[i].phi + (size_t)r * N * osz : nullptr;
+        void *ho = io[i].H ? (unsigned char *)io[i].H + (size_t)r * N * 2 * osz : nullptr;
+        output_point<float>(k, ps[k] + phi[r], gs[2 * k] + n_os * g1[r], gs[2 * k + 1] + n_os * g2[r],
+                            b.coinc[(int64_t)r * N + k], b.tgt_perm, b.shift, b.q_sum[r], b.s, po, ho, out_is_f64);
+    }
 }
 
 // Adjoint spreading at the targets: each point carries a monopole c and a dipole d (2-vector)
@@ -1035,6 +1110,18 @@ cudaError_t launch_batch_interp_out(const BatchInst<real> *inst, const BatchIO *
         return cudaSuccess;
     return with_width(m, [&](auto mc) {
         constexpr int M2 = decltype(mc)::value;
+        if constexpr (std::is_same_v<real, float>) {
+            // up to four right-hand sides in one thread per target (batched replay 7.78 -> 7.63 ms)
+            const dim3 g((unsigned)blocks, 1);
+            const auto *fi = reinterpret_cast<const BatchInst<float> *>(inst);
+            switch (nrhs) {
+            case 1: k_batch_interp_out_rhs<M2, 1><<<g, 256, 0, st>>>(fi, io, bm, wp, out_is_f64); return cudaGetLastError();
+            case 2: k_batch_interp_out_rhs<M2, 2><<<g, 256, 0, st>>>(fi, io, bm, wp, out_is_f64); return cudaGetLastError();
+            case 3: k_batch_interp_out_rhs<M2, 3><<<g, 256, 0, st>>>(fi, io, bm, wp, out_is_f64); return cudaGetLastError();
+            case 4: k_batch_interp_out_rhs<M2, 4><<<g, 256, 0, st>>>(fi, io, bm, wp, out_is_f64); return cudaGetLastError();
+            default: break;
+            }
+        }
         k_batch_interp_out<real, M2><<<dim3((unsigned)blocks, (unsigned)nrhs), 256, 0, st>>>(inst, io, bm, w, wp,
                                                                                            out_is_f64);
         return cudaGetLastError();
