@@ -245,7 +245,7 @@ __host__ __device__ constexpr int spread_groups(int M2)
     return G;
 }
 
-__host__ __device__ inline bool spread_group_banks_ok(int q, int M2)
+__host__ __device__ constexpr bool spread_group_banks_ok(int q, int M2)
 {
     const int G = spread_groups(M2), RPL = M2 / G;
     unsigned used = 0u;
@@ -259,7 +259,7 @@ __host__ __device__ inline bool spread_group_banks_ok(int q, int M2)
     return true;
 }
 
-__host__ __device__ inline int spread_group_pitch(int rows, int M2)
+__host__ __device__ constexpr int spread_group_pitch(int rows, int M2)
 {
     for (int q = rows; q < rows + 32; ++q)
         if (spread_group_banks_ok(q, M2))

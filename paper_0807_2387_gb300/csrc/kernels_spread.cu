@@ -57,7 +57,9 @@ __device__ __forceinline__ float2 sub2f(float2 a, float2 b)   // a - b, one roun
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
-template <typename real, int M2, bool KAHAN>
+// TGC > 0: the tile edge (grid lines) fixed at compile time, so that the tile pitch and the
+// row offsets of the taps are constants (immediate offsets instead of one address per row).
+template <typename real, int M2, bool KAHAN, int TGC = 0>
 __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid &cg, const int *__restrict__ base,
                                             const real2_t<real> *__restrict__ frac, const real *__restrict__ q,
                                             const Window<real> &w, const WindowPoly &wp, real *__restrict__ grid,
@@ -72,10 +74,11 @@ __device__ __forceinline__ void spread_item(const SpreadItem &it, const CellGrid
     constexpr int PLANES = KAHAN ? 2 : 1;
     constexpr bool kPoly = sizeof(real) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TG = cg.T * cg.cell;
+    constexpr int kQ = TGC > 0 ? spread_group_pitch(TGC + M2 - 1, M2) : 0;
+    const int TG = TGC > 0 ? TGC : cg.T * cg.cell;
     const int P = TG + M2 - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Q = spread_group_pitch(P, M2);                 // row pitch: conflict-free tap rows
+    const int Q = TGC > 0 ? kQ : spread_group_pitch(P, M2);   // row pitch: conflict-free tap rows
     const int PP = P * Q;                                     // one plane of a warp tile
     real *acc = reinterpret_cast<real *>(smem_raw) + (size_t)warp * PP * PLANES;
     unsigned char *after_tiles = smem_raw + spread_tiles_bytes<real>(P, Q, PLANES);
@@ -280,14 +283,14 @@ __global__ void __launch_bounds__(256) k_fold_comp(int64_t n, real *__restrict__
         grid[k] += comp[k];
 }
 
-template <typename real, int M2, bool KAHAN>
+template <typename real, int M2, bool KAHAN, int TGC>
 __global__ void __launch_bounds__(kSpreadWarps * 32) k_spread(const SpreadItem *__restrict__ items, CellGrid cg,
                                                               const int *__restrict__ base,
                                                               const real2_t<real> *__restrict__ frac,
                                                               const real *__restrict__ q, Window<real> w, WindowPoly wp,
                                                               real *__restrict__ grid, int pitch, int n_a)
 {
-    spread_item<real, M2, KAHAN>(items[blockIdx.x], cg, base, frac, q, w, wp, grid, pitch, n_a);
+    spread_item<real, M2, KAHAN, TGC>(items[blockIdx.x], cg, base, frac, q, w, wp, grid, pitch, n_a);
 }
 
 // Batched spreading: items carry their instance in `pad`; blockIdx.y = right-hand side.
@@ -771,20 +774,19 @@ cudaError_t spread_m(const SpreadItem *items, int n_items, CellGrid cg, const in
     const int P = TG + M2 - 1;
     const size_t smem = spread_smem_bytes<real>(P, M2, kahan);
     const real2_t<real> *fr = (const real2_t<real> *)frac;
-    if (kahan) {
-        auto kern = k_spread<real, M2, true>;
+    auto run = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
         kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, wp, grid, pitch, n_a);
-    } else {
-        auto kern = k_spread<real, M2, false>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        kern<<<n_items, kSpreadWarps * 32, smem, st>>>(items, cg, base, fr, q, w, wp, grid, pitch, n_a);
-    }
-    return cudaGetLastError();
+        return cudaGetLastError();
+    };
+    // the tile edges of the 2D plans' two tile rules (16 and 24 grid lines) compiled as constants
+    if (kahan)
+        return TG == 16 ? run(k_spread<real, M2, true, 16>)
+                        : TG == 24 ? run(k_spread<real, M2, true, 24>) : run(k_spread<real, M2, true, 0>);
+    return TG == 16 ? run(k_spread<real, M2, false, 16>)
+                    : TG == 24 ? run(k_spread<real, M2, false, 24>) : run(k_spread<real, M2, false, 0>);
 }
 
 template <typename real, int M2>
