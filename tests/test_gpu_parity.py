@@ -563,6 +563,24 @@ def test_spread_mode_choice(pkg):
     assert rel(phi_d, phi_t) <= 1e-6 and rel(H_d, H_t) <= 1e-6, (rel(phi_d, phi_t), rel(H_d, H_t))
 
 
+def test_spread_tile_edges_agree(pkg):
+    """The spreading kernel takes the tile edges of the 2D tile rules (16 and 24 grid lines) as
+    compile-time constants and any other edge at run time: FP64 plans with 16-, 24- and 32-line
+    tiles (cells of 8 lines) match the oracle, and their FP32 plans agree with each other."""
+    from paper_0807_2387_gb300 import workloads as W
+    case = W.small_case(171, 6000, 3000, n=64, m=6, eps_I=4 / 64)
+    phi_o, H_o = oracle_field(case)
+    f32 = {}
+    for t in (2, 3, 4):
+        phi, H, info = gpu_field(pkg, case, 64, cell=8, tile_cells=t)
+        assert info["cell"] == 8 and info["tile_cells"] == t, info
+        assert rel(phi, phi_o) <= 1e-12 and rel(H, H_o) <= 1e-12, (t, rel(phi, phi_o), rel(H, H_o))
+        f32[t] = gpu_field(pkg, case, 32, cell=8, tile_cells=t)
+        assert rel(f32[t][0], phi) <= 1e-5 and rel(f32[t][1], H) <= 1e-5
+    for t in (2, 3):
+        assert rel(f32[t][0], f32[4][0]) <= 2e-6 and rel(f32[t][1], f32[4][1]) <= 2e-6, t
+
+
 def test_4096_point_lines_against_direct_sum(pkg):
     """n = 2048 (oversampled 4096^2) runs the transform's compiled 4096-point lines, which no case
     the oracle's FP64 NFFT can afford reaches: the FP64 path against the direct sum O1 at the
