@@ -302,8 +302,23 @@ __global__ void __launch_bounds__(kSpreadWarps * 32) k_batch_spread(const Spread
     const SpreadItem it = items[blockIdx.x];
     const BatchInst<real> &b = inst[it.pad];
     const int r = blockIdx.y;
-    spread_item<real, M2, KAHAN>(it, b.cg, b.src_base, (const real2_t<real> *)b.src_frac, b.q + (int64_t)r * b.M, w,
-                                 wp, b.grid + (int64_t)r * b.grid_stride, b.pitch, b.n_a);
+    auto go = [&](auto tg) {
+        spread_item<real, M2, KAHAN, decltype(tg)::value>(it, b.cg, b.src_base, (const real2_t<real> *)b.src_frac,
+                                                          b.q + (int64_t)r * b.M, w, wp,
+                                                          b.grid + (int64_t)r * b.grid_stride, b.pitch, b.n_a);
+    };
+    // FP32 compensated batches: the tile edges the autotuner picks for the batched instance
+    // classes compiled as constants (per block: instances differ), any other edge at run time
+    if constexpr (sizeof(real) == 4 && KAHAN) {
+        switch (b.cg.T * b.cg.cell) {
+        case 12: go(std::integral_constant<int, 12>{}); return;
+        case 16: go(std::integral_constant<int, 16>{}); return;
+        case 18: go(std::integral_constant<int, 18>{}); return;
+        case 24: go(std::integral_constant<int, 24>{}); return;
+        default: break;
+        }
+    }
+    go(std::integral_constant<int, 0>{});
 }
 
 // In FP32 with m >= 5 the derivative sums are formed against a reference tap:
